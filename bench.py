@@ -1,0 +1,308 @@
+"""Benchmark of the sub-grid DG shallow-water hot path on GB300.
+
+Workload: the 20 km tidal beach, degree-3 DG on a uniform 256 x 256 mesh,
+16 x 16 pixels of a 4096 x 4096 float32 bathymetry per cell, RK32/TR-BDF2
+IMEX with Manning friction, FP64 arithmetic.  One "step" = one time step of
+the whole hot path: degree switch, three stages (residual + stage update) and
+the final combination.
+
+Metric: DoF-stage updates per second, where one DoF-stage update advances one
+nodal value of (zeta, qx, qy, c) through one stage (residual + stage solve):
+n_cells * 4 (r+1)^2 * 3 updates per step.  Inputs are larger than L2 (the
+working set is about 0.5 GB), so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl swdg|reference]
+
+N > 1 runs one independent replica per GPU (the path has no exchange on one
+box; see the design notes) and reports the whole-job rate ("weak" scaling).
+The reference arm (--impl reference) is the CPU oracle timed on the host's
+cores on a bounded crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2505_18743_gb300 import workloads as W  # noqa: E402
+
+METRIC = "DoF-stage updates/s"
+WORKLOAD = "tidal-beach 256x256 cells, r=3, 16x16 px/cell (4096^2 f32 raster), RK32-IMEX, FP64"
+STAGES = 3
+# kernel-slot names of swdg_step_profile
+SLOTS = ["step_begin", "residual_1", "residual_2", "residual_3", "residual_4", "stage_2",
+         "stage_3", "stage_4", "final"]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def units_per_step(wl):
+    nd = (wl.degree + 1) ** 2
+    return wl.mesh.n * 4 * nd * STAGES
+
+
+def algorithmic_bytes_per_cell(kernel, r=3, P=16, pix_bytes=4, nres=3):
+    """Bytes one launch must move per cell (model of the design notes):
+    residual: own state 4 nd f64 in, 6 nd f64 out, the pixel tile, geometry;
+    stage update: v^n in, H/C~ in, nres residual sets of 6 nd in, state out."""
+    nd = (r + 1) ** 2
+    geo = 16 + 32 + 8 + 1
+    if kernel.startswith("residual"):
+        return 4 * nd * 8 + 6 * nd * 8 + P * P * pix_bytes + geo
+    if kernel.startswith("stage") or kernel == "final":
+        return 4 * nd * 8 + 2 * nd * 8 + 16 + nres * 6 * nd * 8 + 4 * nd * 8 + geo
+    return 4 * nd * 8 + 2 * nd * 8 + 16 + P * P * pix_bytes + geo
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region"""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(seconds=15.0, window=(184, 120, 24, 24)):
+    """the oracle (as it stands) on a crop of the workload, steps until about
+    `seconds` of CPU work; returns (updates/s, cores, sample text)"""
+    from oracle.oracle import Oracle
+    wl = W.tidal_beach(window=window)
+    o = Oracle.from_workload(wl)
+    t = 0.0
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        t = o.step(1, -1.0, t)
+        n += 1
+        if time.perf_counter() - t0 > seconds or n >= 50:
+            break
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    rate = units_per_step(wl) * n / el
+    sample = (f"{n} RK32 steps of the {window[2]}x{window[3]}-cell crop at cell ({window[0]},"
+              f"{window[1]}) of the same workload ({wl.mesh.n} cells, the shoreline band), "
+              f"{el:.1f} s")
+    return rate, cores, sample
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    per = []
+    from oracle.oracle import Oracle
+    wl = W.tidal_beach(window=(184, 120, 16, 16))
+    o = Oracle.from_workload(wl)
+    t = 0.0
+    for _ in range(args.warmup):
+        t = o.step(1, -1.0, t)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s0 = time.perf_counter()
+        t = o.step(1, -1.0, t)
+        per.append(time.perf_counter() - s0)
+    el = time.perf_counter() - t0
+    rate = units_per_step(wl) * args.steps / el
+    cores = int(os.environ["OMP_NUM_THREADS"])
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "16x16-cell crop (184,120), CPU oracle"},
+            "cpu_baseline": {"value": rate, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} RK32 steps of a 16x16-cell crop of the "
+                                       "workload (cells 184..199 x 120..135)"},
+            "e2e": {"value": rate, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    from paper_2505_18743_gb300 import swdg
+    dev = torch.device("cuda", local)
+    wl = W.tidal_beach()
+    stream = torch.cuda.Stream(device=dev)
+    ctx = swdg.Context.from_workload(wl, stream=stream.cuda_stream)
+    units = units_per_step(wl)
+    t = 0.0
+    # warm-up (also captures the step graph)
+    for _ in range(args.warmup):
+        t = ctx.step(1, -1.0, t)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        start.record(stream)
+        t = ctx.step(args.steps, -1.0, t)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+    ms = start.elapsed_time(end)
+    ms = max_over_ranks(ms, world)
+    value = units * args.steps * world / (ms / 1e3)
+    clocks = clk.summary()
+
+    # per-kernel durations (CUDA events on the context's stream, eager launches)
+    kms, t = ctx.step_profile(max(2, min(args.steps, 5)), -1.0, t)
+    nprof = max(2, min(args.steps, 5))
+    per_launch = {SLOTS[i]: kms[i] / nprof for i in range(len(SLOTS)) if kms[i] > 0}
+    total = sum(per_launch.values())
+    dom = max(per_launch, key=per_launch.get)
+    pk, src = peaks()
+    bpc = algorithmic_bytes_per_cell(dom, nres=STAGES)
+    ach = bpc * wl.mesh.n / (per_launch[dom] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+            "peak_source": src, "share": per_launch[dom] / total,
+            "per_launch_ms": {k: round(v, 4) for k, v in per_launch.items()}}
+
+    # end to end: host state in, one step, host state out, every step
+    nd = (wl.degree + 1) ** 2
+    host = [torch.empty((wl.mesh.n, nd), dtype=torch.float64).pin_memory() for _ in range(4)]
+    ctx.get_state(host)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_state(*host)
+        t = ctx.step(1, -1.0, t)
+        ctx.get_state(host)
+    el = time.perf_counter() - t0
+    el = max_over_ranks(el, world)
+    bytes_io = 4 * wl.mesh.n * nd * 8
+    e2e = {"value": units * e2e_steps * world / el, "unit": "updates/s",
+           "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io}
+
+    line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": wl.mesh.n, "degree": wl.degree,
+                       "pixels_per_cell": 256, "stages": STAGES,
+                       "l2": "inputs larger than L2 (about 0.5 GB working set), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clocks, "roofline": roof, "e2e": e2e,
+            "gpu_launches": (2 * STAGES + 1) * args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate()
+        line["cpu_baseline"] = {"value": rate, "unit": "updates/s", "cores": cores,
+                                "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="swdg", choices=["swdg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

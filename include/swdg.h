@@ -1,0 +1,162 @@
+/*
+ * swdg.h -- C-ABI of the GB300 (sm_103a) sub-grid DG shallow-water hot path.
+ *
+ * Method: Arpaia, Orlando, Ferrarin, Bonaventura, "High-order adaptive
+ * discontinuous finite elements for the shallow water equations with sub-grid
+ * irregular bathymetry" (arXiv 2505.18743).  The library evaluates the
+ * matrix-free DG operator of Sec. 3.2 (continuity F, Eq. mass_rhs; momentum G,
+ * Eq. discharge_rhs; friction L, Eq. discharge_rhs_implicit; tracer R,
+ * Eq. r_concentration) with wet depth and wet area taken from the bathymetry
+ * pixels (Sec. 3.3), and advances it with the IMEX Runge-Kutta stage update of
+ * Sec. 3.1 (Eqs. imex_shw, algebraic_elevation, newton, algebraic_discharge,
+ * algebraic_concentration) and the degree switch of Eq. criteria_p.
+ *
+ * Conventions
+ *  - Every call returns SWDG_OK (0) or a negative SWDG_E* code; the message of
+ *    the last failure is kept per context (swdg_last_error).
+ *  - The caller owns every buffer it passes; the library copies inputs and
+ *    owns all the device memory it allocates.  Nothing is thread-safe per
+ *    context.
+ *  - `where` selects host (SWDG_HOST) or device (SWDG_DEVICE) pointers.
+ *    Device pointers must be valid on the context's stream; the library
+ *    synchronises that stream before returning from every call except
+ *    swdg_step, which only synchronises to read the status word.
+ *  - Cell K = [x0, x0+hx] x [y0, y0+hy].  Nodal DoFs sit on the (r+1)^2
+ *    Gauss-Lobatto support points, index a + (r+1) b with x fastest; per-field
+ *    arrays are [n_cells][(r+1)^2] float64.
+ *  - Faces f = 0 W, 1 E, 2 S, 3 N.  nbr[K][f][0] is the neighbour across f, or
+ *    -1 - tag (tag in 0..15) on a boundary face; nbr[K][f][1] is -1 (2:1
+ *    hanging faces are not accepted by this version: SWDG_EINVAL).
+ *  - Bathymetry z_b is a depth, positive down: water depth h = max(zeta+z_b, 0)
+ *    (Eq. zeta2depth-2).
+ *  - Device-side failures never trap: kernels record them in a status word
+ *    that swdg_step reads back.
+ */
+#ifndef SWDG_H
+#define SWDG_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SWDG_OK 0
+#define SWDG_EINVAL (-1)      /* bad argument, size or mesh */
+#define SWDG_ECUDA (-2)       /* a CUDA call failed */
+#define SWDG_ENEWTON (-3)     /* reserved: Newton did not converge (counted, not fatal) */
+#define SWDG_EPOSITIVITY (-4) /* reserved: a cell mass went negative (counted, not fatal) */
+#define SWDG_ENAN (-5)        /* a non-finite value appeared in the state */
+#define SWDG_ESTATE (-6)      /* call out of order (no mesh, no bathymetry, no state) */
+
+#define SWDG_HOST 0
+#define SWDG_DEVICE 1
+
+#define SWDG_BC_WALL 0  /* mirrored ghost state: zero normal mass flux */
+#define SWDG_BC_TIDE 1  /* imposed elevation amp*sin(2 pi t/period + phase), q+ = q- */
+
+#define SWDG_PIX_F32 0
+#define SWDG_PIX_F64 1
+
+typedef struct swdg_ctx swdg_ctx;
+
+typedef struct {
+    int degree;       /* r in 1..3 (Q_r space of Sec. 3.2) */
+    int precision;    /* 0: FP64 everywhere (the only value accepted by this version) */
+    int subgrid_mode; /* 0: S, each quadrature point owns the sub-cell given by the
+                         cumulative weights and integrates max(eta+z_b,0) over its
+                         pixels; 1: P, z_b sampled at the point by bilinear
+                         interpolation of pixel centres (Sec. 5) */
+    int tableau;      /* 0 RK32 + TR-BDF2 IMEX (Table tab:imex_rk2_butch), 1 SSP33
+                         (Table tab:rk3), 2 RK44 (Table tab:rk4), 3 forward Euler;
+                         1-3 take the friction term explicitly */
+    double g;          /* gravity, m s^-2 */
+    double eps_vel;    /* epsilon of the desingularised velocity, Eq. velocity */
+    double h_lim;      /* depth threshold of the degree switch, Eq. criteria_p */
+    double eps0;       /* dry-start lift of Eq. initial_guess */
+    double cfl;        /* dt = cfl * min J_K / (lambda l_Gamma), Eq. deltat_fe */
+    int newton_max;    /* iteration cap of the per-cell Newton solve (>= 1) */
+    double newton_tol; /* stop when sum|dzeta| <= tol * sum(1 + |zeta| + max|z_b|);
+                          0 runs exactly newton_max iterations */
+    void* stream;      /* cudaStream_t to run on, or NULL for the legacy stream */
+} swdg_config;
+
+/* Create a context on the current CUDA device.  Validates cfg. */
+int swdg_create(const swdg_config* cfg, swdg_ctx** out);
+
+/* Upload an axis-aligned quadrilateral mesh (Sec. 3.2): x0y0, hxhy [n][2]
+ * float64 host arrays; nbr [n][4][2] int32 host array (see Conventions).
+ * Errors: SWDG_EINVAL for n < 1, non-positive sizes, out-of-range neighbours,
+ * boundary tags >= 16, or 2:1 hanging faces. */
+int swdg_upload_mesh(swdg_ctx* ctx, int64_t n_cells, const double* x0y0, const double* hxhy,
+                     const int32_t* nbr);
+
+/* Upload the bathymetry raster (host, row-major [ny][nx], dtype SWDG_PIX_F32
+ * or SWDG_PIX_F64, depth positive down) with pixel (i, j) covering
+ * [xo + i dx, xo + (i+1) dx] x [yo + j dy, yo + (j+1) dy].  Requires the mesh.
+ * Mode S requires every cell to cover the same whole number P <= 32 of pixels
+ * per direction, aligned to pixel edges; the raster is re-tiled per cell.
+ * Mode P needs nx, ny >= 2.  Errors: SWDG_EINVAL, SWDG_ESTATE. */
+int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t nx, int64_t ny,
+                           double xo, double yo, double dx, double dy);
+
+/* Boundary condition of tag (0..15): SWDG_BC_WALL or SWDG_BC_TIDE. */
+int swdg_set_boundary(swdg_ctx* ctx, int tag, int kind, double amp, double period, double phase);
+
+/* Per-cell Manning coefficient n (Eq. manning), [n] float64; NULL sets 0. */
+int swdg_set_manning(swdg_ctx* ctx, const double* n_per_cell, int where);
+
+/* Set the state (zeta, qx, qy, c), each [n][(r+1)^2] float64.  Resets the
+ * per-cell degree flags to r. */
+int swdg_set_state(swdg_ctx* ctx, const double* zeta, const double* qx, const double* qy,
+                   const double* c, int where);
+int swdg_get_state(swdg_ctx* ctx, double* zeta, double* qx, double* qy, double* c, int where);
+
+/* Residual of the current state at time t: F, Gx, Gy, R, Lx, Ly (Eqs.
+ * mass_rhs, discharge_rhs, r_concentration, discharge_rhs_implicit), each
+ * [n][(r+1)^2] float64, so that M d(state)/dt = residual.  Any output may be
+ * NULL. */
+int swdg_residual(swdg_ctx* ctx, double t, double* F, double* Gx, double* Gy, double* R,
+                  double* Lx, double* Ly, int where);
+
+/* cfl * min over all face points of J_K / (lambda l_Gamma) for the current
+ * state at time t (Eq. deltat_fe). */
+int swdg_cfl_dt(swdg_ctx* ctx, double t, double* dt);
+
+/* Advance n_steps time steps.  dt_or_neg >= 0: fixed step; < 0: the CFL step
+ * of every step is computed on the device.  t_inout (may be NULL) is the
+ * start time on entry and the end time on return.  Each step: degree switch
+ * (Eq. criteria_p) with mass-exact remap, then the stages and final
+ * combination of the tableau.  Returns SWDG_ENAN if the state became
+ * non-finite. */
+int swdg_step(swdg_ctx* ctx, int n_steps, double dt_or_neg, double* t_inout);
+
+/* Profiling variant of swdg_step: runs n_steps with the kernels launched one
+ * by one (no graph), a CUDA event pair around each launch on the context's
+ * stream.  ms_out[SWDG_PROF_SLOTS] receives the summed time per kernel slot:
+ * 0 step start (degree switch + H(zeta^n)), 1..4 residual of stage 1..4,
+ * 5..7 stage update 2..4, 8 final combination.  Unused slots are 0.  Same
+ * numerics and status handling as swdg_step. */
+#define SWDG_PROF_SLOTS 9
+int swdg_step_profile(swdg_ctx* ctx, int n_steps, double dt_or_neg, double* t_inout,
+                      double* ms_out);
+
+/* Apply the degree switch of Eq. criteria_p (and its remap) to the current
+ * state, as at the start of a step; flags_out [n] uint8 (host) may be NULL. */
+int swdg_degree_switch(swdg_ctx* ctx, uint8_t* flags_out);
+
+/* Zeta at n gauge points xy [n][2] (host), written to zeta_out [n] (host);
+ * NaN for a point outside the mesh. */
+int swdg_gather_gauges(swdg_ctx* ctx, int n, const double* xy, double* zeta_out);
+
+/* out[8] = total mass sum_K Hbar_K (Eq. positivity-7), tracer mass, min wet
+ * depth over mass points, number of r_K = r cells, max Newton iterations of
+ * the last step, positivity violations (cumulative), last dt, t. */
+int swdg_diagnostics(swdg_ctx* ctx, double out[8]);
+
+const char* swdg_last_error(const swdg_ctx* ctx);
+void swdg_destroy(swdg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

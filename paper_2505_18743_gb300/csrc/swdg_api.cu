@@ -1,0 +1,1012 @@
+// swdg_api.cu -- C-ABI of the sub-grid DG shallow-water hot path (see
+// include/swdg.h): context, validation, uploads, per-degree tables, the step
+// driver (one captured CUDA graph per time step) and setup kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/swdg.h"
+#include "swdg_kernels.cuh"
+#include "swdg_launch.h"
+
+using namespace swdg;
+
+namespace swdg {
+bool get_launch(int degree, int mode, int pix, Launch* out) {
+    switch (degree) {
+    case 1: return get_launch_r1(mode, pix, out);
+    case 2: return get_launch_r2(mode, pix, out);
+    case 3: return get_launch_r3(mode, pix, out);
+    default: return false;
+    }
+}
+} // namespace swdg
+
+struct swdg_ctx {
+    swdg_config cfg;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int R = 1, nd = 4;
+    int64_t n = 0;
+    int mode = 0, pix = 1;
+    bool has_mesh = false, has_bathy = false, has_state = false;
+    Launch L{};
+    Tables tb{};
+    Dev d{};
+    int grid = 1;
+    // device allocations
+    double *x0y0 = nullptr, *hxhy = nullptr, *manning = nullptr, *U = nullptr, *res = nullptr,
+           *llin = nullptr, *HN = nullptr, *CN = nullptr, *HNbar = nullptr, *CNbar = nullptr,
+           *zpts = nullptr, *zmax = nullptr, *zabs = nullptr, *diag = nullptr;
+    int32_t* nbr = nullptr;
+    uint8_t *cmask = nullptr, *flag = nullptr;
+    void* tiles = nullptr;
+    Scalars* sc = nullptr;
+    Scalars* sc_host = nullptr; // pinned staging
+    double* pin = nullptr;      // pinned staging for small reads
+    cudaGraphExec_t graph = nullptr;
+    double graph_dt = -2.0;
+    std::vector<double> x0y0_h, hxhy_h;
+    std::string err;
+};
+
+static int fail(swdg_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, SWDG_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// 1D rules in closed form (Table tab:quadrature), mapped to [0, 1]
+// ---------------------------------------------------------------------------
+static bool gauss_legendre(int n, double* x, double* w) {
+    double t[5], v[5];
+    switch (n) {
+    case 1: t[0] = 0; v[0] = 2; break;
+    case 2: t[0] = -1 / std::sqrt(3.0); t[1] = -t[0]; v[0] = v[1] = 1; break;
+    case 3:
+        t[0] = -std::sqrt(0.6); t[1] = 0; t[2] = -t[0];
+        v[0] = v[2] = 5.0 / 9.0; v[1] = 8.0 / 9.0;
+        break;
+    case 4: {
+        double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(1.2));
+        double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(1.2));
+        t[0] = -b; t[1] = -a; t[2] = a; t[3] = b;
+        v[1] = v[2] = (18.0 + std::sqrt(30.0)) / 36.0;
+        v[0] = v[3] = (18.0 - std::sqrt(30.0)) / 36.0;
+        break;
+    }
+    case 5: {
+        double a = std::sqrt(5.0 - 2.0 * std::sqrt(10.0 / 7.0)) / 3.0;
+        double b = std::sqrt(5.0 + 2.0 * std::sqrt(10.0 / 7.0)) / 3.0;
+        t[0] = -b; t[1] = -a; t[2] = 0; t[3] = a; t[4] = b;
+        v[2] = 128.0 / 225.0;
+        v[1] = v[3] = (322.0 + 13.0 * std::sqrt(70.0)) / 900.0;
+        v[0] = v[4] = (322.0 - 13.0 * std::sqrt(70.0)) / 900.0;
+        break;
+    }
+    default: return false;
+    }
+    for (int i = 0; i < n; ++i) {
+        x[i] = 0.5 * (1.0 + t[i]);
+        w[i] = 0.5 * v[i];
+    }
+    return true;
+}
+
+static bool gauss_lobatto(int n, double* x, double* w) {
+    double t[5], v[5];
+    switch (n) {
+    case 2: t[0] = -1; t[1] = 1; v[0] = v[1] = 1; break;
+    case 3: t[0] = -1; t[1] = 0; t[2] = 1; v[0] = v[2] = 1.0 / 3.0; v[1] = 4.0 / 3.0; break;
+    case 4:
+        t[0] = -1; t[1] = -1 / std::sqrt(5.0); t[2] = -t[1]; t[3] = 1;
+        v[0] = v[3] = 1.0 / 6.0; v[1] = v[2] = 5.0 / 6.0;
+        break;
+    case 5:
+        t[0] = -1; t[1] = -std::sqrt(3.0 / 7.0); t[2] = 0; t[3] = -t[1]; t[4] = 1;
+        v[0] = v[4] = 0.1; v[1] = v[3] = 49.0 / 90.0; v[2] = 32.0 / 45.0;
+        break;
+    default: return false;
+    }
+    for (int i = 0; i < n; ++i) {
+        x[i] = 0.5 * (1.0 + t[i]);
+        w[i] = 0.5 * v[i];
+    }
+    x[0] = 0.0;
+    x[n - 1] = 1.0;
+    return true;
+}
+
+// Lagrange basis on the support nodes xs[0..m): value and derivative at x
+static void lagrange(const double* xs, int m, int a, double x, double* v, double* dv) {
+    double p = 1.0;
+    for (int b = 0; b < m; ++b)
+        if (b != a) p *= (x - xs[b]) / (xs[a] - xs[b]);
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) {
+        if (k == a) continue;
+        double q = 1.0 / (xs[a] - xs[k]);
+        for (int b = 0; b < m; ++b)
+            if (b != a && b != k) q *= (x - xs[b]) / (xs[a] - xs[b]);
+        s += q;
+    }
+    *v = p;
+    *dv = s;
+}
+
+// inverse of a small dense matrix by Gauss-Jordan with partial pivoting
+static bool invert(int m, const double* A, double* Ainv) {
+    double W[8][16];
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < 2 * m; ++j) W[i][j] = j < m ? A[i * m + j] : (j - m == i ? 1.0 : 0.0);
+    for (int k = 0; k < m; ++k) {
+        int p = k;
+        for (int i = k + 1; i < m; ++i)
+            if (std::fabs(W[i][k]) > std::fabs(W[p][k])) p = i;
+        if (W[p][k] == 0.0) return false;
+        for (int j = 0; j < 2 * m; ++j) std::swap(W[k][j], W[p][j]);
+        double piv = W[k][k];
+        for (int j = 0; j < 2 * m; ++j) W[k][j] /= piv;
+        for (int i = 0; i < m; ++i) {
+            if (i == k) continue;
+            double f = W[i][k];
+            for (int j = 0; j < 2 * m; ++j) W[i][j] -= f * W[k][j];
+        }
+    }
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) Ainv[i * m + j] = W[i][m + j];
+    return true;
+}
+
+// pixel-overlap fractions of the sub-intervals of a rule with P pixels per cell
+static void overlap_table(const double* w, int n, int P, Tables& tb, int set) {
+    double sb[MXP + 1];
+    sb[0] = 0.0;
+    for (int a = 0; a < n; ++a) sb[a + 1] = sb[a] + w[a];
+    sb[n] = 1.0;
+    for (int a = 0; a <= n; ++a) {
+        double u = sb[a] * P, r = std::floor(u + 0.5);
+        if (std::fabs(u - r) < 1e-9) sb[a] = r / P;
+    }
+    for (int a = 0; a < n; ++a) {
+        int lo = std::max(0, (int)std::floor(sb[a] * P));
+        int hi = std::min(P - 1, (int)std::ceil(sb[a + 1] * P) - 1);
+        tb.lo[set][a] = lo;
+        tb.cnt[set][a] = hi - lo + 1;
+        double width = sb[a + 1] - sb[a];
+        for (int k = lo; k <= hi; ++k) {
+            double ov = std::min(sb[a + 1], (k + 1.0) / P) - std::max(sb[a], (double)k / P);
+            tb.frac[set][a][k - lo] = ov > 0.0 ? ov / width : 0.0;
+        }
+    }
+}
+
+static bool build_tables(int R, Tables& tb) {
+    const int nd1 = R + 1, nv = (3 * R) / 2 + 1, nm = R + 2, ng = R + 1;
+    double w[MXP];
+    memset(&tb, 0, sizeof tb);
+    if (!gauss_lobatto(nd1, tb.xs, w)) return false;
+    double xv[MXP], wv[MXP], xm[MXP], wm[MXP], xg[MXP], wg[MXP];
+    if (!gauss_legendre(nv, xv, wv) || !gauss_lobatto(nm, xm, wm) || !gauss_legendre(ng, xg, wg))
+        return false;
+    for (int q = 0; q < nv; ++q) {
+        tb.wv[q] = wv[q];
+        tb.xq[SET_VOL][q] = xv[q];
+        for (int a = 0; a < nd1; ++a) lagrange(tb.xs, nd1, a, xv[q], &tb.Bv[q][a], &tb.Dv[q][a]);
+    }
+    for (int q = 0; q < nm; ++q) {
+        tb.wm[q] = wm[q];
+        tb.xq[SET_MASS][q] = xm[q];
+        double dv;
+        for (int a = 0; a < nd1; ++a) lagrange(tb.xs, nd1, a, xm[q], &tb.Bm[q][a], &dv);
+    }
+    double Bg[MXN * MXN], Bgi[MXN * MXN];
+    for (int q = 0; q < ng; ++q) {
+        tb.wg[q] = wg[q];
+        tb.xq[SET_MOM][q] = xg[q];
+        double dv;
+        for (int a = 0; a < nd1; ++a) {
+            lagrange(tb.xs, nd1, a, xg[q], &tb.Bg[q][a], &dv);
+            Bg[q * nd1 + a] = tb.Bg[q][a];
+        }
+    }
+    if (!invert(nd1, Bg, Bgi)) return false;
+    for (int a = 0; a < nd1; ++a)
+        for (int q = 0; q < ng; ++q) tb.Bginv[a][q] = Bgi[a * nd1 + q];
+    // 1D Gauss-Lobatto mass matrix (exact for degree 2r) and its inverse
+    double M1[MXN * MXN], M1i[MXN * MXN];
+    for (int a = 0; a < nd1; ++a)
+        for (int c = 0; c < nd1; ++c) {
+            double s = 0.0;
+            for (int q = 0; q < nm; ++q) s += wm[q] * tb.Bm[q][a] * tb.Bm[q][c];
+            M1[a * nd1 + c] = s;
+        }
+    if (!invert(nd1, M1, M1i)) return false;
+    for (int a = 0; a < nd1; ++a)
+        for (int c = 0; c < nd1; ++c) tb.M1inv[a][c] = M1i[a * nd1 + c];
+    return true;
+}
+
+static bool build_overlaps(int R, int P, Tables& tb) {
+    const int nv = (3 * R) / 2 + 1, nm = R + 2, ng = R + 1;
+    if (P < 1 || P > MXPIX) return false;
+    tb.P = P;
+    overlap_table(tb.wv, nv, P, tb, SET_VOL);
+    overlap_table(tb.wm, nm, P, tb, SET_MASS);
+    overlap_table(tb.wg, ng, P, tb, SET_MOM);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// setup kernels (S0: re-tile the raster, point samples, per-cell depth bounds)
+// ---------------------------------------------------------------------------
+template <typename Pix>
+__global__ void k_retile(const Pix* __restrict__ ras, int64_t nx, const int32_t* col0,
+                         const int32_t* row0, int P, Pix* tiles, int64_t n) {
+    const int64_t total = n * (int64_t)P * P;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / ((int64_t)P * P);
+        const int r = (int)(i % ((int64_t)P * P)), jy = r / P, ix = r % P;
+        tiles[i] = ras[(int64_t)(row0[k] + jy) * nx + col0[k] + ix];
+    }
+}
+
+template <typename Pix>
+__global__ void k_tile_bounds(const Pix* __restrict__ tiles, int P, int64_t n, double* zmax,
+                              double* zabs) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = warp; k < n; k += nw) {
+        double m = -INFINITY, a = 0.0;
+        for (int i = lane; i < P * P; i += 32) {
+            const double z = (double)tiles[k * P * P + i];
+            m = fmax(m, z);
+            a = fmax(a, fabs(z));
+        }
+        m = warp_max(m);
+        a = warp_max(a);
+        if (lane == 0) {
+            zmax[k] = m;
+            zabs[k] = a;
+        }
+    }
+}
+
+// bilinear interpolation of pixel-centre values, clamped at the raster edge
+template <typename Pix>
+__device__ double bilinear(const Pix* __restrict__ ras, int64_t nx, int64_t ny, double xo,
+                           double yo, double dx, double dy, double x, double y) {
+    double fi = (x - xo) / dx - 0.5, fj = (y - yo) / dy - 0.5;
+    fi = fmin(fmax(fi, 0.0), (double)(nx - 1));
+    fj = fmin(fmax(fj, 0.0), (double)(ny - 1));
+    int64_t i0 = (int64_t)floor(fi), j0 = (int64_t)floor(fj);
+    if (i0 > nx - 2) i0 = nx - 2;
+    if (j0 > ny - 2) j0 = ny - 2;
+    const double t = fi - i0, s = fj - j0;
+    const double z00 = ras[j0 * nx + i0], z10 = ras[j0 * nx + i0 + 1];
+    const double z01 = ras[(j0 + 1) * nx + i0], z11 = ras[(j0 + 1) * nx + i0 + 1];
+    return (1.0 - t) * (1.0 - s) * z00 + t * (1.0 - s) * z10 + (1.0 - t) * s * z01 + t * s * z11;
+}
+
+template <typename Pix>
+__global__ void k_point_samples(const Pix* __restrict__ ras, int64_t nx, int64_t ny, double xo,
+                                double yo, double dx, double dy, const double* x0y0,
+                                const double* hxhy, const __grid_constant__ Tables tb, int nv,
+                                int nm, int ng, double* zpts, double* zmax, double* zabs,
+                                int64_t n) {
+    const int nzp = nv * nv + nm * nm + ng * ng;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double x0 = x0y0[2 * k], y0 = x0y0[2 * k + 1], hx = hxhy[2 * k], hy = hxhy[2 * k + 1];
+        int off = 0;
+        double m = -INFINITY, a = 0.0;
+        for (int s = 0; s < 3; ++s) {
+            const int q = s == 0 ? nv : (s == 1 ? nm : ng);
+            for (int p = 0; p < q * q; ++p) {
+                const double x = x0 + tb.xq[s][p % q] * hx, y = y0 + tb.xq[s][p / q] * hy;
+                const double z = bilinear<Pix>(ras, nx, ny, xo, yo, dx, dy, x, y);
+                zpts[k * nzp + off + p] = z;
+                if (s == 1) {
+                    m = fmax(m, z);
+                    a = fmax(a, fabs(z));
+                }
+            }
+            off += q * q;
+        }
+        zmax[k] = m;
+        zabs[k] = a;
+    }
+}
+
+// deterministic reduction of the per-cell diagnostics (one block)
+__global__ void k_diag_reduce(const double* part, int64_t n, double* out) {
+    __shared__ double s[4][256];
+    double m = 0.0, tm = 0.0, hmin = INFINITY, rc = 0.0;
+    const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t b = threadIdx.x * chunk, e = min(n, b + chunk);
+    for (int64_t k = b; k < e; ++k) {
+        m += part[4 * k];
+        tm += part[4 * k + 1];
+        hmin = fmin(hmin, part[4 * k + 2]);
+        rc += part[4 * k + 3];
+    }
+    s[0][threadIdx.x] = m;
+    s[1][threadIdx.x] = tm;
+    s[2][threadIdx.x] = hmin;
+    s[3][threadIdx.x] = rc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + o];
+            s[1][threadIdx.x] += s[1][threadIdx.x + o];
+            s[2][threadIdx.x] = fmin(s[2][threadIdx.x], s[2][threadIdx.x + o]);
+            s[3][threadIdx.x] += s[3][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i) out[i] = s[i][0];
+}
+
+// ---------------------------------------------------------------------------
+// tableaux of Appendix A (the same numbers as the paper's Butcher tables)
+// ---------------------------------------------------------------------------
+static bool set_tableau(int tab, Dev& d) {
+    memset(d.a, 0, sizeof d.a);
+    memset(d.at, 0, sizeof d.at);
+    memset(d.b, 0, sizeof d.b);
+    memset(d.bt, 0, sizeof d.bt);
+    memset(d.c, 0, sizeof d.c);
+    if (tab == 0) {
+        const double chi = 1.0 - std::sqrt(2.0) / 2.0, a32 = 0.5;
+        const double b2 = (1.0 - 2.0 * chi) / (4.0 * chi), b1 = 1.0 - b2 - chi, b3 = chi;
+        d.s = 3;
+        d.a[1][0] = 2.0 * chi;
+        d.a[2][0] = 1.0 - a32;
+        d.a[2][1] = a32;
+        d.at[1][0] = chi;
+        d.at[1][1] = chi;
+        d.at[2][0] = b1;
+        d.at[2][1] = b2;
+        d.at[2][2] = b3;
+        d.b[0] = d.bt[0] = b1;
+        d.b[1] = d.bt[1] = b2;
+        d.b[2] = d.bt[2] = b3;
+        d.c[1] = 2.0 * chi;
+        d.c[2] = 1.0;
+        return true;
+    }
+    if (tab == 1) {
+        d.s = 3;
+        d.a[1][0] = 1.0;
+        d.a[2][0] = 0.25;
+        d.a[2][1] = 0.25;
+        d.b[0] = 1.0 / 6.0; d.b[1] = 1.0 / 6.0; d.b[2] = 2.0 / 3.0;
+        d.c[1] = 1.0; d.c[2] = 0.5;
+    } else if (tab == 2) {
+        d.s = 4;
+        d.a[1][0] = 0.5;
+        d.a[2][1] = 0.5;
+        d.a[3][2] = 1.0;
+        d.b[0] = 1.0 / 6.0; d.b[1] = 1.0 / 3.0; d.b[2] = 1.0 / 3.0; d.b[3] = 1.0 / 6.0;
+        d.c[1] = 0.5; d.c[2] = 0.5; d.c[3] = 1.0;
+    } else if (tab == 3) {
+        d.s = 1;
+        d.b[0] = 1.0;
+    } else {
+        return false;
+    }
+    memcpy(d.at, d.a, sizeof d.a);
+    memcpy(d.bt, d.b, sizeof d.b);
+    return true;
+}
+
+static void invalidate_graph(swdg_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+static int grid_for(int64_t n) {
+    int64_t b = (n + WPB - 1) / WPB;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152LL * 64));
+}
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int swdg_create(const swdg_config* cfg, swdg_ctx** out) {
+    swdg_ctx* ctx = nullptr;
+    if (!cfg || !out) return SWDG_EINVAL;
+    *out = nullptr;
+    if (cfg->degree < 1 || cfg->degree > 3 || cfg->precision != 0 || cfg->subgrid_mode < 0 ||
+        cfg->subgrid_mode > 1 || cfg->tableau < 0 || cfg->tableau > 3 || !(cfg->g > 0) ||
+        !(cfg->eps_vel > 0) || !(cfg->h_lim >= 0) || !(cfg->eps0 > 0) || !(cfg->cfl > 0) ||
+        cfg->newton_max < 1 || !(cfg->newton_tol >= 0))
+        return SWDG_EINVAL;
+    ctx = new swdg_ctx();
+    ctx->cfg = *cfg;
+    ctx->st = (cudaStream_t)cfg->stream;
+    if (!ctx->st) {
+        // a private blocking stream: ordered with the legacy default stream and
+        // capturable into a CUDA graph
+        if (cudaStreamCreate(&ctx->st) != cudaSuccess) {
+            delete ctx;
+            return SWDG_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    ctx->R = cfg->degree;
+    ctx->nd = (cfg->degree + 1) * (cfg->degree + 1);
+    ctx->mode = cfg->subgrid_mode;
+    if (!build_tables(ctx->R, ctx->tb)) {
+        delete ctx;
+        return SWDG_EINVAL;
+    }
+    Dev& d = ctx->d;
+    d.mode = ctx->mode;
+    d.g = cfg->g;
+    d.eps = cfg->eps_vel;
+    d.hlim = cfg->h_lim;
+    d.eps0 = cfg->eps0;
+    d.cfl = cfg->cfl;
+    d.newton_tol = cfg->newton_tol;
+    d.newton_max = cfg->newton_max;
+    set_tableau(cfg->tableau, d);
+    for (int i = 0; i < MXTAG; ++i) {
+        d.bc_kind[i] = SWDG_BC_WALL;
+        d.bc_amp[i] = 0.0;
+        d.bc_per[i] = 1.0;
+        d.bc_ph[i] = 0.0;
+    }
+    cudaError_t e = cudaMalloc(&ctx->sc, sizeof(Scalars));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->sc_host, sizeof(Scalars));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->pin, 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sc, 0, sizeof(Scalars), ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) {
+        swdg_destroy(ctx);
+        return SWDG_ECUDA;
+    }
+    d.sc = ctx->sc;
+    *out = ctx;
+    return SWDG_OK;
+}
+
+static void free_mesh(swdg_ctx* c) {
+    cudaFree(c->x0y0); cudaFree(c->hxhy); cudaFree(c->manning); cudaFree(c->U); cudaFree(c->res);
+    cudaFree(c->llin); cudaFree(c->HN); cudaFree(c->CN); cudaFree(c->HNbar); cudaFree(c->CNbar);
+    cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->diag);
+    c->x0y0 = c->hxhy = c->manning = c->U = c->res = c->llin = c->HN = c->CN = c->HNbar =
+        c->CNbar = c->diag = nullptr;
+    c->nbr = nullptr;
+    c->cmask = c->flag = nullptr;
+}
+static void free_bathy(swdg_ctx* c) {
+    cudaFree(c->tiles); cudaFree(c->zpts); cudaFree(c->zmax); cudaFree(c->zabs);
+    c->tiles = nullptr;
+    c->zpts = c->zmax = c->zabs = nullptr;
+}
+
+void swdg_destroy(swdg_ctx* c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    invalidate_graph(c);
+    free_mesh(c);
+    free_bathy(c);
+    cudaFree(c->sc);
+    if (c->sc_host) cudaFreeHost(c->sc_host);
+    if (c->pin) cudaFreeHost(c->pin);
+    if (c->own_stream) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+const char* swdg_last_error(const swdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double* hxhy,
+                     const int32_t* nbr) {
+    if (!ctx) return SWDG_EINVAL;
+    if (n < 1 || !x0y0 || !hxhy || !nbr) return fail(ctx, SWDG_EINVAL, "upload_mesh: bad arguments");
+    for (int64_t k = 0; k < n; ++k) {
+        if (!(hxhy[2 * k] > 0) || !(hxhy[2 * k + 1] > 0) || !std::isfinite(x0y0[2 * k]) ||
+            !std::isfinite(x0y0[2 * k + 1]))
+            return fail(ctx, SWDG_EINVAL, "upload_mesh: cell %lld has a bad size or origin",
+                        (long long)k);
+        for (int f = 0; f < 4; ++f) {
+            int32_t s0 = nbr[k * 8 + 2 * f], s1 = nbr[k * 8 + 2 * f + 1];
+            if (s1 != -1)
+                return fail(ctx, SWDG_EINVAL,
+                            "upload_mesh: cell %lld face %d: 2:1 hanging faces not supported",
+                            (long long)k, f);
+            if (s0 >= n || s0 < -MXTAG)
+                return fail(ctx, SWDG_EINVAL, "upload_mesh: cell %lld face %d: bad neighbour %d",
+                            (long long)k, f, s0);
+            if (s0 >= 0) {
+                // conforming: the neighbour must share the whole face
+                const int fo = f ^ 1;
+                if (nbr[(int64_t)s0 * 8 + 2 * fo] != (int32_t)k)
+                    return fail(ctx, SWDG_EINVAL,
+                                "upload_mesh: cell %lld face %d and cell %d are not mutual "
+                                "neighbours",
+                                (long long)k, f, s0);
+                const double tk = f < 2 ? hxhy[2 * k + 1] : hxhy[2 * k];
+                const double tn = f < 2 ? hxhy[2 * (int64_t)s0 + 1] : hxhy[2 * (int64_t)s0];
+                if (std::fabs(tk - tn) > 1e-9 * tk)
+                    return fail(ctx, SWDG_EINVAL,
+                                "upload_mesh: cell %lld face %d is non-conforming", (long long)k, f);
+            }
+        }
+    }
+    invalidate_graph(ctx);
+    free_mesh(ctx);
+    free_bathy(ctx);
+    ctx->has_bathy = ctx->has_state = false;
+    ctx->n = n;
+    const size_t nd = ctx->nd;
+    CK(cudaMalloc(&ctx->x0y0, 2 * n * sizeof(double)));
+    CK(cudaMalloc(&ctx->hxhy, 2 * n * sizeof(double)));
+    CK(cudaMalloc(&ctx->nbr, 8 * n * sizeof(int32_t)));
+    CK(cudaMalloc(&ctx->manning, n * sizeof(double)));
+    CK(cudaMalloc(&ctx->U, (size_t)NBUF * 4 * n * nd * sizeof(double)));
+    CK(cudaMalloc(&ctx->res, (size_t)MXS * 6 * n * nd * sizeof(double)));
+    CK(cudaMalloc(&ctx->llin, 2 * n * nd * sizeof(double)));
+    CK(cudaMalloc(&ctx->HN, n * nd * sizeof(double)));
+    CK(cudaMalloc(&ctx->CN, n * nd * sizeof(double)));
+    CK(cudaMalloc(&ctx->HNbar, n * sizeof(double)));
+    CK(cudaMalloc(&ctx->CNbar, n * sizeof(double)));
+    CK(cudaMalloc(&ctx->cmask, (size_t)NBUF * n));
+    CK(cudaMalloc(&ctx->flag, n));
+    CK(cudaMalloc(&ctx->diag, 4 * n * sizeof(double) + 8 * sizeof(double)));
+    CK(cudaMemcpyAsync(ctx->x0y0, x0y0, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->hxhy, hxhy, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->nbr, nbr, 8 * n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemsetAsync(ctx->manning, 0, n * sizeof(double), ctx->st));
+    CK(cudaMemsetAsync(ctx->llin, 0, 2 * n * nd * sizeof(double), ctx->st));
+    CK(cudaMemsetAsync(ctx->flag, ctx->R, n, ctx->st));
+    CK(cudaMemsetAsync(ctx->cmask, 0, (size_t)NBUF * n, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->x0y0_h.assign(x0y0, x0y0 + 2 * n);
+    ctx->hxhy_h.assign(hxhy, hxhy + 2 * n);
+    Dev& d = ctx->d;
+    d.n = n;
+    d.x0y0 = ctx->x0y0;
+    d.hxhy = ctx->hxhy;
+    d.nbr = ctx->nbr;
+    d.manning = ctx->manning;
+    d.U = ctx->U;
+    d.cmask = ctx->cmask;
+    d.res = ctx->res;
+    d.llin = ctx->llin;
+    d.HN = ctx->HN;
+    d.CN = ctx->CN;
+    d.HNbar = ctx->HNbar;
+    d.CNbar = ctx->CNbar;
+    d.flag = ctx->flag;
+    d.any_friction = 0;
+    ctx->grid = grid_for(n);
+    ctx->has_mesh = true;
+    return SWDG_OK;
+}
+
+int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t nx, int64_t ny,
+                           double xo, double yo, double dx, double dy) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_mesh) return fail(ctx, SWDG_ESTATE, "upload_bathymetry: no mesh");
+    if (!raster || (dtype != SWDG_PIX_F32 && dtype != SWDG_PIX_F64) || nx < 2 || ny < 2 ||
+        !(dx > 0) || !(dy > 0))
+        return fail(ctx, SWDG_EINVAL, "upload_bathymetry: bad arguments");
+    const int64_t n = ctx->n;
+    const size_t es = dtype == SWDG_PIX_F32 ? 4 : 8;
+    int P = 0;
+    std::vector<int32_t> col0, row0;
+    if (ctx->mode == 0) {
+        col0.resize(n);
+        row0.resize(n);
+        for (int64_t k = 0; k < n; ++k) {
+            const double cx = (ctx->x0y0_h[2 * k] - xo) / dx, cy = (ctx->x0y0_h[2 * k + 1] - yo) / dy;
+            const double px = ctx->hxhy_h[2 * k] / dx, py = ctx->hxhy_h[2 * k + 1] / dy;
+            const double rcx = std::floor(cx + 0.5), rcy = std::floor(cy + 0.5);
+            const double rpx = std::floor(px + 0.5), rpy = std::floor(py + 0.5);
+            if (std::fabs(cx - rcx) > 1e-6 || std::fabs(cy - rcy) > 1e-6 ||
+                std::fabs(px - rpx) > 1e-6 || std::fabs(py - rpy) > 1e-6 || rpx != rpy)
+                return fail(ctx, SWDG_EINVAL,
+                            "upload_bathymetry: cell %lld is not aligned to whole pixels",
+                            (long long)k);
+            if (k == 0) P = (int)rpx;
+            if ((int)rpx != P)
+                return fail(ctx, SWDG_EINVAL,
+                            "upload_bathymetry: cells must all span the same number of pixels");
+            if (rcx < 0 || rcy < 0 || rcx + P > nx || rcy + P > ny)
+                return fail(ctx, SWDG_EINVAL, "upload_bathymetry: raster does not cover cell %lld",
+                            (long long)k);
+            col0[k] = (int32_t)rcx;
+            row0[k] = (int32_t)rcy;
+        }
+        if (P < 1 || P > MXPIX)
+            return fail(ctx, SWDG_EINVAL, "upload_bathymetry: %d pixels per cell (max %d)", P, MXPIX);
+    }
+    invalidate_graph(ctx);
+    free_bathy(ctx);
+    void* ras = nullptr;
+    CK(cudaMalloc(&ras, nx * ny * es));
+    CK(cudaMemcpyAsync(ras, raster, nx * ny * es, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMalloc(&ctx->zmax, n * sizeof(double)));
+    CK(cudaMalloc(&ctx->zabs, n * sizeof(double)));
+    const int grid = (int)std::min<int64_t>(152 * 32, (n * 32 + 255) / 256 + 1);
+    if (ctx->mode == 0) {
+        int32_t *c0 = nullptr, *r0 = nullptr;
+        CK(cudaMalloc(&c0, n * sizeof(int32_t)));
+        CK(cudaMalloc(&r0, n * sizeof(int32_t)));
+        CK(cudaMemcpyAsync(c0, col0.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemcpyAsync(r0, row0.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMalloc(&ctx->tiles, (size_t)n * P * P * es));
+        if (dtype == SWDG_PIX_F32) {
+            k_retile<float><<<152 * 16, 256, 0, ctx->st>>>((const float*)ras, nx, c0, r0, P,
+                                                          (float*)ctx->tiles, n);
+            k_tile_bounds<float><<<grid, 256, 0, ctx->st>>>((const float*)ctx->tiles, P, n, ctx->zmax,
+                                                           ctx->zabs);
+        } else {
+            k_retile<double><<<152 * 16, 256, 0, ctx->st>>>((const double*)ras, nx, c0, r0, P,
+                                                           (double*)ctx->tiles, n);
+            k_tile_bounds<double><<<grid, 256, 0, ctx->st>>>((const double*)ctx->tiles, P, n,
+                                                            ctx->zmax, ctx->zabs);
+        }
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(ctx->st));
+        cudaFree(c0);
+        cudaFree(r0);
+        if (!build_overlaps(ctx->R, P, ctx->tb))
+            return fail(ctx, SWDG_EINVAL, "upload_bathymetry: bad pixel count");
+    } else {
+        const int R = ctx->R, nv = (3 * R) / 2 + 1, nm = R + 2, ng = R + 1;
+        const int nzp = nv * nv + nm * nm + ng * ng;
+        CK(cudaMalloc(&ctx->zpts, (size_t)n * nzp * sizeof(double)));
+        const int g2 = (int)std::min<int64_t>(152 * 16, (n + 127) / 128);
+        if (dtype == SWDG_PIX_F32)
+            k_point_samples<float><<<g2, 128, 0, ctx->st>>>(
+                (const float*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0, ctx->hxhy, ctx->tb, nv, nm, ng,
+                ctx->zpts, ctx->zmax, ctx->zabs, n);
+        else
+            k_point_samples<double><<<g2, 128, 0, ctx->st>>>(
+                (const double*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0, ctx->hxhy, ctx->tb, nv, nm, ng,
+                ctx->zpts, ctx->zmax, ctx->zabs, n);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    cudaFree(ras);
+    ctx->pix = dtype == SWDG_PIX_F32 ? 0 : 1;
+    if (!get_launch(ctx->R, ctx->mode, ctx->pix, &ctx->L))
+        return fail(ctx, SWDG_EINVAL, "upload_bathymetry: no kernels for this configuration");
+    ctx->d.tiles = ctx->tiles;
+    ctx->d.zpts = ctx->zpts;
+    ctx->d.zmax = ctx->zmax;
+    ctx->d.zabs = ctx->zabs;
+    ctx->has_bathy = true;
+    return SWDG_OK;
+}
+
+int swdg_set_boundary(swdg_ctx* ctx, int tag, int kind, double amp, double period, double phase) {
+    if (!ctx) return SWDG_EINVAL;
+    if (tag < 0 || tag >= MXTAG || (kind != SWDG_BC_WALL && kind != SWDG_BC_TIDE) ||
+        (kind == SWDG_BC_TIDE && !(period > 0)) || !std::isfinite(amp) || !std::isfinite(phase))
+        return fail(ctx, SWDG_EINVAL, "set_boundary: bad arguments");
+    ctx->d.bc_kind[tag] = kind;
+    ctx->d.bc_amp[tag] = amp;
+    ctx->d.bc_per[tag] = period;
+    ctx->d.bc_ph[tag] = phase;
+    invalidate_graph(ctx);
+    return SWDG_OK;
+}
+
+int swdg_set_manning(swdg_ctx* ctx, const double* nman, int where) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_mesh) return fail(ctx, SWDG_ESTATE, "set_manning: no mesh");
+    const int64_t n = ctx->n;
+    if (!nman) {
+        CK(cudaMemsetAsync(ctx->manning, 0, n * sizeof(double), ctx->st));
+    } else if (where == SWDG_HOST) {
+        for (int64_t k = 0; k < n; ++k)
+            if (!(nman[k] >= 0) || !std::isfinite(nman[k]))
+                return fail(ctx, SWDG_EINVAL, "set_manning: bad value at cell %lld", (long long)k);
+        CK(cudaMemcpyAsync(ctx->manning, nman, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    } else {
+        CK(cudaMemcpyAsync(ctx->manning, nman, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->st));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return SWDG_OK;
+}
+
+int swdg_set_state(swdg_ctx* ctx, const double* z, const double* qx, const double* qy,
+                   const double* c, int where) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_mesh || !ctx->has_bathy)
+        return fail(ctx, SWDG_ESTATE, "set_state: upload the mesh and bathymetry first");
+    if (!z || !qx || !qy || !c || (where != SWDG_HOST && where != SWDG_DEVICE))
+        return fail(ctx, SWDG_EINVAL, "set_state: bad arguments");
+    const size_t sz = (size_t)ctx->n * ctx->nd * sizeof(double);
+    const double* src[4] = {z, qx, qy, c};
+    for (int f = 0; f < 4; ++f)
+        CK(cudaMemcpyAsync(ctx->U + (size_t)f * ctx->n * ctx->nd, src[f], sz,
+                           where == SWDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           ctx->st));
+    CK(cudaMemsetAsync(ctx->flag, ctx->R, ctx->n, ctx->st));
+    ctx->L.masks(ctx->d, 0, ctx->grid, ctx->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->has_state = true;
+    return SWDG_OK;
+}
+
+int swdg_get_state(swdg_ctx* ctx, double* z, double* qx, double* qy, double* c, int where) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "get_state: no state");
+    const size_t sz = (size_t)ctx->n * ctx->nd * sizeof(double);
+    double* dst[4] = {z, qx, qy, c};
+    for (int f = 0; f < 4; ++f)
+        if (dst[f])
+            CK(cudaMemcpyAsync(dst[f], ctx->U + (size_t)f * ctx->n * ctx->nd, sz,
+                               where == SWDG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                               ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return SWDG_OK;
+}
+
+static int put_time(swdg_ctx* ctx, double t, double fixed_dt) {
+    ctx->pin[0] = t;
+    ctx->pin[1] = fixed_dt;
+    CK(cudaMemcpyAsync(&ctx->sc->t, &ctx->pin[0], sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(&ctx->sc->fixed_dt, &ctx->pin[1], sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->st));
+    return SWDG_OK;
+}
+
+int swdg_residual(swdg_ctx* ctx, double t, double* F, double* Gx, double* Gy, double* R, double* Lx,
+                  double* Ly, int where) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "residual: no state");
+    int rc = put_time(ctx, t, -1.0);
+    if (rc) return rc;
+    ctx->L.residual(ctx->d, ctx->tb, 0, 0, 0.0, 0, ctx->grid, ctx->st);
+    CK(cudaGetLastError());
+    double* dst[6] = {F, Gx, Gy, R, Lx, Ly};
+    const size_t sz = (size_t)ctx->n * ctx->nd * sizeof(double);
+    for (int f = 0; f < 6; ++f)
+        if (dst[f])
+            CK(cudaMemcpyAsync(dst[f], ctx->res + (size_t)f * ctx->n * ctx->nd, sz,
+                               where == SWDG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                               ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return SWDG_OK;
+}
+
+int swdg_cfl_dt(swdg_ctx* ctx, double t, double* dt) {
+    if (!ctx || !dt) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "cfl_dt: no state");
+    int rc = put_time(ctx, t, -1.0);
+    if (rc) return rc;
+    ctx->pin[2] = INFINITY;
+    CK(cudaMemcpyAsync(&ctx->sc->dtmin, &ctx->pin[2], sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->st));
+    ctx->L.residual(ctx->d, ctx->tb, 0, 0, 0.0, 1, ctx->grid, ctx->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&ctx->pin[3], &ctx->sc->dtmin, sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *dt = ctx->cfg.cfl * ctx->pin[3];
+    return SWDG_OK;
+}
+
+// the kernels of one time step, in stream order; with ev != nullptr an event
+// pair brackets every launch (slot layout of swdg_step_profile)
+static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr) {
+    const Dev& d = ctx->d;
+    const int s = d.s;
+    auto mark = [&](int slot, int which) {
+        if (ev) cudaEventRecord(ev[slot][which], ctx->st);
+    };
+    mark(0, 0);
+    ctx->L.step_begin(d, ctx->tb, 1, ctx->grid, ctx->st);
+    mark(0, 1);
+    for (int l = 0; l < s; ++l) {
+        if (l > 0) {
+            StageArgs sa{};
+            sa.out_buf = l;
+            sa.prev_buf = l - 1;
+            sa.nres = l;
+            for (int m = 0; m < l; ++m) {
+                sa.wa[m] = d.a[l][m];
+                sa.wat[m] = d.at[l][m];
+            }
+            sa.add = d.at[l][l];
+            sa.use_llin = 0;
+            sa.make_llin = (l == s - 1 && d.at[l][l] != 0.0) ? 1 : 0;
+            sa.final_ = 0;
+            mark(4 + l, 0);
+            ctx->L.stage(d, ctx->tb, sa, ctx->grid, ctx->st);
+            mark(4 + l, 1);
+        }
+        mark(1 + l, 0);
+        ctx->L.residual(d, ctx->tb, l, l, d.c[l], l == 0 ? 1 : 0, ctx->grid, ctx->st);
+        mark(1 + l, 1);
+    }
+    StageArgs sa{};
+    sa.out_buf = 0;
+    sa.prev_buf = s - 1;
+    sa.nres = s;
+    for (int m = 0; m < s; ++m) {
+        sa.wa[m] = d.b[m];
+        sa.wat[m] = d.bt[m];
+    }
+    sa.add = 0.0;
+    sa.use_llin = (d.at[s - 1][s - 1] != 0.0) ? 1 : 0;
+    sa.make_llin = 0;
+    sa.final_ = 1;
+    mark(8, 0);
+    ctx->L.stage(d, ctx->tb, sa, ctx->grid, ctx->st);
+    mark(8, 1);
+    CK(cudaGetLastError());
+    return SWDG_OK;
+}
+
+static int ensure_graph(swdg_ctx* ctx) {
+    if (ctx->graph) return SWDG_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_step(ctx);
+    cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(ctx, SWDG_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess)
+        return fail(ctx, SWDG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return SWDG_OK;
+}
+
+int swdg_step(swdg_ctx* ctx, int n_steps, double dt, double* t_inout) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "step: no state");
+    if (n_steps < 0 || !std::isfinite(dt)) return fail(ctx, SWDG_EINVAL, "step: bad arguments");
+    if (t_inout) {
+        int rc = put_time(ctx, *t_inout, dt >= 0.0 ? dt : -1.0);
+        if (rc) return rc;
+    } else {
+        ctx->pin[1] = dt >= 0.0 ? dt : -1.0;
+        CK(cudaMemcpyAsync(&ctx->sc->fixed_dt, &ctx->pin[1], sizeof(double), cudaMemcpyHostToDevice,
+                           ctx->st));
+    }
+    int rc = ensure_graph(ctx);
+    if (rc) return rc;
+    for (int i = 0; i < n_steps; ++i) {
+        if (ctx->graph) CK(cudaGraphLaunch(ctx->graph, ctx->st));
+        else {
+            rc = enqueue_step(ctx);
+            if (rc) return rc;
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->sc_host, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (t_inout) *t_inout = ctx->sc_host->t;
+    if (ctx->sc_host->status & ST_NAN) return fail(ctx, SWDG_ENAN, "step: non-finite state");
+    return SWDG_OK;
+}
+
+int swdg_step_profile(swdg_ctx* ctx, int n_steps, double dt, double* t_inout, double* ms_out) {
+    if (!ctx || !ms_out) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "step_profile: no state");
+    if (n_steps < 0 || !std::isfinite(dt)) return fail(ctx, SWDG_EINVAL, "step_profile: bad arguments");
+    int rc = t_inout ? put_time(ctx, *t_inout, dt >= 0.0 ? dt : -1.0) : SWDG_OK;
+    if (rc) return rc;
+    if (!t_inout) {
+        ctx->pin[1] = dt >= 0.0 ? dt : -1.0;
+        CK(cudaMemcpyAsync(&ctx->sc->fixed_dt, &ctx->pin[1], sizeof(double), cudaMemcpyHostToDevice,
+                           ctx->st));
+    }
+    cudaEvent_t ev[SWDG_PROF_SLOTS][2];
+    for (int i = 0; i < SWDG_PROF_SLOTS; ++i) {
+        ms_out[i] = 0.0;
+        CK(cudaEventCreate(&ev[i][0]));
+        CK(cudaEventCreate(&ev[i][1]));
+    }
+    bool used[SWDG_PROF_SLOTS] = {};
+    used[0] = used[8] = true;
+    for (int l = 0; l < ctx->d.s; ++l) {
+        used[1 + l] = true;
+        if (l > 0) used[4 + l] = true;
+    }
+    for (int i = 0; i < n_steps; ++i) {
+        rc = enqueue_step(ctx, ev);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(ctx->st));
+        for (int k = 0; k < SWDG_PROF_SLOTS; ++k) {
+            if (!used[k]) continue;
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, ev[k][0], ev[k][1]));
+            ms_out[k] += ms;
+        }
+    }
+    for (int i = 0; i < SWDG_PROF_SLOTS; ++i) {
+        cudaEventDestroy(ev[i][0]);
+        cudaEventDestroy(ev[i][1]);
+    }
+    CK(cudaMemcpyAsync(ctx->sc_host, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (t_inout) *t_inout = ctx->sc_host->t;
+    if (ctx->sc_host->status & ST_NAN) return fail(ctx, SWDG_ENAN, "step_profile: non-finite state");
+    return SWDG_OK;
+}
+
+int swdg_degree_switch(swdg_ctx* ctx, uint8_t* flags_out) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "degree_switch: no state");
+    ctx->L.step_begin(ctx->d, ctx->tb, 1, ctx->grid, ctx->st);
+    CK(cudaGetLastError());
+    if (flags_out)
+        CK(cudaMemcpyAsync(flags_out, ctx->flag, ctx->n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return SWDG_OK;
+}
+
+int swdg_gather_gauges(swdg_ctx* ctx, int n, const double* xy, double* out) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "gather_gauges: no state");
+    if (n < 0 || (n > 0 && (!xy || !out))) return fail(ctx, SWDG_EINVAL, "gather_gauges: bad arguments");
+    if (n == 0) return SWDG_OK;
+    double* buf = nullptr;
+    CK(cudaMalloc(&buf, 3 * (size_t)n * sizeof(double)));
+    CK(cudaMemcpyAsync(buf, xy, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    ctx->L.gauges(ctx->d, ctx->tb, n, buf, buf + 2 * n, ctx->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, buf + 2 * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    cudaFree(buf);
+    return SWDG_OK;
+}
+
+int swdg_diagnostics(swdg_ctx* ctx, double out[8]) {
+    if (!ctx || !out) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "diagnostics: no state");
+    ctx->L.cell_diag(ctx->d, ctx->tb, ctx->diag, ctx->grid, ctx->st);
+    k_diag_reduce<<<1, 256, 0, ctx->st>>>(ctx->diag, ctx->n, ctx->diag + 4 * ctx->n);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->pin, ctx->diag + 4 * ctx->n, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaMemcpyAsync(ctx->sc_host, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    out[0] = ctx->pin[0];
+    out[1] = ctx->pin[1];
+    out[2] = ctx->pin[2];
+    out[3] = ctx->pin[3];
+    out[4] = ctx->sc_host->maxits;
+    out[5] = ctx->sc_host->viol;
+    out[6] = ctx->sc_host->dt_last;
+    out[7] = ctx->sc_host->t;
+    return SWDG_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,173 @@
+// swdg_common.cuh -- device data structures and warp helpers of the sm_103a
+// sub-grid DG shallow-water hot path (arXiv 2505.18743).
+//
+// Layout in HBM (one context):
+//   state   U[buf][field][cell][(r+1)^2]  float64, field = zeta, qx, qy, c
+//   cmask   [buf][cell] uint8: bit f set when field f is constant on the cell
+//           (such a field is evaluated as that constant, exactly)
+//   resid   R[stage][6][cell][(r+1)^2] float64, 6 = F, Gx, Gy, R, Lx, Ly
+//   tiles   [cell][P][P] float32|float64 bathymetry depth (mode S)
+//   zpts    [cell][NV^2 + NM^2 + NG^2] float64 point samples (mode P)
+// Small per-degree tables (1D interpolation matrices, quadrature weights,
+// pixel-overlap fractions) travel as a __grid_constant__ kernel parameter.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swdg {
+
+constexpr int MXP = 6;    // max quadrature points per direction (GL 5 for r = 3)
+constexpr int MXN = 4;    // max nodes per direction (r + 1)
+constexpr int MXPIX = 32; // max pixels per cell side in mode S
+constexpr int MXTAG = 16;
+constexpr int MXS = 4;    // max RK stages
+constexpr int NBUF = 4;   // state buffers: v^n plus stages 2..4
+
+// point sets
+constexpr int SET_VOL = 0;  // volume Gauss-Legendre, floor(3r/2)+1 per direction
+constexpr int SET_MASS = 1; // face / mass Gauss-Lobatto, r+2 per direction
+constexpr int SET_MOM = 2;  // momentum mass Gauss-Legendre, r+1 per direction
+
+// status bits
+constexpr int ST_NAN = 1;
+
+template <int R>
+struct Sz {
+    static constexpr int ND1 = R + 1, ND = ND1 * ND1;
+    static constexpr int NV = (3 * R) / 2 + 1, NVP = NV * NV;
+    static constexpr int NM = R + 2, NMP = NM * NM;
+    static constexpr int NG = R + 1, NGP = NG * NG;
+    static constexpr int NZP = NVP + NMP + NGP; // mode P samples per cell
+};
+
+struct Tables {
+    double Bv[MXP][MXN], Dv[MXP][MXN], wv[MXP]; // nodal -> volume GL (value, d/dxi)
+    double Bm[MXP][MXN], wm[MXP];               // nodal -> mass / face GLL
+    double Bg[MXP][MXN], wg[MXP];               // nodal -> momentum GL (square)
+    double Bginv[MXN][MXP];                     // inverse of Bg
+    double M1inv[MXN][MXN];                     // inverse of the 1D GLL mass matrix
+    double xs[MXN];                             // support nodes on [0, 1]
+    double xq[3][MXP];                          // nodes of the three point sets on [0, 1]
+    int P;                                      // pixels per cell side (mode S)
+    int lo[3][MXP], cnt[3][MXP];                // first pixel and count per sub-interval
+    double frac[3][MXP][MXPIX + 1];             // pixel fraction of each sub-interval
+};
+
+struct Scalars {
+    double t;                 // time at the start of the current step
+    double fixed_dt;          // >= 0: fixed step, < 0: CFL
+    double dt_last;
+    unsigned long long dtmin; // bits of min J/(lambda l) (positive double)
+    int maxits, viol, fallback, status;
+};
+
+struct Dev {
+    int64_t n;
+    const double* x0y0;
+    const double* hxhy;
+    const int32_t* nbr;
+    const void* tiles;
+    const double* zpts;
+    const double* zmax; // dry-start level of Eq. initial_guess (max z_b of the cell)
+    const double* zabs; // max |z_b| of the cell (Newton tolerance scale)
+    const double* manning;
+    double* U;
+    uint8_t* cmask;
+    double* res;
+    double* llin;
+    double* HN;
+    double* CN;
+    double* HNbar;
+    double* CNbar;
+    uint8_t* flag;
+    Scalars* sc;
+    int mode; // 0 S, 1 P
+    int s;    // stages
+    double g, eps, hlim, eps0, cfl, newton_tol;
+    int newton_max;
+    int any_friction;
+    int bc_kind[MXTAG];
+    double bc_amp[MXTAG], bc_per[MXTAG], bc_ph[MXTAG];
+    double a[MXS][MXS], at[MXS][MXS], b[MXS], bt[MXS], c[MXS];
+};
+
+// ---------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double* ufield(const Dev& d, int buf, int f, int nd) {
+    return d.U + ((size_t)buf * 4 + f) * (size_t)d.n * nd;
+}
+__device__ __forceinline__ double* rfield(const Dev& d, int stage, int f, int nd) {
+    return d.res + ((size_t)stage * 6 + f) * (size_t)d.n * nd;
+}
+
+__device__ __forceinline__ double get_dt(const Dev& d) {
+    return d.sc->fixed_dt >= 0.0 ? d.sc->fixed_dt : d.cfl * __longlong_as_double(d.sc->dtmin);
+}
+
+// desingularised velocity factor u = f q, Eq. velocity
+__device__ __forceinline__ double vel_factor(double h, double eps) {
+    if (h <= 0.0) return 0.0;
+    double h4 = (h * h) * (h * h), e4 = (eps * eps) * (eps * eps);
+    return sqrt(2.0) * h / sqrt(fmax(h4, e4) + h4);
+}
+// Manning coefficient gamma = g n^2 |q| / h_des^(7/3), Eqs. manning, discharge_rhs_implicit
+__device__ __forceinline__ double gamma_manning(double n, double h, double qx, double qy, double g,
+                                                double eps) {
+    if (n == 0.0 || h <= 0.0) return 0.0;
+    double h4 = (h * h) * (h * h), e4 = (eps * eps) * (eps * eps);
+    double hdes = sqrt(fmax(h4, e4) + h4) / (sqrt(2.0) * h);
+    return g * n * n * sqrt(qx * qx + qy * qy) / (hdes * hdes * cbrt(hdes));
+}
+
+// sub-grid wet depth V and wet area A of sub-cell (ia, ib) of point set `set`
+// (mode S): V = sum_k w_k max(eta + z_k, 0), A = sum_k w_k [eta + z_k > 0]
+template <typename Pix>
+__device__ __forceinline__ void subgrid_S(const Pix* __restrict__ tile, const Tables& tb, int set,
+                                          int ia, int ib, double eta, double& V, double& A) {
+    const int P = tb.P;
+    const int lox = tb.lo[set][ia], cx = tb.cnt[set][ia];
+    const int loy = tb.lo[set][ib], cy = tb.cnt[set][ib];
+    double v = 0.0, a = 0.0;
+    for (int j = 0; j < cy; ++j) {
+        const Pix* row = tile + (size_t)(loy + j) * P + lox;
+        double vr = 0.0, ar = 0.0;
+        for (int i = 0; i < cx; ++i) {
+            double dd = eta + (double)row[i];
+            if (dd > 0.0) {
+                double fx = tb.frac[set][ia][i];
+                vr += fx * dd;
+                ar += fx;
+            }
+        }
+        double fy = tb.frac[set][ib][j];
+        v += fy * vr;
+        a += fy * ar;
+    }
+    V = v;
+    A = a;
+}
+
+__device__ __forceinline__ void subgrid_P(double z, double eta, double& V, double& A) {
+    double dd = eta + z;
+    if (dd > 0.0) { V = dd; A = 1.0; }
+    else { V = 0.0; A = 0.0; }
+}
+
+} // namespace swdg

@@ -1,0 +1,239 @@
+"""Thin ctypes binding of the C-ABI in ``include/swdg.h``.
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of ``libswdg.so``.  NumPy arrays are passed as host buffers, torch
+CUDA tensors as device buffers on the current torch stream.  There is no CPU
+fallback: if the library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "libswdg.so")
+
+SWDG_OK = 0
+SWDG_EINVAL = -1
+SWDG_ECUDA = -2
+SWDG_ENEWTON = -3
+SWDG_EPOSITIVITY = -4
+SWDG_ENAN = -5
+SWDG_ESTATE = -6
+SWDG_HOST = 0
+SWDG_DEVICE = 1
+SWDG_BC_WALL = 0
+SWDG_BC_TIDE = 1
+SWDG_PIX_F32 = 0
+SWDG_PIX_F64 = 1
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_I64 = ctypes.c_int64
+
+
+class swdg_config(ctypes.Structure):
+    _fields_ = [("degree", _I), ("precision", _I), ("subgrid_mode", _I), ("tableau", _I),
+                ("g", _D), ("eps_vel", _D), ("h_lim", _D), ("eps0", _D), ("cfl", _D),
+                ("newton_max", _I), ("newton_tol", _D), ("stream", _P)]
+
+
+class SwdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"swdg error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes), mirroring include/swdg.h
+SIGNATURES = {
+    "swdg_create": (_I, [ctypes.POINTER(swdg_config), ctypes.POINTER(_P)]),
+    "swdg_upload_mesh": (_I, [_P, _I64, _P, _P, _P]),
+    "swdg_upload_bathymetry": (_I, [_P, _P, _I, _I64, _I64, _D, _D, _D, _D]),
+    "swdg_set_boundary": (_I, [_P, _I, _I, _D, _D, _D]),
+    "swdg_set_manning": (_I, [_P, _P, _I]),
+    "swdg_set_state": (_I, [_P, _P, _P, _P, _P, _I]),
+    "swdg_get_state": (_I, [_P, _P, _P, _P, _P, _I]),
+    "swdg_residual": (_I, [_P, _D, _P, _P, _P, _P, _P, _P, _I]),
+    "swdg_cfl_dt": (_I, [_P, _D, ctypes.POINTER(_D)]),
+    "swdg_step": (_I, [_P, _I, _D, ctypes.POINTER(_D)]),
+    "swdg_step_profile": (_I, [_P, _I, _D, ctypes.POINTER(_D), _P]),
+    "swdg_degree_switch": (_I, [_P, _P]),
+    "swdg_gather_gauges": (_I, [_P, _I, _P, _P]),
+    "swdg_diagnostics": (_I, [_P, _P]),
+    "swdg_last_error": (ctypes.c_char_p, [_P]),
+    "swdg_destroy": (None, [_P]),
+}
+
+
+def load():
+    """Load the in-tree library (build it with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build the CUDA extension first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except ImportError:  # pragma: no cover
+        return None
+
+
+def _buf(a, dtype):
+    """(pointer, where, keepalive) of a numpy array or torch tensor."""
+    if a is None:
+        return None, SWDG_HOST, None
+    t = _torch()
+    if t is not None and isinstance(a, t.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        want = {np.float64: t.float64, np.float32: t.float32, np.int32: t.int32,
+                np.uint8: t.uint8}[dtype]
+        if a.dtype != want:
+            raise TypeError(f"tensor dtype {a.dtype}, expected {want}")
+        return ctypes.c_void_p(a.data_ptr()), (SWDG_DEVICE if a.is_cuda else SWDG_HOST), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), SWDG_HOST, arr
+
+
+class Context:
+    """One swdg context (owns its device memory).  Methods mirror the C-ABI."""
+
+    def __init__(self, degree=1, subgrid_mode=0, tableau=0, g=9.81, eps_vel=0.01, h_lim=0.01,
+                 eps0=1e-6, cfl=0.1, newton_max=20, newton_tol=1e-12, stream=None):
+        L = load()
+        if stream is None:
+            t = _torch()
+            if t is not None and t.cuda.is_available():
+                stream = t.cuda.current_stream().cuda_stream
+        self.cfg = swdg_config(degree, 0, subgrid_mode, tableau, g, eps_vel, h_lim, eps0, cfl,
+                               newton_max, newton_tol, ctypes.c_void_p(stream or 0))
+        h = ctypes.c_void_p()
+        rc = L.swdg_create(ctypes.byref(self.cfg), ctypes.byref(h))
+        if rc:
+            raise SwdgError(rc, "swdg_create failed")
+        self.h = h
+        self.degree = degree
+        self.nd = (degree + 1) ** 2
+        self.n = 0
+
+    def _ck(self, rc):
+        if rc:
+            raise SwdgError(rc, load().swdg_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.swdg_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def upload_mesh(self, x0y0, hxhy, nbr):
+        a, _, ka = _buf(x0y0, np.float64)
+        b, _, kb = _buf(hxhy, np.float64)
+        c, _, kc = _buf(nbr, np.int32)
+        n = int(np.asarray(ka.shape[0] if hasattr(ka, "shape") else len(x0y0)))
+        self._ck(load().swdg_upload_mesh(self.h, n, a, b, c))
+        self.n = n
+
+    def upload_bathymetry(self, z, xo, yo, dx, dy):
+        z = np.ascontiguousarray(z)
+        dtype = SWDG_PIX_F32 if z.dtype == np.float32 else SWDG_PIX_F64
+        if dtype == SWDG_PIX_F64:
+            z = np.ascontiguousarray(z, dtype=np.float64)
+        ny, nx = z.shape
+        self._ck(load().swdg_upload_bathymetry(self.h, z.ctypes.data_as(_P), dtype, nx, ny, xo, yo,
+                                               dx, dy))
+
+    def set_boundary(self, tag, kind, amp=0.0, period=1.0, phase=0.0):
+        self._ck(load().swdg_set_boundary(self.h, tag, kind, amp, period, phase))
+
+    def set_manning(self, n):
+        p, where, keep = _buf(n, np.float64)
+        self._ck(load().swdg_set_manning(self.h, p, where))
+
+    def set_state(self, zeta, qx, qy, c):
+        bufs = [_buf(v, np.float64) for v in (zeta, qx, qy, c)]
+        where = bufs[0][1]
+        self._ck(load().swdg_set_state(self.h, *[b[0] for b in bufs], where))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = [np.empty((self.n, self.nd)) for _ in range(4)]
+        bufs = [_buf(v, np.float64) for v in out]
+        self._ck(load().swdg_get_state(self.h, *[b[0] for b in bufs], bufs[0][1]))
+        return out
+
+    def residual(self, t=0.0, out=None):
+        if out is None:
+            out = [np.empty((self.n, self.nd)) for _ in range(6)]
+        bufs = [_buf(v, np.float64) for v in out]
+        self._ck(load().swdg_residual(self.h, t, *[b[0] for b in bufs], bufs[0][1]))
+        return dict(zip(("F", "Gx", "Gy", "R", "Lx", "Ly"), out))
+
+    def cfl_dt(self, t=0.0):
+        d = _D(0.0)
+        self._ck(load().swdg_cfl_dt(self.h, t, ctypes.byref(d)))
+        return d.value
+
+    def step(self, n=1, dt=-1.0, t=None):
+        tt = _D(0.0 if t is None else t)
+        self._ck(load().swdg_step(self.h, n, dt, ctypes.byref(tt) if t is not None else None))
+        return tt.value if t is not None else None
+
+    def step_profile(self, n=1, dt=-1.0, t=None):
+        """per-kernel-slot milliseconds (CUDA events) summed over n eager steps"""
+        tt = _D(0.0 if t is None else t)
+        ms = np.zeros(9)
+        self._ck(load().swdg_step_profile(self.h, n, dt, ctypes.byref(tt) if t is not None else None,
+                                          ms.ctypes.data_as(_P)))
+        return ms, (tt.value if t is not None else None)
+
+    def degree_switch(self):
+        f = np.empty(self.n, dtype=np.uint8)
+        self._ck(load().swdg_degree_switch(self.h, f.ctypes.data_as(_P)))
+        return f
+
+    def gather_gauges(self, xy):
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        out = np.empty(len(xy))
+        self._ck(load().swdg_gather_gauges(self.h, len(xy), xy.ctypes.data_as(_P),
+                                           out.ctypes.data_as(_P)))
+        return out
+
+    def diagnostics(self):
+        d = np.empty(8)
+        self._ck(load().swdg_diagnostics(self.h, d.ctypes.data_as(_P)))
+        keys = ("mass", "tracer_mass", "min_h", "r_cells", "newton_max", "positivity_violations",
+                "dt", "t")
+        return dict(zip(keys, d.tolist()))
+
+    @classmethod
+    def from_workload(cls, wl, stream=None, **over):
+        cfg = wl.config(**over)
+        ctx = cls(stream=stream, **cfg)
+        ctx.upload_mesh(wl.mesh.x0y0, wl.mesh.hxhy, wl.mesh.nbr)
+        r = wl.raster
+        ctx.upload_bathymetry(r.z, r.xo, r.yo, r.dx, r.dy)
+        for (tag, kind, amp, per, ph) in wl.boundaries:
+            ctx.set_boundary(tag, kind, amp, per, ph)
+        if wl.manning is not None:
+            ctx.set_manning(wl.manning)
+        ctx.set_state(*wl.state())
+        return ctx

@@ -1,0 +1,35 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+function declared in include/swdg.h (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+from paper_2505_18743_gb300 import build as B
+from paper_2505_18743_gb300 import swdg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    text = open(os.path.join(ROOT, "include", "swdg.h")).read()
+    return sorted(set(re.findall(r"\b(swdg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib_path = B.build()
+    assert os.path.exists(lib_path)
+    lib = ctypes.CDLL(lib_path)
+    names = declared()
+    assert "swdg_step" in names and "swdg_residual" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    # the binding covers the same names
+    assert set(names) <= set(swdg.SIGNATURES)
+
+
+def test_invalid_config_is_rejected_without_touching_the_gpu():
+    lib = swdg.load()
+    cfg = swdg.swdg_config(7, 0, 0, 0, 9.81, 0.01, 0.01, 1e-6, 0.1, 20, 1e-12, None)
+    h = ctypes.c_void_p()
+    assert lib.swdg_create(ctypes.byref(cfg), ctypes.byref(h)) == swdg.SWDG_EINVAL
+    assert not h.value

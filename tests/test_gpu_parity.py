@@ -1,0 +1,297 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Tolerances: residuals within 1e-12 relative per field (max abs difference over
+max(|oracle|, 1e-3 of the largest residual of the case)); states within 1e-10
+relative per field after the stated number of steps; integer decisions (degree
+flags) bit-exact.
+"""
+import numpy as np
+import pytest
+
+from helpers import rel_inf
+from oracle.oracle import Oracle
+from paper_2505_18743_gb300 import swdg
+from paper_2505_18743_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RES_TOL = 1e-12
+STATE_TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2505_18743_gb300 import build as B
+    from oracle import oracle
+    B.build()
+    oracle.build()
+
+
+def pair(wl, **over):
+    return swdg.Context.from_workload(wl, **over), Oracle.from_workload(wl, **over)
+
+
+def check_residual(ctx, ora, t=0.0, tol=RES_TOL):
+    rg = ctx.residual(t)
+    ro = ora.residual(t)
+    scale = max(float(np.abs(v).max()) for v in ro.values())
+    worst = {}
+    for k in ro:
+        err = rel_inf(rg[k], ro[k], floor=1e-3 * scale)
+        worst[k] = err
+        assert err <= tol, (k, err, worst)
+    return worst
+
+
+def check_state(ctx, ora, tol=STATE_TOL):
+    sg, so = ctx.get_state(), ora.get_state()
+    errs = []
+    for name, a, b in zip(("zeta", "qx", "qy", "c"), sg, so):
+        floor = 1.0 if name in ("zeta", "c") else 1e-3
+        e = rel_inf(a, b, floor=floor)
+        errs.append(e)
+        assert e <= tol, (name, e)
+    return errs
+
+
+def randomize(wl, seed=3, amp_q=0.5, amp_z=0.05):
+    rng = np.random.default_rng(seed)
+    sh = wl.zeta.shape
+    wl.zeta = wl.zeta + amp_z * rng.standard_normal(sh)
+    wl.qx = amp_q * rng.standard_normal(sh)
+    wl.qy = amp_q * rng.standard_normal(sh)
+    wl.c = rng.uniform(0, 1, sh)
+    return wl
+
+
+def island(degree=1, amp=0.5, tableau=0, mode=0, n=16):
+    wl = W.closed_basin(degree=degree, n=n)
+    npx = wl.raster.z.shape[0]
+    xc = (np.arange(npx) + 0.5) * wl.raster.dx
+    X, Y = np.meshgrid(xc, xc)
+    wl.raster.z = wl.raster.z - 8.0 * np.exp(-((X - 500) ** 2 + (Y - 500) ** 2) / 150.0 ** 2)
+    Xn, Yn = W.nodal_coordinates(wl.mesh, degree)
+    wl.zeta = amp * np.exp(-((Xn - 300) ** 2 + (Yn - 500) ** 2) / 100.0 ** 2)
+    wl.c = 0.5 + 0.4 * np.cos(Yn / 70.0)
+    wl.tableau = tableau
+    wl.subgrid_mode = mode
+    b = {1: 1 / 6, 2: 1 / 12, 3: 1 / 20}[degree]
+    wl.cfl = 0.9 * (b / (2 - np.sqrt(2)) if tableau == 0 else b)
+    return wl
+
+
+# ----------------------------------------------------------------------------
+# residual
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_residual_closed_basin_random_state(degree, mode):
+    wl = randomize(W.closed_basin(degree=degree))
+    wl.subgrid_mode = mode
+    ctx, ora = pair(wl)
+    check_residual(ctx, ora)
+
+
+def test_residual_closed_basin_paper_config():
+    wl = W.closed_basin()
+    ctx, ora = pair(wl)
+    check_residual(ctx, ora)
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_residual_wet_dry_island_with_friction(degree):
+    wl = island(degree, amp=1.5)
+    wl.manning = np.full(wl.mesh.n, 0.03)
+    wl.qx = 0.3 * np.ones_like(wl.zeta)
+    ctx, ora = pair(wl)
+    check_residual(ctx, ora)
+
+
+def test_residual_tidal_beach_crops_float32_raster():
+    # west-boundary crop (tide) and a shoreline crop (wet-dry, east wall)
+    for window, t in [((0, 100, 8, 8), 3000.0), ((236, 120, 20, 12), 0.0)]:
+        wl = W.tidal_beach(window=window)
+        Xn, Yn = W.nodal_coordinates(wl.mesh, 3)
+        wl.zeta = 0.3 * np.sin(Xn / 400.0) * np.cos(Yn / 300.0)
+        wl.qx = 0.2 * np.cos(Yn / 200.0) * np.ones_like(Xn)
+        ctx, ora = pair(wl)
+        assert wl.raster.z.dtype == np.float32
+        check_residual(ctx, ora, t)
+
+
+# ----------------------------------------------------------------------------
+# time step, degree switch, diagnostics, gauges
+# ----------------------------------------------------------------------------
+def test_cfl_dt_matches():
+    for wl in (randomize(W.closed_basin(degree=2)), island(2)):
+        ctx, ora = pair(wl)
+        dg, do = ctx.cfl_dt(0.0), ora.cfl_dt(0.0)
+        assert abs(dg - do) <= 1e-13 * do
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_degree_switch_flags_bitexact_and_remap(degree):
+    wl = island(degree, amp=0.5)
+    Xn, Yn = W.nodal_coordinates(wl.mesh, degree)
+    wl.qx = 0.1 * np.sin(Xn / 90.0)
+    ctx, ora = pair(wl)
+    fg = ctx.degree_switch()
+    ora.degree_switch()
+    fo = ora.flags()
+    np.testing.assert_array_equal(fg, fo)
+    assert (fo == 0).sum() > 0
+    check_state(ctx, ora, tol=1e-12)
+
+
+def test_diagnostics_and_gauges_match():
+    wl = island(2, amp=0.5)
+    ctx, ora = pair(wl)
+    dg, do = ctx.diagnostics(), ora.diagnostics()
+    for k in ("mass", "tracer_mass"):
+        assert abs(dg[k] - do[k]) <= 1e-13 * do[k], k
+    assert abs(dg["min_h"] - do["min_h"]) <= 1e-12
+    rng = np.random.default_rng(5)
+    xy = rng.uniform(1.0, 999.0, size=(50, 2))
+    zg, zo = ctx.gather_gauges(xy), ora.gauges(xy)
+    assert np.abs(zg - zo).max() <= 1e-13
+
+
+def test_closed_basin_100_ssp33_steps():
+    """the paper-scale closed basin: 100 SSP33 steps at CFL 0.1"""
+    wl = W.closed_basin()
+    ctx, ora = pair(wl)
+    tg = ctx.step(100, -1.0, 0.0)
+    to = ora.step(100, -1.0, 0.0)
+    assert abs(tg - to) <= 1e-10 * to
+    check_state(ctx, ora)
+    dg, do = ctx.diagnostics(), ora.diagnostics()
+    assert dg["newton_max"] == do["newton_max"] == 2
+
+
+@pytest.mark.parametrize("degree,mode", [(1, 0), (2, 0), (1, 1), (3, 0)])
+def test_wet_dry_island_steps(degree, mode):
+    wl = island(degree, amp=0.5, mode=mode, n=12 if degree == 3 else 16)
+    ctx, ora = pair(wl)
+    d0 = ctx.diagnostics()
+    tg = ctx.step(20, -1.0, 0.0)
+    to = ora.step(20, -1.0, 0.0)
+    assert abs(tg - to) <= 1e-10 * to
+    check_state(ctx, ora)
+    d1 = ctx.diagnostics()
+    assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+    assert d1["positivity_violations"] == 0
+    assert d1["r_cells"] == ora.diagnostics()["r_cells"]
+
+
+def test_tidal_beach_crop_rk32_imex_with_friction():
+    wl = W.tidal_beach(window=(0, 120, 12, 8))
+    wl.zeta = 0.2 * np.ones_like(wl.zeta)
+    ctx, ora = pair(wl)
+    tg = ctx.step(20, -1.0, 1000.0)
+    to = ora.step(20, -1.0, 1000.0)
+    assert abs(tg - to) <= 1e-10 * to
+    check_state(ctx, ora)
+
+
+def test_shoreline_crop_rk32_wet_dry():
+    wl = W.tidal_beach(window=(236, 120, 16, 8))
+    Xn, Yn = W.nodal_coordinates(wl.mesh, 3)
+    wl.zeta = 0.5 * np.exp(-((Xn - 18900.0) / 200.0) ** 2)
+    ctx, ora = pair(wl)
+    ctx.step(10, -1.0, 0.0)
+    ora.step(10, -1.0, 0.0)
+    check_state(ctx, ora)
+
+
+@pytest.mark.parametrize("tableau", [2, 3])
+def test_other_tableaux(tableau):
+    wl = randomize(W.closed_basin(degree=2), amp_q=0.05, amp_z=0.01)
+    wl.tableau = tableau
+    wl.cfl = 0.05
+    ctx, ora = pair(wl)
+    ctx.step(5, -1.0, 0.0)
+    ora.step(5, -1.0, 0.0)
+    check_state(ctx, ora)
+
+
+# ----------------------------------------------------------------------------
+# invariants on the GPU path itself
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_gpu_lake_at_rest_well_balanced(degree):
+    wl = W.lake_at_rest_bump(n=8, pix=4, degree=degree, submerged=False)
+    ora = Oracle.from_workload(wl)
+    z = ora.lake_at_rest(0.0)
+    zero = np.zeros_like(z)
+    wl.zeta, wl.qx, wl.qy, wl.c = z, zero, zero.copy(), np.ones_like(z)
+    ctx = swdg.Context.from_workload(wl)
+    r = ctx.residual(0.0)
+    for k, v in r.items():
+        assert np.abs(v).max() < 1e-13 * 9.81, k
+    ctx.step(25, -1.0, 0.0)
+    zg, qxg, qyg, cg = ctx.get_state()
+    assert np.abs(zg - z).max() < 1e-13
+    assert np.abs(qxg).max() < 1e-13 and np.abs(qyg).max() < 1e-13
+    assert np.abs(cg - 1).max() < 1e-13
+
+
+def test_gpu_mass_conservation_closed_basin_wet_dry():
+    wl = island(2, amp=1.0)
+    ctx = swdg.Context.from_workload(wl)
+    d0 = ctx.diagnostics()
+    ctx.step(100, -1.0, 0.0)
+    d1 = ctx.diagnostics()
+    assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+    assert abs(d1["tracer_mass"] - d0["tracer_mass"]) <= 1e-13 * d0["tracer_mass"]
+
+
+def test_full_size_tidal_beach_sampled_residual():
+    """the 256 x 256, r = 3, 16 x 16 px/cell workload at full size: the oracle
+    evaluates a sample of cells one by one"""
+    wl = W.tidal_beach()
+    Xn, Yn = W.nodal_coordinates(wl.mesh, 3)
+    wl.zeta = 0.4 * np.sin(Xn / 700.0) * np.cos(Yn / 500.0)
+    wl.qx = 0.3 * np.cos(Yn / 900.0)
+    ctx = swdg.Context.from_workload(wl)
+    ora = Oracle.from_workload(wl)
+    rg = ctx.residual(2000.0)
+    rng = np.random.default_rng(8)
+    cells = np.concatenate([rng.choice(wl.mesh.n, 200, replace=False),
+                            np.arange(0, wl.mesh.n, 256)[:50],              # west boundary (tide)
+                            np.arange(250, wl.mesh.n, 256)[::5]])           # shoreline
+    ro = ora.residual(2000.0, cells=cells)
+    scale = max(float(np.abs(v).max()) for v in ro.values())
+    for k in ro:
+        assert rel_inf(rg[k][cells], ro[k], floor=1e-3 * scale) <= RES_TOL, k
+
+
+# ----------------------------------------------------------------------------
+# errors are reported, never trapped
+# ----------------------------------------------------------------------------
+def test_errors_are_reported():
+    wl = W.closed_basin()
+    ctx = swdg.Context(**wl.config())
+    with pytest.raises(swdg.SwdgError) as e:
+        ctx.set_state(*wl.state())
+    assert e.value.code == swdg.SWDG_ESTATE
+    bad = wl.mesh.nbr.copy()
+    bad[3, 1, 1] = 5  # a hanging face
+    with pytest.raises(swdg.SwdgError) as e:
+        ctx.upload_mesh(wl.mesh.x0y0, wl.mesh.hxhy, bad)
+    assert e.value.code == swdg.SWDG_EINVAL
+    ctx.upload_mesh(wl.mesh.x0y0, wl.mesh.hxhy, wl.mesh.nbr)
+    with pytest.raises(swdg.SwdgError) as e:  # pixels not aligned with the cells
+        ctx.upload_bathymetry(wl.raster.z, 1.3, 0.0, wl.raster.dx, wl.raster.dy)
+    assert e.value.code == swdg.SWDG_EINVAL
+    ctx.upload_bathymetry(wl.raster.z, 0.0, 0.0, wl.raster.dx, wl.raster.dy)
+    ctx.set_state(*wl.state())
+    # a NaN elevation reads as dry (every wet/dry comparison is false) and is
+    # absorbed; a NaN discharge propagates through the fluxes and is reported
+    qx = wl.qx.copy()
+    qx[7, 0] = np.nan
+    ctx.set_state(wl.zeta, qx, wl.qy, wl.c)
+    with pytest.raises(swdg.SwdgError) as e:
+        ctx.step(1, -1.0, 0.0)
+    assert e.value.code == swdg.SWDG_ENAN
