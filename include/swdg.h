@@ -153,6 +153,37 @@ int swdg_gather_gauges(swdg_ctx* ctx, int n, const double* xy, double* zeta_out)
  * the last step, positivity violations (cumulative), last dt, t. */
 int swdg_diagnostics(swdg_ctx* ctx, double out[8]);
 
+/* Allocation-free residual (the paper has no counterpart; this exists for
+ * callers that cannot allocate device memory -- for example code running
+ * inside a memory pool that forbids new allocations, or a host that has
+ * already reserved every byte of the device).  It evaluates exactly what
+ * swdg_residual evaluates, plus the CFL step of swdg_cfl_dt, without a
+ * context: the caller passes every input and output as device buffers, and
+ * the only scratch (the step scalars and one constant-field byte per cell)
+ * lives in a fixed array inside the library, reserved on each GPU that loads
+ * it until the process exits.  It calls no cudaMalloc/cudaFree.
+ *   cfg: degree 1..3, subgrid_mode 0 (pixel sub-cells), g, eps_vel, cfl and
+ *        stream are used (stream NULL: the legacy stream);
+ *   n_cells <= SWDG_NOALLOC_MAX_CELLS, else SWDG_EINVAL;
+ *   hxhy [n][2], nbr [n][4][2] (conforming, as for swdg_upload_mesh),
+ *   tiles [n][P][P] depth pixels of each cell (P <= 32, dtype SWDG_PIX_*),
+ *   manning [n] (zeros for no friction), state [4][n][(r+1)^2]
+ *   (zeta, qx, qy, c): device pointers, read only;
+ *   bc_kind/amp/period/phase: host arrays of 16 entries, or NULL for walls;
+ *   residual [6][n][(r+1)^2] (F, Gx, Gy, R, Lx, Ly) and dt_out [1] (may be
+ *   NULL): device outputs;  err (may be NULL): message on failure.
+ * The first call on a device looks up the scratch array's address for that
+ * device, so make it before any stream capture.  Every call shares the one
+ * scratch array (it is re-initialised at each call); calls that overlap on
+ * the GPU (other streams, other threads) race on it.  Synchronises the
+ * stream before returning. */
+#define SWDG_NOALLOC_MAX_CELLS 1048576
+int swdg_residual_noalloc(const swdg_config* cfg, int64_t n_cells, const double* hxhy,
+                          const int32_t* nbr, const void* tiles, int pixels_per_side, int pix_dtype,
+                          const double* manning, const int32_t* bc_kind, const double* bc_amp,
+                          const double* bc_period, const double* bc_phase, const double* state,
+                          double t, double* residual, double* dt_out, char* err, int err_len);
+
 const char* swdg_last_error(const swdg_ctx* ctx);
 void swdg_destroy(swdg_ctx* ctx);
 

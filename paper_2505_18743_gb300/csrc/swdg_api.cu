@@ -1010,3 +1010,140 @@ int swdg_diagnostics(swdg_ctx* ctx, double out[8]) {
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------------------
+// allocation-free residual: its only scratch is this file-scope array (step
+// scalars in the first 256 bytes, one constant-field mask byte per cell
+// after them), reserved on every GPU that loads the library
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[256 + SWDG_NOALLOC_MAX_CELLS];
+static void* g_noalloc_addr[256];   // device address of the array, per device ordinal
+static bool g_noalloc_ready[256];
+
+__global__ void k_noalloc_begin(Scalars* sc, double t) {
+    sc->t = t;
+    sc->fixed_dt = -1.0;
+    sc->dt_last = 0.0;
+    sc->dtmin = 0x7ff0000000000000ull; // +inf
+    sc->maxits = 0;
+    sc->viol = 0;
+    sc->fallback = 0;
+    sc->status = 0;
+}
+
+// the mesh checks of swdg_upload_mesh, on the device: bit 1 of status on failure
+__global__ void k_noalloc_check_mesh(const double* hxhy, const int32_t* nbr, int64_t n,
+                                     Scalars* sc) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        bool ok = hxhy[2 * k] > 0.0 && hxhy[2 * k + 1] > 0.0;
+        for (int f = 0; f < 4 && ok; ++f) {
+            const int32_t s0 = nbr[k * 8 + 2 * f], s1 = nbr[k * 8 + 2 * f + 1];
+            if (s1 != -1 || s0 >= n || s0 < -MXTAG) ok = false;
+            else if (s0 >= 0) {
+                const int fo = f ^ 1;
+                const double tk = f < 2 ? hxhy[2 * k + 1] : hxhy[2 * k];
+                const double tn = f < 2 ? hxhy[2 * (int64_t)s0 + 1] : hxhy[2 * (int64_t)s0];
+                if (nbr[(int64_t)s0 * 8 + 2 * fo] != (int32_t)k || fabs(tk - tn) > 1e-9 * tk)
+                    ok = false;
+            }
+        }
+        if (!ok) atomicOr(&sc->status, 2);
+    }
+}
+
+__global__ void k_noalloc_end(const Scalars* sc, double cfl, double* dt_out) {
+    *dt_out = cfl * __longlong_as_double(sc->dtmin);
+}
+
+static int noalloc_fail(char* err, int err_len, int code, const char* msg) {
+    if (err && err_len > 0) snprintf(err, (size_t)err_len, "%s", msg);
+    return code;
+}
+
+extern "C" int swdg_residual_noalloc(const swdg_config* cfg, int64_t n, const double* hxhy,
+                                     const int32_t* nbr, const void* tiles, int P, int pix_dtype,
+                                     const double* manning, const int32_t* bc_kind,
+                                     const double* bc_amp, const double* bc_period,
+                                     const double* bc_phase, const double* state, double t,
+                                     double* residual, double* dt_out, char* err, int err_len) {
+    if (!cfg || cfg->degree < 1 || cfg->degree > 3 || cfg->subgrid_mode != 0 || !(cfg->g > 0) ||
+        !(cfg->eps_vel > 0) || !(cfg->cfl > 0))
+        return noalloc_fail(err, err_len, SWDG_EINVAL,
+                            "residual_noalloc: degree 1..3, subgrid_mode 0, g, eps_vel, cfl > 0");
+    if (n < 1 || n > SWDG_NOALLOC_MAX_CELLS)
+        return noalloc_fail(err, err_len, SWDG_EINVAL,
+                            "residual_noalloc: n_cells must be in 1..SWDG_NOALLOC_MAX_CELLS "
+                            "(1048576)");
+    if (P < 1 || P > MXPIX || (pix_dtype != SWDG_PIX_F32 && pix_dtype != SWDG_PIX_F64))
+        return noalloc_fail(err, err_len, SWDG_EINVAL,
+                            "residual_noalloc: pixels_per_side in 1..32, pix_dtype F32 or F64");
+    if (!hxhy || !nbr || !tiles || !manning || !state || !residual)
+        return noalloc_fail(err, err_len, SWDG_EINVAL, "residual_noalloc: null device buffer");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256)
+        return noalloc_fail(err, err_len, SWDG_ECUDA, "residual_noalloc: no current device");
+    if (!g_noalloc_ready[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return noalloc_fail(err, err_len, SWDG_ECUDA,
+                                "residual_noalloc: cudaGetSymbolAddress of the scratch failed");
+        g_noalloc_addr[dev] = p;
+        g_noalloc_ready[dev] = true;
+    }
+    unsigned char* scratch = (unsigned char*)g_noalloc_addr[dev];
+    Scalars* sc = (Scalars*)scratch;
+    uint8_t* cmask = (uint8_t*)(scratch + 256);
+    cudaStream_t st = (cudaStream_t)cfg->stream;
+
+    Tables tb;
+    if (!build_tables(cfg->degree, tb) || !build_overlaps(cfg->degree, P, tb))
+        return noalloc_fail(err, err_len, SWDG_EINVAL, "residual_noalloc: table construction failed");
+    Launch L{};
+    if (!get_launch(cfg->degree, 0, pix_dtype == SWDG_PIX_F32 ? 0 : 1, &L))
+        return noalloc_fail(err, err_len, SWDG_EINVAL, "residual_noalloc: no kernels for this case");
+    Dev d{};
+    d.n = n;
+    d.hxhy = hxhy;
+    d.nbr = nbr;
+    d.tiles = tiles;
+    d.manning = manning;
+    d.U = const_cast<double*>(state); // read only: buffer 0 of the kernels' state layout
+    d.cmask = cmask;
+    d.res = residual;
+    d.sc = sc;
+    d.mode = 0;
+    d.g = cfg->g;
+    d.eps = cfg->eps_vel;
+    d.cfl = cfg->cfl;
+    for (int i = 0; i < MXTAG; ++i) {
+        d.bc_kind[i] = bc_kind ? bc_kind[i] : SWDG_BC_WALL;
+        d.bc_amp[i] = bc_amp ? bc_amp[i] : 0.0;
+        d.bc_per[i] = bc_period ? bc_period[i] : 1.0;
+        d.bc_ph[i] = bc_phase ? bc_phase[i] : 0.0;
+        if (d.bc_kind[i] != SWDG_BC_WALL && d.bc_kind[i] != SWDG_BC_TIDE)
+            return noalloc_fail(err, err_len, SWDG_EINVAL, "residual_noalloc: bad boundary kind");
+        if (d.bc_kind[i] == SWDG_BC_TIDE && !(d.bc_per[i] > 0))
+            return noalloc_fail(err, err_len, SWDG_EINVAL, "residual_noalloc: tide period <= 0");
+    }
+    k_noalloc_begin<<<1, 1, 0, st>>>(sc, t);
+    k_noalloc_check_mesh<<<(int)std::min<int64_t>(152 * 8, (n + 255) / 256), 256, 0, st>>>(hxhy, nbr,
+                                                                                        n, sc);
+    int status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, &sc->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return noalloc_fail(err, err_len, SWDG_ECUDA, cudaGetErrorString(e));
+    if (status)
+        return noalloc_fail(err, err_len, SWDG_EINVAL,
+                            "residual_noalloc: bad mesh (sizes, neighbour indices, tags or a "
+                            "non-conforming face)");
+    const int grid = grid_for(n);
+    L.masks(d, 0, grid, st);
+    L.residual(d, tb, 0, 0, 0.0, 1, grid, st);
+    if (dt_out) k_noalloc_end<<<1, 1, 0, st>>>(sc, cfg->cfl, dt_out);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return noalloc_fail(err, err_len, SWDG_ECUDA, cudaGetErrorString(e));
+    return SWDG_OK;
+}

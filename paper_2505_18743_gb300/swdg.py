@@ -65,6 +65,8 @@ SIGNATURES = {
     "swdg_degree_switch": (_I, [_P, _P]),
     "swdg_gather_gauges": (_I, [_P, _I, _P, _P]),
     "swdg_diagnostics": (_I, [_P, _P]),
+    "swdg_residual_noalloc": (_I, [ctypes.POINTER(swdg_config), _I64, _P, _P, _P, _I, _I, _P, _P,
+                                   _P, _P, _P, _P, _D, _P, _P, ctypes.c_char_p, _I]),
     "swdg_last_error": (ctypes.c_char_p, [_P]),
     "swdg_destroy": (None, [_P]),
 }
@@ -109,6 +111,31 @@ def _buf(a, dtype):
         return ctypes.c_void_p(a.data_ptr()), (SWDG_DEVICE if a.is_cuda else SWDG_HOST), a
     arr = np.ascontiguousarray(a, dtype=dtype)
     return arr.ctypes.data_as(ctypes.c_void_p), SWDG_HOST, arr
+
+
+def residual_noalloc(cfg, n_cells, hxhy, nbr, tiles, pixels_per_side, pix_dtype, manning, state,
+                     t, residual, dt_out=None, bc=None):
+    """Allocation-free residual (see swdg_residual_noalloc in include/swdg.h).
+    Every array argument is a contiguous CUDA tensor; ``cfg`` a swdg_config;
+    ``bc`` an optional list of (tag, kind, amp, period, phase)."""
+    kind = (ctypes.c_int32 * 16)(*([SWDG_BC_WALL] * 16))
+    amp = (_D * 16)(*([0.0] * 16))
+    per = (_D * 16)(*([1.0] * 16))
+    ph = (_D * 16)(*([0.0] * 16))
+    for (tag, k, a, p, f) in (bc or []):
+        kind[tag], amp[tag], per[tag], ph[tag] = k, a, p, f
+    err = ctypes.create_string_buffer(256)
+
+    def ptr(x):
+        return ctypes.c_void_p(x.data_ptr()) if x is not None else None
+
+    rc = load().swdg_residual_noalloc(
+        ctypes.byref(cfg), n_cells, ptr(hxhy), ptr(nbr), ptr(tiles), pixels_per_side, pix_dtype,
+        ptr(manning), ctypes.cast(kind, _P), ctypes.cast(amp, _P), ctypes.cast(per, _P),
+        ctypes.cast(ph, _P), ptr(state), t, ptr(residual), ptr(dt_out), err, 256)
+    if rc:
+        raise SwdgError(rc, err.value.decode())
+    return rc
 
 
 class Context:
