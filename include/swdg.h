@@ -75,8 +75,10 @@ typedef struct {
     double eps0;       /* dry-start lift of Eq. initial_guess */
     double cfl;        /* dt = cfl * min J_K / (lambda l_Gamma), Eq. deltat_fe */
     int newton_max;    /* iteration cap of the per-cell Newton solve (>= 1) */
-    double newton_tol; /* stop when sum|dzeta| <= tol * sum(1 + |zeta| + max|z_b|);
-                          0 runs exactly newton_max iterations */
+    double newton_tol; /* stop when sum|dzeta| <= tol * sum(1 + |zeta| + max|z_b|), or
+                          when every pixel of the cell is wet at two successive
+                          iterates (H is then affine between them and the last
+                          iterate is the solution); 0 disables the first test */
     void* stream;      /* cudaStream_t to run on, or NULL for the legacy stream */
 } swdg_config;
 

@@ -43,7 +43,7 @@ struct swdg_ctx {
     // device allocations
     double *x0y0 = nullptr, *hxhy = nullptr, *manning = nullptr, *U = nullptr, *res = nullptr,
            *llin = nullptr, *HN = nullptr, *CN = nullptr, *HNbar = nullptr, *CNbar = nullptr,
-           *zpts = nullptr, *zmax = nullptr, *zabs = nullptr, *diag = nullptr;
+           *zpts = nullptr, *zmax = nullptr, *zmin = nullptr, *zabs = nullptr, *diag = nullptr;
     int32_t* nbr = nullptr;
     uint8_t *cmask = nullptr, *flag = nullptr;
     void* tiles = nullptr;
@@ -272,22 +272,58 @@ __global__ void k_retile(const Pix* __restrict__ ras, int64_t nx, const int32_t*
 
 template <typename Pix>
 __global__ void k_tile_bounds(const Pix* __restrict__ tiles, int P, int64_t n, double* zmax,
-                              double* zabs) {
+                              double* zmin, double* zabs) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int64_t k = warp; k < n; k += nw) {
-        double m = -INFINITY, a = 0.0;
+        double m = -INFINITY, mn = INFINITY, a = 0.0;
         for (int i = lane; i < P * P; i += 32) {
             const double z = (double)tiles[k * P * P + i];
             m = fmax(m, z);
+            mn = fmin(mn, z);
             a = fmax(a, fabs(z));
         }
         m = warp_max(m);
+        mn = warp_min(mn);
         a = warp_max(a);
         if (lane == 0) {
             zmax[k] = m;
+            zmin[k] = mn;
             zabs[k] = a;
         }
+    }
+}
+
+// mean depth sum_k w_k z_k of every sub-cell of the three point sets (mode S)
+template <typename Pix>
+__global__ void k_subcell_means(const Pix* __restrict__ tiles, const __grid_constant__ Tables tb,
+                                int nv, int nm, int ng, double* zpts, int64_t n) {
+    const int nzp = nv * nv + nm * nm + ng * ng, P = tb.P;
+    const int64_t total = n * nzp;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / nzp;
+        int p = (int)(i % nzp), set = 0, q = nv;
+        if (p >= nv * nv) {
+            p -= nv * nv;
+            set = 1;
+            q = nm;
+            if (p >= nm * nm) {
+                p -= nm * nm;
+                set = 2;
+                q = ng;
+            }
+        }
+        const int ia = p % q, ib = p / q;
+        const Pix* tile = tiles + k * P * P;
+        double s = 0.0;
+        for (int j = 0; j < tb.cnt[set][ib]; ++j) {
+            double r = 0.0;
+            for (int a = 0; a < tb.cnt[set][ia]; ++a)
+                r += tb.frac[set][ia][a] * (double)tile[(size_t)(tb.lo[set][ib] + j) * P + tb.lo[set][ia] + a];
+            s += tb.frac[set][ib][j] * r;
+        }
+        zpts[i] = s;
     }
 }
 
@@ -311,14 +347,14 @@ template <typename Pix>
 __global__ void k_point_samples(const Pix* __restrict__ ras, int64_t nx, int64_t ny, double xo,
                                 double yo, double dx, double dy, const double* x0y0,
                                 const double* hxhy, const __grid_constant__ Tables tb, int nv,
-                                int nm, int ng, double* zpts, double* zmax, double* zabs,
-                                int64_t n) {
+                                int nm, int ng, double* zpts, double* zmax, double* zmin,
+                                double* zabs, int64_t n) {
     const int nzp = nv * nv + nm * nm + ng * ng;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const double x0 = x0y0[2 * k], y0 = x0y0[2 * k + 1], hx = hxhy[2 * k], hy = hxhy[2 * k + 1];
         int off = 0;
-        double m = -INFINITY, a = 0.0;
+        double m = -INFINITY, mn = INFINITY, a = 0.0;
         for (int s = 0; s < 3; ++s) {
             const int q = s == 0 ? nv : (s == 1 ? nm : ng);
             for (int p = 0; p < q * q; ++p) {
@@ -327,12 +363,14 @@ __global__ void k_point_samples(const Pix* __restrict__ ras, int64_t nx, int64_t
                 zpts[k * nzp + off + p] = z;
                 if (s == 1) {
                     m = fmax(m, z);
+                    mn = fmin(mn, z);
                     a = fmax(a, fabs(z));
                 }
             }
             off += q * q;
         }
         zmax[k] = m;
+        zmin[k] = mn;
         zabs[k] = a;
     }
 }
@@ -503,9 +541,9 @@ static void free_mesh(swdg_ctx* c) {
     c->cmask = c->flag = nullptr;
 }
 static void free_bathy(swdg_ctx* c) {
-    cudaFree(c->tiles); cudaFree(c->zpts); cudaFree(c->zmax); cudaFree(c->zabs);
+    cudaFree(c->tiles); cudaFree(c->zpts); cudaFree(c->zmax); cudaFree(c->zmin); cudaFree(c->zabs);
     c->tiles = nullptr;
-    c->zpts = c->zmax = c->zabs = nullptr;
+    c->zpts = c->zmax = c->zmin = c->zabs = nullptr;
 }
 
 void swdg_destroy(swdg_ctx* c) {
@@ -652,7 +690,11 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
     CK(cudaMalloc(&ras, nx * ny * es));
     CK(cudaMemcpyAsync(ras, raster, nx * ny * es, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMalloc(&ctx->zmax, n * sizeof(double)));
+    CK(cudaMalloc(&ctx->zmin, n * sizeof(double)));
     CK(cudaMalloc(&ctx->zabs, n * sizeof(double)));
+    const int R_ = ctx->R, nv_ = (3 * R_) / 2 + 1, nm_ = R_ + 2, ng_ = R_ + 1;
+    const int nzp_ = nv_ * nv_ + nm_ * nm_ + ng_ * ng_;
+    CK(cudaMalloc(&ctx->zpts, (size_t)n * nzp_ * sizeof(double)));
     const int grid = (int)std::min<int64_t>(152 * 32, (n * 32 + 255) / 256 + 1);
     if (ctx->mode == 0) {
         int32_t *c0 = nullptr, *r0 = nullptr;
@@ -661,36 +703,38 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
         CK(cudaMemcpyAsync(c0, col0.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
         CK(cudaMemcpyAsync(r0, row0.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
         CK(cudaMalloc(&ctx->tiles, (size_t)n * P * P * es));
+        if (!build_overlaps(ctx->R, P, ctx->tb))
+            return fail(ctx, SWDG_EINVAL, "upload_bathymetry: bad pixel count");
         if (dtype == SWDG_PIX_F32) {
             k_retile<float><<<152 * 16, 256, 0, ctx->st>>>((const float*)ras, nx, c0, r0, P,
                                                           (float*)ctx->tiles, n);
             k_tile_bounds<float><<<grid, 256, 0, ctx->st>>>((const float*)ctx->tiles, P, n, ctx->zmax,
-                                                           ctx->zabs);
+                                                           ctx->zmin, ctx->zabs);
+            k_subcell_means<float><<<152 * 16, 256, 0, ctx->st>>>((const float*)ctx->tiles, ctx->tb,
+                                                                 nv_, nm_, ng_, ctx->zpts, n);
         } else {
             k_retile<double><<<152 * 16, 256, 0, ctx->st>>>((const double*)ras, nx, c0, r0, P,
                                                            (double*)ctx->tiles, n);
             k_tile_bounds<double><<<grid, 256, 0, ctx->st>>>((const double*)ctx->tiles, P, n,
-                                                            ctx->zmax, ctx->zabs);
+                                                            ctx->zmax, ctx->zmin, ctx->zabs);
+            k_subcell_means<double><<<152 * 16, 256, 0, ctx->st>>>(
+                (const double*)ctx->tiles, ctx->tb, nv_, nm_, ng_, ctx->zpts, n);
         }
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->st));
         cudaFree(c0);
         cudaFree(r0);
-        if (!build_overlaps(ctx->R, P, ctx->tb))
-            return fail(ctx, SWDG_EINVAL, "upload_bathymetry: bad pixel count");
     } else {
-        const int R = ctx->R, nv = (3 * R) / 2 + 1, nm = R + 2, ng = R + 1;
-        const int nzp = nv * nv + nm * nm + ng * ng;
-        CK(cudaMalloc(&ctx->zpts, (size_t)n * nzp * sizeof(double)));
+        const int nv = nv_, nm = nm_, ng = ng_;
         const int g2 = (int)std::min<int64_t>(152 * 16, (n + 127) / 128);
         if (dtype == SWDG_PIX_F32)
             k_point_samples<float><<<g2, 128, 0, ctx->st>>>(
                 (const float*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0, ctx->hxhy, ctx->tb, nv, nm, ng,
-                ctx->zpts, ctx->zmax, ctx->zabs, n);
+                ctx->zpts, ctx->zmax, ctx->zmin, ctx->zabs, n);
         else
             k_point_samples<double><<<g2, 128, 0, ctx->st>>>(
                 (const double*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0, ctx->hxhy, ctx->tb, nv, nm, ng,
-                ctx->zpts, ctx->zmax, ctx->zabs, n);
+                ctx->zpts, ctx->zmax, ctx->zmin, ctx->zabs, n);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->st));
     }
@@ -701,6 +745,7 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
     ctx->d.tiles = ctx->tiles;
     ctx->d.zpts = ctx->zpts;
     ctx->d.zmax = ctx->zmax;
+    ctx->d.zmin = ctx->zmin;
     ctx->d.zabs = ctx->zabs;
     ctx->has_bathy = true;
     return SWDG_OK;

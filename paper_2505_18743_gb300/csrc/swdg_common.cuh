@@ -7,7 +7,8 @@
 //           (such a field is evaluated as that constant, exactly)
 //   resid   R[stage][6][cell][(r+1)^2] float64, 6 = F, Gx, Gy, R, Lx, Ly
 //   tiles   [cell][P][P] float32|float64 bathymetry depth (mode S)
-//   zpts    [cell][NV^2 + NM^2 + NG^2] float64 point samples (mode P)
+//   zpts    [cell][NV^2 + NM^2 + NG^2] float64: point samples (mode P) or
+//           sub-cell mean depths sum_k w_k z_k (mode S)
 // Small per-degree tables (1D interpolation matrices, quadrature weights,
 // pixel-overlap fractions) travel as a __grid_constant__ kernel parameter.
 #pragma once
@@ -69,6 +70,7 @@ struct Dev {
     const void* tiles;
     const double* zpts;
     const double* zmax; // dry-start level of Eq. initial_guess (max z_b of the cell)
+    const double* zmin; // min z_b of the cell: every pixel is wet when eta > -zmin
     const double* zabs; // max |z_b| of the cell (Newton tolerance scale)
     const double* manning;
     double* U;
@@ -124,15 +126,19 @@ __device__ __forceinline__ double get_dt(const Dev& d) {
 // desingularised velocity factor u = f q, Eq. velocity
 __device__ __forceinline__ double vel_factor(double h, double eps) {
     if (h <= 0.0) return 0.0;
+    if (h >= eps) return 1.0 / h; // max(h^4, eps^4) = h^4: sqrt(2) h / sqrt(2 h^4) = 1/h
     double h4 = (h * h) * (h * h), e4 = (eps * eps) * (eps * eps);
-    return sqrt(2.0) * h / sqrt(fmax(h4, e4) + h4);
+    return sqrt(2.0) * h / sqrt(e4 + h4);
 }
 // Manning coefficient gamma = g n^2 |q| / h_des^(7/3), Eqs. manning, discharge_rhs_implicit
 __device__ __forceinline__ double gamma_manning(double n, double h, double qx, double qy, double g,
                                                 double eps) {
     if (n == 0.0 || h <= 0.0) return 0.0;
-    double h4 = (h * h) * (h * h), e4 = (eps * eps) * (eps * eps);
-    double hdes = sqrt(fmax(h4, e4) + h4) / (sqrt(2.0) * h);
+    double hdes = h; // h_des = h when h >= eps
+    if (h < eps) {
+        double h4 = (h * h) * (h * h), e4 = (eps * eps) * (eps * eps);
+        hdes = sqrt(e4 + h4) / (sqrt(2.0) * h);
+    }
     return g * n * n * sqrt(qx * qx + qy * qy) / (hdes * hdes * cbrt(hdes));
 }
 
@@ -140,11 +146,13 @@ __device__ __forceinline__ double gamma_manning(double n, double h, double qx, d
 // (mode S): V = sum_k w_k max(eta + z_k, 0), A = sum_k w_k [eta + z_k > 0]
 template <typename Pix>
 __device__ __forceinline__ void subgrid_S(const Pix* __restrict__ tile, const Tables& tb, int set,
-                                          int ia, int ib, double eta, double& V, double& A) {
+                                          int ia, int ib, double eta, double& V, double& A,
+                                          bool& full) {
     const int P = tb.P;
     const int lox = tb.lo[set][ia], cx = tb.cnt[set][ia];
     const int loy = tb.lo[set][ib], cy = tb.cnt[set][ib];
     double v = 0.0, a = 0.0;
+    bool f = true;
     for (int j = 0; j < cy; ++j) {
         const Pix* row = tile + (size_t)(loy + j) * P + lox;
         double vr = 0.0, ar = 0.0;
@@ -154,6 +162,8 @@ __device__ __forceinline__ void subgrid_S(const Pix* __restrict__ tile, const Ta
                 double fx = tb.frac[set][ia][i];
                 vr += fx * dd;
                 ar += fx;
+            } else {
+                f = false;
             }
         }
         double fy = tb.frac[set][ib][j];
@@ -162,6 +172,7 @@ __device__ __forceinline__ void subgrid_S(const Pix* __restrict__ tile, const Ta
     }
     V = v;
     A = a;
+    full = f;
 }
 
 __device__ __forceinline__ void subgrid_P(double z, double eta, double& V, double& A) {

@@ -89,34 +89,49 @@ __device__ __forceinline__ void kron_apply(const double (*M)[LD], const double* 
 template <int R, typename Pix, int MODE>
 struct Site {
     using S = Sz<R>;
-    // V, A and whether some pixel of the sub-cell is dry
+    static __device__ __forceinline__ int offset(int set) {
+        return set == SET_VOL ? 0 : (set == SET_MASS ? S::NVP : S::NVP + S::NMP);
+    }
+    static __device__ __forceinline__ int count(int set) {
+        return set == SET_VOL ? S::NV : (set == SET_MASS ? S::NM : S::NG);
+    }
+    // V, A of sub-cell (ia, ib) of point set `set` of cell k at elevation eta,
+    // and whether every pixel of it is wet.  Mode S: a sub-cell whose cell is
+    // entirely wet (eta > -min z_b) has V = eta + its mean depth and A = 1; an
+    // entirely dry one (eta <= -max z_b) has V = A = 0; otherwise the pixels
+    // are summed.
     static __device__ __forceinline__ void VA(const Dev& d, const Tables& tb, int64_t k, int set,
-                                              int ia, int ib, double eta, double& V, double& A) {
+                                              int ia, int ib, double eta, double& V, double& A,
+                                              bool& full) {
         if (MODE == 0) {
+            // the per-cell bounds and sub-cell means are optional (a caller of
+            // the allocation-free residual has none): without them every
+            // sub-cell sums its pixels
+            if (d.zmin != nullptr) {
+                if (eta > -d.zmin[k]) {
+                    V = eta + d.zpts[(size_t)k * S::NZP + offset(set) + ia + count(set) * ib];
+                    A = 1.0;
+                    full = true;
+                    return;
+                }
+                if (!(eta > -d.zmax[k])) {
+                    V = 0.0;
+                    A = 0.0;
+                    full = false;
+                    return;
+                }
+            }
             const Pix* tile = (const Pix*)d.tiles + (size_t)k * tb.P * tb.P;
-            subgrid_S<Pix>(tile, tb, set, ia, ib, eta, V, A);
+            subgrid_S<Pix>(tile, tb, set, ia, ib, eta, V, A, full);
         } else {
-            int off = set == SET_VOL ? 0 : (set == SET_MASS ? S::NVP : S::NVP + S::NMP);
-            int n = set == SET_VOL ? S::NV : (set == SET_MASS ? S::NM : S::NG);
-            subgrid_P(d.zpts[(size_t)k * S::NZP + off + ia + n * ib], eta, V, A);
+            subgrid_P(d.zpts[(size_t)k * S::NZP + offset(set) + ia + count(set) * ib], eta, V, A);
+            full = A > 0.0;
         }
     }
-    // true when every pixel of the sub-cell is wet at eta (A == 1 exactly in law)
-    static __device__ __forceinline__ bool full(const Dev& d, const Tables& tb, int64_t k, int set,
-                                                int ia, int ib, double eta) {
-        if (MODE == 0) {
-            const Pix* tile = (const Pix*)d.tiles + (size_t)k * tb.P * tb.P;
-            const int lox = tb.lo[set][ia], cx = tb.cnt[set][ia];
-            const int loy = tb.lo[set][ib], cy = tb.cnt[set][ib];
-            for (int j = 0; j < cy; ++j)
-                for (int i = 0; i < cx; ++i)
-                    if (!(eta + (double)tile[(size_t)(loy + j) * tb.P + lox + i] > 0.0)) return false;
-            return true;
-        } else {
-            int off = set == SET_VOL ? 0 : (set == SET_MASS ? S::NVP : S::NVP + S::NMP);
-            int n = set == SET_VOL ? S::NV : (set == SET_MASS ? S::NM : S::NG);
-            return eta + d.zpts[(size_t)k * S::NZP + off + ia + n * ib] > 0.0;
-        }
+    static __device__ __forceinline__ void VA(const Dev& d, const Tables& tb, int64_t k, int set,
+                                              int ia, int ib, double eta, double& V, double& A) {
+        bool full;
+        VA(d, tb, k, set, ia, ib, eta, V, A, full);
     }
 };
 
@@ -596,21 +611,27 @@ template <int R>
 constexpr int stage_smem() {
     using S = Sz<R>;
     return 4 * S::ND + 5 * S::ND + 3 * S::NMP + 2 * S::NM * S::NM + S::ND1 * S::ND1 * S::NM +
-           S::ND * S::ND + 6 * S::NGP + 4 * S::ND;
+           S::ND * S::ND + 6 * S::NGP + 4 * S::ND + S::ND;
 }
 
 // Cholesky of the SPD matrix M (ND x ND, row-major, lower part used) on a
-// warp, then solve M x = b in place; returns false on a non-positive pivot
+// warp, then M x = b in place by column-oriented forward and back
+// substitution (one reciprocal per column, the updates spread over lanes);
+// returns false on a non-positive pivot
 template <int ND>
-__device__ bool chol_solve(double* M, double* b, int lane) {
+__device__ bool chol_solve(double* M, double* b, double* inv, int lane) {
     for (int j = 0; j < ND; ++j) {
         __syncwarp();
         const double djj = M[j * ND + j];
         if (!(djj > 0.0)) return false;
         const double ljj = sqrt(djj);
+        const double r = 1.0 / ljj;
         __syncwarp();
-        for (int i = j + 1 + lane; i < ND; i += 32) M[i * ND + j] /= ljj;
-        if (lane == 0) M[j * ND + j] = ljj;
+        for (int i = j + 1 + lane; i < ND; i += 32) M[i * ND + j] *= r;
+        if (lane == 0) {
+            M[j * ND + j] = ljj;
+            inv[j] = r;
+        }
         __syncwarp();
         const int m = ND - j - 1;
         for (int idx = lane; idx < m * m; idx += 32) {
@@ -619,19 +640,20 @@ __device__ bool chol_solve(double* M, double* b, int lane) {
         }
     }
     __syncwarp();
-    if (lane == 0) {
-        for (int i = 0; i < ND; ++i) {
-            double s = b[i];
-            for (int l = 0; l < i; ++l) s -= M[i * ND + l] * b[l];
-            b[i] = s / M[i * ND + i];
-        }
-        for (int i = ND - 1; i >= 0; --i) {
-            double s = b[i];
-            for (int l = i + 1; l < ND; ++l) s -= M[l * ND + i] * b[l];
-            b[i] = s / M[i * ND + i];
-        }
+    for (int j = 0; j < ND; ++j) { // L y = b
+        const double yj = b[j] * inv[j];
+        __syncwarp();
+        for (int i = j + 1 + lane; i < ND; i += 32) b[i] -= M[i * ND + j] * yj;
+        if (lane == 0) b[j] = yj;
+        __syncwarp();
     }
-    __syncwarp();
+    for (int j = ND - 1; j >= 0; --j) { // L^T x = y
+        const double xj = b[j] * inv[j];
+        __syncwarp();
+        for (int i = lane; i < j; i += 32) b[i] -= M[j * ND + i] * xj;
+        if (lane == 0) b[j] = xj;
+        __syncwarp();
+    }
     return true;
 }
 
@@ -681,6 +703,7 @@ __global__ void __launch_bounds__(TPB)
     double* M = Y + ND1 * ND1 * NM;             // [ND ND]
     double* pg = M + ND * ND;                   // [6][NGP]
     double* o = pg + 6 * NGP;                   // [4][ND]
+    double* pinv = o + 4 * ND;                  // [ND] reciprocal Cholesky pivots
     const int64_t n = d.n;
     const double dt = get_dt(d);
     const double g = d.g, eps = d.eps;
@@ -721,34 +744,45 @@ __global__ void __launch_bounds__(TPB)
         if (!scalar) {
             for (int i = lane; i < ND; i += 32) z[i] = su[i];
             bool zc = (cm0 & 1u) != 0;
+            bool prev_full = false;
             __syncwarp();
-            for (int kk = 0; kk < d.newton_max; ++kk) {
+            // each pass evaluates V, A at the current iterate; the last pass is
+            // the evaluation at the result (for the tracer matrix and the
+            // completely-dry test)
+            for (int kk = 0;; ++kk) {
                 tens_interp<ND1, NM>(tb.Bm, z, tmp, pe, lane);
                 int ndry = 0, npart = 0;
                 for (int p = lane; p < NMP; p += 32) {
                     if (zc) pe[p] = z[0];
                     double V, A;
-                    ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pe[p], V, A);
+                    bool full;
+                    ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pe[p], V, A, full);
                     pV[p] = J * tb.wm[p % NM] * tb.wm[p / NM] * V;
                     pA[p] = J * tb.wm[p % NM] * tb.wm[p / NM] * A;
                     if (A == 0.0) ndry++;
-                    else if (!ST::full(d, tb, k, SET_MASS, p % NM, p / NM, pe[p])) npart++;
+                    else if (!full) npart++;
                 }
                 ndry = __reduce_add_sync(0xffffffffu, ndry);
                 npart = __reduce_add_sync(0xffffffffu, npart);
                 if (ndry) { scalar = true; break; }
+                // every pixel wet at the previous and at this iterate: H is affine
+                // on the segment between them and M(previous) is its exact
+                // Jacobian, so this iterate solves H = T (the fully wet case of
+                // Sec. 3.4); no verification step is needed
+                if (kk > 0 && prev_full && npart == 0) break;
+                if (kk == d.newton_max) break;
                 __syncwarp();
                 tens_test<ND1, NM>(tb.Bm, pV, tmp, o, lane); // H_i(zeta_k)
                 for (int i = lane; i < ND; i += 32) o[i] -= T[i];
                 __syncwarp();
                 if (npart == 0) {
-                    // every pixel wet: M is the constant mass matrix, inverted by its tensor factors
+                    // M is the constant mass matrix, inverted by its tensor factors
                     kron_apply<ND1, false, MXN>(tb.M1inv, o, tmp, o + ND, 1.0 / J, lane);
                 } else {
                     assemble_mass<ND1, NM>(tb, pA, Y, M, lane);
                     for (int i = lane; i < ND; i += 32) o[ND + i] = o[i];
                     __syncwarp();
-                    if (!chol_solve<ND>(M, o + ND, lane)) { scalar = true; break; }
+                    if (!chol_solve<ND>(M, o + ND, pinv, lane)) { scalar = true; break; }
                 }
                 double inc = 0.0, scale = 0.0;
                 for (int i = lane; i < ND; i += 32) {
@@ -759,26 +793,14 @@ __global__ void __launch_bounds__(TPB)
                 inc = warp_sum(inc);
                 scale = warp_sum(scale);
                 its++;
+                prev_full = (npart == 0);
                 __syncwarp();
                 {
                     bool eq = true;
                     for (int i = lane; i < ND; i += 32) eq = eq && (z[i] == z[0]);
                     zc = __all_sync(0xffffffffu, eq);
                 }
-                if (inc <= d.newton_tol * scale) break;
-            }
-            if (!scalar) {
-                tens_interp<ND1, NM>(tb.Bm, z, tmp, pe, lane);
-                int ndry = 0;
-                for (int p = lane; p < NMP; p += 32) {
-                    if (zc) pe[p] = z[0];
-                    double V, A;
-                    ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pe[p], V, A);
-                    pV[p] = J * tb.wm[p % NM] * tb.wm[p / NM] * V;
-                    if (A == 0.0) ndry++;
-                }
-                ndry = __reduce_add_sync(0xffffffffu, ndry);
-                if (ndry) scalar = true;
+                if (inc <= d.newton_tol * scale) prev_full = false, kk = d.newton_max - 1;
             }
             if (scalar) {
                 fb++;
@@ -909,7 +931,7 @@ __global__ void __launch_bounds__(TPB)
                 o[3 * ND + i] = rc[i];
             }
             __syncwarp();
-            chol_solve<ND>(M, o + 3 * ND, lane);
+            chol_solve<ND>(M, o + 3 * ND, pinv, lane);
         }
         __syncwarp();
         // write v^(l) and its constant-field mask

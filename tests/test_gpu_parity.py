@@ -167,7 +167,9 @@ def test_closed_basin_100_ssp33_steps():
     assert abs(tg - to) <= 1e-10 * to
     check_state(ctx, ora)
     dg, do = ctx.diagnostics(), ora.diagnostics()
-    assert dg["newton_max"] == do["newton_max"] == 2
+    # fully wet: the oracle verifies the first iterate with a second Newton step
+    # (Sec. 3.4); the CUDA path certifies it instead (affine H, exact Jacobian)
+    assert do["newton_max"] == 2 and dg["newton_max"] == 1
 
 
 @pytest.mark.parametrize("degree,mode", [(1, 0), (2, 0), (1, 1), (3, 0)])
