@@ -287,3 +287,185 @@ def flat_periodic(nx: int, ny: int, Lx: float, Ly: float, depth: float, degree: 
     dy = Ly / (ny * pix)
     z = np.full((ny * pix, nx * pix), depth)
     return mesh, Raster(z, 0.0, 0.0, dx, dy)
+
+
+# ----------------------------------------------------------------------------
+# 2:1-balanced quadtree forests (non-conforming meshes with hanging faces)
+# ----------------------------------------------------------------------------
+def forest_mesh(nx0: int, ny0: int, Lx: float, Ly: float, levels: int, refine,
+                x0: float = 0.0, y0: float = 0.0, tags=(0, 0, 0, 0),
+                periodic=(False, False)) -> tuple[Mesh, np.ndarray]:
+    """Leaves of a forest of nx0 x ny0 quadtrees over [x0, x0+Lx] x [y0, y0+Ly],
+    refined while ``refine(level, xc, yc, hx, hy)`` (vectorised over cells)
+    says so, up to ``levels`` levels, then 2:1 balanced across faces.
+    Returns the mesh (neighbour slots as in the module docstring) and the level
+    of each leaf.  Leaves are sorted along a Morton curve."""
+    leaves = {(0, i, j) for i in range(nx0) for j in range(ny0)}
+
+    def geom(l, i, j):
+        hx, hy = Lx / (nx0 << l), Ly / (ny0 << l)
+        return x0 + i * hx, y0 + j * hy, hx, hy
+
+    for lev in range(levels - 1):
+        cur = [c for c in leaves if c[0] == lev]
+        if not cur:
+            break
+        arr = np.array(cur)
+        hx, hy = Lx / (nx0 << lev), Ly / (ny0 << lev)
+        xc = x0 + (arr[:, 1] + 0.5) * hx
+        yc = y0 + (arr[:, 2] + 0.5) * hy
+        mask = np.asarray(refine(lev, xc, yc, hx, hy), dtype=bool)
+        for (l, i, j), m in zip(cur, mask):
+            if m:
+                leaves.remove((l, i, j))
+                leaves.update({(l + 1, 2 * i + a, 2 * j + b) for a in (0, 1) for b in (0, 1)})
+
+    def covering(l, i, j):
+        """the leaf covering cell (l, i, j) if it is this cell or an ancestor"""
+        while l >= 0:
+            if (l, i, j) in leaves:
+                return (l, i, j)
+            l, i, j = l - 1, i // 2, j // 2
+        return None
+
+    # 2:1 balance: a leaf whose face neighbour region is covered by a leaf two
+    # or more levels coarser forces that coarse leaf to split
+    changed = True
+    while changed:
+        changed = False
+        for (l, i, j) in list(leaves):
+            if (l, i, j) not in leaves:
+                continue
+            nxl, nyl = nx0 << l, ny0 << l
+            for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                ii, jj = i + di, j + dj
+                if periodic[0]:
+                    ii %= nxl
+                if periodic[1]:
+                    jj %= nyl
+                if not (0 <= ii < nxl and 0 <= jj < nyl):
+                    continue
+                c = covering(l, ii, jj)
+                if c is not None and c[0] < l - 1:
+                    leaves.remove(c)
+                    cl, ci, cj = c
+                    leaves.update({(cl + 1, 2 * ci + a, 2 * cj + b) for a in (0, 1) for b in (0, 1)})
+                    changed = True
+
+    # Morton order on the finest grid of the leaf's lower-left corner
+    L = max(c[0] for c in leaves)
+
+    def morton(c):
+        l, i, j = c
+        x, y = i << (L - l), j << (L - l)
+        key = 0
+        for bit in range(24):
+            key |= ((x >> bit) & 1) << (2 * bit) | ((y >> bit) & 1) << (2 * bit + 1)
+        return key
+
+    order = sorted(leaves, key=morton)
+    index = {c: k for k, c in enumerate(order)}
+    n = len(order)
+    x0y0 = np.zeros((n, 2))
+    hxhy = np.zeros((n, 2))
+    nbr = np.full((n, 4, 2), -1, dtype=np.int32)
+    level = np.zeros(n, dtype=np.int32)
+    for k, (l, i, j) in enumerate(order):
+        gx, gy, hx, hy = geom(l, i, j)
+        x0y0[k] = (gx, gy)
+        hxhy[k] = (hx, hy)
+        level[k] = l
+        nxl, nyl = nx0 << l, ny0 << l
+        for f, (di, dj) in enumerate(((-1, 0), (1, 0), (0, -1), (0, 1))):
+            ii, jj = i + di, j + dj
+            if periodic[0]:
+                ii %= nxl
+            if periodic[1]:
+                jj %= nyl
+            if not (0 <= ii < nxl and 0 <= jj < nyl):
+                nbr[k, f, 0] = -1 - tags[f]
+                continue
+            if (l, ii, jj) in leaves:
+                nbr[k, f, 0] = index[(l, ii, jj)]
+            elif l > 0 and (l - 1, ii // 2, jj // 2) in leaves:
+                nbr[k, f, 0] = index[(l - 1, ii // 2, jj // 2)]
+            else:
+                # two finer leaves along the face, by increasing tangential coordinate
+                if di != 0:
+                    a = 0 if di > 0 else 1
+                    kids = [(l + 1, 2 * ii + a, 2 * jj + b) for b in (0, 1)]
+                else:
+                    b = 0 if dj > 0 else 1
+                    kids = [(l + 1, 2 * ii + a, 2 * jj + b) for a in (0, 1)]
+                nbr[k, f, 0] = index[kids[0]]  # ii, jj are already wrapped
+                nbr[k, f, 1] = index[kids[1]]
+    return Mesh(x0y0, hxhy, nbr), level
+
+
+def fractal_curve(rng, n: int, amp: float, rough: float = 0.55) -> np.ndarray:
+    """1D midpoint-displacement curve with n + 1 samples (n a power of two)"""
+    y = np.zeros(n + 1)
+    step, a = n, amp
+    while step > 1:
+        half = step // 2
+        y[half::step] = 0.5 * (y[:-1:step] + y[step::step]) + rng.normal(0.0, a, size=len(y[half::step]))
+        step, a = half, a * rough
+    return y
+
+
+# ----------------------------------------------------------------------------
+# configuration 3: degree 2 on a 3-level 2:1 forest over a 50 km x 30 km lagoon
+# ----------------------------------------------------------------------------
+def lagoon(seed: int = DEFAULT_SEED, nx0: int = 256, ny0: int = 128, levels: int = 3,
+           degree: int = 2, Lx: float = 50000.0, Ly: float = 30000.0, pix0: int = 32,
+           band=(8000.0, 4200.0), window=None) -> Workload:
+    """Barrier-island lagoon: open sea to the south (tide on the south
+    boundary), a barrier along a seeded fractal coastline cut by two 15 m
+    inlets, a 0.5-3 m lagoon with tidal flats at datum +-0.3 m to the north.
+    Cells are refined toward the coastline (levels 1..3: 32, 16, 8 pixels per
+    side) and 2:1 balanced.  ``window=(x0, y0, Lx, Ly, nx0, ny0)`` builds the
+    same construction over a sub-rectangle (a small case for parity tests)."""
+    rng = np.random.default_rng(seed)
+    npx, npy = nx0 * pix0, ny0 * pix0
+    dx, dy = Lx / npx, Ly / npy
+    coast = 12000.0 + fractal_curve(rng, 1 << 12, 1500.0)
+    xs = np.linspace(0.0, Lx, len(coast))
+    xc = (np.arange(npx) + 0.5) * dx
+    yc = (np.arange(npy) + 0.5) * dy
+    cy = np.interp(xc, xs, coast)
+    X, Y = np.meshgrid(xc, yc)
+    d = Y - cy[None, :]                      # signed distance north of the coast (in y)
+    sea = 3.0 + 12.0 * np.clip(-d / 8000.0, 0.0, 1.0)
+    lag = 0.5 + 2.5 * (0.5 + 0.5 * np.sin(X / 2300.0 + 1.3) * np.cos(Y / 1700.0))
+    flats = fractal_noise(rng, npy, npx, 1.0)
+    lag = np.where(flats > 0.9, 0.3 * np.tanh(flats - 1.2), lag)   # tidal flats around datum
+    z = np.where(d < -300.0, sea, np.where(d > 300.0, lag, -2.0))   # barrier 2 m above datum
+    for xi in (0.3 * Lx, 0.68 * Lx):                                # two inlets, 15 m deep
+        m = (np.abs(X - xi) < 250.0) & (np.abs(d) < 900.0)
+        z[m] = 15.0 - 10.0 * np.abs(d[m]) / 900.0
+    z = z.astype(np.float32)
+
+    def refine(lev, xcc, ycc, hx, hy):
+        yy = np.interp(xcc, xs, coast)
+        return np.abs(ycc - yy) < band[lev] + 0.5 * hy
+
+    if window is None:
+        wx0, wy0, wLx, wLy, wnx, wny = 0.0, 0.0, Lx, Ly, nx0, ny0
+    else:
+        wx0, wy0, wLx, wLy, wnx, wny = window
+    tags = (0, 0, 1 if wy0 == 0.0 else 0, 0)
+    mesh, level = forest_mesh(wnx, wny, wLx, wLy, levels, refine, x0=wx0, y0=wy0, tags=tags)
+    i0, j0 = int(round(wx0 / dx)), int(round(wy0 / dy))
+    ni, nj = int(round(wLx / dx)), int(round(wLy / dy))
+    zc = np.ascontiguousarray(z[j0:j0 + nj, i0:i0 + ni])
+    Xn, Yn = nodal_coordinates(mesh, degree)
+    rng_c = np.random.default_rng(seed + 2)
+    c = smooth_field(rng_c, Xn, Yn, Lx)
+    zero = np.zeros_like(Xn)
+    name = f"lagoon-forest-{mesh.n}cells-r{degree}" + ("" if window is None else "-window")
+    wl = Workload(name, degree, mesh, Raster(zc, wx0, wy0, dx, dy), zero.copy(), zero.copy(),
+                  zero.copy(), c, tableau=0, cfl=0.8 * {1: 0.28, 2: 0.14, 3: 0.085}[degree],
+                  eps_vel=0.1, h_lim=0.1, boundaries=[(1, BC_TIDE, 1.0, 44712.0, 0.0)],
+                  manning=np.full(mesh.n, 0.02), steps=1000)
+    wl.level = level
+    return wl
