@@ -25,8 +25,12 @@
  *    Gauss-Lobatto support points, index a + (r+1) b with x fastest; per-field
  *    arrays are [n_cells][(r+1)^2] float64.
  *  - Faces f = 0 W, 1 E, 2 S, 3 N.  nbr[K][f][0] is the neighbour across f, or
- *    -1 - tag (tag in 0..15) on a boundary face; nbr[K][f][1] is -1 (2:1
- *    hanging faces are not accepted by this version: SWDG_EINVAL).
+ *    -1 - tag (tag in 0..15) on a boundary face; nbr[K][f][1] is -1, except on
+ *    the coarse side of a 2:1 (hanging) face, where slots 0 and 1 are the two
+ *    fine neighbours by increasing tangential coordinate.  A fine cell lists
+ *    the coarse cell in slot 0.  Each fine half face is integrated with its
+ *    own r+2 Gauss-Lobatto points; the coarse side evaluates its polynomial
+ *    there and its sub-grid operator on the strip under each point.
  *  - Bathymetry z_b is a depth, positive down: water depth h = max(zeta+z_b, 0)
  *    (Eq. zeta2depth-2).
  *  - Device-side failures never trap: kernels record them in a status word
@@ -88,15 +92,17 @@ int swdg_create(const swdg_config* cfg, swdg_ctx** out);
 /* Upload an axis-aligned quadrilateral mesh (Sec. 3.2): x0y0, hxhy [n][2]
  * float64 host arrays; nbr [n][4][2] int32 host array (see Conventions).
  * Errors: SWDG_EINVAL for n < 1, non-positive sizes, out-of-range neighbours,
- * boundary tags >= 16, or 2:1 hanging faces. */
+ * boundary tags >= 16, non-mutual neighbours, or faces that are neither
+ * conforming nor an exact 2:1 split. */
 int swdg_upload_mesh(swdg_ctx* ctx, int64_t n_cells, const double* x0y0, const double* hxhy,
                      const int32_t* nbr);
 
 /* Upload the bathymetry raster (host, row-major [ny][nx], dtype SWDG_PIX_F32
  * or SWDG_PIX_F64, depth positive down) with pixel (i, j) covering
  * [xo + i dx, xo + (i+1) dx] x [yo + j dy, yo + (j+1) dy].  Requires the mesh.
- * Mode S requires every cell to cover the same whole number P <= 32 of pixels
- * per direction, aligned to pixel edges; the raster is re-tiled per cell.
+ * Mode S requires every cell to cover a whole number P <= 32 of pixels in
+ * both directions, aligned to pixel edges (at most 4 distinct P per mesh);
+ * the raster is re-tiled per cell.
  * Mode P needs nx, ny >= 2.  Errors: SWDG_EINVAL, SWDG_ESTATE. */
 int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t nx, int64_t ny,
                            double xo, double yo, double dx, double dy);
@@ -161,13 +167,14 @@ int swdg_diagnostics(swdg_ctx* ctx, double out[8]);
  * already reserved every byte of the device).  It evaluates exactly what
  * swdg_residual evaluates, plus the CFL step of swdg_cfl_dt, without a
  * context: the caller passes every input and output as device buffers, and
- * the only scratch (the step scalars and one constant-field byte per cell)
- * lives in a fixed array inside the library, reserved on each GPU that loads
- * it until the process exits.  It calls no cudaMalloc/cudaFree.
+ * the only scratch (the step scalars, the pixel-overlap table and one
+ * constant-field byte per cell, about 1.01 MiB in all) lives in a fixed array
+ * inside the library, reserved on each GPU that loads it until the process
+ * exits.  It calls no cudaMalloc/cudaFree.
  *   cfg: degree 1..3, subgrid_mode 0 (pixel sub-cells), g, eps_vel, cfl and
  *        stream are used (stream NULL: the legacy stream);
  *   n_cells <= SWDG_NOALLOC_MAX_CELLS, else SWDG_EINVAL;
- *   hxhy [n][2], nbr [n][4][2] (conforming, as for swdg_upload_mesh),
+ *   hxhy [n][2], nbr [n][4][2] (conforming faces only),
  *   tiles [n][P][P] depth pixels of each cell (P <= 32, dtype SWDG_PIX_*),
  *   manning [n] (zeros for no friction), state [4][n][(r+1)^2]
  *   (zeta, qx, qy, c): device pointers, read only;

@@ -45,7 +45,10 @@ struct swdg_ctx {
            *llin = nullptr, *HN = nullptr, *CN = nullptr, *HNbar = nullptr, *CNbar = nullptr,
            *zpts = nullptr, *zmax = nullptr, *zmin = nullptr, *zabs = nullptr, *diag = nullptr;
     int32_t* nbr = nullptr;
-    uint8_t *cmask = nullptr, *flag = nullptr;
+    uint8_t *cmask = nullptr, *flag = nullptr, *finfo = nullptr, *pcls = nullptr;
+    int64_t* tile_off = nullptr;
+    OvTab* ov = nullptr;
+    double* zhang = nullptr;
     void* tiles = nullptr;
     Scalars* sc = nullptr;
     Scalars* sc_host = nullptr; // pinned staging
@@ -53,6 +56,7 @@ struct swdg_ctx {
     cudaGraphExec_t graph = nullptr;
     double graph_dt = -2.0;
     std::vector<double> x0y0_h, hxhy_h;
+    std::vector<uint8_t> finfo_h;
     std::string err;
 };
 
@@ -176,27 +180,31 @@ static bool invert(int m, const double* A, double* Ainv) {
     return true;
 }
 
-// pixel-overlap fractions of the sub-intervals of a rule with P pixels per cell
-static void overlap_table(const double* w, int n, int P, Tables& tb, int set) {
-    double sb[MXP + 1];
-    sb[0] = 0.0;
-    for (int a = 0; a < n; ++a) sb[a + 1] = sb[a] + w[a];
-    sb[n] = 1.0;
+// pixel-overlap fractions of the sub-intervals [sb[a], sb[a+1]] (reference
+// units of the cell) with P pixels per cell side
+static void overlap_set(const double* sb_in, int n, int P, OvTab& ov, int set) {
+    double sb[MXI + 1];
     for (int a = 0; a <= n; ++a) {
-        double u = sb[a] * P, r = std::floor(u + 0.5);
-        if (std::fabs(u - r) < 1e-9) sb[a] = r / P;
+        double u = sb_in[a] * P, r = std::floor(u + 0.5);
+        sb[a] = std::fabs(u - r) < 1e-9 ? r / P : sb_in[a];
     }
     for (int a = 0; a < n; ++a) {
         int lo = std::max(0, (int)std::floor(sb[a] * P));
         int hi = std::min(P - 1, (int)std::ceil(sb[a + 1] * P) - 1);
-        tb.lo[set][a] = lo;
-        tb.cnt[set][a] = hi - lo + 1;
+        ov.lo[set][a] = lo;
+        ov.cnt[set][a] = hi - lo + 1;
         double width = sb[a + 1] - sb[a];
         for (int k = lo; k <= hi; ++k) {
-            double ov = std::min(sb[a + 1], (k + 1.0) / P) - std::max(sb[a], (double)k / P);
-            tb.frac[set][a][k - lo] = ov > 0.0 ? ov / width : 0.0;
+            double o = std::min(sb[a + 1], (k + 1.0) / P) - std::max(sb[a], (double)k / P);
+            ov.frac[set][a][k - lo] = o > 0.0 ? o / width : 0.0;
         }
     }
+}
+
+static void breakpoints(const double* w, int n, double* sb) {
+    sb[0] = 0.0;
+    for (int a = 0; a < n; ++a) sb[a + 1] = sb[a] + w[a];
+    sb[n] = 1.0;
 }
 
 static bool build_tables(int R, Tables& tb) {
@@ -216,7 +224,11 @@ static bool build_tables(int R, Tables& tb) {
         tb.wm[q] = wm[q];
         tb.xq[SET_MASS][q] = xm[q];
         double dv;
-        for (int a = 0; a < nd1; ++a) lagrange(tb.xs, nd1, a, xm[q], &tb.Bm[q][a], &dv);
+        for (int a = 0; a < nd1; ++a) {
+            lagrange(tb.xs, nd1, a, xm[q], &tb.Bm[q][a], &dv);
+            // the fine-face GLL point q of half h in the coarse face's coordinate
+            for (int h = 0; h < 2; ++h) lagrange(tb.xs, nd1, a, 0.5 * (h + xm[q]), &tb.BmH[h][q][a], &dv);
+        }
     }
     double Bg[MXN * MXN], Bgi[MXN * MXN];
     for (int q = 0; q < ng; ++q) {
@@ -245,40 +257,67 @@ static bool build_tables(int R, Tables& tb) {
     return true;
 }
 
-static bool build_overlaps(int R, int P, Tables& tb) {
+// overlap tables of the four point sets for P pixels per cell side
+static bool build_overlaps(int R, int P, const Tables& tb, OvTab& ov) {
     const int nv = (3 * R) / 2 + 1, nm = R + 2, ng = R + 1;
     if (P < 1 || P > MXPIX) return false;
-    tb.P = P;
-    overlap_table(tb.wv, nv, P, tb, SET_VOL);
-    overlap_table(tb.wm, nm, P, tb, SET_MASS);
-    overlap_table(tb.wg, ng, P, tb, SET_MOM);
+    memset(&ov, 0, sizeof ov);
+    ov.P = P;
+    double sb[MXI + 1];
+    breakpoints(tb.wv, nv, sb);
+    overlap_set(sb, nv, P, ov, SET_VOL);
+    breakpoints(tb.wm, nm, sb);
+    overlap_set(sb, nm, P, ov, SET_MASS);
+    double sm[MXP + 1];
+    memcpy(sm, sb, sizeof sm);
+    breakpoints(tb.wg, ng, sb);
+    overlap_set(sb, ng, P, ov, SET_MOM);
+    // the GLL sub-intervals of the two fine halves of a face, in coarse units:
+    // interval h nm + a is [(h + sm[a]) / 2, (h + sm[a+1]) / 2]
+    for (int h = 0; h < 2; ++h) {
+        double hb[MXP + 1];
+        for (int a = 0; a <= nm; ++a) hb[a] = 0.5 * (h + sm[a]);
+        OvTab tmp;
+        memset(&tmp, 0, sizeof tmp);
+        overlap_set(hb, nm, P, tmp, SET_HALF);
+        for (int a = 0; a < nm; ++a) {
+            ov.lo[SET_HALF][h * nm + a] = tmp.lo[SET_HALF][a];
+            ov.cnt[SET_HALF][h * nm + a] = tmp.cnt[SET_HALF][a];
+            memcpy(ov.frac[SET_HALF][h * nm + a], tmp.frac[SET_HALF][a], sizeof(ov.frac[0][0]));
+        }
+    }
     return true;
 }
 
 // ---------------------------------------------------------------------------
 // setup kernels (S0: re-tile the raster, point samples, per-cell depth bounds)
 // ---------------------------------------------------------------------------
+// one warp per cell: the cell's P x P pixels to its tile
 template <typename Pix>
 __global__ void k_retile(const Pix* __restrict__ ras, int64_t nx, const int32_t* col0,
-                         const int32_t* row0, int P, Pix* tiles, int64_t n) {
-    const int64_t total = n * (int64_t)P * P;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = i / ((int64_t)P * P);
-        const int r = (int)(i % ((int64_t)P * P)), jy = r / P, ix = r % P;
-        tiles[i] = ras[(int64_t)(row0[k] + jy) * nx + col0[k] + ix];
+                         const int32_t* row0, const int64_t* off, const uint8_t* pcls,
+                         const OvTab* ov, Pix* tiles, int64_t n) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = warp; k < n; k += nw) {
+        const int P = ov[pcls[k]].P;
+        for (int i = lane; i < P * P; i += 32)
+            tiles[off[k] + i] = ras[(int64_t)(row0[k] + i / P) * nx + col0[k] + i % P];
     }
 }
 
+// per-cell min / max / max |.| of the pixel depths
 template <typename Pix>
-__global__ void k_tile_bounds(const Pix* __restrict__ tiles, int P, int64_t n, double* zmax,
+__global__ void k_tile_bounds(const Pix* __restrict__ tiles, const int64_t* off,
+                              const uint8_t* pcls, const OvTab* ov, int64_t n, double* zmax,
                               double* zmin, double* zabs) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int64_t k = warp; k < n; k += nw) {
+        const int P = ov[pcls[k]].P;
         double m = -INFINITY, mn = INFINITY, a = 0.0;
         for (int i = lane; i < P * P; i += 32) {
-            const double z = (double)tiles[k * P * P + i];
+            const double z = (double)tiles[off[k] + i];
             m = fmax(m, z);
             mn = fmin(mn, z);
             a = fmax(a, fabs(z));
@@ -294,36 +333,57 @@ __global__ void k_tile_bounds(const Pix* __restrict__ tiles, int P, int64_t n, d
     }
 }
 
-// mean depth sum_k w_k z_k of every sub-cell of the three point sets (mode S)
+// mean depth sum_k w_k z_k of a sub-cell (sets setx / sety, intervals ia / ib)
 template <typename Pix>
-__global__ void k_subcell_means(const Pix* __restrict__ tiles, const __grid_constant__ Tables tb,
-                                int nv, int nm, int ng, double* zpts, int64_t n) {
-    const int nzp = nv * nv + nm * nm + ng * ng, P = tb.P;
-    const int64_t total = n * nzp;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = i / nzp;
-        int p = (int)(i % nzp), set = 0, q = nv;
-        if (p >= nv * nv) {
-            p -= nv * nv;
-            set = 1;
-            q = nm;
-            if (p >= nm * nm) {
-                p -= nm * nm;
-                set = 2;
-                q = ng;
+__device__ double subcell_mean(const Pix* tile, const OvTab& o, int setx, int ia, int sety, int ib) {
+    double s = 0.0;
+    for (int j = 0; j < o.cnt[sety][ib]; ++j) {
+        double r = 0.0;
+        for (int a = 0; a < o.cnt[setx][ia]; ++a)
+            r += o.frac[setx][ia][a] *
+                 (double)tile[(size_t)(o.lo[sety][ib] + j) * o.P + o.lo[setx][ia] + a];
+        s += o.frac[sety][ib][j] * r;
+    }
+    return s;
+}
+
+// one warp per cell: mean depth of every sub-cell of the three point sets and
+// of the coarse-side strips of its 2:1 faces (mode S)
+template <typename Pix>
+__global__ void k_subcell_means(const Pix* __restrict__ tiles, const int64_t* off,
+                                const uint8_t* pcls, const OvTab* ov, const uint8_t* finfo, int nv,
+                                int nm, int ng, double* zpts, double* zhang, int64_t n) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int nzp = nv * nv + nm * nm + ng * ng;
+    for (int64_t k = warp; k < n; k += nw) {
+        const OvTab& o = ov[pcls[k]];
+        const Pix* tile = tiles + off[k];
+        for (int i = lane; i < nzp + 8 * nm; i += 32) {
+            if (i < nzp) {
+                int p = i, set = SET_VOL, q = nv;
+                if (p >= nv * nv) {
+                    p -= nv * nv;
+                    set = SET_MASS;
+                    q = nm;
+                    if (p >= nm * nm) {
+                        p -= nm * nm;
+                        set = SET_MOM;
+                        q = ng;
+                    }
+                }
+                zpts[k * nzp + i] = subcell_mean(tile, o, set, p % q, set, p / q);
+            } else {
+                const int r = i - nzp, f = r / (2 * nm), h = (r / nm) % 2, al = r % nm;
+                double v = 0.0;
+                if ((finfo[k * 4 + f] & 3) == FI_COARSE) {
+                    const int m = (f == 0 || f == 2) ? 0 : nm - 1;
+                    v = f < 2 ? subcell_mean(tile, o, SET_MASS, m, SET_HALF, h * nm + al)
+                              : subcell_mean(tile, o, SET_HALF, h * nm + al, SET_MASS, m);
+                }
+                zhang[((k * 4 + f) * 2 + h) * nm + al] = v;
             }
         }
-        const int ia = p % q, ib = p / q;
-        const Pix* tile = tiles + k * P * P;
-        double s = 0.0;
-        for (int j = 0; j < tb.cnt[set][ib]; ++j) {
-            double r = 0.0;
-            for (int a = 0; a < tb.cnt[set][ia]; ++a)
-                r += tb.frac[set][ia][a] * (double)tile[(size_t)(tb.lo[set][ib] + j) * P + tb.lo[set][ia] + a];
-            s += tb.frac[set][ib][j] * r;
-        }
-        zpts[i] = s;
     }
 }
 
@@ -343,11 +403,14 @@ __device__ double bilinear(const Pix* __restrict__ ras, int64_t nx, int64_t ny, 
     return (1.0 - t) * (1.0 - s) * z00 + t * (1.0 - s) * z10 + (1.0 - t) * s * z01 + t * s * z11;
 }
 
+// mode P: z_b at every point of the three point sets and at the fine-face
+// points of 2:1 faces seen from the coarse side
 template <typename Pix>
 __global__ void k_point_samples(const Pix* __restrict__ ras, int64_t nx, int64_t ny, double xo,
                                 double yo, double dx, double dy, const double* x0y0,
-                                const double* hxhy, const __grid_constant__ Tables tb, int nv,
-                                int nm, int ng, double* zpts, double* zmax, double* zmin,
+                                const double* hxhy, const uint8_t* finfo,
+                                const __grid_constant__ Tables tb, int nv, int nm, int ng,
+                                double* zpts, double* zhang, double* zmax, double* zmin,
                                 double* zabs, int64_t n) {
     const int nzp = nv * nv + nm * nm + ng * ng;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -369,6 +432,18 @@ __global__ void k_point_samples(const Pix* __restrict__ ras, int64_t nx, int64_t
             }
             off += q * q;
         }
+        for (int f = 0; f < 4; ++f)
+            for (int h = 0; h < 2; ++h)
+                for (int al = 0; al < nm; ++al) {
+                    double z = 0.0;
+                    if ((finfo[k * 4 + f] & 3) == FI_COARSE) {
+                        const double tq = 0.5 * (h + tb.xq[SET_MASS][al]);
+                        const double x = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + tq * hx;
+                        const double y = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + tq * hy;
+                        z = bilinear<Pix>(ras, nx, ny, xo, yo, dx, dy, x, y);
+                    }
+                    zhang[((k * 4 + f) * 2 + h) * nm + al] = z;
+                }
         zmax[k] = m;
         zmin[k] = mn;
         zabs[k] = a;
@@ -534,16 +609,20 @@ int swdg_create(const swdg_config* cfg, swdg_ctx** out) {
 static void free_mesh(swdg_ctx* c) {
     cudaFree(c->x0y0); cudaFree(c->hxhy); cudaFree(c->manning); cudaFree(c->U); cudaFree(c->res);
     cudaFree(c->llin); cudaFree(c->HN); cudaFree(c->CN); cudaFree(c->HNbar); cudaFree(c->CNbar);
-    cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->diag);
+    cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->diag); cudaFree(c->finfo);
     c->x0y0 = c->hxhy = c->manning = c->U = c->res = c->llin = c->HN = c->CN = c->HNbar =
         c->CNbar = c->diag = nullptr;
     c->nbr = nullptr;
-    c->cmask = c->flag = nullptr;
+    c->cmask = c->flag = c->finfo = nullptr;
 }
 static void free_bathy(swdg_ctx* c) {
     cudaFree(c->tiles); cudaFree(c->zpts); cudaFree(c->zmax); cudaFree(c->zmin); cudaFree(c->zabs);
+    cudaFree(c->zhang); cudaFree(c->tile_off); cudaFree(c->pcls); cudaFree(c->ov);
     c->tiles = nullptr;
-    c->zpts = c->zmax = c->zmin = c->zabs = nullptr;
+    c->zpts = c->zmax = c->zmin = c->zabs = c->zhang = nullptr;
+    c->tile_off = nullptr;
+    c->pcls = nullptr;
+    c->ov = nullptr;
 }
 
 void swdg_destroy(swdg_ctx* c) {
@@ -562,40 +641,77 @@ void swdg_destroy(swdg_ctx* c) {
 
 const char* swdg_last_error(const swdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
-int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double* hxhy,
-                     const int32_t* nbr) {
-    if (!ctx) return SWDG_EINVAL;
-    if (n < 1 || !x0y0 || !hxhy || !nbr) return fail(ctx, SWDG_EINVAL, "upload_mesh: bad arguments");
+// face info of every cell face (FI_*), validating conforming and 2:1 faces
+static int classify_faces(swdg_ctx* ctx, int64_t n, const double* x0y0, const double* hxhy,
+                          const int32_t* nbr, std::vector<uint8_t>& fi) {
+    fi.assign(4 * n, 0);
+    auto tang = [&](int64_t k, int f, double& t0, double& L) {
+        t0 = f < 2 ? x0y0[2 * k + 1] : x0y0[2 * k];
+        L = f < 2 ? hxhy[2 * k + 1] : hxhy[2 * k];
+    };
     for (int64_t k = 0; k < n; ++k) {
         if (!(hxhy[2 * k] > 0) || !(hxhy[2 * k + 1] > 0) || !std::isfinite(x0y0[2 * k]) ||
             !std::isfinite(x0y0[2 * k + 1]))
             return fail(ctx, SWDG_EINVAL, "upload_mesh: cell %lld has a bad size or origin",
                         (long long)k);
         for (int f = 0; f < 4; ++f) {
-            int32_t s0 = nbr[k * 8 + 2 * f], s1 = nbr[k * 8 + 2 * f + 1];
-            if (s1 != -1)
-                return fail(ctx, SWDG_EINVAL,
-                            "upload_mesh: cell %lld face %d: 2:1 hanging faces not supported",
+            const int32_t s0 = nbr[k * 8 + 2 * f], s1 = nbr[k * 8 + 2 * f + 1];
+            const int fo = f ^ 1;
+            if (s0 >= n || s1 >= n || s0 < -MXTAG || s1 < -1 || (s0 < 0 && s1 != -1))
+                return fail(ctx, SWDG_EINVAL, "upload_mesh: cell %lld face %d: bad neighbour slots",
                             (long long)k, f);
-            if (s0 >= n || s0 < -MXTAG)
-                return fail(ctx, SWDG_EINVAL, "upload_mesh: cell %lld face %d: bad neighbour %d",
+            if (s0 < 0) continue;
+            double tk0, Lk;
+            tang(k, f, tk0, Lk);
+            if (s1 >= 0) {
+                // coarse side: two fine neighbours covering the lower and upper halves
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t q = h ? s1 : s0;
+                    double tq0, Lq;
+                    tang(q, fo, tq0, Lq);
+                    if (nbr[q * 8 + 2 * fo] != (int32_t)k || nbr[q * 8 + 2 * fo + 1] != -1 ||
+                        std::fabs(2.0 * Lq - Lk) > 1e-9 * Lk ||
+                        std::fabs(tq0 - (tk0 + 0.5 * h * Lk)) > 1e-9 * Lk)
+                        return fail(ctx, SWDG_EINVAL,
+                                    "upload_mesh: cell %lld face %d: inconsistent 2:1 face",
+                                    (long long)k, f);
+                }
+                fi[4 * k + f] = FI_COARSE;
+                continue;
+            }
+            const int32_t b0 = nbr[(int64_t)s0 * 8 + 2 * fo], b1 = nbr[(int64_t)s0 * 8 + 2 * fo + 1];
+            double tn0, Ln;
+            tang(s0, fo, tn0, Ln);
+            if (b0 == (int32_t)k && b1 == -1) {
+                if (std::fabs(Ln - Lk) > 1e-9 * Lk)
+                    return fail(ctx, SWDG_EINVAL,
+                                "upload_mesh: cell %lld face %d is non-conforming without a 2:1 "
+                                "neighbour list",
+                                (long long)k, f);
+            } else if (b1 >= 0 && (b0 == (int32_t)k || b1 == (int32_t)k)) {
+                const int h = b1 == (int32_t)k ? 1 : 0;
+                if (std::fabs(2.0 * Lk - Ln) > 1e-9 * Ln ||
+                    std::fabs(tk0 - (tn0 + 0.5 * h * Ln)) > 1e-9 * Ln)
+                    return fail(ctx, SWDG_EINVAL, "upload_mesh: cell %lld face %d: bad 2:1 geometry",
+                                (long long)k, f);
+                fi[4 * k + f] = (uint8_t)(FI_FINE | (h << 2));
+            } else {
+                return fail(ctx, SWDG_EINVAL,
+                            "upload_mesh: cell %lld face %d and cell %d are not mutual neighbours",
                             (long long)k, f, s0);
-            if (s0 >= 0) {
-                // conforming: the neighbour must share the whole face
-                const int fo = f ^ 1;
-                if (nbr[(int64_t)s0 * 8 + 2 * fo] != (int32_t)k)
-                    return fail(ctx, SWDG_EINVAL,
-                                "upload_mesh: cell %lld face %d and cell %d are not mutual "
-                                "neighbours",
-                                (long long)k, f, s0);
-                const double tk = f < 2 ? hxhy[2 * k + 1] : hxhy[2 * k];
-                const double tn = f < 2 ? hxhy[2 * (int64_t)s0 + 1] : hxhy[2 * (int64_t)s0];
-                if (std::fabs(tk - tn) > 1e-9 * tk)
-                    return fail(ctx, SWDG_EINVAL,
-                                "upload_mesh: cell %lld face %d is non-conforming", (long long)k, f);
             }
         }
     }
+    return SWDG_OK;
+}
+
+int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double* hxhy,
+                     const int32_t* nbr) {
+    if (!ctx) return SWDG_EINVAL;
+    if (n < 1 || !x0y0 || !hxhy || !nbr) return fail(ctx, SWDG_EINVAL, "upload_mesh: bad arguments");
+    std::vector<uint8_t> fi;
+    int rc = classify_faces(ctx, n, x0y0, hxhy, nbr, fi);
+    if (rc) return rc;
     invalidate_graph(ctx);
     free_mesh(ctx);
     free_bathy(ctx);
@@ -605,6 +721,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     CK(cudaMalloc(&ctx->x0y0, 2 * n * sizeof(double)));
     CK(cudaMalloc(&ctx->hxhy, 2 * n * sizeof(double)));
     CK(cudaMalloc(&ctx->nbr, 8 * n * sizeof(int32_t)));
+    CK(cudaMalloc(&ctx->finfo, 4 * n));
     CK(cudaMalloc(&ctx->manning, n * sizeof(double)));
     CK(cudaMalloc(&ctx->U, (size_t)NBUF * 4 * n * nd * sizeof(double)));
     CK(cudaMalloc(&ctx->res, (size_t)MXS * 6 * n * nd * sizeof(double)));
@@ -619,6 +736,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     CK(cudaMemcpyAsync(ctx->x0y0, x0y0, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->hxhy, hxhy, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->nbr, nbr, 8 * n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->finfo, fi.data(), 4 * n, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemsetAsync(ctx->manning, 0, n * sizeof(double), ctx->st));
     CK(cudaMemsetAsync(ctx->llin, 0, 2 * n * nd * sizeof(double), ctx->st));
     CK(cudaMemsetAsync(ctx->flag, ctx->R, n, ctx->st));
@@ -626,11 +744,13 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     CK(cudaStreamSynchronize(ctx->st));
     ctx->x0y0_h.assign(x0y0, x0y0 + 2 * n);
     ctx->hxhy_h.assign(hxhy, hxhy + 2 * n);
+    ctx->finfo_h = fi;
     Dev& d = ctx->d;
     d.n = n;
     d.x0y0 = ctx->x0y0;
     d.hxhy = ctx->hxhy;
     d.nbr = ctx->nbr;
+    d.finfo = ctx->finfo;
     d.manning = ctx->manning;
     d.U = ctx->U;
     d.cmask = ctx->cmask;
@@ -656,11 +776,18 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
         return fail(ctx, SWDG_EINVAL, "upload_bathymetry: bad arguments");
     const int64_t n = ctx->n;
     const size_t es = dtype == SWDG_PIX_F32 ? 4 : 8;
-    int P = 0;
+    const int R_ = ctx->R, nv_ = (3 * R_) / 2 + 1, nm_ = R_ + 2, ng_ = R_ + 1;
+    const int nzp_ = nv_ * nv_ + nm_ * nm_ + ng_ * ng_;
     std::vector<int32_t> col0, row0;
+    std::vector<int64_t> toff;
+    std::vector<uint8_t> cls;
+    std::vector<int> Ps;
+    int64_t npix = 0;
     if (ctx->mode == 0) {
         col0.resize(n);
         row0.resize(n);
+        toff.resize(n);
+        cls.resize(n);
         for (int64_t k = 0; k < n; ++k) {
             const double cx = (ctx->x0y0_h[2 * k] - xo) / dx, cy = (ctx->x0y0_h[2 * k + 1] - yo) / dy;
             const double px = ctx->hxhy_h[2 * k] / dx, py = ctx->hxhy_h[2 * k + 1] / dy;
@@ -669,20 +796,33 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
             if (std::fabs(cx - rcx) > 1e-6 || std::fabs(cy - rcy) > 1e-6 ||
                 std::fabs(px - rpx) > 1e-6 || std::fabs(py - rpy) > 1e-6 || rpx != rpy)
                 return fail(ctx, SWDG_EINVAL,
-                            "upload_bathymetry: cell %lld is not aligned to whole pixels",
+                            "upload_bathymetry: cell %lld does not span the same whole number of "
+                            "pixels in x and y, aligned to pixel edges",
                             (long long)k);
-            if (k == 0) P = (int)rpx;
-            if ((int)rpx != P)
-                return fail(ctx, SWDG_EINVAL,
-                            "upload_bathymetry: cells must all span the same number of pixels");
+            const int P = (int)rpx;
+            if (P < 1 || P > MXPIX)
+                return fail(ctx, SWDG_EINVAL, "upload_bathymetry: %d pixels per cell side (max %d)",
+                            P, MXPIX);
             if (rcx < 0 || rcy < 0 || rcx + P > nx || rcy + P > ny)
                 return fail(ctx, SWDG_EINVAL, "upload_bathymetry: raster does not cover cell %lld",
                             (long long)k);
+            int c = -1;
+            for (size_t i = 0; i < Ps.size(); ++i)
+                if (Ps[i] == P) c = (int)i;
+            if (c < 0) {
+                if ((int)Ps.size() == MXCLS)
+                    return fail(ctx, SWDG_EINVAL,
+                                "upload_bathymetry: more than %d distinct pixel counts per cell",
+                                MXCLS);
+                Ps.push_back(P);
+                c = (int)Ps.size() - 1;
+            }
             col0[k] = (int32_t)rcx;
             row0[k] = (int32_t)rcy;
+            cls[k] = (uint8_t)c;
+            toff[k] = npix;
+            npix += (int64_t)P * P;
         }
-        if (P < 1 || P > MXPIX)
-            return fail(ctx, SWDG_EINVAL, "upload_bathymetry: %d pixels per cell (max %d)", P, MXPIX);
     }
     invalidate_graph(ctx);
     free_bathy(ctx);
@@ -692,49 +832,61 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
     CK(cudaMalloc(&ctx->zmax, n * sizeof(double)));
     CK(cudaMalloc(&ctx->zmin, n * sizeof(double)));
     CK(cudaMalloc(&ctx->zabs, n * sizeof(double)));
-    const int R_ = ctx->R, nv_ = (3 * R_) / 2 + 1, nm_ = R_ + 2, ng_ = R_ + 1;
-    const int nzp_ = nv_ * nv_ + nm_ * nm_ + ng_ * ng_;
     CK(cudaMalloc(&ctx->zpts, (size_t)n * nzp_ * sizeof(double)));
-    const int grid = (int)std::min<int64_t>(152 * 32, (n * 32 + 255) / 256 + 1);
+    CK(cudaMalloc(&ctx->zhang, (size_t)n * 8 * nm_ * sizeof(double)));
+    const int gw = (int)std::min<int64_t>(152 * 32, (n * 32 + 255) / 256 + 1); // warp-per-cell grids
     if (ctx->mode == 0) {
+        std::vector<OvTab> ovh(Ps.size());
+        for (size_t i = 0; i < Ps.size(); ++i)
+            if (!build_overlaps(ctx->R, Ps[i], ctx->tb, ovh[i]))
+                return fail(ctx, SWDG_EINVAL, "upload_bathymetry: bad pixel count");
         int32_t *c0 = nullptr, *r0 = nullptr;
         CK(cudaMalloc(&c0, n * sizeof(int32_t)));
         CK(cudaMalloc(&r0, n * sizeof(int32_t)));
+        CK(cudaMalloc(&ctx->tile_off, n * sizeof(int64_t)));
+        CK(cudaMalloc(&ctx->pcls, n));
+        CK(cudaMalloc(&ctx->ov, Ps.size() * sizeof(OvTab)));
         CK(cudaMemcpyAsync(c0, col0.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
         CK(cudaMemcpyAsync(r0, row0.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
-        CK(cudaMalloc(&ctx->tiles, (size_t)n * P * P * es));
-        if (!build_overlaps(ctx->R, P, ctx->tb))
-            return fail(ctx, SWDG_EINVAL, "upload_bathymetry: bad pixel count");
+        CK(cudaMemcpyAsync(ctx->tile_off, toff.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           ctx->st));
+        CK(cudaMemcpyAsync(ctx->pcls, cls.data(), n, cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemcpyAsync(ctx->ov, ovh.data(), Ps.size() * sizeof(OvTab), cudaMemcpyHostToDevice,
+                           ctx->st));
+        CK(cudaMalloc(&ctx->tiles, (size_t)npix * es));
         if (dtype == SWDG_PIX_F32) {
-            k_retile<float><<<152 * 16, 256, 0, ctx->st>>>((const float*)ras, nx, c0, r0, P,
-                                                          (float*)ctx->tiles, n);
-            k_tile_bounds<float><<<grid, 256, 0, ctx->st>>>((const float*)ctx->tiles, P, n, ctx->zmax,
-                                                           ctx->zmin, ctx->zabs);
-            k_subcell_means<float><<<152 * 16, 256, 0, ctx->st>>>((const float*)ctx->tiles, ctx->tb,
-                                                                 nv_, nm_, ng_, ctx->zpts, n);
+            k_retile<float><<<gw, 256, 0, ctx->st>>>((const float*)ras, nx, c0, r0, ctx->tile_off,
+                                                    ctx->pcls, ctx->ov, (float*)ctx->tiles, n);
+            k_tile_bounds<float><<<gw, 256, 0, ctx->st>>>((const float*)ctx->tiles, ctx->tile_off,
+                                                         ctx->pcls, ctx->ov, n, ctx->zmax, ctx->zmin,
+                                                         ctx->zabs);
+            k_subcell_means<float><<<gw, 256, 0, ctx->st>>>(
+                (const float*)ctx->tiles, ctx->tile_off, ctx->pcls, ctx->ov, ctx->finfo, nv_, nm_, ng_,
+                ctx->zpts, ctx->zhang, n);
         } else {
-            k_retile<double><<<152 * 16, 256, 0, ctx->st>>>((const double*)ras, nx, c0, r0, P,
-                                                           (double*)ctx->tiles, n);
-            k_tile_bounds<double><<<grid, 256, 0, ctx->st>>>((const double*)ctx->tiles, P, n,
-                                                            ctx->zmax, ctx->zmin, ctx->zabs);
-            k_subcell_means<double><<<152 * 16, 256, 0, ctx->st>>>(
-                (const double*)ctx->tiles, ctx->tb, nv_, nm_, ng_, ctx->zpts, n);
+            k_retile<double><<<gw, 256, 0, ctx->st>>>((const double*)ras, nx, c0, r0, ctx->tile_off,
+                                                     ctx->pcls, ctx->ov, (double*)ctx->tiles, n);
+            k_tile_bounds<double><<<gw, 256, 0, ctx->st>>>((const double*)ctx->tiles, ctx->tile_off,
+                                                          ctx->pcls, ctx->ov, n, ctx->zmax,
+                                                          ctx->zmin, ctx->zabs);
+            k_subcell_means<double><<<gw, 256, 0, ctx->st>>>(
+                (const double*)ctx->tiles, ctx->tile_off, ctx->pcls, ctx->ov, ctx->finfo, nv_, nm_,
+                ng_, ctx->zpts, ctx->zhang, n);
         }
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->st));
         cudaFree(c0);
         cudaFree(r0);
     } else {
-        const int nv = nv_, nm = nm_, ng = ng_;
         const int g2 = (int)std::min<int64_t>(152 * 16, (n + 127) / 128);
         if (dtype == SWDG_PIX_F32)
             k_point_samples<float><<<g2, 128, 0, ctx->st>>>(
-                (const float*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0, ctx->hxhy, ctx->tb, nv, nm, ng,
-                ctx->zpts, ctx->zmax, ctx->zmin, ctx->zabs, n);
+                (const float*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0, ctx->hxhy, ctx->finfo, ctx->tb,
+                nv_, nm_, ng_, ctx->zpts, ctx->zhang, ctx->zmax, ctx->zmin, ctx->zabs, n);
         else
             k_point_samples<double><<<g2, 128, 0, ctx->st>>>(
-                (const double*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0, ctx->hxhy, ctx->tb, nv, nm, ng,
-                ctx->zpts, ctx->zmax, ctx->zmin, ctx->zabs, n);
+                (const double*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0, ctx->hxhy, ctx->finfo, ctx->tb,
+                nv_, nm_, ng_, ctx->zpts, ctx->zhang, ctx->zmax, ctx->zmin, ctx->zabs, n);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->st));
     }
@@ -742,11 +894,16 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
     ctx->pix = dtype == SWDG_PIX_F32 ? 0 : 1;
     if (!get_launch(ctx->R, ctx->mode, ctx->pix, &ctx->L))
         return fail(ctx, SWDG_EINVAL, "upload_bathymetry: no kernels for this configuration");
-    ctx->d.tiles = ctx->tiles;
-    ctx->d.zpts = ctx->zpts;
-    ctx->d.zmax = ctx->zmax;
-    ctx->d.zmin = ctx->zmin;
-    ctx->d.zabs = ctx->zabs;
+    Dev& d = ctx->d;
+    d.tiles = ctx->tiles;
+    d.tile_off = ctx->tile_off;
+    d.pcls = ctx->pcls;
+    d.ov = ctx->ov;
+    d.zhang = ctx->zhang;
+    d.zpts = ctx->zpts;
+    d.zmax = ctx->zmax;
+    d.zmin = ctx->zmin;
+    d.zabs = ctx->zabs;
     ctx->has_bathy = true;
     return SWDG_OK;
 }
@@ -1058,10 +1215,13 @@ int swdg_diagnostics(swdg_ctx* ctx, double out[8]) {
 
 // ---------------------------------------------------------------------------
 // allocation-free residual: its only scratch is this file-scope array (step
-// scalars in the first 256 bytes, one constant-field mask byte per cell
-// after them), reserved on every GPU that loads the library
+// scalars in the first 256 bytes, then the pixel-overlap table, then one
+// constant-field mask byte per cell), reserved on every GPU that loads the
+// library
 // ---------------------------------------------------------------------------
-static __device__ __align__(256) unsigned char g_noalloc_scratch[256 + SWDG_NOALLOC_MAX_CELLS];
+constexpr size_t NOALLOC_OV_BYTES = ((sizeof(OvTab) + 255) / 256) * 256;
+static __device__ __align__(256) unsigned char
+    g_noalloc_scratch[256 + NOALLOC_OV_BYTES + SWDG_NOALLOC_MAX_CELLS];
 static void* g_noalloc_addr[256];   // device address of the array, per device ordinal
 static bool g_noalloc_ready[256];
 
@@ -1139,11 +1299,13 @@ extern "C" int swdg_residual_noalloc(const swdg_config* cfg, int64_t n, const do
     }
     unsigned char* scratch = (unsigned char*)g_noalloc_addr[dev];
     Scalars* sc = (Scalars*)scratch;
-    uint8_t* cmask = (uint8_t*)(scratch + 256);
+    OvTab* ovd = (OvTab*)(scratch + 256);
+    uint8_t* cmask = (uint8_t*)(scratch + 256 + NOALLOC_OV_BYTES);
     cudaStream_t st = (cudaStream_t)cfg->stream;
 
     Tables tb;
-    if (!build_tables(cfg->degree, tb) || !build_overlaps(cfg->degree, P, tb))
+    static OvTab ovh; // host copy, reused by every call (not thread-safe, like the scratch)
+    if (!build_tables(cfg->degree, tb) || !build_overlaps(cfg->degree, P, tb, ovh))
         return noalloc_fail(err, err_len, SWDG_EINVAL, "residual_noalloc: table construction failed");
     Launch L{};
     if (!get_launch(cfg->degree, 0, pix_dtype == SWDG_PIX_F32 ? 0 : 1, &L))
@@ -1153,6 +1315,7 @@ extern "C" int swdg_residual_noalloc(const swdg_config* cfg, int64_t n, const do
     d.hxhy = hxhy;
     d.nbr = nbr;
     d.tiles = tiles;
+    d.ov = ovd; // one pixel count; tile k starts at k P^2; conforming faces only
     d.manning = manning;
     d.U = const_cast<double*>(state); // read only: buffer 0 of the kernels' state layout
     d.cmask = cmask;
@@ -1172,6 +1335,8 @@ extern "C" int swdg_residual_noalloc(const swdg_config* cfg, int64_t n, const do
         if (d.bc_kind[i] == SWDG_BC_TIDE && !(d.bc_per[i] > 0))
             return noalloc_fail(err, err_len, SWDG_EINVAL, "residual_noalloc: tide period <= 0");
     }
+    cudaError_t ec = cudaMemcpyAsync(ovd, &ovh, sizeof(OvTab), cudaMemcpyHostToDevice, st);
+    if (ec != cudaSuccess) return noalloc_fail(err, err_len, SWDG_ECUDA, cudaGetErrorString(ec));
     k_noalloc_begin<<<1, 1, 0, st>>>(sc, t);
     k_noalloc_check_mesh<<<(int)std::min<int64_t>(152 * 8, (n + 255) / 256), 256, 0, st>>>(hxhy, nbr,
                                                                                         n, sc);

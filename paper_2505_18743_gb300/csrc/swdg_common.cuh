@@ -28,6 +28,25 @@ constexpr int NBUF = 4;   // state buffers: v^n plus stages 2..4
 constexpr int SET_VOL = 0;  // volume Gauss-Legendre, floor(3r/2)+1 per direction
 constexpr int SET_MASS = 1; // face / mass Gauss-Lobatto, r+2 per direction
 constexpr int SET_MOM = 2;  // momentum mass Gauss-Legendre, r+1 per direction
+constexpr int SET_HALF = 3; // coarse side of a 2:1 face: the GLL sub-intervals of each
+                            // fine half face, h NM + al, in coarse coordinates
+constexpr int NSET = 4;
+constexpr int MXI = 2 * MXP; // max sub-intervals per set
+constexpr int MXCLS = 4;     // max distinct pixel counts per cell side
+
+// face info byte of a cell's face: FI_COARSE = this cell is the coarse side of
+// a 2:1 face (two fine neighbours); FI_FINE | half << 2 = this cell is one of
+// the two fine cells (half 0: lower tangential half of the coarse face)
+constexpr int FI_COARSE = 1;
+constexpr int FI_FINE = 2;
+
+// pixel-overlap fractions of the sub-intervals of the four point sets for
+// one pixel count P per cell side
+struct OvTab {
+    int P;
+    int lo[NSET][MXI], cnt[NSET][MXI];
+    double frac[NSET][MXI][MXPIX + 1];
+};
 
 // status bits
 constexpr int ST_NAN = 1;
@@ -47,11 +66,9 @@ struct Tables {
     double Bg[MXP][MXN], wg[MXP];               // nodal -> momentum GL (square)
     double Bginv[MXN][MXP];                     // inverse of Bg
     double M1inv[MXN][MXN];                     // inverse of the 1D GLL mass matrix
+    double BmH[2][MXP][MXN];                    // nodal -> fine-face GLL points of half h
     double xs[MXN];                             // support nodes on [0, 1]
     double xq[3][MXP];                          // nodes of the three point sets on [0, 1]
-    int P;                                      // pixels per cell side (mode S)
-    int lo[3][MXP], cnt[3][MXP];                // first pixel and count per sub-interval
-    double frac[3][MXP][MXPIX + 1];             // pixel fraction of each sub-interval
 };
 
 struct Scalars {
@@ -68,6 +85,11 @@ struct Dev {
     const double* hxhy;
     const int32_t* nbr;
     const void* tiles;
+    const int64_t* tile_off; // first pixel of each cell's tile (null: k P^2)
+    const uint8_t* pcls;     // pixel-count class of each cell (null: class 0)
+    const OvTab* ov;         // overlap tables per class
+    const uint8_t* finfo;    // [cell][4] face info (null: all conforming)
+    const double* zhang;     // [cell][4][2][NM]: coarse-side strip means / samples
     const double* zpts;
     const double* zmax; // dry-start level of Eq. initial_guess (max z_b of the cell)
     const double* zmin; // min z_b of the cell: every pixel is wet when eta > -zmin
@@ -145,12 +167,12 @@ __device__ __forceinline__ double gamma_manning(double n, double h, double qx, d
 // sub-grid wet depth V and wet area A of sub-cell (ia, ib) of point set `set`
 // (mode S): V = sum_k w_k max(eta + z_k, 0), A = sum_k w_k [eta + z_k > 0]
 template <typename Pix>
-__device__ __forceinline__ void subgrid_S(const Pix* __restrict__ tile, const Tables& tb, int set,
-                                          int ia, int ib, double eta, double& V, double& A,
-                                          bool& full) {
-    const int P = tb.P;
-    const int lox = tb.lo[set][ia], cx = tb.cnt[set][ia];
-    const int loy = tb.lo[set][ib], cy = tb.cnt[set][ib];
+__device__ __forceinline__ void subgrid_S(const Pix* __restrict__ tile, const OvTab& ov, int setx,
+                                          int ia, int sety, int ib, double eta, double& V,
+                                          double& A, bool& full) {
+    const int P = ov.P;
+    const int lox = ov.lo[setx][ia], cx = ov.cnt[setx][ia];
+    const int loy = ov.lo[sety][ib], cy = ov.cnt[sety][ib];
     double v = 0.0, a = 0.0;
     bool f = true;
     for (int j = 0; j < cy; ++j) {
@@ -159,14 +181,14 @@ __device__ __forceinline__ void subgrid_S(const Pix* __restrict__ tile, const Ta
         for (int i = 0; i < cx; ++i) {
             double dd = eta + (double)row[i];
             if (dd > 0.0) {
-                double fx = tb.frac[set][ia][i];
+                double fx = ov.frac[setx][ia][i];
                 vr += fx * dd;
                 ar += fx;
             } else {
                 f = false;
             }
         }
-        double fy = tb.frac[set][ib][j];
+        double fy = ov.frac[sety][ib][j];
         v += fy * vr;
         a += fy * ar;
     }

@@ -95,34 +95,45 @@ struct Site {
     static __device__ __forceinline__ int count(int set) {
         return set == SET_VOL ? S::NV : (set == SET_MASS ? S::NM : S::NG);
     }
+    static __device__ __forceinline__ const OvTab& tab(const Dev& d, int64_t k) {
+        return d.ov[d.pcls ? d.pcls[k] : 0];
+    }
+    static __device__ __forceinline__ const Pix* tile(const Dev& d, const OvTab& o, int64_t k) {
+        return (const Pix*)d.tiles + (d.tile_off ? d.tile_off[k] : (int64_t)k * o.P * o.P);
+    }
+    // mode S: a cell entirely wet (eta > -min z_b) gives V = eta + the sub-cell
+    // mean depth and A = 1; entirely dry (eta <= -max z_b) gives V = A = 0;
+    // otherwise the pixels are summed.  The per-cell bounds are optional (the
+    // allocation-free residual has none): without them every sub-cell sums.
+    static __device__ __forceinline__ bool shortcut(const Dev& d, int64_t k, double eta,
+                                                    double zbar, double& V, double& A, bool& full) {
+        if (d.zmin == nullptr) return false;
+        if (eta > -d.zmin[k]) {
+            V = eta + zbar;
+            A = 1.0;
+            full = true;
+            return true;
+        }
+        if (!(eta > -d.zmax[k])) {
+            V = 0.0;
+            A = 0.0;
+            full = false;
+            return true;
+        }
+        return false;
+    }
     // V, A of sub-cell (ia, ib) of point set `set` of cell k at elevation eta,
-    // and whether every pixel of it is wet.  Mode S: a sub-cell whose cell is
-    // entirely wet (eta > -min z_b) has V = eta + its mean depth and A = 1; an
-    // entirely dry one (eta <= -max z_b) has V = A = 0; otherwise the pixels
-    // are summed.
+    // and whether every pixel of it is wet
     static __device__ __forceinline__ void VA(const Dev& d, const Tables& tb, int64_t k, int set,
                                               int ia, int ib, double eta, double& V, double& A,
                                               bool& full) {
         if (MODE == 0) {
-            // the per-cell bounds and sub-cell means are optional (a caller of
-            // the allocation-free residual has none): without them every
-            // sub-cell sums its pixels
-            if (d.zmin != nullptr) {
-                if (eta > -d.zmin[k]) {
-                    V = eta + d.zpts[(size_t)k * S::NZP + offset(set) + ia + count(set) * ib];
-                    A = 1.0;
-                    full = true;
-                    return;
-                }
-                if (!(eta > -d.zmax[k])) {
-                    V = 0.0;
-                    A = 0.0;
-                    full = false;
-                    return;
-                }
-            }
-            const Pix* tile = (const Pix*)d.tiles + (size_t)k * tb.P * tb.P;
-            subgrid_S<Pix>(tile, tb, set, ia, ib, eta, V, A, full);
+            if (d.zmin != nullptr &&
+                shortcut(d, k, eta, d.zpts[(size_t)k * S::NZP + offset(set) + ia + count(set) * ib],
+                         V, A, full))
+                return;
+            const OvTab& o = tab(d, k);
+            subgrid_S<Pix>(tile(d, o, k), o, set, ia, set, ib, eta, V, A, full);
         } else {
             subgrid_P(d.zpts[(size_t)k * S::NZP + offset(set) + ia + count(set) * ib], eta, V, A);
             full = A > 0.0;
@@ -132,6 +143,27 @@ struct Site {
                                               int ia, int ib, double eta, double& V, double& A) {
         bool full;
         VA(d, tb, k, set, ia, ib, eta, V, A, full);
+    }
+    // the strip of the coarse cell k on its face f under GLL point al of the
+    // fine half face h (a 2:1 face): normal extent = its first/last mass
+    // sub-interval, tangential extent = the fine point's sub-interval
+    static __device__ __forceinline__ void VA_half(const Dev& d, int64_t k, int f, int h, int al,
+                                                   double eta, double& V, double& A) {
+        const double zh = d.zhang[(((size_t)k * 4 + f) * 2 + h) * S::NM + al];
+        if (MODE == 0) {
+            bool full;
+            if (shortcut(d, k, eta, zh, V, A, full)) return;
+            const OvTab& o = tab(d, k);
+            const int m = (f == 0 || f == 2) ? 0 : S::NM - 1;
+            if (f < 2)
+                subgrid_S<Pix>(tile(d, o, k), o, SET_MASS, m, SET_HALF, h * S::NM + al, eta, V, A,
+                               full);
+            else
+                subgrid_S<Pix>(tile(d, o, k), o, SET_HALF, h * S::NM + al, SET_MASS, m, eta, V, A,
+                               full);
+        } else {
+            subgrid_P(zh, eta, V, A);
+        }
     }
 };
 
@@ -150,6 +182,25 @@ __device__ __forceinline__ int face_node(int f, int j) {
     if (f == 1) return (ND1 - 1) + ND1 * j;
     if (f == 2) return j;
     return j + ND1 * (ND1 - 1);
+}
+
+// the four fields of a cell at face point al of face f: sum_j B[al][j] u(node(f, j));
+// fields are fstride apart; a field constant on the cell is that constant
+template <int ND1>
+__device__ __forceinline__ void face_trace(const double* u, size_t fstride, unsigned cm, int f,
+                                           const double (*B)[MXN], int al, double t[4]) {
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl) {
+        const double* uf = u + fl * fstride;
+        if (cm & (1u << fl)) {
+            t[fl] = uf[0];
+            continue;
+        }
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < ND1; ++j) s += B[al][j] * uf[face_node<ND1>(f, j)];
+        t[fl] = s;
+    }
 }
 
 // Rusanov flux with hydrostatic reconstruction at one face point, seen from
@@ -189,7 +240,7 @@ template <int R>
 constexpr int res_smem() {
     using S = Sz<R>;
     return 4 * S::ND + 5 * S::ND1 * S::NV + 6 * S::NVP + 12 * S::NVP + 12 * S::NV * S::ND1 +
-           16 * S::NM + 6 * S::ND;
+           32 * S::NM + 6 * S::ND;
 }
 
 template <int R, typename Pix, int MODE>
@@ -206,8 +257,8 @@ __global__ void __launch_bounds__(TPB)
     double* pv = tx + 5 * ND1 * NV;  // unused slot kept for alignment of later arrays
     double* X = pv + 6 * NVP;        // [12][NVP]
     double* sy = X + 12 * NVP;       // [12][NV][ND1]
-    double* fh = sy + 12 * NV * ND1; // [4][4 NM]
-    double* rs = fh + 16 * NM;       // [6][ND]
+    double* fh = sy + 12 * NV * ND1; // [4 fields][4 faces][2 halves][NM]
+    double* rs = fh + 32 * NM;       // [6][ND]
     const double g = d.g, eps = d.eps;
     const double t = (c_stage == 0.0) ? d.sc->t : d.sc->t + c_stage * get_dt(d);
     const int64_t n = d.n;
@@ -302,51 +353,57 @@ __global__ void __launch_bounds__(TPB)
                      tb.Bv[al][a] * sy[((cf * 2 + 1) * NV + al) * ND1 + b];
             rs[i] = s;
         }
-        // faces: one face point per lane
+        // faces: one (sub)face point per lane; a coarse cell integrates each
+        // 2:1 face over the GLL points of both fine halves
         double dtl = INFINITY;
-        if (lane < 4 * NM) {
-            const int f = lane / NM, al = lane % NM;
+        unsigned char fi[4];
+        int base[5];
+        base[0] = 0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            fi[f] = d.finfo ? d.finfo[k * 4 + f] : 0;
+            base[f + 1] = base[f] + (((fi[f] & 3) == FI_COARSE) ? 2 : 1) * NM;
+        }
+        for (int it = lane; it < base[4]; it += 32) {
+            const int f = (it >= base[1]) + (it >= base[2]) + (it >= base[3]);
+            const int r_ = it - base[f], h = r_ / NM, al = r_ % NM;
+            const unsigned info = fi[f];
+            const bool coarse = (info & 3) == FI_COARSE, fine = (info & 3) == FI_FINE;
+            const int half = (int)(info >> 2);
             const double nx = (f == 0) ? -1.0 : (f == 1) ? 1.0 : 0.0;
             const double ny = (f == 2) ? -1.0 : (f == 3) ? 1.0 : 0.0;
-            const double L = (f < 2) ? hy : hx;
+            const double L = ((f < 2) ? hy : hx) * (coarse ? 0.5 : 1.0);
             double tm[4];
-#pragma unroll
-            for (int fl = 0; fl < 4; ++fl) {
-                if (cm & (1u << fl)) { tm[fl] = su[fl * ND]; continue; }
-                double s = 0.0;
-#pragma unroll
-                for (int j = 0; j < ND1; ++j) s += tb.Bm[al][j] * su[fl * ND + face_node<ND1>(f, j)];
-                tm[fl] = s;
-            }
+            face_trace<ND1>(su, ND, cm, f, coarse ? tb.BmH[h] : tb.Bm, al, tm);
             int ia, ib;
             face_site_index<NM>(f, al, ia, ib);
-            double hm, Am, Vmp;
-            ST::VA(d, tb, k, SET_MASS, ia, ib, tm[0], hm, Am);
+            auto own_V = [&](double eta) {
+                double V, A;
+                if (coarse) ST::VA_half(d, k, f, h, al, eta, V, A);
+                else ST::VA(d, tb, k, SET_MASS, ia, ib, eta, V, A);
+                return V;
+            };
             const int32_t s0 = d.nbr[k * 8 + f * 2];
-            double tp[4], hp, hsm, hsp;
+            const double hm = own_V(tm[0]);
+            double tp[4], hp, hsm, hsp, out[4], pres, lam;
             if (s0 >= 0) {
-                const int64_t nb = s0;
+                const int64_t nb = coarse ? (int64_t)(h ? d.nbr[k * 8 + f * 2 + 1] : s0) : (int64_t)s0;
                 const int fo = f ^ 1;
-                const unsigned cmn = d.cmask[(size_t)buf * n + nb];
-#pragma unroll
-                for (int fl = 0; fl < 4; ++fl) {
-                    const double* un = ufield(d, buf, fl, ND) + nb * ND;
-                    if (cmn & (1u << fl)) { tp[fl] = un[0]; continue; }
-                    double s = 0.0;
-#pragma unroll
-                    for (int j = 0; j < ND1; ++j) s += tb.Bm[al][j] * un[face_node<ND1>(fo, j)];
-                    tp[fl] = s;
-                }
+                face_trace<ND1>(ufield(d, buf, 0, ND) + nb * ND, (size_t)n * ND,
+                                d.cmask[(size_t)buf * n + nb], fo, fine ? tb.BmH[half] : tb.Bm, al, tp);
                 int ja, jb;
                 face_site_index<NM>(fo, al, ja, jb);
-                double Ap, Vpm;
-                ST::VA(d, tb, nb, SET_MASS, ja, jb, tp[0], hp, Ap);
-                ST::VA(d, tb, nb, SET_MASS, ja, jb, tm[0], Vpm, Ap); // V+(zeta-)
-                ST::VA(d, tb, k, SET_MASS, ia, ib, tp[0], Vmp, Am);  // V-(zeta+)
-                hsm = fmin(hm, Vpm);
-                hsp = fmin(hp, Vmp);
-                // canonical side order: the lower cell index is side A
-                double out[4], pres, lam;
+                auto nb_V = [&](double eta) {
+                    double V, A;
+                    if (fine) ST::VA_half(d, nb, fo, half, al, eta, V, A);
+                    else ST::VA(d, tb, nb, SET_MASS, ja, jb, eta, V, A);
+                    return V;
+                };
+                hp = nb_V(tp[0]);
+                hsm = fmin(hm, nb_V(tm[0]));  // min(V-(zeta-), V+(zeta-))
+                hsp = fmin(hp, own_V(tp[0])); // min(V+(zeta+), V-(zeta+))
+                // canonical side order: the lower cell index is side A, so both
+                // cells of the face compute bit-identical fluxes
                 const bool own_first = k < nb;
                 if (own_first)
                     rusanov(tm[1], tm[2], tm[3], hm, hsm, tp[1], tp[2], tp[3], hp, hsp, nx, ny, g, eps,
@@ -355,15 +412,13 @@ __global__ void __launch_bounds__(TPB)
                     rusanov(tp[1], tp[2], tp[3], hp, hsp, tm[1], tm[2], tm[3], hm, hsm, -nx, -ny, g,
                             eps, out, pres, lam);
                 const double sg = own_first ? 1.0 : -1.0;
-                // pressure vector g {{h*}} (h*A - h*B)/2 n_A is the same for both sides
+                // the pressure vector g {{h*}} (h*A - h*B)/2 n_A is the same for both sides
                 const double pnx = own_first ? pres * nx : pres * (-nx);
                 const double pny = own_first ? pres * ny : pres * (-ny);
-                const double wl = L * tb.wm[al];
-                fh[0 * 4 * NM + lane] = wl * sg * out[0];
-                fh[1 * 4 * NM + lane] = wl * (sg * out[1] - pnx);
-                fh[2 * 4 * NM + lane] = wl * (sg * out[2] - pny);
-                fh[3 * 4 * NM + lane] = wl * sg * out[3];
-                dtl = J / (fmax(lam, 1e-12) * L);
+                out[0] *= sg;
+                out[1] = sg * out[1] - pnx;
+                out[2] = sg * out[2] - pny;
+                out[3] *= sg;
             } else {
                 const int tag = -1 - s0;
                 tp[0] = tm[0]; tp[1] = tm[1]; tp[2] = tm[2]; tp[3] = tm[3];
@@ -374,20 +429,18 @@ __global__ void __launch_bounds__(TPB)
                     tp[1] = tm[1] - 2.0 * qn * nx;
                     tp[2] = tm[2] - 2.0 * qn * ny;
                 }
-                double Ap;
-                ST::VA(d, tb, k, SET_MASS, ia, ib, tp[0], hp, Ap);
-                hsm = hm;           // min(V-(zeta-), V-(zeta-)) with the same operator
+                hp = own_V(tp[0]); // ghost: same sub-grid operator
+                hsm = hm;
                 hsp = hp;
-                double out[4], pres, lam;
                 rusanov(tm[1], tm[2], tm[3], hm, hsm, tp[1], tp[2], tp[3], hp, hsp, nx, ny, g, eps, out,
                         pres, lam);
-                const double wl = L * tb.wm[al];
-                fh[0 * 4 * NM + lane] = wl * out[0];
-                fh[1 * 4 * NM + lane] = wl * (out[1] - pres * nx);
-                fh[2 * 4 * NM + lane] = wl * (out[2] - pres * ny);
-                fh[3 * 4 * NM + lane] = wl * out[3];
-                dtl = J / (fmax(lam, 1e-12) * L);
+                out[1] -= pres * nx;
+                out[2] -= pres * ny;
             }
+            const double wl = L * tb.wm[al];
+#pragma unroll
+            for (int cf = 0; cf < 4; ++cf) fh[((cf * 4 + f) * 2 + h) * NM + al] = wl * out[cf];
+            dtl = fmin(dtl, J / (fmax(lam, 1e-12) * L));
         }
         if (want_dt) {
             const double m = warp_min(dtl);
@@ -398,16 +451,21 @@ __global__ void __launch_bounds__(TPB)
         for (int i = lane; i < 4 * ND; i += 32) {
             const int cf = i / ND, j = i % ND, a = j % ND1, b = j / ND1;
             double s = 0.0;
-            if (a == 0)
-                for (int al = 0; al < NM; ++al) s += tb.Bm[al][b] * fh[cf * 4 * NM + 0 * NM + al];
-            if (a == ND1 - 1)
-                for (int al = 0; al < NM; ++al) s += tb.Bm[al][b] * fh[cf * 4 * NM + 1 * NM + al];
-            if (b == 0)
-                for (int al = 0; al < NM; ++al) s += tb.Bm[al][a] * fh[cf * 4 * NM + 2 * NM + al];
-            if (b == ND1 - 1)
-                for (int al = 0; al < NM; ++al) s += tb.Bm[al][a] * fh[cf * 4 * NM + 3 * NM + al];
-            const int oc = cf == 0 ? 0 : cf == 1 ? 1 : cf == 2 ? 2 : 3;
-            rs[oc * ND + j] -= s;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const bool on = (f == 0 && a == 0) || (f == 1 && a == ND1 - 1) || (f == 2 && b == 0) ||
+                                (f == 3 && b == ND1 - 1);
+                if (!on) continue;
+                const int tn = f < 2 ? b : a; // tangential node index along the face
+                const double* fp = fh + (cf * 4 + f) * 2 * NM;
+                if ((fi[f] & 3) == FI_COARSE) {
+                    for (int al = 0; al < NM; ++al)
+                        s += tb.BmH[0][al][tn] * fp[al] + tb.BmH[1][al][tn] * fp[NM + al];
+                } else {
+                    for (int al = 0; al < NM; ++al) s += tb.Bm[al][tn] * fp[al];
+                }
+            }
+            rs[cf * ND + j] -= s;
         }
         __syncwarp();
         for (int i = lane; i < 6 * ND; i += 32)

@@ -270,6 +270,92 @@ def test_full_size_tidal_beach_sampled_residual():
 
 
 # ----------------------------------------------------------------------------
+# 2:1 non-conforming forests (hanging faces), pixel counts 32/16/8 per level
+# ----------------------------------------------------------------------------
+def small_lagoon(degree=1, levels=3):
+    return W.lagoon(nx0=32, ny0=16, pix0=8, degree=degree, levels=levels,
+                    band=(5000.0, 2500.0))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_residual_forest_random_state(degree, mode):
+    wl = randomize(small_lagoon(degree), amp_q=0.3, amp_z=0.2)
+    wl.subgrid_mode = mode
+    assert (wl.mesh.nbr[:, :, 1] >= 0).sum() > 0
+    ctx, ora = pair(wl)
+    check_residual(ctx, ora, 3000.0)
+
+
+def test_forest_lake_at_rest_and_steps():
+    wl = small_lagoon(2)
+    wl.boundaries = []
+    ora = Oracle.from_workload(wl)
+    z = ora.lake_at_rest(0.0)
+    zero = np.zeros_like(z)
+    wl.zeta, wl.qx, wl.qy, wl.c = z, zero, zero.copy(), np.ones_like(z)
+    ctx = swdg.Context.from_workload(wl)
+    for k, v in ctx.residual(0.0).items():
+        assert np.abs(v).max() < 1e-9, k
+    ctx.step(10, -1.0, 0.0)
+    zg, qxg, qyg, _ = ctx.get_state()
+    assert np.abs(zg - z).max() < 1e-13 and np.abs(qxg).max() < 1e-13
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+def test_forest_tidal_steps(degree):
+    wl = small_lagoon(degree)
+    Xn, Yn = W.nodal_coordinates(wl.mesh, degree)
+    wl.zeta = 0.3 * np.exp(-((Xn - 20000.0) ** 2 + (Yn - 12000.0) ** 2) / 4000.0 ** 2)
+    ctx, ora = pair(wl)
+    d0 = ctx.diagnostics()
+    tg = ctx.step(15, -1.0, 2000.0)
+    to = ora.step(15, -1.0, 2000.0)
+    assert abs(tg - to) <= 1e-10 * to
+    check_state(ctx, ora)
+    assert ctx.diagnostics()["positivity_violations"] == 0
+
+
+def test_forest_vortex_steps_match():
+    from helpers import Vortex
+    v = Vortex()
+    N = 10
+    mesh, _ = W.forest_mesh(2 * N, N, v.Lx, v.Ly, 2, lambda l, x, y, hx, hy: np.abs(y - 0.5) < 0.12,
+                            periodic=(True, True))
+    ras = W.Raster(np.full((N * 8, 2 * N * 8), v.h0), 0.0, 0.0, v.Lx / (2 * N * 8), v.Ly / (N * 8))
+    X, Y = W.nodal_coordinates(mesh, 2)
+    h, u, w = v(X, Y, 0.0)
+    wl = W.Workload("vortex-forest", 2, mesh, ras, h - v.h0, h * u, h * w, np.ones_like(h),
+                    tableau=1, cfl=0.1, eps_vel=1e-3, h_lim=1e-3)
+    ctx, ora = pair(wl)
+    ctx.step(30, -1.0, 0.0)
+    ora.step(30, -1.0, 0.0)
+    check_state(ctx, ora)
+
+
+def test_full_size_lagoon_sampled_residual():
+    """the 50 km x 30 km lagoon forest (about 200k cells, r = 2) at full size:
+    the oracle evaluates a sample of cells one by one, hanging ones included"""
+    wl = W.lagoon()
+    Xn, Yn = W.nodal_coordinates(wl.mesh, 2)
+    wl.zeta = 0.4 * np.sin(Xn / 3000.0) * np.cos(Yn / 2000.0)
+    wl.qx = 0.2 * np.cos(Yn / 4000.0)
+    ctx = swdg.Context.from_workload(wl)
+    ora = Oracle.from_workload(wl)
+    rg = ctx.residual(5000.0)
+    rng = np.random.default_rng(9)
+    hang = np.where((wl.mesh.nbr[:, :, 1] >= 0).any(axis=1))[0]
+    fine = np.where((wl.level == 2))[0]
+    cells = np.unique(np.concatenate([rng.choice(wl.mesh.n, 150, replace=False),
+                                      rng.choice(hang, 100, replace=False),
+                                      rng.choice(fine, 50, replace=False)]))
+    ro = ora.residual(5000.0, cells=cells)
+    scale = max(float(np.abs(v).max()) for v in ro.values())
+    for k in ro:
+        assert rel_inf(rg[k][cells], ro[k], floor=1e-3 * scale) <= RES_TOL, k
+
+
+# ----------------------------------------------------------------------------
 # errors are reported, never trapped
 # ----------------------------------------------------------------------------
 def test_errors_are_reported():
@@ -279,7 +365,7 @@ def test_errors_are_reported():
         ctx.set_state(*wl.state())
     assert e.value.code == swdg.SWDG_ESTATE
     bad = wl.mesh.nbr.copy()
-    bad[3, 1, 1] = 5  # a hanging face
+    bad[3, 1, 1] = 5  # a 2:1 face whose fine cells do not fit the coarse face
     with pytest.raises(swdg.SwdgError) as e:
         ctx.upload_mesh(wl.mesh.x0y0, wl.mesh.hxhy, bad)
     assert e.value.code == swdg.SWDG_EINVAL
