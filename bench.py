@@ -57,6 +57,21 @@ def units_per_step(wl):
     return wl.mesh.n * 4 * nd * STAGES
 
 
+# FP64 flops one launch performs per cell on this workload: active-lane
+# 2 DFMA + DMUL + DADD counted by ncu (profiles/fp64_ops_tidal_beach_256x256_r3.md).
+# These kernels are bound by the FP64 pipe: GB300's FP64 rate is the roofline.
+FLOPS_PER_CELL = {"step_begin": 2190, "residual": 13000, "stage_2": 10450, "stage_3": 11230,
+                  "final": 8930}
+# DRAM bytes per launch from the same ncu capture; None once the kernel changed
+DRAM_BYTES_PER_LAUNCH = {"residual": 96.1e6, "stage_2": 156.3e6, "stage_3": 248.9e6,
+                         "final": 254.0e6, "step_begin": 59.3e6}
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
+
+
+def slot_kind(slot):
+    return "residual" if slot.startswith("residual") else slot
+
+
 def algorithmic_bytes_per_cell(kernel, r=3, P=16, pix_bytes=4, nres=3):
     """Bytes one launch must move per cell (model of the design notes):
     residual: own state 4 nd f64 in, 6 nd f64 out, the pixel tile, geometry;
@@ -241,13 +256,28 @@ def run_gpu(args, rank, world, local):
     nprof = max(2, min(args.steps, 5))
     per_launch = {SLOTS[i]: kms[i] / nprof for i in range(len(SLOTS)) if kms[i] > 0}
     total = sum(per_launch.values())
-    dom = max(per_launch, key=per_launch.get)
+    # the dominant kernel: the kernel function with the largest share of the step
+    share = {"k_residual": sum(v for k, v in per_launch.items() if k.startswith("residual")),
+             "k_stage": sum(v for k, v in per_launch.items() if k.startswith("stage") or k == "final"),
+             "k_step_begin": per_launch.get("step_begin", 0.0)}
+    dom_fn = max(share, key=share.get)
+    slots = [k for k in per_launch if (dom_fn == "k_residual" and k.startswith("residual")) or
+             (dom_fn == "k_stage" and (k.startswith("stage") or k == "final")) or
+             (dom_fn == "k_step_begin" and k == "step_begin")]
+    avg_ms = sum(per_launch[k] for k in slots) / len(slots)
+    flops = sum(FLOPS_PER_CELL[slot_kind(k)] for k in slots) / len(slots) * wl.mesh.n
+    ach = flops / (avg_ms / 1e3) / 1e12
     pk, src = peaks()
-    bpc = algorithmic_bytes_per_cell(dom, nres=STAGES)
-    ach = bpc * wl.mesh.n / (per_launch[dom] / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm_gbs"],
-            "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
-            "peak_source": src, "share": per_launch[dom] / total,
+    bpc = algorithmic_bytes_per_cell(slots[0], nres=STAGES)
+    hbm_ach = bpc * wl.mesh.n / (avg_ms / 1e3) / 1e9
+    traffic = [DRAM_BYTES_PER_LAUNCH.get(slot_kind(k)) for k in slots]
+    roof = {"bound": "alu", "kernel": dom_fn, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+            "traffic": (sum(traffic) / len(traffic)) if all(x is not None for x in traffic) else None,
+            "peak_source": "FP64 pipe, recipe nominal 1.25 TFLOP/s (probe 1.19-1.26)",
+            "flops_per_launch": flops, "avg_launch_ms": avg_ms, "share": share[dom_fn] / total,
+            "hbm_view": {"achieved_gbs": hbm_ach, "peak_gbs": pk["hbm_gbs"],
+                         "frac": hbm_ach / pk["hbm_gbs"], "peak_source": src},
             "per_launch_ms": {k: round(v, 4) for k, v in per_launch.items()}}
 
     # end to end: host state in, one step, host state out, every step

@@ -41,7 +41,7 @@ struct swdg_ctx {
     Dev d{};
     int grid = 1;
     // device allocations
-    double *x0y0 = nullptr, *hxhy = nullptr, *manning = nullptr, *U = nullptr, *res = nullptr,
+    double *x0y0 = nullptr, *hxhy = nullptr, *ihxhy = nullptr, *manning = nullptr, *U = nullptr, *res = nullptr,
            *llin = nullptr, *HN = nullptr, *CN = nullptr, *HNbar = nullptr, *CNbar = nullptr,
            *zpts = nullptr, *zmax = nullptr, *zmin = nullptr, *zabs = nullptr, *diag = nullptr;
     int32_t* nbr = nullptr;
@@ -607,10 +607,10 @@ int swdg_create(const swdg_config* cfg, swdg_ctx** out) {
 }
 
 static void free_mesh(swdg_ctx* c) {
-    cudaFree(c->x0y0); cudaFree(c->hxhy); cudaFree(c->manning); cudaFree(c->U); cudaFree(c->res);
+    cudaFree(c->x0y0); cudaFree(c->hxhy); cudaFree(c->ihxhy); cudaFree(c->manning); cudaFree(c->U); cudaFree(c->res);
     cudaFree(c->llin); cudaFree(c->HN); cudaFree(c->CN); cudaFree(c->HNbar); cudaFree(c->CNbar);
     cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->diag); cudaFree(c->finfo);
-    c->x0y0 = c->hxhy = c->manning = c->U = c->res = c->llin = c->HN = c->CN = c->HNbar =
+    c->x0y0 = c->hxhy = c->ihxhy = c->manning = c->U = c->res = c->llin = c->HN = c->CN = c->HNbar =
         c->CNbar = c->diag = nullptr;
     c->nbr = nullptr;
     c->cmask = c->flag = c->finfo = nullptr;
@@ -720,6 +720,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     const size_t nd = ctx->nd;
     CK(cudaMalloc(&ctx->x0y0, 2 * n * sizeof(double)));
     CK(cudaMalloc(&ctx->hxhy, 2 * n * sizeof(double)));
+    CK(cudaMalloc(&ctx->ihxhy, 2 * n * sizeof(double)));
     CK(cudaMalloc(&ctx->nbr, 8 * n * sizeof(int32_t)));
     CK(cudaMalloc(&ctx->finfo, 4 * n));
     CK(cudaMalloc(&ctx->manning, n * sizeof(double)));
@@ -737,6 +738,10 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     CK(cudaMemcpyAsync(ctx->hxhy, hxhy, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->nbr, nbr, 8 * n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->finfo, fi.data(), 4 * n, cudaMemcpyHostToDevice, ctx->st));
+    std::vector<double> inv(2 * n);
+    for (int64_t i = 0; i < 2 * n; ++i) inv[i] = 1.0 / hxhy[i];
+    CK(cudaMemcpyAsync(ctx->ihxhy, inv.data(), 2 * n * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->st));
     CK(cudaMemsetAsync(ctx->manning, 0, n * sizeof(double), ctx->st));
     CK(cudaMemsetAsync(ctx->llin, 0, 2 * n * nd * sizeof(double), ctx->st));
     CK(cudaMemsetAsync(ctx->flag, ctx->R, n, ctx->st));
@@ -749,6 +754,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     d.n = n;
     d.x0y0 = ctx->x0y0;
     d.hxhy = ctx->hxhy;
+    d.ihxhy = ctx->ihxhy;
     d.nbr = ctx->nbr;
     d.finfo = ctx->finfo;
     d.manning = ctx->manning;
@@ -1008,15 +1014,15 @@ int swdg_cfl_dt(swdg_ctx* ctx, double t, double* dt) {
     if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "cfl_dt: no state");
     int rc = put_time(ctx, t, -1.0);
     if (rc) return rc;
-    ctx->pin[2] = INFINITY;
-    CK(cudaMemcpyAsync(&ctx->sc->dtmin, &ctx->pin[2], sizeof(double), cudaMemcpyHostToDevice,
+    ctx->pin[2] = 0.0;
+    CK(cudaMemcpyAsync(&ctx->sc->rmax, &ctx->pin[2], sizeof(double), cudaMemcpyHostToDevice,
                        ctx->st));
     ctx->L.residual(ctx->d, ctx->tb, 0, 0, 0.0, 1, ctx->grid, ctx->st);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(&ctx->pin[3], &ctx->sc->dtmin, sizeof(double), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(&ctx->pin[3], &ctx->sc->rmax, sizeof(double), cudaMemcpyDeviceToHost,
                        ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    *dt = ctx->cfg.cfl * ctx->pin[3];
+    *dt = ctx->cfg.cfl / ctx->pin[3];
     return SWDG_OK;
 }
 
@@ -1229,7 +1235,7 @@ __global__ void k_noalloc_begin(Scalars* sc, double t) {
     sc->t = t;
     sc->fixed_dt = -1.0;
     sc->dt_last = 0.0;
-    sc->dtmin = 0x7ff0000000000000ull; // +inf
+    sc->rmax = 0ull;
     sc->maxits = 0;
     sc->viol = 0;
     sc->fallback = 0;
@@ -1258,7 +1264,7 @@ __global__ void k_noalloc_check_mesh(const double* hxhy, const int32_t* nbr, int
 }
 
 __global__ void k_noalloc_end(const Scalars* sc, double cfl, double* dt_out) {
-    *dt_out = cfl * __longlong_as_double(sc->dtmin);
+    *dt_out = cfl / __longlong_as_double(sc->rmax);
 }
 
 static int noalloc_fail(char* err, int err_len, int code, const char* msg) {

@@ -75,7 +75,7 @@ struct Scalars {
     double t;                 // time at the start of the current step
     double fixed_dt;          // >= 0: fixed step, < 0: CFL
     double dt_last;
-    unsigned long long dtmin; // bits of min J/(lambda l) (positive double)
+    unsigned long long rmax;  // bits of max lambda l_Gamma / J_K (non-negative double)
     int maxits, viol, fallback, status;
 };
 
@@ -83,6 +83,7 @@ struct Dev {
     int64_t n;
     const double* x0y0;
     const double* hxhy;
+    const double* ihxhy; // 1/hx, 1/hy per cell (null: computed in the kernel)
     const int32_t* nbr;
     const void* tiles;
     const int64_t* tile_off; // first pixel of each cell's tile (null: k P^2)
@@ -142,7 +143,8 @@ __device__ __forceinline__ double* rfield(const Dev& d, int stage, int f, int nd
 }
 
 __device__ __forceinline__ double get_dt(const Dev& d) {
-    return d.sc->fixed_dt >= 0.0 ? d.sc->fixed_dt : d.cfl * __longlong_as_double(d.sc->dtmin);
+    // dt = cfl min J/(lambda l) = cfl / max(lambda l / J), Eq. deltat_fe
+    return d.sc->fixed_dt >= 0.0 ? d.sc->fixed_dt : d.cfl / __longlong_as_double(d.sc->rmax);
 }
 
 // desingularised velocity factor u = f q, Eq. velocity

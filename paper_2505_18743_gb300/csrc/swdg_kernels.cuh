@@ -226,9 +226,9 @@ __device__ __forceinline__ void rusanov(double qxA, double qyA, double cA, doubl
     lam = l;
 }
 
-__device__ __forceinline__ void atomic_min_pos(unsigned long long* addr, double v) {
-    // positive doubles order like their bit patterns
-    atomicMin(addr, (unsigned long long)__double_as_longlong(v));
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
 // ---------------------------------------------------------------------------
@@ -268,6 +268,8 @@ __global__ void __launch_bounds__(TPB)
             su[i] = ufield(d, buf, i / ND, ND)[k * ND + (i % ND)];
         const unsigned cm = d.cmask[(size_t)buf * n + k];
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
+        const double ihx = d.ihxhy ? d.ihxhy[2 * k] : 1.0 / hx;
+        const double ihy = d.ihxhy ? d.ihxhy[2 * k + 1] : 1.0 / hy;
         const double man = d.manning[k];
         __syncwarp();
         // x-contraction of the four fields (values) and of zeta (d/dxi)
@@ -303,14 +305,14 @@ __global__ void __launch_bounds__(TPB)
             if (cm & 2u) qx = su[ND];
             if (cm & 4u) qy = su[2 * ND];
             if (cm & 8u) c = su[3 * ND];
-            zx /= hx;
-            zy /= hy;
+            zx *= ihx;
+            zy *= ihy;
             double h, A;
             ST::VA(d, tb, k, SET_VOL, al, be, z, h, A);
             const double fv = vel_factor(h, eps);
             const double ux = fv * qx, uy = fv * qy;
             const double gam = gamma_manning(man, h, qx, qy, g, eps);
-            const double w = J * tb.wv[al] * tb.wv[be], wx = w / hx, wy = w / hy;
+            const double w = J * tb.wv[al] * tb.wv[be], wx = w * ihx, wy = w * ihy;
             X[0 * NVP + p] = wx * qx;
             X[1 * NVP + p] = wy * qy;
             X[2 * NVP + p] = wx * qx * ux;
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(TPB)
         }
         // faces: one (sub)face point per lane; a coarse cell integrates each
         // 2:1 face over the GLL points of both fine halves
-        double dtl = INFINITY;
+        double dtl = 0.0;
         unsigned char fi[4];
         int base[5];
         base[0] = 0;
@@ -440,11 +442,12 @@ __global__ void __launch_bounds__(TPB)
             const double wl = L * tb.wm[al];
 #pragma unroll
             for (int cf = 0; cf < 4; ++cf) fh[((cf * 4 + f) * 2 + h) * NM + al] = wl * out[cf];
-            dtl = fmin(dtl, J / (fmax(lam, 1e-12) * L));
+            // lambda l / J for the positivity step (l = L, J = hx hy)
+            dtl = fmax(dtl, fmax(lam, 1e-12) * ((f < 2) ? ihx : ihy) * (coarse ? 0.5 : 1.0));
         }
         if (want_dt) {
-            const double m = warp_min(dtl);
-            if (lane == 0) atomic_min_pos(&d.sc->dtmin, m);
+            const double m = warp_max(dtl);
+            if (lane == 0) atomic_max_pos(&d.sc->rmax, m);
         }
         __syncwarp();
         // lift the face fluxes onto the nodes of each face
@@ -542,7 +545,7 @@ __global__ void __launch_bounds__(TPB)
     double* out = pg + 3 * NGP;  // [2][ND]
     const int64_t n = d.n;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        d.sc->dtmin = 0x7ff0000000000000ull; // +inf
+        d.sc->rmax = 0ull;
         d.sc->maxits = 0;
     }
     for (int64_t k = (int64_t)blockIdx.x * WPB + warp; k < n; k += (int64_t)gridDim.x * WPB) {
@@ -669,7 +672,9 @@ template <int R>
 constexpr int stage_smem() {
     using S = Sz<R>;
     return 4 * S::ND + 5 * S::ND + 3 * S::NMP + 2 * S::NM * S::NM + S::ND1 * S::ND1 * S::NM +
-           S::ND * S::ND + 6 * S::NGP + 4 * S::ND + S::ND;
+           S::ND * S::ND + 6 * S::NGP + 4 * S::ND + S::ND +
+           // mixed-precision solve: x, r (ND), q (NMP), float M, Y, inv, r
+           2 * S::ND + S::NMP + (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 2 * S::ND + 1) / 2 + 1;
 }
 
 // Cholesky of the SPD matrix M (ND x ND, row-major, lower part used) on a
@@ -715,6 +720,78 @@ __device__ bool chol_solve(double* M, double* b, double* inv, int lane) {
     return true;
 }
 
+// FP32 Cholesky factorisation (lower part of M, reciprocal pivots in inv);
+// returns false on a non-positive pivot
+template <int ND>
+__device__ bool chol_factor_f(float* M, float* inv, int lane) {
+    for (int j = 0; j < ND; ++j) {
+        __syncwarp();
+        const float djj = M[j * ND + j];
+        if (!(djj > 0.0f)) return false;
+        const float ljj = sqrtf(djj);
+        const float r = 1.0f / ljj;
+        __syncwarp();
+        for (int i = j + 1 + lane; i < ND; i += 32) M[i * ND + j] *= r;
+        if (lane == 0) {
+            M[j * ND + j] = ljj;
+            inv[j] = r;
+        }
+        __syncwarp();
+        const int m = ND - j - 1;
+        for (int idx = lane; idx < m * m; idx += 32) {
+            const int i = j + 1 + idx / m, l = j + 1 + idx % m;
+            if (l <= i) M[i * ND + l] -= M[i * ND + j] * M[l * ND + j];
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// (L L^T)^-1 b in FP32 with the factor of chol_factor_f, in place
+template <int ND>
+__device__ void chol_subst_f(const float* M, const float* inv, float* b, int lane) {
+    for (int j = 0; j < ND; ++j) {
+        const float yj = b[j] * inv[j];
+        __syncwarp();
+        for (int i = j + 1 + lane; i < ND; i += 32) b[i] -= M[i * ND + j] * yj;
+        if (lane == 0) b[j] = yj;
+        __syncwarp();
+    }
+    for (int j = ND - 1; j >= 0; --j) {
+        const float xj = b[j] * inv[j];
+        __syncwarp();
+        for (int i = lane; i < j; i += 32) b[i] -= M[j * ND + i] * xj;
+        if (lane == 0) b[j] = xj;
+        __syncwarp();
+    }
+}
+
+// FP32 copy of M_(a,b),(c,d) = sum c_{al,be} Bm[al][a] Bm[al][c] Bm[be][b] Bm[be][d]
+template <int ND1, int NM>
+__device__ __forceinline__ void assemble_mass_f(const Tables& tb, const double* cw, float* Y,
+                                                float* M, int lane) {
+    constexpr int ND = ND1 * ND1;
+    for (int i = lane; i < ND1 * ND1 * NM; i += 32) {
+        const int a = i / (ND1 * NM), r_ = i % (ND1 * NM), c = r_ / NM, be = r_ % NM;
+        float s = 0.0f;
+#pragma unroll
+        for (int al = 0; al < NM; ++al)
+            s += (float)cw[al + NM * be] * (float)tb.Bm[al][a] * (float)tb.Bm[al][c];
+        Y[i] = s;
+    }
+    __syncwarp();
+    for (int i = lane; i < ND * ND; i += 32) {
+        const int r_ = i / ND, s_ = i % ND;
+        const int a = r_ % ND1, b = r_ / ND1, c = s_ % ND1, dd = s_ / ND1;
+        float s = 0.0f;
+#pragma unroll
+        for (int be = 0; be < NM; ++be)
+            s += Y[(a * ND1 + c) * NM + be] * (float)tb.Bm[be][b] * (float)tb.Bm[be][dd];
+        M[i] = s;
+    }
+    __syncwarp();
+}
+
 // M_(a,b),(c,d) = sum_{al,be} c_{al,be} Bm[al][a] Bm[al][c] Bm[be][b] Bm[be][d]
 template <int ND1, int NM>
 __device__ __forceinline__ void assemble_mass(const Tables& tb, const double* cw, double* Y,
@@ -740,6 +817,66 @@ __device__ __forceinline__ void assemble_mass(const Tables& tb, const double* cw
     __syncwarp();
 }
 
+// Solve H x = b for the depth-weighted mass matrix H = B^T diag(cw) B (the
+// tracer matrix of Eq. mass_matrix_concentration, or the masked Jacobian of
+// Eq. mass_matrix) by mixed-precision iterative refinement: H is assembled and
+// factored in FP32, each correction is solved in FP32, and the residual
+// b - H x is formed in FP64 matrix-free by sum factorisation.  If the
+// corrections do not fall below 1e-15 of x within 6 sweeps (an ill-conditioned
+// near-dry cell), the FP64 Cholesky decides.  x (FP64, in place of b on
+// return).  Scratch: Mf, Yf (float), r, t (ND doubles), q (NMP doubles),
+// tmp (2 NM NM doubles), M, Y (double, fallback).
+template <int ND1, int NM>
+__device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, float* Mf,
+                                 float* Yf, float* invf, float* rf, double* x, double* r,
+                                 double* q, double* tmp, double* M, double* Y, double* inv,
+                                 int lane) {
+    constexpr int ND = ND1 * ND1, NMP = NM * NM;
+    assemble_mass_f<ND1, NM>(tb, cw, Yf, Mf, lane);
+    bool ok = chol_factor_f<ND>(Mf, invf, lane);
+    if (ok) {
+        for (int i = lane; i < ND; i += 32) {
+            x[i] = 0.0;
+            r[i] = b[i];
+        }
+        __syncwarp();
+        ok = false;
+        for (int sweep = 0; sweep < 6; ++sweep) {
+            for (int i = lane; i < ND; i += 32) rf[i] = (float)r[i];
+            __syncwarp();
+            chol_subst_f<ND>(Mf, invf, rf, lane);
+            double dmax = 0.0, xmax = 0.0;
+            for (int i = lane; i < ND; i += 32) {
+                x[i] += (double)rf[i];
+                dmax = fmax(dmax, fabs((double)rf[i]));
+                xmax = fmax(xmax, fabs(x[i]));
+            }
+            dmax = warp_max(dmax);
+            xmax = warp_max(xmax);
+            if (!(dmax <= 1e-15 * xmax) && !(dmax == 0.0)) {
+                // r = b - H x, H x = B^T (cw * (B x))
+                __syncwarp();
+                tens_interp<ND1, NM>(tb.Bm, x, tmp, q, lane);
+                for (int p = lane; p < NMP; p += 32) q[p] *= cw[p];
+                __syncwarp();
+                tens_test<ND1, NM>(tb.Bm, q, tmp, r, lane);
+                for (int i = lane; i < ND; i += 32) r[i] = b[i] - r[i];
+                __syncwarp();
+            } else {
+                ok = true;
+                break;
+            }
+        }
+    }
+    if (ok) {
+        for (int i = lane; i < ND; i += 32) b[i] = x[i];
+        __syncwarp();
+        return true;
+    }
+    assemble_mass<ND1, NM>(tb, cw, Y, M, lane);
+    return chol_solve<ND>(M, b, inv, lane);
+}
+
 template <int R, typename Pix, int MODE>
 __global__ void __launch_bounds__(TPB)
     k_stage(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, const StageArgs sa) {
@@ -762,6 +899,13 @@ __global__ void __launch_bounds__(TPB)
     double* pg = M + ND * ND;                   // [6][NGP]
     double* o = pg + 6 * NGP;                   // [4][ND]
     double* pinv = o + 4 * ND;                  // [ND] reciprocal Cholesky pivots
+    double* xs = pinv + ND;                     // [ND] refinement iterate
+    double* rs = xs + ND;                       // [ND] refinement residual
+    double* qs = rs + ND;                       // [NMP]
+    float* Mf = (float*)(qs + NMP);             // [ND ND]
+    float* Yf = Mf + ND * ND;                   // [ND1 ND1 NM]
+    float* invf = Yf + ND1 * ND1 * NM;          // [ND]
+    float* rf = invf + ND;                      // [ND]
     const int64_t n = d.n;
     const double dt = get_dt(d);
     const double g = d.g, eps = d.eps;
@@ -837,10 +981,13 @@ __global__ void __launch_bounds__(TPB)
                     // M is the constant mass matrix, inverted by its tensor factors
                     kron_apply<ND1, false, MXN>(tb.M1inv, o, tmp, o + ND, 1.0 / J, lane);
                 } else {
-                    assemble_mass<ND1, NM>(tb, pA, Y, M, lane);
                     for (int i = lane; i < ND; i += 32) o[ND + i] = o[i];
                     __syncwarp();
-                    if (!chol_solve<ND>(M, o + ND, pinv, lane)) { scalar = true; break; }
+                    if (!solve_mass_mixed<ND1, NM>(tb, pA, o + ND, Mf, Yf, invf, rf, xs, rs, qs, tmp, M,
+                                                   Y, pinv, lane)) {
+                        scalar = true;
+                        break;
+                    }
                 }
                 double inc = 0.0, scale = 0.0;
                 for (int i = lane; i < ND; i += 32) {
@@ -983,13 +1130,13 @@ __global__ void __launch_bounds__(TPB)
                 __syncwarp();
             }
             // tracer: H(zeta^(l)) C = C~ + dt sum a R with the depth-weighted mass matrix
-            assemble_mass<ND1, NM>(tb, pV, Y, M, lane);
             for (int i = lane; i < ND; i += 32) {
                 o[i] = z[i];
                 o[3 * ND + i] = rc[i];
             }
             __syncwarp();
-            chol_solve<ND>(M, o + 3 * ND, pinv, lane);
+            solve_mass_mixed<ND1, NM>(tb, pV, o + 3 * ND, Mf, Yf, invf, rf, xs, rs, qs, tmp, M, Y,
+                                      pinv, lane);
         }
         __syncwarp();
         // write v^(l) and its constant-field mask
