@@ -297,6 +297,41 @@ def run_gpu(args, rank, world, local):
     e2e = {"value": units * e2e_steps * world / el, "unit": "updates/s",
            "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io}
 
+    # FP32-bulk variant on the same workload: same timing, plus its state error
+    # against this FP64 run after the same steps from the same initial state
+    variants = {}
+    if not args.no_variants:
+        ref_state = ctx.get_state()
+        t_ref = t
+        ctx32 = swdg.Context.from_workload(wl, stream=stream.cuda_stream, precision=1)
+        t32 = 0.0
+        for _ in range(args.warmup):
+            t32 = ctx32.step(1, -1.0, t32)
+        torch.cuda.synchronize(dev)
+        s32, e32 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s32.record(stream)
+        t32 = ctx32.step(args.steps, -1.0, t32)
+        e32.record(stream)
+        torch.cuda.synchronize(dev)
+        ms32 = max_over_ranks(s32.elapsed_time(e32), world)
+        # replay the FP64 context's extra profile/e2e steps so both reach the same step count
+        extra = nprof + e2e_steps
+        t32 = ctx32.step(extra, -1.0, t32)
+        st32 = ctx32.get_state()
+        errs = {}
+        for name, a, b in zip(("zeta", "qx", "qy", "c"), st32, ref_state):
+            den = max(float(np.abs(b).max()), 1.0 if name in ("zeta", "c") else 1e-3)
+            errs[name] = float(np.abs(a - b).max()) / den
+        d64, d32 = ctx.diagnostics(), ctx32.diagnostics()
+        variants["fp32_bulk"] = {
+            "value": units * args.steps * world / (ms32 / 1e3), "unit": "updates/s",
+            "ms_per_step": ms32 / args.steps, "dtype": "f64 elevation/sub-grid/solves, f32 bulk",
+            "max_rel_state_err_vs_fp64": errs,
+            "steps_compared": args.warmup + args.steps + extra,
+            "mass_rel_diff_vs_fp64": abs(d32["mass"] - d64["mass"]) / d64["mass"],
+            "time_matches": abs(t32 - t_ref) <= 1e-9 * max(t_ref, 1.0)}
+        ctx32.close()
+
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -305,7 +340,7 @@ def run_gpu(args, rank, world, local):
                        "pixels_per_cell": 256, "stages": STAGES,
                        "l2": "inputs larger than L2 (about 0.5 GB working set), no flush",
                        "parallelism": f"replicas x{world}"},
-            "clocks": clocks, "roofline": roof, "e2e": e2e,
+            "clocks": clocks, "roofline": roof, "e2e": e2e, "variants": variants,
             "gpu_launches": (2 * STAGES + 1) * args.steps}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate()
@@ -323,6 +358,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="swdg", choices=["swdg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     rank, world, local = dist_init(args.gpus)
     if args.impl == "reference":

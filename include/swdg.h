@@ -65,7 +65,13 @@ typedef struct swdg_ctx swdg_ctx;
 
 typedef struct {
     int degree;       /* r in 1..3 (Q_r space of Sec. 3.2) */
-    int precision;    /* 0: FP64 everywhere (the only value accepted by this version) */
+    int precision;    /* 0: FP64 everywhere (the plain method);
+                         1: FP32-bulk -- the momentum, friction and flux arithmetic
+                         of the residual in FP32, while the elevation, the sub-grid
+                         integrals, the hydrostatic reconstruction, the continuity
+                         and tracer test integrals and every stage solve stay FP64
+                         (mass, tracer mass, c = 1 and the lake at rest keep FP64
+                         round-off; other results carry FP32 error) */
     int subgrid_mode; /* 0: S, each quadrature point owns the sub-cell given by the
                          cumulative weights and integrates max(eta+z_b,0) over its
                          pixels; 1: P, z_b sampled at the point by bilinear

@@ -18,11 +18,11 @@
 using namespace swdg;
 
 namespace swdg {
-bool get_launch(int degree, int mode, int pix, Launch* out) {
+bool get_launch(int degree, int mode, int pix, int prec, Launch* out) {
     switch (degree) {
-    case 1: return get_launch_r1(mode, pix, out);
-    case 2: return get_launch_r2(mode, pix, out);
-    case 3: return get_launch_r3(mode, pix, out);
+    case 1: return get_launch_r1(mode, pix, prec, out);
+    case 2: return get_launch_r2(mode, pix, prec, out);
+    case 3: return get_launch_r3(mode, pix, prec, out);
     default: return false;
     }
 }
@@ -254,6 +254,16 @@ static bool build_tables(int R, Tables& tb) {
     if (!invert(nd1, M1, M1i)) return false;
     for (int a = 0; a < nd1; ++a)
         for (int c = 0; c < nd1; ++c) tb.M1inv[a][c] = M1i[a * nd1 + c];
+    for (int q = 0; q < MXP; ++q)
+        for (int a = 0; a < MXN; ++a) {
+            tb.BvF[q][a] = (float)tb.Bv[q][a];
+            tb.DvF[q][a] = (float)tb.Dv[q][a];
+            tb.BmF[q][a] = (float)tb.Bm[q][a];
+            tb.BgF[q][a] = (float)tb.Bg[q][a];
+            tb.BmHF[0][q][a] = (float)tb.BmH[0][q][a];
+            tb.BmHF[1][q][a] = (float)tb.BmH[1][q][a];
+            tb.BginvF[a][q] = (float)tb.Bginv[a][q];
+        }
     return true;
 }
 
@@ -552,7 +562,8 @@ int swdg_create(const swdg_config* cfg, swdg_ctx** out) {
     swdg_ctx* ctx = nullptr;
     if (!cfg || !out) return SWDG_EINVAL;
     *out = nullptr;
-    if (cfg->degree < 1 || cfg->degree > 3 || cfg->precision != 0 || cfg->subgrid_mode < 0 ||
+    if (cfg->degree < 1 || cfg->degree > 3 || cfg->precision < 0 || cfg->precision > 1 ||
+        cfg->subgrid_mode < 0 ||
         cfg->subgrid_mode > 1 || cfg->tableau < 0 || cfg->tableau > 3 || !(cfg->g > 0) ||
         !(cfg->eps_vel > 0) || !(cfg->h_lim >= 0) || !(cfg->eps0 > 0) || !(cfg->cfl > 0) ||
         cfg->newton_max < 1 || !(cfg->newton_tol >= 0))
@@ -898,7 +909,7 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
     }
     cudaFree(ras);
     ctx->pix = dtype == SWDG_PIX_F32 ? 0 : 1;
-    if (!get_launch(ctx->R, ctx->mode, ctx->pix, &ctx->L))
+    if (!get_launch(ctx->R, ctx->mode, ctx->pix, ctx->cfg.precision, &ctx->L))
         return fail(ctx, SWDG_EINVAL, "upload_bathymetry: no kernels for this configuration");
     Dev& d = ctx->d;
     d.tiles = ctx->tiles;
@@ -1314,7 +1325,7 @@ extern "C" int swdg_residual_noalloc(const swdg_config* cfg, int64_t n, const do
     if (!build_tables(cfg->degree, tb) || !build_overlaps(cfg->degree, P, tb, ovh))
         return noalloc_fail(err, err_len, SWDG_EINVAL, "residual_noalloc: table construction failed");
     Launch L{};
-    if (!get_launch(cfg->degree, 0, pix_dtype == SWDG_PIX_F32 ? 0 : 1, &L))
+    if (!get_launch(cfg->degree, 0, pix_dtype == SWDG_PIX_F32 ? 0 : 1, 0, &L))
         return noalloc_fail(err, err_len, SWDG_EINVAL, "residual_noalloc: no kernels for this case");
     Dev d{};
     d.n = n;

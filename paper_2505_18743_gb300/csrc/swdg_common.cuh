@@ -67,6 +67,9 @@ struct Tables {
     double Bginv[MXN][MXP];                     // inverse of Bg
     double M1inv[MXN][MXN];                     // inverse of the 1D GLL mass matrix
     double BmH[2][MXP][MXN];                    // nodal -> fine-face GLL points of half h
+    // FP32 copies for the FP32-bulk kernels
+    float BvF[MXP][MXN], DvF[MXP][MXN], BmF[MXP][MXN], BmHF[2][MXP][MXN], BgF[MXP][MXN];
+    float BginvF[MXN][MXP];
     double xs[MXN];                             // support nodes on [0, 1]
     double xq[3][MXP];                          // nodes of the three point sets on [0, 1]
 };
@@ -147,21 +150,22 @@ __device__ __forceinline__ double get_dt(const Dev& d) {
     return d.sc->fixed_dt >= 0.0 ? d.sc->fixed_dt : d.cfl / __longlong_as_double(d.sc->rmax);
 }
 
-// desingularised velocity factor u = f q, Eq. velocity
-__device__ __forceinline__ double vel_factor(double h, double eps) {
-    if (h <= 0.0) return 0.0;
-    if (h >= eps) return 1.0 / h; // max(h^4, eps^4) = h^4: sqrt(2) h / sqrt(2 h^4) = 1/h
-    double h4 = (h * h) * (h * h), e4 = (eps * eps) * (eps * eps);
-    return sqrt(2.0) * h / sqrt(e4 + h4);
+// desingularised velocity factor u = f q, Eq. velocity (T = double or float)
+template <typename T>
+__device__ __forceinline__ T vel_factor(T h, T eps) {
+    if (h <= T(0)) return T(0);
+    if (h >= eps) return T(1) / h; // max(h^4, eps^4) = h^4: sqrt(2) h / sqrt(2 h^4) = 1/h
+    T h4 = (h * h) * (h * h), e4 = (eps * eps) * (eps * eps);
+    return sqrt(T(2)) * h / sqrt(e4 + h4);
 }
 // Manning coefficient gamma = g n^2 |q| / h_des^(7/3), Eqs. manning, discharge_rhs_implicit
-__device__ __forceinline__ double gamma_manning(double n, double h, double qx, double qy, double g,
-                                                double eps) {
-    if (n == 0.0 || h <= 0.0) return 0.0;
-    double hdes = h; // h_des = h when h >= eps
+template <typename T>
+__device__ __forceinline__ T gamma_manning(T n, T h, T qx, T qy, T g, T eps) {
+    if (n == T(0) || h <= T(0)) return T(0);
+    T hdes = h; // h_des = h when h >= eps
     if (h < eps) {
-        double h4 = (h * h) * (h * h), e4 = (eps * eps) * (eps * eps);
-        hdes = sqrt(e4 + h4) / (sqrt(2.0) * h);
+        T h4 = (h * h) * (h * h), e4 = (eps * eps) * (eps * eps);
+        hdes = sqrt(e4 + h4) / (sqrt(T(2)) * h);
     }
     return g * n * n * sqrt(qx * qx + qy * qy) / (hdes * hdes * cbrt(hdes));
 }

@@ -6,12 +6,12 @@
 
 namespace swdg {
 
-template <int R, typename Pix, int MODE>
+template <int R, typename Pix, int MODE, typename B>
 struct Launchers {
     static void residual(const Dev& d, const Tables& tb, int buf, int stage, double c_stage,
                          int want_dt, int grid, cudaStream_t st) {
-        size_t sm = sizeof(double) * res_smem<R>() * WPB;
-        k_residual<R, Pix, MODE><<<grid, TPB, sm, st>>>(d, tb, buf, stage, c_stage, want_dt);
+        size_t sm = sizeof(double) * res_smem<R, B>() * WPB;
+        k_residual<R, Pix, MODE, B><<<grid, TPB, sm, st>>>(d, tb, buf, stage, c_stage, want_dt);
     }
     static void step_begin(const Dev& d, const Tables& tb, int do_switch, int grid, cudaStream_t st) {
         size_t sm = sizeof(double) * begin_smem<R>() * WPB;
@@ -19,7 +19,7 @@ struct Launchers {
     }
     static void stage(const Dev& d, const Tables& tb, const StageArgs& sa, int grid, cudaStream_t st) {
         size_t sm = sizeof(double) * stage_smem<R>() * WPB;
-        k_stage<R, Pix, MODE><<<grid, TPB, sm, st>>>(d, tb, sa);
+        k_stage<R, Pix, MODE, B><<<grid, TPB, sm, st>>>(d, tb, sa);
     }
     static void masks(const Dev& d, int buf, int grid, cudaStream_t st) {
         k_masks<R><<<grid, TPB, 0, st>>>(d, buf);
@@ -44,13 +44,21 @@ struct Launchers {
     }
 };
 
-template <int R>
-bool get_launch_degree(int mode, int pix, Launch* L) {
-    if (mode == 1) Launchers<R, double, 1>::fill(L);
-    else if (pix == 0) Launchers<R, float, 0>::fill(L);
-    else if (pix == 1) Launchers<R, double, 0>::fill(L);
+template <int R, typename B>
+bool get_launch_prec(int mode, int pix, Launch* L) {
+    if (mode == 1) Launchers<R, double, 1, B>::fill(L);
+    else if (pix == 0) Launchers<R, float, 0, B>::fill(L);
+    else if (pix == 1) Launchers<R, double, 0, B>::fill(L);
     else return false;
     return true;
+}
+
+// precision 0: FP64; 1: FP32-bulk residual arithmetic
+template <int R>
+bool get_launch_degree(int mode, int pix, int prec, Launch* L) {
+    if (prec == 0) return get_launch_prec<R, double>(mode, pix, L);
+    if (prec == 1) return get_launch_prec<R, float>(mode, pix, L);
+    return false;
 }
 
 } // namespace swdg

@@ -18,12 +18,12 @@ constexpr int TPB = 32 * WPB;
 // small tensor contractions on a warp (all arrays in shared memory, x fastest)
 // ---------------------------------------------------------------------------
 // out[q1 NO + q0] = sum_b B[q1][b] sum_a B[q0][a] in[b NI + a]
-template <int NI, int NO>
-__device__ __forceinline__ void tens_interp(const double (*B)[MXN], const double* in, double* tmp,
-                                            double* out, int lane) {
+template <int NI, int NO, typename T = double>
+__device__ __forceinline__ void tens_interp(const T (*B)[MXN], const T* in, T* tmp, T* out,
+                                            int lane) {
     for (int i = lane; i < NI * NO; i += 32) {
         int b = i / NO, q0 = i % NO;
-        double s = 0.0;
+        T s = T(0);
 #pragma unroll
         for (int a = 0; a < NI; ++a) s += B[q0][a] * in[b * NI + a];
         tmp[i] = s;
@@ -31,7 +31,7 @@ __device__ __forceinline__ void tens_interp(const double (*B)[MXN], const double
     __syncwarp();
     for (int i = lane; i < NO * NO; i += 32) {
         int q1 = i / NO, q0 = i % NO;
-        double s = 0.0;
+        T s = T(0);
 #pragma unroll
         for (int b = 0; b < NI; ++b) s += B[q1][b] * tmp[b * NO + q0];
         out[i] = s;
@@ -40,12 +40,12 @@ __device__ __forceinline__ void tens_interp(const double (*B)[MXN], const double
 }
 
 // out[b NI + a] = sum_q1 B[q1][b] sum_q0 B[q0][a] in[q1 NO + q0]   (transpose)
-template <int NI, int NO>
-__device__ __forceinline__ void tens_test(const double (*B)[MXN], const double* in, double* tmp,
-                                          double* out, int lane) {
+template <int NI, int NO, typename T = double>
+__device__ __forceinline__ void tens_test(const T (*B)[MXN], const T* in, T* tmp, T* out,
+                                          int lane) {
     for (int i = lane; i < NO * NI; i += 32) {
         int q1 = i / NI, a = i % NI;
-        double s = 0.0;
+        T s = T(0);
 #pragma unroll
         for (int q0 = 0; q0 < NO; ++q0) s += B[q0][a] * in[q1 * NO + q0];
         tmp[i] = s;
@@ -53,7 +53,7 @@ __device__ __forceinline__ void tens_test(const double (*B)[MXN], const double* 
     __syncwarp();
     for (int i = lane; i < NI * NI; i += 32) {
         int b = i / NI, a = i % NI;
-        double s = 0.0;
+        T s = T(0);
 #pragma unroll
         for (int q1 = 0; q1 < NO; ++q1) s += B[q1][b] * tmp[q1 * NI + a];
         out[i] = s;
@@ -62,12 +62,12 @@ __device__ __forceinline__ void tens_test(const double (*B)[MXN], const double* 
 }
 
 // out[b N + a] = scale * sum_d C(b,d) sum_c C(a,c) in[d N + c], C(i,j) = T ? M[j][i] : M[i][j]
-template <int N, bool T, int LD>
-__device__ __forceinline__ void kron_apply(const double (*M)[LD], const double* in, double* tmp,
-                                           double* out, double scale, int lane) {
+template <int N, bool T, int LD, typename E = double>
+__device__ __forceinline__ void kron_apply(const E (*M)[LD], const E* in, E* tmp, E* out, E scale,
+                                           int lane) {
     for (int i = lane; i < N * N; i += 32) {
         int d = i / N, a = i % N;
-        double s = 0.0;
+        E s = E(0);
 #pragma unroll
         for (int c = 0; c < N; ++c) s += (T ? M[c][a] : M[a][c]) * in[d * N + c];
         tmp[i] = s;
@@ -75,7 +75,7 @@ __device__ __forceinline__ void kron_apply(const double (*M)[LD], const double* 
     __syncwarp();
     for (int i = lane; i < N * N; i += 32) {
         int b = i / N, a = i % N;
-        double s = 0.0;
+        E s = E(0);
 #pragma unroll
         for (int d = 0; d < N; ++d) s += (T ? M[d][b] : M[b][d]) * tmp[d * N + a];
         out[i] = scale * s;
@@ -208,21 +208,24 @@ __device__ __forceinline__ void face_trace(const double* u, size_t fstride, unsi
 // hydro_rec_vars, mass_rhs, discharge_rhs, r_concentration).  hA = V_A(zeta_A),
 // hsA = min(V_A(zeta_A), V_B(zeta_A)).  out = {F, Gx_cons, Gy_cons, R}; the
 // non-conservative pressure scalar g {{h*}} (h*A - h*B)/2 is returned apart.
-__device__ __forceinline__ void rusanov(double qxA, double qyA, double cA, double hA, double hsA,
-                                        double qxB, double qyB, double cB, double hB, double hsB,
-                                        double nx, double ny, double g, double eps, double out[4],
-                                        double& pres, double& lam) {
-    double fA = vel_factor(hA, eps), fB = vel_factor(hB, eps);
-    double uAx = fA * qxA, uAy = fA * qyA, uBx = fB * qxB, uBy = fB * qyB;
-    double unA = uAx * nx + uAy * ny, unB = uBx * nx + uBy * ny;
-    double l = fmax(fabs(unA) + sqrt(g * hA), fabs(unB) + sqrt(g * hB));
-    double qsAx = hsA * uAx, qsAy = hsA * uAy, qsBx = hsB * uBx, qsBy = hsB * uBy;
-    out[0] = 0.5 * ((qsAx + qsBx) * nx + (qsAy + qsBy) * ny) + 0.5 * l * (hsA - hsB);
-    out[1] = 0.5 * (qsAx * unA + qsBx * unB) + 0.5 * l * (qsAx - qsBx);
-    out[2] = 0.5 * (qsAy * unA + qsBy * unB) + 0.5 * l * (qsAy - qsBy);
-    out[3] = 0.5 * ((qsAx * cA + qsBx * cB) * nx + (qsAy * cA + qsBy * cB) * ny) +
-             0.5 * l * (hsA * cA - hsB * cB);
-    pres = g * 0.5 * (hsA + hsB) * 0.5 * (hsA - hsB);
+template <typename T>
+__device__ __forceinline__ void rusanov(T qxA, T qyA, T cA, T hA, T hsA, T qxB, T qyB, T cB, T hB,
+                                        T hsB, T dhAB, T nx, T ny, T g, T eps, T out[4], T& pres,
+                                        T& lam) {
+    // dhAB = h*A - h*B, formed in FP64 by the caller (the well-balanced part of
+    // the reconstruction); the tracer jump h*A cA - h*B cB = dhAB cA + h*B (cA - cB)
+    const T half = T(0.5);
+    T fA = vel_factor<T>(hA, eps), fB = vel_factor<T>(hB, eps);
+    T uAx = fA * qxA, uAy = fA * qyA, uBx = fB * qxB, uBy = fB * qyB;
+    T unA = uAx * nx + uAy * ny, unB = uBx * nx + uBy * ny;
+    T l = fmax(fabs(unA) + sqrt(g * hA), fabs(unB) + sqrt(g * hB));
+    T qsAx = hsA * uAx, qsAy = hsA * uAy, qsBx = hsB * uBx, qsBy = hsB * uBy;
+    out[0] = half * ((qsAx + qsBx) * nx + (qsAy + qsBy) * ny) + half * l * dhAB;
+    out[1] = half * (qsAx * unA + qsBx * unB) + half * l * (qsAx - qsBx);
+    out[2] = half * (qsAy * unA + qsBy * unB) + half * l * (qsAy - qsBy);
+    out[3] = half * ((qsAx * cA + qsBx * cB) * nx + (qsAy * cA + qsBy * cB) * ny) +
+             half * l * (dhAB * cA + hsB * (cA - cB));
+    pres = g * half * (hsA + hsB) * half * dhAB;
     lam = l;
 }
 
@@ -236,15 +239,56 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
 // r+2 Gauss-Lobatto points per face (Eqs. mass_rhs, discharge_rhs,
 // discharge_rhs_implicit, r_concentration)
 // ---------------------------------------------------------------------------
-template <int R>
+template <int R, typename B>
 constexpr int res_smem() {
+    // in doubles: su [4 ND], tz [2 ND1 NV], Xd [4 NVP], sd [4 NV ND1], fh [32 NM], rs [6 ND],
+    // then B-typed: suB [4 ND], tB [3 ND1 NV], XB [8 NVP], sB [8 NV ND1]
     using S = Sz<R>;
-    return 4 * S::ND + 5 * S::ND1 * S::NV + 6 * S::NVP + 12 * S::NVP + 12 * S::NV * S::ND1 +
-           32 * S::NM + 6 * S::ND;
+    constexpr int nd = 4 * S::ND + 2 * S::ND1 * S::NV + 4 * S::NVP + 4 * S::NV * S::ND1 +
+                       32 * S::NM + 6 * S::ND;
+    constexpr int nb = 4 * S::ND + 3 * S::ND1 * S::NV + 8 * S::NVP + 8 * S::NV * S::ND1;
+    return nd + (nb * (int)sizeof(B) + 7) / 8;
 }
 
-template <int R, typename Pix, int MODE>
-__global__ void __launch_bounds__(TPB)
+// traces of zeta (FP64) and of qx, qy, c (type B) at face point al of face f
+template <int ND1, typename B>
+__device__ __forceinline__ void face_trace_mixed(const double* u, size_t fstride, unsigned cm, int f,
+                                                 const double (*Bd)[MXN], const B (*Bb)[MXN],
+                                                 int al, double& z, B t[3]) {
+    if (cm & 1u) z = u[0];
+    else {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < ND1; ++j) s += Bd[al][j] * u[face_node<ND1>(f, j)];
+        z = s;
+    }
+#pragma unroll
+    for (int fl = 1; fl < 4; ++fl) {
+        const double* uf = u + fl * fstride;
+        if (cm & (1u << fl)) {
+            t[fl - 1] = (B)uf[0];
+            continue;
+        }
+        B s = B(0);
+#pragma unroll
+        for (int j = 0; j < ND1; ++j) s += Bb[al][j] * (B)uf[face_node<ND1>(f, j)];
+        t[fl - 1] = s;
+    }
+}
+
+template <typename B>
+__device__ __forceinline__ const B (*tab_or(const double (*d)[MXN], const float (*f)[MXN]))[MXN] {
+    if constexpr (sizeof(B) == sizeof(double)) return (const B(*)[MXN])d;
+    else return (const B(*)[MXN])f;
+}
+
+// B = double: the plain FP64 method.  B = float (FP32-bulk): elevation,
+// sub-grid integrals, hydrostatic reconstruction and the continuity and
+// tracer test integrals stay FP64 (so mass, tracer mass and c = 1 are kept to
+// FP64 round-off and the lake at rest exactly); the momentum, friction and
+// flux arithmetic is FP32.
+template <int R, typename Pix, int MODE, typename B>
+__global__ void __launch_bounds__(TPB, 5)
     k_residual(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, int buf,
                int stage, double c_stage, int want_dt) {
     using S = Sz<R>;
@@ -252,108 +296,164 @@ __global__ void __launch_bounds__(TPB)
     constexpr int ND1 = S::ND1, ND = S::ND, NV = S::NV, NVP = S::NVP, NM = S::NM;
     extern __shared__ double smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double* su = smem + warp * res_smem<R>();
-    double* tx = su + 4 * ND;        // [5][ND1][NV]
-    double* pv = tx + 5 * ND1 * NV;  // unused slot kept for alignment of later arrays
-    double* X = pv + 6 * NVP;        // [12][NVP]
-    double* sy = X + 12 * NVP;       // [12][NV][ND1]
-    double* fh = sy + 12 * NV * ND1; // [4 fields][4 faces][2 halves][NM]
-    double* rs = fh + 32 * NM;       // [6][ND]
+    double* su = smem + warp * res_smem<R, B>();
+    double* tz = su + 4 * ND;           // [2][ND1][NV] x-contractions of zeta: value, d/dxi
+    double* Xd = tz + 2 * ND1 * NV;     // [4][NVP]: F_x, F_y, R_x, R_y
+    double* sd = Xd + 4 * NVP;          // [4][NV][ND1]
+    double* fh = sd + 4 * NV * ND1;     // [4 fields][4 faces][2 halves][NM]
+    double* rs = fh + 32 * NM;          // [6][ND]
+    constexpr bool F64 = sizeof(B) == sizeof(double);
+    B* suB = F64 ? (B*)su : (B*)(rs + 6 * ND); // [4][ND] (the FP64 state itself when B = double)
+    B* tB = (B*)(rs + 6 * ND) + 4 * ND;        // [3][ND1][NV]: qx, qy, c
+    B* XB = tB + 3 * ND1 * NV;          // [8][NVP]: Gx (x, y, v), Gy (x, y, v), Lx, Ly
+    B* sB = XB + 8 * NVP;               // [8][NV][ND1]
+    const auto BvB = tab_or<B>(tb.Bv, tb.BvF);
+    const auto DvB = tab_or<B>(tb.Dv, tb.DvF);
+    const auto BmB = tab_or<B>(tb.Bm, tb.BmF);
     const double g = d.g, eps = d.eps;
+    const B gB = (B)g, epsB = (B)eps;
     const double t = (c_stage == 0.0) ? d.sc->t : d.sc->t + c_stage * get_dt(d);
     const int64_t n = d.n;
 
     for (int64_t k = (int64_t)blockIdx.x * WPB + warp; k < n; k += (int64_t)gridDim.x * WPB) {
-        for (int i = lane; i < 4 * ND; i += 32)
-            su[i] = ufield(d, buf, i / ND, ND)[k * ND + (i % ND)];
+        for (int i = lane; i < 4 * ND; i += 32) {
+            const double v = ufield(d, buf, i / ND, ND)[k * ND + (i % ND)];
+            su[i] = v;
+            if constexpr (!F64) suB[i] = (B)v;
+        }
         const unsigned cm = d.cmask[(size_t)buf * n + k];
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
         const double ihx = d.ihxhy ? d.ihxhy[2 * k] : 1.0 / hx;
         const double ihy = d.ihxhy ? d.ihxhy[2 * k + 1] : 1.0 / hy;
-        const double man = d.manning[k];
+        const B manB = (B)d.manning[k];
         __syncwarp();
-        // x-contraction of the four fields (values) and of zeta (d/dxi)
-        for (int i = lane; i < 5 * ND1 * NV; i += 32) {
-            int f = i / (ND1 * NV), r_ = i % (ND1 * NV), b = r_ / NV, al = r_ % NV;
-            const double* u = su + (f < 4 ? f : 0) * ND + ND1 * b;
+        // x-contractions: zeta (value, d/dxi) in FP64, qx, qy, c in B
+        for (int i = lane; i < 2 * ND1 * NV; i += 32) {
+            const int f = i / (ND1 * NV), r_ = i % (ND1 * NV), b = r_ / NV, al = r_ % NV;
             double s = 0.0;
-            if (f < 4) {
+            if (f == 0) {
 #pragma unroll
-                for (int a = 0; a < ND1; ++a) s += tb.Bv[al][a] * u[a];
+                for (int a = 0; a < ND1; ++a) s += tb.Bv[al][a] * su[ND1 * b + a];
             } else {
 #pragma unroll
-                for (int a = 0; a < ND1; ++a) s += tb.Dv[al][a] * u[a];
+                for (int a = 0; a < ND1; ++a) s += tb.Dv[al][a] * su[ND1 * b + a];
             }
-            tx[i] = s;
+            tz[i] = s;
+        }
+        for (int i = lane; i < 3 * ND1 * NV; i += 32) {
+            const int f = i / (ND1 * NV), r_ = i % (ND1 * NV), b = r_ / NV, al = r_ % NV;
+            const B* u = suB + (1 + f) * ND + ND1 * b;
+            B s = B(0);
+#pragma unroll
+            for (int a = 0; a < ND1; ++a) s += BvB[al][a] * u[a];
+            tB[i] = s;
         }
         __syncwarp();
         // y-contraction and pointwise physics, one volume point per lane
         for (int p = lane; p < NVP; p += 32) {
             const int al = p % NV, be = p / NV;
-            double z = 0, zx = 0, zy = 0, qx = 0, qy = 0, c = 0;
+            double z = 0.0, zxd = 0.0, zyd = 0.0;
+            B qx = B(0), qy = B(0), c = B(0);
 #pragma unroll
             for (int b = 0; b < ND1; ++b) {
-                const double B = tb.Bv[be][b], D = tb.Dv[be][b];
-                z += B * tx[(0 * ND1 + b) * NV + al];
-                qx += B * tx[(1 * ND1 + b) * NV + al];
-                qy += B * tx[(2 * ND1 + b) * NV + al];
-                c += B * tx[(3 * ND1 + b) * NV + al];
-                zx += B * tx[(4 * ND1 + b) * NV + al];
-                zy += D * tx[(0 * ND1 + b) * NV + al];
+                z += tb.Bv[be][b] * tz[b * NV + al];
+                zxd += tb.Bv[be][b] * tz[(ND1 + b) * NV + al];
+                zyd += tb.Dv[be][b] * tz[b * NV + al];
+                const B Bb = BvB[be][b];
+                qx += Bb * tB[(0 * ND1 + b) * NV + al];
+                qy += Bb * tB[(1 * ND1 + b) * NV + al];
+                c += Bb * tB[(2 * ND1 + b) * NV + al];
             }
-            if (cm & 1u) { z = su[0]; zx = 0.0; zy = 0.0; }
-            if (cm & 2u) qx = su[ND];
-            if (cm & 4u) qy = su[2 * ND];
-            if (cm & 8u) c = su[3 * ND];
-            zx *= ihx;
-            zy *= ihy;
+            if (cm & 1u) { z = su[0]; zxd = 0.0; zyd = 0.0; }
+            if (cm & 2u) qx = suB[ND];
+            if (cm & 4u) qy = suB[2 * ND];
+            if (cm & 8u) c = suB[3 * ND];
+            const B zx = (B)(zxd * ihx), zy = (B)(zyd * ihy);
             double h, A;
             ST::VA(d, tb, k, SET_VOL, al, be, z, h, A);
-            const double fv = vel_factor(h, eps);
-            const double ux = fv * qx, uy = fv * qy;
-            const double gam = gamma_manning(man, h, qx, qy, g, eps);
-            const double w = J * tb.wv[al] * tb.wv[be], wx = w * ihx, wy = w * ihy;
-            X[0 * NVP + p] = wx * qx;
-            X[1 * NVP + p] = wy * qy;
-            X[2 * NVP + p] = wx * qx * ux;
-            X[3 * NVP + p] = wy * qx * uy;
-            X[4 * NVP + p] = -w * g * h * zx;
-            X[5 * NVP + p] = wx * qy * ux;
-            X[6 * NVP + p] = wy * qy * uy;
-            X[7 * NVP + p] = -w * g * h * zy;
-            X[8 * NVP + p] = wx * c * qx;
-            X[9 * NVP + p] = wy * c * qy;
-            X[10 * NVP + p] = -w * gam * qx;
-            X[11 * NVP + p] = -w * gam * qy;
+            const B hB = (B)h;
+            const B fv = vel_factor<B>(hB, epsB);
+            const B ux = fv * qx, uy = fv * qy;
+            const B gam = gamma_manning<B>(manB, hB, qx, qy, gB, epsB);
+            const double w = J * tb.wv[al] * tb.wv[be];
+            const B wB = (B)w, wx = (B)(w * ihx), wy = (B)(w * ihy);
+            Xd[0 * NVP + p] = (double)(wx * qx);
+            Xd[1 * NVP + p] = (double)(wy * qy);
+            Xd[2 * NVP + p] = (double)(wx * c * qx);
+            Xd[3 * NVP + p] = (double)(wy * c * qy);
+            XB[0 * NVP + p] = wx * qx * ux;
+            XB[1 * NVP + p] = wy * qx * uy;
+            XB[2 * NVP + p] = -wB * gB * hB * zx;
+            XB[3 * NVP + p] = wx * qy * ux;
+            XB[4 * NVP + p] = wy * qy * uy;
+            XB[5 * NVP + p] = -wB * gB * hB * zy;
+            XB[6 * NVP + p] = -wB * gam * qx;
+            XB[7 * NVP + p] = -wB * gam * qy;
         }
         __syncwarp();
-        // test integration, y-contraction: sy[c][0: grad-x part, 1: rest][al][b]
-        // fields: F (0,1,-), Gx (2,3,4), Gy (5,6,7), R (8,9,-), Lx (-,-,10), Ly (-,-,11)
-        for (int i = lane; i < 6 * NV * ND1; i += 32) {
+        // test integration, y-contraction.  FP64: F (x, y), R (x, y); B: Gx, Gy
+        // (x; y + v), Lx, Ly (v)
+        for (int i = lane; i < 2 * NV * ND1; i += 32) {
             const int cf = i / (NV * ND1), r_ = i % (NV * ND1), al = r_ / ND1, b = r_ % ND1;
-            const int ix = cf == 0 ? 0 : cf == 1 ? 2 : cf == 2 ? 5 : cf == 3 ? 8 : -1;
-            const int iy = cf == 0 ? 1 : cf == 1 ? 3 : cf == 2 ? 6 : cf == 3 ? 9 : -1;
-            const int iv = cf == 1 ? 4 : cf == 2 ? 7 : cf == 4 ? 10 : cf == 5 ? 11 : -1;
             double sx = 0.0, so = 0.0;
 #pragma unroll
             for (int be = 0; be < NV; ++be) {
                 const int p = al + NV * be;
-                if (ix >= 0) sx += tb.Bv[be][b] * X[ix * NVP + p];
-                if (iy >= 0) so += tb.Dv[be][b] * X[iy * NVP + p];
-                if (iv >= 0) so += tb.Bv[be][b] * X[iv * NVP + p];
+                sx += tb.Bv[be][b] * Xd[(2 * cf) * NVP + p];
+                so += tb.Dv[be][b] * Xd[(2 * cf + 1) * NVP + p];
             }
-            sy[((cf * 2 + 0) * NV + al) * ND1 + b] = sx;
-            sy[((cf * 2 + 1) * NV + al) * ND1 + b] = so;
+            sd[((cf * 2 + 0) * NV + al) * ND1 + b] = sx;
+            sd[((cf * 2 + 1) * NV + al) * ND1 + b] = so;
+        }
+        // Gx, Gy: grad-x part, and grad-y + value parts
+        for (int i = lane; i < 2 * NV * ND1; i += 32) {
+            const int cg = i / (NV * ND1), r_ = i % (NV * ND1), al = r_ / ND1, b = r_ % ND1;
+            const B* Xg = XB + 3 * cg * NVP;
+            B sx = B(0), so = B(0);
+#pragma unroll
+            for (int be = 0; be < NV; ++be) {
+                const int p = al + NV * be;
+                sx += BvB[be][b] * Xg[p];
+                so += DvB[be][b] * Xg[NVP + p] + BvB[be][b] * Xg[2 * NVP + p];
+            }
+            sB[((cg * 2 + 0) * NV + al) * ND1 + b] = sx;
+            sB[((cg * 2 + 1) * NV + al) * ND1 + b] = so;
+        }
+        // Lx, Ly: value parts only
+        for (int i = lane; i < 2 * NV * ND1; i += 32) {
+            const int cl = i / (NV * ND1), r_ = i % (NV * ND1), al = r_ / ND1, b = r_ % ND1;
+            const B* Xl = XB + (6 + cl) * NVP;
+            B so = B(0);
+#pragma unroll
+            for (int be = 0; be < NV; ++be) so += BvB[be][b] * Xl[al + NV * be];
+            sB[(((2 + cl) * 2 + 1) * NV + al) * ND1 + b] = so;
         }
         __syncwarp();
-        for (int i = lane; i < 6 * ND; i += 32) {
+        // x-contraction into rs = [F, Gx, Gy, R, Lx, Ly]: F and R in FP64
+        for (int i = lane; i < 2 * ND; i += 32) {
             const int cf = i / ND, j = i % ND, a = j % ND1, b = j / ND1;
             double s = 0.0;
 #pragma unroll
             for (int al = 0; al < NV; ++al)
-                s += tb.Dv[al][a] * sy[((cf * 2 + 0) * NV + al) * ND1 + b] +
-                     tb.Bv[al][a] * sy[((cf * 2 + 1) * NV + al) * ND1 + b];
-            rs[i] = s;
+                s += tb.Dv[al][a] * sd[((cf * 2 + 0) * NV + al) * ND1 + b] +
+                     tb.Bv[al][a] * sd[((cf * 2 + 1) * NV + al) * ND1 + b];
+            rs[(cf == 0 ? 0 : 3) * ND + j] = s;
+        }
+        for (int i = lane; i < 2 * ND; i += 32) { // Gx, Gy
+            const int cg = i / ND, j = i % ND, a = j % ND1, b = j / ND1;
+            B s = B(0);
+#pragma unroll
+            for (int al = 0; al < NV; ++al)
+                s += DvB[al][a] * sB[((cg * 2 + 0) * NV + al) * ND1 + b] +
+                     BvB[al][a] * sB[((cg * 2 + 1) * NV + al) * ND1 + b];
+            rs[(1 + cg) * ND + j] = (double)s;
+        }
+        for (int i = lane; i < 2 * ND; i += 32) { // Lx, Ly
+            const int cl = i / ND, j = i % ND, a = j % ND1, b = j / ND1;
+            B s = B(0);
+#pragma unroll
+            for (int al = 0; al < NV; ++al) s += BvB[al][a] * sB[(((2 + cl) * 2 + 1) * NV + al) * ND1 + b];
+            rs[(4 + cl) * ND + j] = (double)s;
         }
         // faces: one (sub)face point per lane; a coarse cell integrates each
         // 2:1 face over the GLL points of both fine halves
@@ -375,8 +475,10 @@ __global__ void __launch_bounds__(TPB)
             const double nx = (f == 0) ? -1.0 : (f == 1) ? 1.0 : 0.0;
             const double ny = (f == 2) ? -1.0 : (f == 3) ? 1.0 : 0.0;
             const double L = ((f < 2) ? hy : hx) * (coarse ? 0.5 : 1.0);
-            double tm[4];
-            face_trace<ND1>(su, ND, cm, f, coarse ? tb.BmH[h] : tb.Bm, al, tm);
+            double zm;
+            B tm[3];
+            face_trace_mixed<ND1, B>(su, ND, cm, f, coarse ? tb.BmH[h] : tb.Bm,
+                                     coarse ? tab_or<B>(tb.BmH[h], tb.BmHF[h]) : BmB, al, zm, tm);
             int ia, ib;
             face_site_index<NM>(f, al, ia, ib);
             auto own_V = [&](double eta) {
@@ -386,13 +488,17 @@ __global__ void __launch_bounds__(TPB)
                 return V;
             };
             const int32_t s0 = d.nbr[k * 8 + f * 2];
-            const double hm = own_V(tm[0]);
-            double tp[4], hp, hsm, hsp, out[4], pres, lam;
+            const double hm = own_V(zm);
+            double zp, hp, hsm, hsp;
+            B tp[3], out[4], pres, lam;
             if (s0 >= 0) {
                 const int64_t nb = coarse ? (int64_t)(h ? d.nbr[k * 8 + f * 2 + 1] : s0) : (int64_t)s0;
                 const int fo = f ^ 1;
-                face_trace<ND1>(ufield(d, buf, 0, ND) + nb * ND, (size_t)n * ND,
-                                d.cmask[(size_t)buf * n + nb], fo, fine ? tb.BmH[half] : tb.Bm, al, tp);
+                face_trace_mixed<ND1, B>(ufield(d, buf, 0, ND) + nb * ND, (size_t)n * ND,
+                                         d.cmask[(size_t)buf * n + nb], fo,
+                                         fine ? tb.BmH[half] : tb.Bm,
+                                         fine ? tab_or<B>(tb.BmH[half], tb.BmHF[half]) : BmB, al, zp,
+                                         tp);
                 int ja, jb;
                 face_site_index<NM>(fo, al, ja, jb);
                 auto nb_V = [&](double eta) {
@@ -401,49 +507,51 @@ __global__ void __launch_bounds__(TPB)
                     else ST::VA(d, tb, nb, SET_MASS, ja, jb, eta, V, A);
                     return V;
                 };
-                hp = nb_V(tp[0]);
-                hsm = fmin(hm, nb_V(tm[0]));  // min(V-(zeta-), V+(zeta-))
-                hsp = fmin(hp, own_V(tp[0])); // min(V+(zeta+), V-(zeta+))
+                hp = nb_V(zp);
+                hsm = fmin(hm, nb_V(zm)); // min(V-(zeta-), V+(zeta-)), FP64
+                hsp = fmin(hp, own_V(zp)); // min(V+(zeta+), V-(zeta+)), FP64
                 // canonical side order: the lower cell index is side A, so both
                 // cells of the face compute bit-identical fluxes
                 const bool own_first = k < nb;
                 if (own_first)
-                    rusanov(tm[1], tm[2], tm[3], hm, hsm, tp[1], tp[2], tp[3], hp, hsp, nx, ny, g, eps,
-                            out, pres, lam);
+                    rusanov<B>(tm[0], tm[1], tm[2], (B)hm, (B)hsm, tp[0], tp[1], tp[2], (B)hp, (B)hsp,
+                               (B)(hsm - hsp), (B)nx, (B)ny, gB, epsB, out, pres, lam);
                 else
-                    rusanov(tp[1], tp[2], tp[3], hp, hsp, tm[1], tm[2], tm[3], hm, hsm, -nx, -ny, g,
-                            eps, out, pres, lam);
-                const double sg = own_first ? 1.0 : -1.0;
+                    rusanov<B>(tp[0], tp[1], tp[2], (B)hp, (B)hsp, tm[0], tm[1], tm[2], (B)hm, (B)hsm,
+                               (B)(hsp - hsm), (B)(-nx), (B)(-ny), gB, epsB, out, pres, lam);
+                const B sg = own_first ? B(1) : B(-1);
                 // the pressure vector g {{h*}} (h*A - h*B)/2 n_A is the same for both sides
-                const double pnx = own_first ? pres * nx : pres * (-nx);
-                const double pny = own_first ? pres * ny : pres * (-ny);
+                const B pnx = own_first ? pres * (B)nx : pres * (B)(-nx);
+                const B pny = own_first ? pres * (B)ny : pres * (B)(-ny);
                 out[0] *= sg;
                 out[1] = sg * out[1] - pnx;
                 out[2] = sg * out[2] - pny;
                 out[3] *= sg;
             } else {
                 const int tag = -1 - s0;
-                tp[0] = tm[0]; tp[1] = tm[1]; tp[2] = tm[2]; tp[3] = tm[3];
+                zp = zm;
+                tp[0] = tm[0]; tp[1] = tm[1]; tp[2] = tm[2];
                 if (d.bc_kind[tag] == 1) {
-                    tp[0] = d.bc_amp[tag] * sin(2.0 * M_PI * t / d.bc_per[tag] + d.bc_ph[tag]);
+                    zp = d.bc_amp[tag] * sin(2.0 * M_PI * t / d.bc_per[tag] + d.bc_ph[tag]);
                 } else {
-                    const double qn = tm[1] * nx + tm[2] * ny;
-                    tp[1] = tm[1] - 2.0 * qn * nx;
-                    tp[2] = tm[2] - 2.0 * qn * ny;
+                    const B qn = tm[0] * (B)nx + tm[1] * (B)ny;
+                    tp[0] = tm[0] - B(2) * qn * (B)nx;
+                    tp[1] = tm[1] - B(2) * qn * (B)ny;
                 }
-                hp = own_V(tp[0]); // ghost: same sub-grid operator
+                hp = own_V(zp); // ghost: same sub-grid operator
                 hsm = hm;
                 hsp = hp;
-                rusanov(tm[1], tm[2], tm[3], hm, hsm, tp[1], tp[2], tp[3], hp, hsp, nx, ny, g, eps, out,
-                        pres, lam);
-                out[1] -= pres * nx;
-                out[2] -= pres * ny;
+                rusanov<B>(tm[0], tm[1], tm[2], (B)hm, (B)hsm, tp[0], tp[1], tp[2], (B)hp, (B)hsp,
+                           (B)(hsm - hsp), (B)nx, (B)ny, gB, epsB, out, pres, lam);
+                out[1] -= pres * (B)nx;
+                out[2] -= pres * (B)ny;
             }
             const double wl = L * tb.wm[al];
 #pragma unroll
-            for (int cf = 0; cf < 4; ++cf) fh[((cf * 4 + f) * 2 + h) * NM + al] = wl * out[cf];
+            for (int cf = 0; cf < 4; ++cf)
+                fh[((cf * 4 + f) * 2 + h) * NM + al] = wl * (double)out[cf];
             // lambda l / J for the positivity step (l = L, J = hx hy)
-            dtl = fmax(dtl, fmax(lam, 1e-12) * ((f < 2) ? ihx : ihy) * (coarse ? 0.5 : 1.0));
+            dtl = fmax(dtl, fmax((double)lam, 1e-12) * ((f < 2) ? ihx : ihy) * (coarse ? 0.5 : 1.0));
         }
         if (want_dt) {
             const double m = warp_max(dtl);
@@ -674,7 +782,9 @@ constexpr int stage_smem() {
     return 4 * S::ND + 5 * S::ND + 3 * S::NMP + 2 * S::NM * S::NM + S::ND1 * S::ND1 * S::NM +
            S::ND * S::ND + 6 * S::NGP + 4 * S::ND + S::ND +
            // mixed-precision solve: x, r (ND), q (NMP), float M, Y, inv, r
-           2 * S::ND + S::NMP + (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 2 * S::ND + 1) / 2 + 1;
+           2 * S::ND + S::NMP + (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 2 * S::ND + 1) / 2 + 1 +
+           // momentum block scratch (B-typed, sized in doubles)
+           S::ND + 6 * S::NGP + S::ND1 * S::NG;
 }
 
 // Cholesky of the SPD matrix M (ND x ND, row-major, lower part used) on a
@@ -877,7 +987,94 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
     return chol_solve<ND>(M, b, inv, lane);
 }
 
-template <int R, typename Pix, int MODE>
+// Momentum stage solve of an r_K = r cell in arithmetic T (Eq. algebraic_discharge
+// with the friction-modified mass matrix of Eq. mass_matrix_discharge on the
+// (r+1)^2 Gauss-Legendre points, inverted as S^-1 D^-1 S^-T):
+//   S Q = [D0 q^n + S^-T rq] / D,  D = D0 (1 + add dt gamma),  D0 = J w.
+// gamma (of the previous stage) is formed here from prev (zeta in FP64 for the
+// sub-grid depth, q in T).  Optionally the linearised friction term
+// Llin = -S^T (J w gamma S Q).  Inputs su (v^n, FP64), rq [2][ND] (FP64);
+// outputs Q [2][ND] (FP64) and llin [2][ND] (FP64).
+template <int R, typename Pix, int MODE, typename T>
+__device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double J, double man,
+                               double dt, double add, bool need_gam, bool make_llin, int prev_buf,
+                               const double* su, unsigned cm0, const double* rq, T* w0, T* w1,
+                               double* zp, double* tmpd, double* Q, double* llin, int lane) {
+    using S = Sz<R>;
+    constexpr int ND1 = S::ND1, ND = S::ND, NG = S::NG, NGP = S::NGP;
+    const auto Bg = tab_or<T>(tb.Bg, tb.BgF);
+    const T(*Bginv)[MXP] = nullptr;
+    if constexpr (sizeof(T) == sizeof(double)) Bginv = (const T(*)[MXP])tb.Bginv;
+    else Bginv = (const T(*)[MXP])tb.BginvF;
+    // w0: [ND] scratch nodal, [NGP x 6] point arrays; w1: [ND1 NG] tmp
+    T* nod = w0;              // [ND]
+    T* pg = w0 + ND;          // [6][NGP]: 0,1 S^-T rq / point values; 2 gamma; 3,4 q^n; 5 spare
+    T* tmp = w1;
+    T* gam = pg + 2 * NGP;
+    const int64_t n = d.n;
+    if (need_gam) {
+        const unsigned cmp = d.cmask[(size_t)prev_buf * n + k];
+        const double* uz = ufield(d, prev_buf, 0, ND) + k * ND;
+        tens_interp<ND1, NG>(tb.Bg, uz, tmpd, zp, lane); // zeta of v^(l-1), FP64
+        if (cmp & 1u)
+            for (int p = lane; p < NGP; p += 32) zp[p] = uz[0];
+        for (int f = 0; f < 2; ++f) {
+            const double* up = ufield(d, prev_buf, 1 + f, ND) + k * ND;
+            for (int i = lane; i < ND; i += 32) nod[i] = (T)up[i];
+            __syncwarp();
+            tens_interp<ND1, NG, T>(Bg, nod, tmp, pg + (3 + f) * NGP, lane);
+            if (cmp & (2u << f))
+                for (int p = lane; p < NGP; p += 32) pg[(3 + f) * NGP + p] = (T)up[0];
+            __syncwarp();
+        }
+        for (int p = lane; p < NGP; p += 32) {
+            double V, A;
+            Site<R, Pix, MODE>::VA(d, tb, k, SET_MOM, p % NG, p / NG, zp[p], V, A);
+            gam[p] = gamma_manning<T>((T)man, (T)V, pg[3 * NGP + p], pg[4 * NGP + p], (T)d.g,
+                                      (T)d.eps);
+        }
+    } else {
+        for (int p = lane; p < NGP; p += 32) gam[p] = T(0);
+    }
+    __syncwarp();
+    for (int f = 0; f < 2; ++f) {
+        for (int i = lane; i < ND; i += 32) nod[i] = (T)su[(1 + f) * ND + i];
+        __syncwarp();
+        tens_interp<ND1, NG, T>(Bg, nod, tmp, pg + (3 + f) * NGP, lane);
+        if (cm0 & (2u << f))
+            for (int p = lane; p < NGP; p += 32) pg[(3 + f) * NGP + p] = (T)su[(1 + f) * ND];
+        for (int i = lane; i < ND; i += 32) nod[i] = (T)rq[f * ND + i];
+        __syncwarp();
+        kron_apply<ND1, true, MXP, T>(Bginv, nod, tmp, pg + f * NGP, T(1), lane);
+    }
+    for (int p = lane; p < NGP; p += 32) {
+        const T w = (T)(J * tb.wg[p % NG] * tb.wg[p / NG]);
+        const T rD = T(1) / (w * (T(1) + (T)(add * dt) * gam[p]));
+        pg[0 * NGP + p] = (w * pg[3 * NGP + p] + pg[0 * NGP + p]) * rD;
+        pg[1 * NGP + p] = (w * pg[4 * NGP + p] + pg[1 * NGP + p]) * rD;
+    }
+    __syncwarp();
+    for (int f = 0; f < 2; ++f) {
+        kron_apply<ND1, false, MXP, T>(Bginv, pg + f * NGP, tmp, nod, T(1), lane);
+        for (int i = lane; i < ND; i += 32) Q[f * ND + i] = (double)nod[i];
+        __syncwarp();
+    }
+    if (make_llin) {
+        for (int p = lane; p < NGP; p += 32) {
+            const T w = (T)(J * tb.wg[p % NG] * tb.wg[p / NG]) * gam[p];
+            pg[3 * NGP + p] = -w * pg[p];
+            pg[4 * NGP + p] = -w * pg[NGP + p];
+        }
+        __syncwarp();
+        for (int f = 0; f < 2; ++f) {
+            tens_test<ND1, NG, T>(Bg, pg + (3 + f) * NGP, tmp, nod, lane);
+            for (int i = lane; i < ND; i += 32) llin[f * ND + i] = (double)nod[i];
+            __syncwarp();
+        }
+    }
+}
+
+template <int R, typename Pix, int MODE, typename B>
 __global__ void __launch_bounds__(TPB)
     k_stage(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, const StageArgs sa) {
     using S = Sz<R>;
@@ -906,6 +1103,9 @@ __global__ void __launch_bounds__(TPB)
     float* Yf = Mf + ND * ND;                   // [ND1 ND1 NM]
     float* invf = Yf + ND1 * ND1 * NM;          // [ND]
     float* rf = invf + ND;                      // [ND]
+    // momentum scratch, 8-byte aligned after the float arrays
+    double* mw = (double*)((((uintptr_t)(rf + ND)) + 7) & ~(uintptr_t)7);
+    double* mt = mw + ND + 6 * NGP;
     const int64_t n = d.n;
     const double dt = get_dt(d);
     const double g = d.g, eps = d.eps;
@@ -1015,9 +1215,10 @@ __global__ void __launch_bounds__(TPB)
             __syncwarp();
         }
         // friction coefficient of the previous stage on the momentum GL points
+        // (scalar path; the r path forms it inside momentum_block)
         double* gam = pg + 5 * NGP;
         const bool need_gam = (sa.add != 0.0 || sa.make_llin) && man != 0.0;
-        if (need_gam) {
+        if (need_gam && scalar) {
             const unsigned cmp = d.cmask[(size_t)sa.prev_buf * n + k];
             for (int f = 0; f < 3; ++f) {
                 const double* up = ufield(d, sa.prev_buf, f, ND) + k * ND;
@@ -1031,7 +1232,7 @@ __global__ void __launch_bounds__(TPB)
             for (int p = lane; p < NGP; p += 32) {
                 double V, A;
                 ST::VA(d, tb, k, SET_MOM, p % NG, p / NG, pg[p], V, A);
-                gam[p] = gamma_manning(man, V, pg[NGP + p], pg[2 * NGP + p], g, eps);
+                gam[p] = gamma_manning<double>(man, V, pg[NGP + p], pg[2 * NGP + p], g, eps);
             }
         } else {
             for (int p = lane; p < NGP; p += 32) gam[p] = 0.0;
@@ -1097,32 +1298,11 @@ __global__ void __launch_bounds__(TPB)
                 }
             }
         } else {
-            // momentum: point values on the GL (r+1)^2 points, S Q = [D0 q^n + S^-T rq] / D
-            for (int f = 0; f < 2; ++f) {
-                tens_interp<ND1, NG>(tb.Bg, su + (1 + f) * ND, tmp, pg + (3 + f) * NGP, lane);
-                if (cm0 & (2u << f))
-                    for (int p = lane; p < NGP; p += 32) pg[(3 + f) * NGP + p] = su[(1 + f) * ND];
-                __syncwarp();
-                kron_apply<ND1, true, MXP>(tb.Bginv, rq + f * ND, tmp, pg + f * NGP, 1.0, lane);
-            }
-            for (int p = lane; p < NGP; p += 32) {
-                const double w = J * tb.wg[p % NG] * tb.wg[p / NG];
-                const double D = w * (1.0 + sa.add * dt * gam[p]);
-                pg[0 * NGP + p] = (w * pg[3 * NGP + p] + pg[0 * NGP + p]) / D;
-                pg[1 * NGP + p] = (w * pg[4 * NGP + p] + pg[1 * NGP + p]) / D;
-            }
-            __syncwarp();
-            kron_apply<ND1, false, MXP>(tb.Bginv, pg, tmp, o + ND, 1.0, lane);
-            kron_apply<ND1, false, MXP>(tb.Bginv, pg + NGP, tmp, o + 2 * ND, 1.0, lane);
+            // momentum (FP64, or FP32 in the FP32-bulk path)
+            momentum_block<R, Pix, MODE, B>(d, tb, k, J, man, dt, sa.add, need_gam, sa.make_llin != 0,
+                                            sa.prev_buf, su, cm0, rq, (B*)mw, (B*)mt, pe, tmp, o + ND,
+                                            M, lane);
             if (sa.make_llin) {
-                for (int p = lane; p < NGP; p += 32) {
-                    const double w = J * tb.wg[p % NG] * tb.wg[p / NG] * gam[p];
-                    pg[3 * NGP + p] = -w * pg[p];
-                    pg[4 * NGP + p] = -w * pg[NGP + p];
-                }
-                __syncwarp();
-                tens_test<ND1, NG>(tb.Bg, pg + 3 * NGP, tmp, M, lane);
-                tens_test<ND1, NG>(tb.Bg, pg + 4 * NGP, tmp, M + ND, lane);
                 for (int i = lane; i < ND; i += 32) {
                     d.llin[(size_t)k * ND + i] = M[i];
                     d.llin[(size_t)n * ND + (size_t)k * ND + i] = M[ND + i];

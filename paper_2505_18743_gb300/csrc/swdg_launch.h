@@ -18,10 +18,10 @@ struct Launch {
     int nzp; // mode P samples per cell
 };
 
-// mode: 0 S, 1 P; pix: 0 float32, 1 float64
-bool get_launch(int degree, int mode, int pix, Launch* out);
-bool get_launch_r1(int mode, int pix, Launch* out);
-bool get_launch_r2(int mode, int pix, Launch* out);
-bool get_launch_r3(int mode, int pix, Launch* out);
+// mode: 0 S, 1 P; pix: 0 float32, 1 float64; prec: 0 FP64, 1 FP32-bulk
+bool get_launch(int degree, int mode, int pix, int prec, Launch* out);
+bool get_launch_r1(int mode, int pix, int prec, Launch* out);
+bool get_launch_r2(int mode, int pix, int prec, Launch* out);
+bool get_launch_r3(int mode, int pix, int prec, Launch* out);
 
 } // namespace swdg

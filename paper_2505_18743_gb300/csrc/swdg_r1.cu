@@ -3,5 +3,7 @@
 #include "swdg_degree.cuh"
 
 namespace swdg {
-bool get_launch_r1(int mode, int pix, Launch* out) { return get_launch_degree<1>(mode, pix, out); }
+bool get_launch_r1(int mode, int pix, int prec, Launch* out) {
+    return get_launch_degree<1>(mode, pix, prec, out);
+}
 } // namespace swdg

@@ -3,5 +3,7 @@
 #include "swdg_degree.cuh"
 
 namespace swdg {
-bool get_launch_r2(int mode, int pix, Launch* out) { return get_launch_degree<2>(mode, pix, out); }
+bool get_launch_r2(int mode, int pix, int prec, Launch* out) {
+    return get_launch_degree<2>(mode, pix, prec, out);
+}
 } // namespace swdg

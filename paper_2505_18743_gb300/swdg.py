@@ -142,14 +142,14 @@ class Context:
     """One swdg context (owns its device memory).  Methods mirror the C-ABI."""
 
     def __init__(self, degree=1, subgrid_mode=0, tableau=0, g=9.81, eps_vel=0.01, h_lim=0.01,
-                 eps0=1e-6, cfl=0.1, newton_max=20, newton_tol=1e-12, stream=None):
+                 eps0=1e-6, cfl=0.1, newton_max=20, newton_tol=1e-12, stream=None, precision=0):
         L = load()
         if stream is None:
             t = _torch()
             if t is not None and t.cuda.is_available():
                 stream = t.cuda.current_stream().cuda_stream
-        self.cfg = swdg_config(degree, 0, subgrid_mode, tableau, g, eps_vel, h_lim, eps0, cfl,
-                               newton_max, newton_tol, ctypes.c_void_p(stream or 0))
+        self.cfg = swdg_config(degree, precision, subgrid_mode, tableau, g, eps_vel, h_lim, eps0,
+                               cfl, newton_max, newton_tol, ctypes.c_void_p(stream or 0))
         h = ctypes.c_void_p()
         rc = L.swdg_create(ctypes.byref(self.cfg), ctypes.byref(h))
         if rc:
