@@ -226,6 +226,83 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def ensemble_variant(args, stream, dev, world, members=64):
+    """A 64-member parameter sweep of tidal beaches (mesh N x N with N drawn
+    from 32, 64, 128, 256; r = 2; 8 x 8 px per cell; tide amplitude and
+    Manning coefficient drawn per member) in FP32-bulk, every step one
+    CUDA-graph launch sequence over all members after the autotuner picked
+    the launch shapes; against it the same members as 64 sequential FP64
+    contexts and as one FP64 ensemble, and the FP32-bulk members' state error
+    against the sequential FP64 runs."""
+    import torch
+    from paper_2505_18743_gb300 import swdg
+    wls = W.beach_ensemble(members=members)
+    nd = (wls[0].degree + 1) ** 2
+    cells = sum(w.mesh.n for w in wls)
+    units = cells * 4 * nd * STAGES
+    steps = max(2, min(args.steps, 5))
+
+    def timed(fn):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        s0.record(stream)
+        fn()
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(s0.elapsed_time(s1), world)
+
+    out = {"workload": f"{members} tidal beaches, N x N cells with N drawn from 32/64/128/256 "
+                       f"({cells} cells in all), r=2, 8x8 px/cell, RK32-IMEX, per-member tide "
+                       "and Manning n, each member its own CFL step",
+           "cells": cells, "steps": steps}
+    ens = swdg.Ensemble.from_workloads(wls, stream=stream.cuda_stream, precision=1)
+    tune = ens.autotune(repeats=1)
+    for _ in range(args.warmup):
+        ens.step(1)
+    ms = timed(lambda: ens.step(steps))
+    out["fp32_bulk_ensemble"] = {"value": units * steps * world / (ms / 1e3), "unit": "updates/s",
+                                 "ms_per_step": ms / steps, "launch_shapes": tune}
+    ens64 = swdg.Ensemble.from_workloads(wls, stream=stream.cuda_stream)
+    ens64.autotune(repeats=1)
+    for _ in range(args.warmup):
+        ens64.step(1)
+    ms64 = timed(lambda: ens64.step(steps))
+    out["fp64_ensemble"] = {"value": units * steps * world / (ms64 / 1e3), "unit": "updates/s",
+                            "ms_per_step": ms64 / steps}
+    del ens64
+    seq = [swdg.Context.from_workload(w, stream=stream.cuda_stream) for w in wls]
+    ts = [0.0] * len(seq)
+    for i, c in enumerate(seq):
+        for _ in range(args.warmup):
+            ts[i] = c.step(1, -1.0, ts[i])
+
+    def run_seq():
+        for i, c in enumerate(seq):
+            ts[i] = c.step(steps, -1.0, ts[i])
+
+    mss = timed(run_seq)
+    out["fp64_sequential_baseline"] = {"value": units * steps * world / (mss / 1e3),
+                                       "unit": "updates/s", "ms_per_step": mss / steps,
+                                       "kind": "64 stand-alone FP64 contexts stepped one after "
+                                               "another (each its own CUDA graph)"}
+    out["speedup_fp32_bulk_ensemble_vs_sequential_fp64"] = mss / ms
+    # FP32-bulk members against the FP64 runs after the same number of steps
+    worst = {"zeta": 0.0, "q": 0.0, "c": 0.0}
+    for m, c in enumerate(seq):
+        a, b = ens.member_state(m), c.get_state()
+        qs = max(float(np.abs(b[1]).max()), float(np.abs(b[2]).max()), 1e-3)
+        worst["zeta"] = max(worst["zeta"], float(np.abs(a[0] - b[0]).max()) /
+                            max(float(np.abs(b[0]).max()), 1.0))
+        worst["q"] = max(worst["q"], max(float(np.abs(a[i] - b[i]).max()) for i in (1, 2)) / qs)
+        worst["c"] = max(worst["c"], float(np.abs(a[3] - b[3]).max()))
+    out["max_rel_member_err_fp32_bulk_vs_fp64"] = worst
+    out["steps_compared"] = args.warmup + steps
+    for c in seq:
+        c.close()
+    ens.close()
+    return out
+
+
 def run_gpu(args, rank, world, local):
     import torch
     from paper_2505_18743_gb300 import swdg
@@ -338,6 +415,9 @@ def run_gpu(args, rank, world, local):
             "mass_rel_diff_vs_fp64": abs(d32["mass"] - d64["mass"]) / d64["mass"],
             "time_matches": abs(t32 - t_ref) <= 1e-9 * max(t_ref, 1.0)}
         ctx32.close()
+
+    if not args.no_variants and prec == 0:
+        variants["ensemble"] = ensemble_variant(args, stream, dev, world)
 
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -128,12 +128,13 @@ int swdg_get_state(swdg_ctx* ctx, double* zeta, double* qx, double* qy, double* 
 /* Residual of the current state at time t: F, Gx, Gy, R, Lx, Ly (Eqs.
  * mass_rhs, discharge_rhs, r_concentration, discharge_rhs_implicit), each
  * [n][(r+1)^2] float64, so that M d(state)/dt = residual.  Any output may be
- * NULL. */
+ * NULL.  Sets every member's clock to t. */
 int swdg_residual(swdg_ctx* ctx, double t, double* F, double* Gx, double* Gy, double* R,
                   double* Lx, double* Ly, int where);
 
 /* cfl * min over all face points of J_K / (lambda l_Gamma) for the current
- * state at time t (Eq. deltat_fe). */
+ * state at time t (Eq. deltat_fe); on an ensemble, the smallest member step.
+ * Sets every member's clock to t. */
 int swdg_cfl_dt(swdg_ctx* ctx, double t, double* dt);
 
 /* Advance n_steps time steps.  dt_or_neg >= 0: fixed step; < 0: the CFL step
@@ -141,7 +142,11 @@ int swdg_cfl_dt(swdg_ctx* ctx, double t, double* dt);
  * start time on entry and the end time on return.  Each step: degree switch
  * (Eq. criteria_p) with mass-exact remap, then the stages and final
  * combination of the tableau.  Returns SWDG_ENAN if the state became
- * non-finite. */
+ * non-finite.  On an ensemble (swdg_set_members) every member takes its own
+ * CFL step and keeps its own clock: t_inout must be NULL (SWDG_EINVAL
+ * otherwise) and the clocks are read with swdg_member_times.  The kernels of
+ * a step are launched once for the whole ensemble and captured in one CUDA
+ * graph. */
 int swdg_step(swdg_ctx* ctx, int n_steps, double dt_or_neg, double* t_inout);
 
 /* Profiling variant of swdg_step: runs n_steps with the kernels launched one
@@ -159,13 +164,84 @@ int swdg_step_profile(swdg_ctx* ctx, int n_steps, double dt_or_neg, double* t_in
 int swdg_degree_switch(swdg_ctx* ctx, uint8_t* flags_out);
 
 /* Zeta at n gauge points xy [n][2] (host), written to zeta_out [n] (host);
- * NaN for a point outside the mesh. */
+ * NaN for a point outside the mesh.  On an ensemble the first cell (in cell
+ * order) containing the point answers; see swdg_gather_gauges_member. */
 int swdg_gather_gauges(swdg_ctx* ctx, int n, const double* xy, double* zeta_out);
 
 /* out[8] = total mass sum_K Hbar_K (Eq. positivity-7), tracer mass, min wet
  * depth over mass points, number of r_K = r cells, max Newton iterations of
- * the last step, positivity violations (cumulative), last dt, t. */
+ * the last step, positivity violations (cumulative), last dt, t.  On an
+ * ensemble the first four are over all members and dt, t are member 0's. */
 int swdg_diagnostics(swdg_ctx* ctx, double out[8]);
+
+/* ---- ensembles (the paper has no counterpart: many independent problems,
+ * e.g. a parameter sweep of tides, friction and bathymetry, advanced by the
+ * same kernel launches) ----
+ *
+ * The mesh uploaded with swdg_upload_mesh is the disjoint union of the
+ * members' meshes: member m owns cells [first_cell[m], first_cell[m+1]),
+ * first_cell [n_members + 1] (host) running from 0 to n_cells, and no face
+ * may join cells of two members (SWDG_EINVAL).  Members may overlap in
+ * space.  Each member has its own CFL step, clock and boundary table (all
+ * initialised from the context's: every boundary set so far, clock 0); state,
+ * Manning coefficients and diagnostics stay per cell.  Re-uploading the mesh
+ * ends the ensemble.  n_members = 1 turns a context back into a plain one. */
+#define SWDG_MAX_MEMBERS 65536
+int swdg_set_members(swdg_ctx* ctx, int n_members, const int64_t* first_cell);
+
+/* Bathymetry of an ensemble: member m's cells take their pixels (or point
+ * samples) from rasters[m] (host, dtype SWDG_PIX_*, [ny][nx] row-major) of
+ * size nxny[2m], nxny[2m+1] and geometry geo[4m..4m+3] = x_origin, y_origin,
+ * dx, dy -- the rules of swdg_upload_bathymetry apply per member, and at most
+ * 4 distinct pixel counts per cell over the whole ensemble.  Each raster is
+ * on the device only while its member is re-tiled. */
+int swdg_upload_bathymetry_members(swdg_ctx* ctx, const void* const* rasters, int dtype,
+                                   const int64_t* nxny, const double* geo);
+
+/* Boundary tag of one member (as swdg_set_boundary, which sets the tag of
+ * every member). */
+int swdg_set_boundary_member(swdg_ctx* ctx, int member, int tag, int kind, double amp,
+                             double period, double phase);
+
+/* The members' clocks: set != 0 writes t [n_members] (host) as every
+ * member's time; set == 0 reads t and dt_last [n_members] (host, either may be
+ * NULL). */
+int swdg_member_times(swdg_ctx* ctx, double* t, double* dt_last, int set);
+
+/* out [n_members][8]: swdg_diagnostics per member (mass, tracer mass and min
+ * depth over the member's cells, its r_K = r cell count, the context-wide
+ * Newton maximum and violation count, its last dt and t). */
+int swdg_member_diagnostics(swdg_ctx* ctx, double* out);
+
+/* swdg_gather_gauges over the cells of one member. */
+int swdg_gather_gauges_member(swdg_ctx* ctx, int member, int n, const double* xy,
+                              double* zeta_out);
+
+/* ---- launch shapes (the paper has no counterpart) ----
+ * Each kernel kind runs one warp per cell, grid-stride over all cells: kind
+ * SWDG_KIND_BEGIN (degree switch and H, C~), SWDG_KIND_RESIDUAL,
+ * SWDG_KIND_STAGE (stage update and final combination), SWDG_KIND_AUX (masks,
+ * diagnostics).  A shape is (grid blocks, warps per block 1..8); the default
+ * is 4 warps per block and one block per 4 cells (at most 9728 blocks).
+ * Shapes change speed only: every cell's arithmetic is the same, so results
+ * are bitwise identical under any shape. */
+#define SWDG_KIND_BEGIN 0
+#define SWDG_KIND_RESIDUAL 1
+#define SWDG_KIND_STAGE 2
+#define SWDG_KIND_AUX 3
+int swdg_set_shape(swdg_ctx* ctx, int kind, int grid, int warps_per_block);
+/* out [4][2] = grid, warps per block of each kind. */
+int swdg_get_shapes(const swdg_ctx* ctx, int* out);
+
+/* Autotuner: times every candidate shape of the begin, residual and stage
+ * kernels on the context's own mesh and state (warps per block 1, 2, 4, 8;
+ * grid = SMs x resident blocks, i.e. a persistent launch, or one block per
+ * wpb cells), `repeats` eager steps each after one warm-up step, and keeps the
+ * fastest per kind.  The state, masks, counters and clocks are restored
+ * afterwards, so the tuning steps leave no trace.  report [3][3] (may be
+ * NULL): grid, warps per block and ms per step of the chosen shape of each
+ * kind.  Requires a state; call it outside stream capture. */
+int swdg_autotune(swdg_ctx* ctx, int repeats, double* report);
 
 /* Allocation-free residual (the paper has no counterpart; this exists for
  * callers that cannot allocate device memory -- for example code running

@@ -39,7 +39,18 @@ struct swdg_ctx {
     Launch L{};
     Tables tb{};
     Dev d{};
-    int grid = 1;
+    int nsm = 152;           // SMs of the context's device
+    Shape shp[KK_N] = {};    // launch shape per kernel kind (default or autotuned)
+    bool tuned = false;
+    // ensemble members: cells [first[m], first[m+1]) form member m
+    int nmemb = 1;
+    std::vector<int64_t> first;
+    int32_t* memb = nullptr;
+    Member* mb = nullptr;
+    Bc* bcd = nullptr;
+    int64_t* first_d = nullptr; // [nmemb + 1]
+    double* mdiag = nullptr;    // [nmemb][4]
+    std::vector<Bc> bch;
     // device allocations
     double *x0y0 = nullptr, *hxhy = nullptr, *ihxhy = nullptr, *manning = nullptr, *U = nullptr, *res = nullptr,
            *llin = nullptr, *HN = nullptr, *CN = nullptr, *HNbar = nullptr, *CNbar = nullptr,
@@ -56,6 +67,7 @@ struct swdg_ctx {
     cudaGraphExec_t graph = nullptr;
     double graph_dt = -2.0;
     std::vector<double> x0y0_h, hxhy_h;
+    std::vector<int32_t> nbr_h;
     std::vector<uint8_t> finfo_h;
     std::string err;
 };
@@ -461,8 +473,18 @@ __global__ void k_point_samples(const Pix* __restrict__ ras, int64_t nx, int64_t
 }
 
 // deterministic reduction of the per-cell diagnostics (one block)
-__global__ void k_diag_reduce(const double* part, int64_t n, double* out) {
+// block i reduces cells [first[i], first[i+1]) to out[4 i ..] (first == null:
+// one block over [k0, k1))
+__global__ void k_diag_reduce(const double* part, const int64_t* first, int64_t k0, int64_t k1,
+                              double* out) {
     __shared__ double s[4][256];
+    if (first) {
+        k0 = first[blockIdx.x];
+        k1 = first[blockIdx.x + 1];
+        out += 4 * blockIdx.x;
+    }
+    const int64_t n = k1 - k0;
+    part += 4 * k0;
     double m = 0.0, tm = 0.0, hmin = INFINITY, rc = 0.0;
     const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
     const int64_t b = threadIdx.x * chunk, e = min(n, b + chunk);
@@ -548,9 +570,32 @@ static void invalidate_graph(swdg_ctx* c) {
     c->graph = nullptr;
 }
 
-static int grid_for(int64_t n) {
-    int64_t b = (n + WPB - 1) / WPB;
+static int grid_for(int64_t n, int wpb = WPB) {
+    int64_t b = (n + wpb - 1) / wpb;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152LL * 64));
+}
+
+// default shapes: WPB warps per block, one block per WPB cells (grid-stride
+// beyond 152 x 64 blocks)
+static void default_shapes(swdg_ctx* c) {
+    for (int i = 0; i < KK_N; ++i) c->shp[i] = Shape{grid_for(c->n), WPB};
+    c->tuned = false;
+}
+
+static void free_members(swdg_ctx* c) {
+    cudaFree(c->memb); cudaFree(c->mb); cudaFree(c->bcd); cudaFree(c->first_d); cudaFree(c->mdiag);
+    c->memb = nullptr;
+    c->mb = nullptr;
+    c->bcd = nullptr;
+    c->first_d = nullptr;
+    c->mdiag = nullptr;
+    c->nmemb = 1;
+    c->first.assign({0, c->n});
+    c->bch.clear();
+    c->d.memb = nullptr;
+    c->d.mbc = nullptr;
+    c->d.mb = &c->sc->m0;
+    c->d.nmemb = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -613,6 +658,11 @@ int swdg_create(const swdg_config* cfg, swdg_ctx** out) {
         return SWDG_ECUDA;
     }
     d.sc = ctx->sc;
+    d.mb = &ctx->sc->m0;
+    d.nmemb = 1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
     *out = ctx;
     return SWDG_OK;
 }
@@ -643,6 +693,7 @@ void swdg_destroy(swdg_ctx* c) {
     invalidate_graph(c);
     free_mesh(c);
     free_bathy(c);
+    cudaFree(c->memb); cudaFree(c->mb); cudaFree(c->bcd); cudaFree(c->first_d); cudaFree(c->mdiag);
     cudaFree(c->sc);
     if (c->sc_host) cudaFreeHost(c->sc_host);
     if (c->pin) cudaFreeHost(c->pin);
@@ -728,6 +779,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     free_bathy(ctx);
     ctx->has_bathy = ctx->has_state = false;
     ctx->n = n;
+    free_members(ctx);
     const size_t nd = ctx->nd;
     CK(cudaMalloc(&ctx->x0y0, 2 * n * sizeof(double)));
     CK(cudaMalloc(&ctx->hxhy, 2 * n * sizeof(double)));
@@ -761,6 +813,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     ctx->x0y0_h.assign(x0y0, x0y0 + 2 * n);
     ctx->hxhy_h.assign(hxhy, hxhy + 2 * n);
     ctx->finfo_h = fi;
+    ctx->nbr_h.assign(nbr, nbr + 8 * n);
     Dev& d = ctx->d;
     d.n = n;
     d.x0y0 = ctx->x0y0;
@@ -779,18 +832,24 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     d.CNbar = ctx->CNbar;
     d.flag = ctx->flag;
     d.any_friction = 0;
-    ctx->grid = grid_for(n);
+    default_shapes(ctx);
     ctx->has_mesh = true;
     return SWDG_OK;
 }
 
-int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t nx, int64_t ny,
-                           double xo, double yo, double dx, double dy) {
-    if (!ctx) return SWDG_EINVAL;
-    if (!ctx->has_mesh) return fail(ctx, SWDG_ESTATE, "upload_bathymetry: no mesh");
-    if (!raster || (dtype != SWDG_PIX_F32 && dtype != SWDG_PIX_F64) || nx < 2 || ny < 2 ||
-        !(dx > 0) || !(dy > 0))
-        return fail(ctx, SWDG_EINVAL, "upload_bathymetry: bad arguments");
+// bathymetry of every cell from nseg rasters: cells [first[i], first[i+1])
+// take their pixels (mode S) or point samples (mode P) from raster i, whose
+// geometry is geo[4 i ..] = (x_origin, y_origin, dx, dy) and size nxny[2 i ..]
+static int upload_bathy(swdg_ctx* ctx, int nseg, const void* const* rasters, int dtype,
+                        const int64_t* nxny, const double* geo, const int64_t* first) {
+    const char* who = "upload_bathymetry";
+    if (!ctx->has_mesh) return fail(ctx, SWDG_ESTATE, "%s: no mesh", who);
+    if (dtype != SWDG_PIX_F32 && dtype != SWDG_PIX_F64)
+        return fail(ctx, SWDG_EINVAL, "%s: bad pixel dtype", who);
+    for (int i = 0; i < nseg; ++i)
+        if (!rasters[i] || nxny[2 * i] < 2 || nxny[2 * i + 1] < 2 || !(geo[4 * i + 2] > 0) ||
+            !(geo[4 * i + 3] > 0) || !std::isfinite(geo[4 * i]) || !std::isfinite(geo[4 * i + 1]))
+            return fail(ctx, SWDG_EINVAL, "%s: bad raster %d", who, i);
     const int64_t n = ctx->n;
     const size_t es = dtype == SWDG_PIX_F32 ? 4 : 8;
     const int R_ = ctx->R, nv_ = (3 * R_) / 2 + 1, nm_ = R_ + 2, ng_ = R_ + 1;
@@ -805,58 +864,67 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
         row0.resize(n);
         toff.resize(n);
         cls.resize(n);
-        for (int64_t k = 0; k < n; ++k) {
-            const double cx = (ctx->x0y0_h[2 * k] - xo) / dx, cy = (ctx->x0y0_h[2 * k + 1] - yo) / dy;
-            const double px = ctx->hxhy_h[2 * k] / dx, py = ctx->hxhy_h[2 * k + 1] / dy;
-            const double rcx = std::floor(cx + 0.5), rcy = std::floor(cy + 0.5);
-            const double rpx = std::floor(px + 0.5), rpy = std::floor(py + 0.5);
-            if (std::fabs(cx - rcx) > 1e-6 || std::fabs(cy - rcy) > 1e-6 ||
-                std::fabs(px - rpx) > 1e-6 || std::fabs(py - rpy) > 1e-6 || rpx != rpy)
-                return fail(ctx, SWDG_EINVAL,
-                            "upload_bathymetry: cell %lld does not span the same whole number of "
-                            "pixels in x and y, aligned to pixel edges",
-                            (long long)k);
-            const int P = (int)rpx;
-            if (P < 1 || P > MXPIX)
-                return fail(ctx, SWDG_EINVAL, "upload_bathymetry: %d pixels per cell side (max %d)",
-                            P, MXPIX);
-            if (rcx < 0 || rcy < 0 || rcx + P > nx || rcy + P > ny)
-                return fail(ctx, SWDG_EINVAL, "upload_bathymetry: raster does not cover cell %lld",
-                            (long long)k);
-            int c = -1;
-            for (size_t i = 0; i < Ps.size(); ++i)
-                if (Ps[i] == P) c = (int)i;
-            if (c < 0) {
-                if ((int)Ps.size() == MXCLS)
+        for (int sg = 0; sg < nseg; ++sg) {
+            const double xo = geo[4 * sg], yo = geo[4 * sg + 1], dx = geo[4 * sg + 2],
+                         dy = geo[4 * sg + 3];
+            const int64_t nx = nxny[2 * sg], ny = nxny[2 * sg + 1];
+            for (int64_t k = first[sg]; k < first[sg + 1]; ++k) {
+                const double cx = (ctx->x0y0_h[2 * k] - xo) / dx,
+                             cy = (ctx->x0y0_h[2 * k + 1] - yo) / dy;
+                const double px = ctx->hxhy_h[2 * k] / dx, py = ctx->hxhy_h[2 * k + 1] / dy;
+                const double rcx = std::floor(cx + 0.5), rcy = std::floor(cy + 0.5);
+                const double rpx = std::floor(px + 0.5), rpy = std::floor(py + 0.5);
+                if (std::fabs(cx - rcx) > 1e-6 || std::fabs(cy - rcy) > 1e-6 ||
+                    std::fabs(px - rpx) > 1e-6 || std::fabs(py - rpy) > 1e-6 || rpx != rpy)
                     return fail(ctx, SWDG_EINVAL,
-                                "upload_bathymetry: more than %d distinct pixel counts per cell",
-                                MXCLS);
-                Ps.push_back(P);
-                c = (int)Ps.size() - 1;
+                                "%s: cell %lld does not span the same whole number of pixels in x "
+                                "and y, aligned to pixel edges",
+                                who, (long long)k);
+                const int P = (int)rpx;
+                if (P < 1 || P > MXPIX)
+                    return fail(ctx, SWDG_EINVAL, "%s: %d pixels per cell side (max %d)", who, P,
+                                MXPIX);
+                if (rcx < 0 || rcy < 0 || rcx + P > nx || rcy + P > ny)
+                    return fail(ctx, SWDG_EINVAL, "%s: raster %d does not cover cell %lld", who, sg,
+                                (long long)k);
+                int c = -1;
+                for (size_t i = 0; i < Ps.size(); ++i)
+                    if (Ps[i] == P) c = (int)i;
+                if (c < 0) {
+                    if ((int)Ps.size() == MXCLS)
+                        return fail(ctx, SWDG_EINVAL,
+                                    "%s: more than %d distinct pixel counts per cell", who, MXCLS);
+                    Ps.push_back(P);
+                    c = (int)Ps.size() - 1;
+                }
+                col0[k] = (int32_t)rcx;
+                row0[k] = (int32_t)rcy;
+                cls[k] = (uint8_t)c;
+                toff[k] = npix;
+                npix += (int64_t)P * P;
             }
-            col0[k] = (int32_t)rcx;
-            row0[k] = (int32_t)rcy;
-            cls[k] = (uint8_t)c;
-            toff[k] = npix;
-            npix += (int64_t)P * P;
         }
     }
     invalidate_graph(ctx);
     free_bathy(ctx);
-    void* ras = nullptr;
-    CK(cudaMalloc(&ras, nx * ny * es));
-    CK(cudaMemcpyAsync(ras, raster, nx * ny * es, cudaMemcpyHostToDevice, ctx->st));
+    ctx->has_bathy = false;
     CK(cudaMalloc(&ctx->zmax, n * sizeof(double)));
     CK(cudaMalloc(&ctx->zmin, n * sizeof(double)));
     CK(cudaMalloc(&ctx->zabs, n * sizeof(double)));
     CK(cudaMalloc(&ctx->zpts, (size_t)n * nzp_ * sizeof(double)));
     CK(cudaMalloc(&ctx->zhang, (size_t)n * 8 * nm_ * sizeof(double)));
-    const int gw = (int)std::min<int64_t>(152 * 32, (n * 32 + 255) / 256 + 1); // warp-per-cell grids
+    // one raster on the device at a time
+    auto put_raster = [&](int sg, void** ras) -> int {
+        const size_t bytes = (size_t)nxny[2 * sg] * nxny[2 * sg + 1] * es;
+        CK(cudaMalloc(ras, bytes));
+        CK(cudaMemcpyAsync(*ras, rasters[sg], bytes, cudaMemcpyHostToDevice, ctx->st));
+        return SWDG_OK;
+    };
     if (ctx->mode == 0) {
         std::vector<OvTab> ovh(Ps.size());
         for (size_t i = 0; i < Ps.size(); ++i)
             if (!build_overlaps(ctx->R, Ps[i], ctx->tb, ovh[i]))
-                return fail(ctx, SWDG_EINVAL, "upload_bathymetry: bad pixel count");
+                return fail(ctx, SWDG_EINVAL, "%s: bad pixel count", who);
         int32_t *c0 = nullptr, *r0 = nullptr;
         CK(cudaMalloc(&c0, n * sizeof(int32_t)));
         CK(cudaMalloc(&r0, n * sizeof(int32_t)));
@@ -871,9 +939,28 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
         CK(cudaMemcpyAsync(ctx->ov, ovh.data(), Ps.size() * sizeof(OvTab), cudaMemcpyHostToDevice,
                            ctx->st));
         CK(cudaMalloc(&ctx->tiles, (size_t)npix * es));
+        for (int sg = 0; sg < nseg; ++sg) {
+            const int64_t k0 = first[sg], nk = first[sg + 1] - first[sg];
+            if (nk == 0) continue;
+            void* ras = nullptr;
+            int rc = put_raster(sg, &ras);
+            if (rc) return rc;
+            const int gw = (int)std::min<int64_t>(152 * 32, (nk * 32 + 255) / 256 + 1);
+            if (dtype == SWDG_PIX_F32)
+                k_retile<float><<<gw, 256, 0, ctx->st>>>((const float*)ras, nxny[2 * sg], c0 + k0,
+                                                        r0 + k0, ctx->tile_off + k0, ctx->pcls + k0,
+                                                        ctx->ov, (float*)ctx->tiles, nk);
+            else
+                k_retile<double><<<gw, 256, 0, ctx->st>>>((const double*)ras, nxny[2 * sg], c0 + k0,
+                                                         r0 + k0, ctx->tile_off + k0,
+                                                         ctx->pcls + k0, ctx->ov,
+                                                         (double*)ctx->tiles, nk);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(ctx->st));
+            cudaFree(ras);
+        }
+        const int gw = (int)std::min<int64_t>(152 * 32, (n * 32 + 255) / 256 + 1); // warp per cell
         if (dtype == SWDG_PIX_F32) {
-            k_retile<float><<<gw, 256, 0, ctx->st>>>((const float*)ras, nx, c0, r0, ctx->tile_off,
-                                                    ctx->pcls, ctx->ov, (float*)ctx->tiles, n);
             k_tile_bounds<float><<<gw, 256, 0, ctx->st>>>((const float*)ctx->tiles, ctx->tile_off,
                                                          ctx->pcls, ctx->ov, n, ctx->zmax, ctx->zmin,
                                                          ctx->zabs);
@@ -881,8 +968,6 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
                 (const float*)ctx->tiles, ctx->tile_off, ctx->pcls, ctx->ov, ctx->finfo, nv_, nm_, ng_,
                 ctx->zpts, ctx->zhang, n);
         } else {
-            k_retile<double><<<gw, 256, 0, ctx->st>>>((const double*)ras, nx, c0, r0, ctx->tile_off,
-                                                     ctx->pcls, ctx->ov, (double*)ctx->tiles, n);
             k_tile_bounds<double><<<gw, 256, 0, ctx->st>>>((const double*)ctx->tiles, ctx->tile_off,
                                                           ctx->pcls, ctx->ov, n, ctx->zmax,
                                                           ctx->zmin, ctx->zabs);
@@ -895,22 +980,38 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
         cudaFree(c0);
         cudaFree(r0);
     } else {
-        const int g2 = (int)std::min<int64_t>(152 * 16, (n + 127) / 128);
-        if (dtype == SWDG_PIX_F32)
-            k_point_samples<float><<<g2, 128, 0, ctx->st>>>(
-                (const float*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0, ctx->hxhy, ctx->finfo, ctx->tb,
-                nv_, nm_, ng_, ctx->zpts, ctx->zhang, ctx->zmax, ctx->zmin, ctx->zabs, n);
-        else
-            k_point_samples<double><<<g2, 128, 0, ctx->st>>>(
-                (const double*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0, ctx->hxhy, ctx->finfo, ctx->tb,
-                nv_, nm_, ng_, ctx->zpts, ctx->zhang, ctx->zmax, ctx->zmin, ctx->zabs, n);
-        CK(cudaGetLastError());
-        CK(cudaStreamSynchronize(ctx->st));
+        for (int sg = 0; sg < nseg; ++sg) {
+            const int64_t k0 = first[sg], nk = first[sg + 1] - first[sg];
+            if (nk == 0) continue;
+            void* ras = nullptr;
+            int rc = put_raster(sg, &ras);
+            if (rc) return rc;
+            const double xo = geo[4 * sg], yo = geo[4 * sg + 1], dx = geo[4 * sg + 2],
+                         dy = geo[4 * sg + 3];
+            const int64_t nx = nxny[2 * sg], ny = nxny[2 * sg + 1];
+            const int g2 = (int)std::min<int64_t>(152 * 16, (nk + 127) / 128);
+            if (dtype == SWDG_PIX_F32)
+                k_point_samples<float><<<g2, 128, 0, ctx->st>>>(
+                    (const float*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0 + 2 * k0,
+                    ctx->hxhy + 2 * k0, ctx->finfo + 4 * k0, ctx->tb, nv_, nm_, ng_,
+                    ctx->zpts + k0 * nzp_, ctx->zhang + k0 * 8 * nm_, ctx->zmax + k0,
+                    ctx->zmin + k0, ctx->zabs + k0, nk);
+            else
+                k_point_samples<double><<<g2, 128, 0, ctx->st>>>(
+                    (const double*)ras, nx, ny, xo, yo, dx, dy, ctx->x0y0 + 2 * k0,
+                    ctx->hxhy + 2 * k0, ctx->finfo + 4 * k0, ctx->tb, nv_, nm_, ng_,
+                    ctx->zpts + k0 * nzp_, ctx->zhang + k0 * 8 * nm_, ctx->zmax + k0,
+                    ctx->zmin + k0, ctx->zabs + k0, nk);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(ctx->st));
+            cudaFree(ras);
+        }
     }
-    cudaFree(ras);
     ctx->pix = dtype == SWDG_PIX_F32 ? 0 : 1;
     if (!get_launch(ctx->R, ctx->mode, ctx->pix, ctx->cfg.precision, &ctx->L))
-        return fail(ctx, SWDG_EINVAL, "upload_bathymetry: no kernels for this configuration");
+        return fail(ctx, SWDG_EINVAL, "%s: no kernels for this configuration", who);
+    if (!ctx->L.prepare())
+        return fail(ctx, SWDG_ECUDA, "%s: shared-memory opt-in of the kernels failed", who);
     Dev& d = ctx->d;
     d.tiles = ctx->tiles;
     d.tile_off = ctx->tile_off;
@@ -925,6 +1026,25 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
     return SWDG_OK;
 }
 
+int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t nx, int64_t ny,
+                           double xo, double yo, double dx, double dy) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!raster) return fail(ctx, SWDG_EINVAL, "upload_bathymetry: bad arguments");
+    const void* r[1] = {raster};
+    const int64_t nxny[2] = {nx, ny};
+    const double geo[4] = {xo, yo, dx, dy};
+    const int64_t first[2] = {0, ctx->n};
+    return upload_bathy(ctx, 1, r, dtype, nxny, geo, first);
+}
+
+int swdg_upload_bathymetry_members(swdg_ctx* ctx, const void* const* rasters, int dtype,
+                                   const int64_t* nxny, const double* geo) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!rasters || !nxny || !geo)
+        return fail(ctx, SWDG_EINVAL, "upload_bathymetry_members: bad arguments");
+    return upload_bathy(ctx, ctx->nmemb, rasters, dtype, nxny, geo, ctx->first.data());
+}
+
 int swdg_set_boundary(swdg_ctx* ctx, int tag, int kind, double amp, double period, double phase) {
     if (!ctx) return SWDG_EINVAL;
     if (tag < 0 || tag >= MXTAG || (kind != SWDG_BC_WALL && kind != SWDG_BC_TIDE) ||
@@ -935,6 +1055,18 @@ int swdg_set_boundary(swdg_ctx* ctx, int tag, int kind, double amp, double perio
     ctx->d.bc_per[tag] = period;
     ctx->d.bc_ph[tag] = phase;
     invalidate_graph(ctx);
+    if (ctx->nmemb > 1) {
+        // an ensemble: the same boundary for every member
+        for (Bc& b : ctx->bch) {
+            b.kind[tag] = kind;
+            b.amp[tag] = amp;
+            b.per[tag] = period;
+            b.ph[tag] = phase;
+        }
+        CK(cudaMemcpyAsync(ctx->bcd, ctx->bch.data(), ctx->bch.size() * sizeof(Bc),
+                           cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
     return SWDG_OK;
 }
 
@@ -971,7 +1103,7 @@ int swdg_set_state(swdg_ctx* ctx, const double* z, const double* qx, const doubl
                            where == SWDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                            ctx->st));
     CK(cudaMemsetAsync(ctx->flag, ctx->R, ctx->n, ctx->st));
-    ctx->L.masks(ctx->d, 0, ctx->grid, ctx->st);
+    ctx->L.masks(ctx->d, 0, ctx->shp[KK_AUX], ctx->st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->st));
     ctx->has_state = true;
@@ -992,12 +1124,39 @@ int swdg_get_state(swdg_ctx* ctx, double* z, double* qx, double* qy, double* c, 
     return SWDG_OK;
 }
 
-static int put_time(swdg_ctx* ctx, double t, double fixed_dt) {
-    ctx->pin[0] = t;
+__global__ void k_set_clocks(Member* mb, int nm, double t, int reset_rmax) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
+        mb[i].t = t;
+        if (reset_rmax) mb[i].rmax = 0ull;
+    }
+}
+
+// every member's clock to t (reset_rmax: also the CFL maximum)
+static int put_clocks(swdg_ctx* ctx, double t, int reset_rmax) {
+    k_set_clocks<<<(ctx->d.nmemb + 255) / 256, 256, 0, ctx->st>>>(ctx->d.mb, ctx->d.nmemb, t,
+                                                                 reset_rmax);
+    CK(cudaGetLastError());
+    return SWDG_OK;
+}
+
+static int put_fixed_dt(swdg_ctx* ctx, double fixed_dt) {
     ctx->pin[1] = fixed_dt;
-    CK(cudaMemcpyAsync(&ctx->sc->t, &ctx->pin[0], sizeof(double), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(&ctx->sc->fixed_dt, &ctx->pin[1], sizeof(double), cudaMemcpyHostToDevice,
                        ctx->st));
+    return SWDG_OK;
+}
+
+static int put_time(swdg_ctx* ctx, double t, double fixed_dt) {
+    int rc = put_clocks(ctx, t, 0);
+    return rc ? rc : put_fixed_dt(ctx, fixed_dt);
+}
+
+// the member clocks on the host
+static int read_clocks(swdg_ctx* ctx, std::vector<Member>& out) {
+    out.resize(ctx->d.nmemb);
+    CK(cudaMemcpyAsync(out.data(), ctx->d.mb, out.size() * sizeof(Member), cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
     return SWDG_OK;
 }
 
@@ -1007,7 +1166,7 @@ int swdg_residual(swdg_ctx* ctx, double t, double* F, double* Gx, double* Gy, do
     if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "residual: no state");
     int rc = put_time(ctx, t, -1.0);
     if (rc) return rc;
-    ctx->L.residual(ctx->d, ctx->tb, 0, 0, 0.0, 0, ctx->grid, ctx->st);
+    ctx->L.residual(ctx->d, ctx->tb, 0, 0, 0.0, 0, ctx->shp[KK_RESIDUAL], ctx->st);
     CK(cudaGetLastError());
     double* dst[6] = {F, Gx, Gy, R, Lx, Ly};
     const size_t sz = (size_t)ctx->n * ctx->nd * sizeof(double);
@@ -1023,17 +1182,22 @@ int swdg_residual(swdg_ctx* ctx, double t, double* F, double* Gx, double* Gy, do
 int swdg_cfl_dt(swdg_ctx* ctx, double t, double* dt) {
     if (!ctx || !dt) return SWDG_EINVAL;
     if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "cfl_dt: no state");
-    int rc = put_time(ctx, t, -1.0);
+    int rc = put_clocks(ctx, t, 1);
+    if (!rc) rc = put_fixed_dt(ctx, -1.0);
     if (rc) return rc;
-    ctx->pin[2] = 0.0;
-    CK(cudaMemcpyAsync(&ctx->sc->rmax, &ctx->pin[2], sizeof(double), cudaMemcpyHostToDevice,
-                       ctx->st));
-    ctx->L.residual(ctx->d, ctx->tb, 0, 0, 0.0, 1, ctx->grid, ctx->st);
+    ctx->L.residual(ctx->d, ctx->tb, 0, 0, 0.0, 1, ctx->shp[KK_RESIDUAL], ctx->st);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(&ctx->pin[3], &ctx->sc->rmax, sizeof(double), cudaMemcpyDeviceToHost,
-                       ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
-    *dt = ctx->cfg.cfl / ctx->pin[3];
+    std::vector<Member> mh;
+    rc = read_clocks(ctx, mh);
+    if (rc) return rc;
+    // the smallest member step: cfl / max over members of max lambda l / J
+    double rmax = 0.0;
+    for (const Member& m : mh) {
+        double r;
+        memcpy(&r, &m.rmax, sizeof r);
+        rmax = std::max(rmax, r);
+    }
+    *dt = ctx->cfg.cfl / rmax;
     return SWDG_OK;
 }
 
@@ -1046,7 +1210,7 @@ static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr) {
         if (ev) cudaEventRecord(ev[slot][which], ctx->st);
     };
     mark(0, 0);
-    ctx->L.step_begin(d, ctx->tb, 1, ctx->grid, ctx->st);
+    ctx->L.step_begin(d, ctx->tb, 1, ctx->shp[KK_BEGIN], ctx->st);
     mark(0, 1);
     for (int l = 0; l < s; ++l) {
         if (l > 0) {
@@ -1063,11 +1227,11 @@ static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr) {
             sa.make_llin = (l == s - 1 && d.at[l][l] != 0.0) ? 1 : 0;
             sa.final_ = 0;
             mark(4 + l, 0);
-            ctx->L.stage(d, ctx->tb, sa, ctx->grid, ctx->st);
+            ctx->L.stage(d, ctx->tb, sa, ctx->shp[KK_STAGE], ctx->st);
             mark(4 + l, 1);
         }
         mark(1 + l, 0);
-        ctx->L.residual(d, ctx->tb, l, l, d.c[l], l == 0 ? 1 : 0, ctx->grid, ctx->st);
+        ctx->L.residual(d, ctx->tb, l, l, d.c[l], l == 0 ? 1 : 0, ctx->shp[KK_RESIDUAL], ctx->st);
         mark(1 + l, 1);
     }
     StageArgs sa{};
@@ -1083,7 +1247,7 @@ static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr) {
     sa.make_llin = 0;
     sa.final_ = 1;
     mark(8, 0);
-    ctx->L.stage(d, ctx->tb, sa, ctx->grid, ctx->st);
+    ctx->L.stage(d, ctx->tb, sa, ctx->shp[KK_STAGE], ctx->st);
     mark(8, 1);
     CK(cudaGetLastError());
     return SWDG_OK;
@@ -1111,13 +1275,14 @@ int swdg_step(swdg_ctx* ctx, int n_steps, double dt, double* t_inout) {
     if (!ctx) return SWDG_EINVAL;
     if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "step: no state");
     if (n_steps < 0 || !std::isfinite(dt)) return fail(ctx, SWDG_EINVAL, "step: bad arguments");
-    if (t_inout) {
-        int rc = put_time(ctx, *t_inout, dt >= 0.0 ? dt : -1.0);
-        if (rc) return rc;
-    } else {
-        ctx->pin[1] = dt >= 0.0 ? dt : -1.0;
-        CK(cudaMemcpyAsync(&ctx->sc->fixed_dt, &ctx->pin[1], sizeof(double), cudaMemcpyHostToDevice,
-                           ctx->st));
+    if (t_inout && ctx->nmemb > 1)
+        return fail(ctx, SWDG_EINVAL,
+                    "step: an ensemble keeps one clock per member; pass t_inout = NULL and use "
+                    "swdg_member_times");
+    {
+        int rc0 = t_inout ? put_time(ctx, *t_inout, dt >= 0.0 ? dt : -1.0)
+                          : put_fixed_dt(ctx, dt >= 0.0 ? dt : -1.0);
+        if (rc0) return rc0;
     }
     int rc = ensure_graph(ctx);
     if (rc) return rc;
@@ -1130,7 +1295,7 @@ int swdg_step(swdg_ctx* ctx, int n_steps, double dt, double* t_inout) {
     }
     CK(cudaMemcpyAsync(ctx->sc_host, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    if (t_inout) *t_inout = ctx->sc_host->t;
+    if (t_inout) *t_inout = ctx->sc_host->m0.t;
     if (ctx->sc_host->status & ST_NAN) return fail(ctx, SWDG_ENAN, "step: non-finite state");
     return SWDG_OK;
 }
@@ -1139,13 +1304,11 @@ int swdg_step_profile(swdg_ctx* ctx, int n_steps, double dt, double* t_inout, do
     if (!ctx || !ms_out) return SWDG_EINVAL;
     if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "step_profile: no state");
     if (n_steps < 0 || !std::isfinite(dt)) return fail(ctx, SWDG_EINVAL, "step_profile: bad arguments");
-    int rc = t_inout ? put_time(ctx, *t_inout, dt >= 0.0 ? dt : -1.0) : SWDG_OK;
+    if (t_inout && ctx->nmemb > 1)
+        return fail(ctx, SWDG_EINVAL, "step_profile: pass t_inout = NULL for an ensemble");
+    int rc = t_inout ? put_time(ctx, *t_inout, dt >= 0.0 ? dt : -1.0)
+                     : put_fixed_dt(ctx, dt >= 0.0 ? dt : -1.0);
     if (rc) return rc;
-    if (!t_inout) {
-        ctx->pin[1] = dt >= 0.0 ? dt : -1.0;
-        CK(cudaMemcpyAsync(&ctx->sc->fixed_dt, &ctx->pin[1], sizeof(double), cudaMemcpyHostToDevice,
-                           ctx->st));
-    }
     cudaEvent_t ev[SWDG_PROF_SLOTS][2];
     for (int i = 0; i < SWDG_PROF_SLOTS; ++i) {
         ms_out[i] = 0.0;
@@ -1175,7 +1338,7 @@ int swdg_step_profile(swdg_ctx* ctx, int n_steps, double dt, double* t_inout, do
     }
     CK(cudaMemcpyAsync(ctx->sc_host, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    if (t_inout) *t_inout = ctx->sc_host->t;
+    if (t_inout) *t_inout = ctx->sc_host->m0.t;
     if (ctx->sc_host->status & ST_NAN) return fail(ctx, SWDG_ENAN, "step_profile: non-finite state");
     return SWDG_OK;
 }
@@ -1183,7 +1346,7 @@ int swdg_step_profile(swdg_ctx* ctx, int n_steps, double dt, double* t_inout, do
 int swdg_degree_switch(swdg_ctx* ctx, uint8_t* flags_out) {
     if (!ctx) return SWDG_EINVAL;
     if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "degree_switch: no state");
-    ctx->L.step_begin(ctx->d, ctx->tb, 1, ctx->grid, ctx->st);
+    ctx->L.step_begin(ctx->d, ctx->tb, 1, ctx->shp[KK_BEGIN], ctx->st);
     CK(cudaGetLastError());
     if (flags_out)
         CK(cudaMemcpyAsync(flags_out, ctx->flag, ctx->n, cudaMemcpyDeviceToHost, ctx->st));
@@ -1199,7 +1362,7 @@ int swdg_gather_gauges(swdg_ctx* ctx, int n, const double* xy, double* out) {
     double* buf = nullptr;
     CK(cudaMalloc(&buf, 3 * (size_t)n * sizeof(double)));
     CK(cudaMemcpyAsync(buf, xy, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-    ctx->L.gauges(ctx->d, ctx->tb, n, buf, buf + 2 * n, ctx->st);
+    ctx->L.gauges(ctx->d, ctx->tb, n, buf, buf + 2 * n, 0, ctx->n, ctx->st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, buf + 2 * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
@@ -1210,8 +1373,8 @@ int swdg_gather_gauges(swdg_ctx* ctx, int n, const double* xy, double* out) {
 int swdg_diagnostics(swdg_ctx* ctx, double out[8]) {
     if (!ctx || !out) return SWDG_EINVAL;
     if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "diagnostics: no state");
-    ctx->L.cell_diag(ctx->d, ctx->tb, ctx->diag, ctx->grid, ctx->st);
-    k_diag_reduce<<<1, 256, 0, ctx->st>>>(ctx->diag, ctx->n, ctx->diag + 4 * ctx->n);
+    ctx->L.cell_diag(ctx->d, ctx->tb, ctx->diag, ctx->shp[KK_AUX], ctx->st);
+    k_diag_reduce<<<1, 256, 0, ctx->st>>>(ctx->diag, nullptr, 0, ctx->n, ctx->diag + 4 * ctx->n);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ctx->pin, ctx->diag + 4 * ctx->n, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                        ctx->st));
@@ -1223,8 +1386,294 @@ int swdg_diagnostics(swdg_ctx* ctx, double out[8]) {
     out[3] = ctx->pin[3];
     out[4] = ctx->sc_host->maxits;
     out[5] = ctx->sc_host->viol;
-    out[6] = ctx->sc_host->dt_last;
-    out[7] = ctx->sc_host->t;
+    std::vector<Member> mh;
+    int rc = read_clocks(ctx, mh);
+    if (rc) return rc;
+    out[6] = mh[0].dt_last; // member 0 of an ensemble
+    out[7] = mh[0].t;
+    return SWDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ensembles: independent members stepped by the same launches
+// ---------------------------------------------------------------------------
+int swdg_set_members(swdg_ctx* ctx, int n_members, const int64_t* first_cell) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_mesh) return fail(ctx, SWDG_ESTATE, "set_members: no mesh");
+    if (n_members < 1 || n_members > SWDG_MAX_MEMBERS || !first_cell)
+        return fail(ctx, SWDG_EINVAL, "set_members: 1..%d members and first_cell required",
+                    SWDG_MAX_MEMBERS);
+    const int64_t n = ctx->n;
+    if (first_cell[0] != 0 || first_cell[n_members] != n)
+        return fail(ctx, SWDG_EINVAL, "set_members: first_cell must run from 0 to n_cells");
+    for (int m = 0; m < n_members; ++m)
+        if (first_cell[m + 1] <= first_cell[m])
+            return fail(ctx, SWDG_EINVAL, "set_members: member %d has no cells", m);
+    // members are independent problems: no face may join two of them
+    std::vector<int32_t> mh(n);
+    for (int m = 0; m < n_members; ++m)
+        for (int64_t k = first_cell[m]; k < first_cell[m + 1]; ++k) mh[k] = m;
+    for (int64_t k = 0; k < n; ++k)
+        for (int j = 0; j < 8; ++j) {
+            const int32_t nb = ctx->nbr_h[8 * k + j];
+            if (nb >= 0 && mh[nb] != mh[k])
+                return fail(ctx, SWDG_EINVAL,
+                            "set_members: cell %lld (member %d) neighbours cell %d of member %d",
+                            (long long)k, mh[k], nb, mh[nb]);
+        }
+    invalidate_graph(ctx);
+    free_members(ctx);
+    if (n_members == 1) return SWDG_OK;
+    ctx->nmemb = n_members;
+    ctx->first.assign(first_cell, first_cell + n_members + 1);
+    Bc b0{};
+    for (int i = 0; i < MXTAG; ++i) {
+        b0.kind[i] = ctx->d.bc_kind[i];
+        b0.amp[i] = ctx->d.bc_amp[i];
+        b0.per[i] = ctx->d.bc_per[i];
+        b0.ph[i] = ctx->d.bc_ph[i];
+    }
+    ctx->bch.assign(n_members, b0);
+    CK(cudaMalloc(&ctx->memb, n * sizeof(int32_t)));
+    CK(cudaMalloc(&ctx->mb, n_members * sizeof(Member)));
+    CK(cudaMalloc(&ctx->bcd, n_members * sizeof(Bc)));
+    CK(cudaMalloc(&ctx->first_d, (n_members + 1) * sizeof(int64_t)));
+    CK(cudaMalloc(&ctx->mdiag, 4 * (size_t)n_members * sizeof(double)));
+    CK(cudaMemcpyAsync(ctx->memb, mh.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemsetAsync(ctx->mb, 0, n_members * sizeof(Member), ctx->st));
+    CK(cudaMemcpyAsync(ctx->bcd, ctx->bch.data(), n_members * sizeof(Bc), cudaMemcpyHostToDevice,
+                       ctx->st));
+    CK(cudaMemcpyAsync(ctx->first_d, first_cell, (n_members + 1) * sizeof(int64_t),
+                       cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->d.memb = ctx->memb;
+    ctx->d.mb = ctx->mb;
+    ctx->d.mbc = ctx->bcd;
+    ctx->d.nmemb = n_members;
+    return SWDG_OK;
+}
+
+int swdg_set_boundary_member(swdg_ctx* ctx, int member, int tag, int kind, double amp,
+                             double period, double phase) {
+    if (!ctx) return SWDG_EINVAL;
+    if (ctx->nmemb == 1 && member == 0) return swdg_set_boundary(ctx, tag, kind, amp, period, phase);
+    if (member < 0 || member >= ctx->nmemb || tag < 0 || tag >= MXTAG ||
+        (kind != SWDG_BC_WALL && kind != SWDG_BC_TIDE) || (kind == SWDG_BC_TIDE && !(period > 0)) ||
+        !std::isfinite(amp) || !std::isfinite(phase))
+        return fail(ctx, SWDG_EINVAL, "set_boundary_member: bad arguments");
+    Bc& b = ctx->bch[member];
+    b.kind[tag] = kind;
+    b.amp[tag] = amp;
+    b.per[tag] = period;
+    b.ph[tag] = phase;
+    CK(cudaMemcpyAsync(ctx->bcd + member, &b, sizeof(Bc), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return SWDG_OK;
+}
+
+int swdg_member_times(swdg_ctx* ctx, double* t, double* dt_last, int set) {
+    if (!ctx) return SWDG_EINVAL;
+    const int M = ctx->d.nmemb;
+    std::vector<Member> mh;
+    int rc = read_clocks(ctx, mh);
+    if (rc) return rc;
+    if (set) {
+        if (!t) return fail(ctx, SWDG_EINVAL, "member_times: t required to set");
+        for (int m = 0; m < M; ++m)
+            if (!std::isfinite(t[m]))
+                return fail(ctx, SWDG_EINVAL, "member_times: t[%d] is not finite", m);
+        for (int m = 0; m < M; ++m) mh[m].t = t[m];
+        CK(cudaMemcpyAsync(ctx->d.mb, mh.data(), M * sizeof(Member), cudaMemcpyHostToDevice,
+                           ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        return SWDG_OK;
+    }
+    for (int m = 0; m < M; ++m) {
+        if (t) t[m] = mh[m].t;
+        if (dt_last) dt_last[m] = mh[m].dt_last;
+    }
+    return SWDG_OK;
+}
+
+int swdg_member_diagnostics(swdg_ctx* ctx, double* out) {
+    if (!ctx || !out) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "member_diagnostics: no state");
+    if (ctx->nmemb == 1) return swdg_diagnostics(ctx, out);
+    const int M = ctx->nmemb;
+    ctx->L.cell_diag(ctx->d, ctx->tb, ctx->diag, ctx->shp[KK_AUX], ctx->st);
+    k_diag_reduce<<<M, 256, 0, ctx->st>>>(ctx->diag, ctx->first_d, 0, 0, ctx->mdiag);
+    CK(cudaGetLastError());
+    std::vector<double> part(4 * (size_t)M);
+    CK(cudaMemcpyAsync(part.data(), ctx->mdiag, part.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(ctx->sc_host, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st));
+    std::vector<Member> mh;
+    int rc = read_clocks(ctx, mh);
+    if (rc) return rc;
+    for (int m = 0; m < M; ++m) {
+        double* o = out + 8 * (size_t)m;
+        for (int i = 0; i < 4; ++i) o[i] = part[4 * m + i];
+        o[4] = ctx->sc_host->maxits; // context-wide counters
+        o[5] = ctx->sc_host->viol;
+        o[6] = mh[m].dt_last;
+        o[7] = mh[m].t;
+    }
+    return SWDG_OK;
+}
+
+int swdg_gather_gauges_member(swdg_ctx* ctx, int member, int n, const double* xy, double* out) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "gather_gauges_member: no state");
+    if (member < 0 || member >= ctx->nmemb || n < 0 || (n > 0 && (!xy || !out)))
+        return fail(ctx, SWDG_EINVAL, "gather_gauges_member: bad arguments");
+    if (n == 0) return SWDG_OK;
+    double* buf = nullptr;
+    CK(cudaMalloc(&buf, 3 * (size_t)n * sizeof(double)));
+    CK(cudaMemcpyAsync(buf, xy, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    ctx->L.gauges(ctx->d, ctx->tb, n, buf, buf + 2 * n, ctx->first[member], ctx->first[member + 1],
+                  ctx->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, buf + 2 * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    cudaFree(buf);
+    return SWDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch shapes and their autotuner
+// ---------------------------------------------------------------------------
+int swdg_set_shape(swdg_ctx* ctx, int kind, int grid, int warps_per_block) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_bathy) return fail(ctx, SWDG_ESTATE, "set_shape: upload the bathymetry first");
+    if (kind < 0 || kind >= KK_N || warps_per_block < 1 || warps_per_block > MAXWPB || grid < 1 ||
+        ctx->L.occupancy(kind, warps_per_block) < 1)
+        return fail(ctx, SWDG_EINVAL, "set_shape: bad kind, grid or warps per block");
+    ctx->shp[kind] = Shape{grid, warps_per_block};
+    invalidate_graph(ctx);
+    return SWDG_OK;
+}
+
+int swdg_get_shapes(const swdg_ctx* ctx, int* out) {
+    if (!ctx || !out) return SWDG_EINVAL;
+    for (int i = 0; i < KK_N; ++i) {
+        out[2 * i] = ctx->shp[i].grid;
+        out[2 * i + 1] = ctx->shp[i].wpb;
+    }
+    return SWDG_OK;
+}
+
+// candidate c of kind k: warps per block and grid (persistent: SMs x resident
+// blocks; full: one block per wpb cells)
+static bool candidate(swdg_ctx* ctx, int kind, int c, Shape& s) {
+    static const int wpbs[4] = {1, 2, 4, 8};
+    if (c < 0 || c >= 8) return false;
+    const int wpb = wpbs[c / 2];
+    const int occ = ctx->L.occupancy(kind, wpb);
+    if (occ < 1) return false;
+    const int64_t cover = (ctx->n + wpb - 1) / wpb;
+    const int64_t pers = (int64_t)ctx->nsm * occ;
+    int64_t g = (c % 2 == 0) ? std::min(pers, cover) : std::min<int64_t>(cover, 152LL * 64 * 4 / wpb);
+    s = Shape{(int)std::max<int64_t>(1, g), wpb};
+    return true;
+}
+
+int swdg_autotune(swdg_ctx* ctx, int repeats, double* report) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "autotune: no state");
+    if (repeats < 1) repeats = 1;
+    const int64_t n = ctx->n;
+    const size_t ubytes = 4 * (size_t)n * ctx->nd * sizeof(double);
+    // snapshot: state buffer 0, its masks, the counters and every member clock
+    double* usave = nullptr;
+    uint8_t* msave = nullptr;
+    CK(cudaMalloc(&usave, ubytes));
+    CK(cudaMalloc(&msave, n));
+    std::vector<Member> clocks;
+    int rc = read_clocks(ctx, clocks);
+    if (rc) return rc;
+    Scalars sc0;
+    CK(cudaMemcpyAsync(&sc0, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(usave, ctx->U, ubytes, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(msave, ctx->cmask, n, cudaMemcpyDeviceToDevice, ctx->st));
+    rc = put_fixed_dt(ctx, -1.0); // tuning steps take the CFL step
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->st));
+    const Shape keep[KK_N] = {ctx->shp[0], ctx->shp[1], ctx->shp[2], ctx->shp[3]};
+    double best[KK_N];
+    Shape pick[KK_N];
+    for (int k = 0; k < KK_N; ++k) {
+        best[k] = INFINITY;
+        pick[k] = keep[k];
+    }
+    cudaEvent_t ev[SWDG_PROF_SLOTS][2];
+    for (int i = 0; i < SWDG_PROF_SLOTS; ++i) {
+        cudaEventCreate(&ev[i][0]);
+        cudaEventCreate(&ev[i][1]);
+    }
+    bool used[SWDG_PROF_SLOTS] = {};
+    used[0] = used[8] = true;
+    for (int l = 0; l < ctx->d.s; ++l) {
+        used[1 + l] = true;
+        if (l > 0) used[4 + l] = true;
+    }
+    for (int c = 0; c < 8 && !rc; ++c) {
+        Shape cs[KK_N];
+        bool ok[KK_N];
+        for (int k = 0; k < KK_N; ++k) {
+            ok[k] = candidate(ctx, k, c, cs[k]);
+            ctx->shp[k] = ok[k] ? cs[k] : keep[k];
+        }
+        double tk[KK_N] = {0, 0, 0, 0};
+        for (int r = 0; r < repeats + 1 && !rc; ++r) { // first pass: warm-up
+            rc = enqueue_step(ctx, ev);
+            if (rc) break;
+            if (cudaStreamSynchronize(ctx->st) != cudaSuccess) {
+                rc = fail(ctx, SWDG_ECUDA, "autotune: step failed");
+                break;
+            }
+            if (r == 0) continue;
+            for (int sl = 0; sl < SWDG_PROF_SLOTS; ++sl) {
+                if (!used[sl]) continue;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, ev[sl][0], ev[sl][1]);
+                const int k = sl == 0 ? KK_BEGIN : (sl <= 4 ? KK_RESIDUAL : KK_STAGE);
+                tk[k] += ms;
+            }
+        }
+        for (int k = 0; k < 3 && !rc; ++k)
+            if (ok[k] && tk[k] < best[k]) {
+                best[k] = tk[k];
+                pick[k] = cs[k];
+            }
+    }
+    for (int i = 0; i < SWDG_PROF_SLOTS; ++i) {
+        cudaEventDestroy(ev[i][0]);
+        cudaEventDestroy(ev[i][1]);
+    }
+    // restore the state, masks, counters and clocks the tuning steps advanced
+    cudaMemcpyAsync(ctx->U, usave, ubytes, cudaMemcpyDeviceToDevice, ctx->st);
+    cudaMemcpyAsync(ctx->cmask, msave, n, cudaMemcpyDeviceToDevice, ctx->st);
+    cudaMemcpyAsync(ctx->sc, &sc0, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->st);
+    cudaMemcpyAsync(ctx->d.mb, clocks.data(), clocks.size() * sizeof(Member),
+                    cudaMemcpyHostToDevice, ctx->st);
+    cudaError_t e = cudaStreamSynchronize(ctx->st);
+    cudaFree(usave);
+    cudaFree(msave);
+    if (rc) {
+        for (int k = 0; k < KK_N; ++k) ctx->shp[k] = keep[k];
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(ctx, SWDG_ECUDA, "autotune: restore failed");
+    for (int k = 0; k < 3; ++k) ctx->shp[k] = pick[k];
+    ctx->shp[KK_AUX] = keep[KK_AUX];
+    ctx->tuned = true;
+    invalidate_graph(ctx);
+    if (report)
+        for (int k = 0; k < 3; ++k) {
+            report[3 * k] = pick[k].grid;
+            report[3 * k + 1] = pick[k].wpb;
+            report[3 * k + 2] = best[k] / repeats;
+        }
     return SWDG_OK;
 }
 
@@ -1243,10 +1692,10 @@ static void* g_noalloc_addr[256];   // device address of the array, per device o
 static bool g_noalloc_ready[256];
 
 __global__ void k_noalloc_begin(Scalars* sc, double t) {
-    sc->t = t;
+    sc->m0.t = t;
     sc->fixed_dt = -1.0;
-    sc->dt_last = 0.0;
-    sc->rmax = 0ull;
+    sc->m0.dt_last = 0.0;
+    sc->m0.rmax = 0ull;
     sc->maxits = 0;
     sc->viol = 0;
     sc->fallback = 0;
@@ -1275,7 +1724,7 @@ __global__ void k_noalloc_check_mesh(const double* hxhy, const int32_t* nbr, int
 }
 
 __global__ void k_noalloc_end(const Scalars* sc, double cfl, double* dt_out) {
-    *dt_out = cfl / __longlong_as_double(sc->rmax);
+    *dt_out = cfl / __longlong_as_double(sc->m0.rmax);
 }
 
 static int noalloc_fail(char* err, int err_len, int code, const char* msg) {
@@ -1338,6 +1787,8 @@ extern "C" int swdg_residual_noalloc(const swdg_config* cfg, int64_t n, const do
     d.cmask = cmask;
     d.res = residual;
     d.sc = sc;
+    d.mb = &sc->m0;
+    d.nmemb = 1;
     d.mode = 0;
     d.g = cfg->g;
     d.eps = cfg->eps_vel;
@@ -1365,9 +1816,9 @@ extern "C" int swdg_residual_noalloc(const swdg_config* cfg, int64_t n, const do
         return noalloc_fail(err, err_len, SWDG_EINVAL,
                             "residual_noalloc: bad mesh (sizes, neighbour indices, tags or a "
                             "non-conforming face)");
-    const int grid = grid_for(n);
-    L.masks(d, 0, grid, st);
-    L.residual(d, tb, 0, 0, 0.0, 1, grid, st);
+    const Shape shp{grid_for(n), WPB};
+    L.masks(d, 0, shp, st);
+    L.residual(d, tb, 0, 0, 0.0, 1, shp, st);
     if (dt_out) k_noalloc_end<<<1, 1, 0, st>>>(sc, cfg->cfl, dt_out);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

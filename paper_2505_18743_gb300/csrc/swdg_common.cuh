@@ -74,11 +74,23 @@ struct Tables {
     double xq[3][MXP];                          // nodes of the three point sets on [0, 1]
 };
 
-struct Scalars {
+// clock of one ensemble member (a plain context is an ensemble of one)
+struct Member {
     double t;                 // time at the start of the current step
-    double fixed_dt;          // >= 0: fixed step, < 0: CFL
     double dt_last;
-    unsigned long long rmax;  // bits of max lambda l_Gamma / J_K (non-negative double)
+    unsigned long long rmax;  // bits of max lambda l_Gamma / J_K over the member (non-negative double)
+    double pad_;
+};
+
+// boundary table of one member: kind (SWDG_BC_*) and tide of every tag
+struct Bc {
+    int kind[MXTAG];
+    double amp[MXTAG], per[MXTAG], ph[MXTAG];
+};
+
+struct Scalars {
+    Member m0;                // the clock of a single-member context
+    double fixed_dt;          // >= 0: fixed step, < 0: CFL
     int maxits, viol, fallback, status;
 };
 
@@ -109,6 +121,10 @@ struct Dev {
     double* CNbar;
     uint8_t* flag;
     Scalars* sc;
+    Member* mb;            // member clocks [nmemb] (a single member: &sc->m0)
+    const int32_t* memb;   // member of each cell (null: every cell in member 0)
+    const Bc* mbc;         // per-member boundary tables (null: the tables below)
+    int nmemb;
     int mode; // 0 S, 1 P
     int s;    // stages
     double g, eps, hlim, eps0, cfl, newton_tol;
@@ -145,9 +161,14 @@ __device__ __forceinline__ double* rfield(const Dev& d, int stage, int f, int nd
     return d.res + ((size_t)stage * 6 + f) * (size_t)d.n * nd;
 }
 
-__device__ __forceinline__ double get_dt(const Dev& d) {
-    // dt = cfl min J/(lambda l) = cfl / max(lambda l / J), Eq. deltat_fe
-    return d.sc->fixed_dt >= 0.0 ? d.sc->fixed_dt : d.cfl / __longlong_as_double(d.sc->rmax);
+__device__ __forceinline__ int member_of(const Dev& d, int64_t k) {
+    return d.memb ? d.memb[k] : 0;
+}
+
+__device__ __forceinline__ double get_dt(const Dev& d, int m) {
+    // dt = cfl min J/(lambda l) = cfl / max(lambda l / J) over the member's
+    // cells, Eq. deltat_fe
+    return d.sc->fixed_dt >= 0.0 ? d.sc->fixed_dt : d.cfl / __longlong_as_double(d.mb[m].rmax);
 }
 
 // desingularised velocity factor u = f q, Eq. velocity (T = double or float)

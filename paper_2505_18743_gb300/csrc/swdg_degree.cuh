@@ -8,30 +8,60 @@ namespace swdg {
 
 template <int R, typename Pix, int MODE, typename B>
 struct Launchers {
+    using S = Sz<R>;
+    static constexpr size_t res_b = sizeof(double) * res_smem<R, B>();   // per warp
+    static constexpr size_t begin_b = sizeof(double) * begin_smem<R>();
+    static constexpr size_t stage_b = sizeof(double) * stage_smem<R>();
+    static constexpr size_t diag_b = sizeof(double) * (2 * S::ND + 2 * S::NMP + 2 * S::NM * S::NM);
+
     static void residual(const Dev& d, const Tables& tb, int buf, int stage, double c_stage,
-                         int want_dt, int grid, cudaStream_t st) {
-        size_t sm = sizeof(double) * res_smem<R, B>() * WPB;
-        k_residual<R, Pix, MODE, B><<<grid, TPB, sm, st>>>(d, tb, buf, stage, c_stage, want_dt);
+                         int want_dt, Shape s, cudaStream_t st) {
+        k_residual<R, Pix, MODE, B><<<s.grid, 32 * s.wpb, res_b * s.wpb, st>>>(d, tb, buf, stage,
+                                                                              c_stage, want_dt);
     }
-    static void step_begin(const Dev& d, const Tables& tb, int do_switch, int grid, cudaStream_t st) {
-        size_t sm = sizeof(double) * begin_smem<R>() * WPB;
-        k_step_begin<R, Pix, MODE><<<grid, TPB, sm, st>>>(d, tb, do_switch);
+    static void step_begin(const Dev& d, const Tables& tb, int do_switch, Shape s, cudaStream_t st) {
+        k_step_begin<R, Pix, MODE><<<s.grid, 32 * s.wpb, begin_b * s.wpb, st>>>(d, tb, do_switch);
     }
-    static void stage(const Dev& d, const Tables& tb, const StageArgs& sa, int grid, cudaStream_t st) {
-        size_t sm = sizeof(double) * stage_smem<R>() * WPB;
-        k_stage<R, Pix, MODE, B><<<grid, TPB, sm, st>>>(d, tb, sa);
+    static void stage(const Dev& d, const Tables& tb, const StageArgs& sa, Shape s, cudaStream_t st) {
+        k_stage<R, Pix, MODE, B><<<s.grid, 32 * s.wpb, stage_b * s.wpb, st>>>(d, tb, sa);
     }
-    static void masks(const Dev& d, int buf, int grid, cudaStream_t st) {
-        k_masks<R><<<grid, TPB, 0, st>>>(d, buf);
+    static void masks(const Dev& d, int buf, Shape s, cudaStream_t st) {
+        k_masks<R><<<s.grid, 32 * s.wpb, 0, st>>>(d, buf);
     }
-    static void cell_diag(const Dev& d, const Tables& tb, double* part, int grid, cudaStream_t st) {
-        using S = Sz<R>;
-        size_t sm = sizeof(double) * (2 * S::ND + 2 * S::NMP + 2 * S::NM * S::NM) * WPB;
-        k_cell_diag<R, Pix, MODE><<<grid, TPB, sm, st>>>(d, tb, part);
+    static void cell_diag(const Dev& d, const Tables& tb, double* part, Shape s, cudaStream_t st) {
+        k_cell_diag<R, Pix, MODE><<<s.grid, 32 * s.wpb, diag_b * s.wpb, st>>>(d, tb, part);
     }
     static void gauges(const Dev& d, const Tables& tb, int ng, const double* xy, double* out,
-                       cudaStream_t st) {
-        k_gauges<R><<<(ng + 63) / 64, 64, 0, st>>>(d, tb, ng, xy, out);
+                       int64_t k0, int64_t k1, cudaStream_t st) {
+        k_gauges<R><<<(ng + 63) / 64, 64, 0, st>>>(d, tb, ng, xy, out, k0, k1);
+    }
+    template <typename K>
+    static bool opt_in(K kern, size_t per_warp) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(per_warp * MAXWPB)) == cudaSuccess;
+    }
+    static bool prepare() {
+        return opt_in(k_residual<R, Pix, MODE, B>, res_b) &&
+               opt_in(k_step_begin<R, Pix, MODE>, begin_b) &&
+               opt_in(k_stage<R, Pix, MODE, B>, stage_b) &&
+               opt_in(k_cell_diag<R, Pix, MODE>, diag_b);
+    }
+    template <typename K>
+    static int occ(K kern, int wpb, size_t per_warp) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * wpb, per_warp * wpb) !=
+            cudaSuccess)
+            return 0;
+        return nb;
+    }
+    static int occupancy(int kind, int wpb) {
+        if (wpb < 1 || wpb > MAXWPB) return 0;
+        switch (kind) {
+        case KK_BEGIN: return occ(k_step_begin<R, Pix, MODE>, wpb, begin_b);
+        case KK_RESIDUAL: return occ(k_residual<R, Pix, MODE, B>, wpb, res_b);
+        case KK_STAGE: return occ(k_stage<R, Pix, MODE, B>, wpb, stage_b);
+        default: return occ(k_cell_diag<R, Pix, MODE>, wpb, diag_b);
+        }
     }
     static void fill(Launch* L) {
         L->residual = &residual;
@@ -40,6 +70,8 @@ struct Launchers {
         L->masks = &masks;
         L->cell_diag = &cell_diag;
         L->gauges = &gauges;
+        L->prepare = &prepare;
+        L->occupancy = &occupancy;
         L->nzp = Sz<R>::NZP;
     }
 };

@@ -2,7 +2,9 @@
 // path (arXiv 2505.18743): residual (Sec. 3.2), degree switch (Eq.
 // criteria_p), stage update (Sec. 3.1) and auxiliary reductions.
 //
-// Mapping: one warp per cell, four warps per block, grid-stride over cells.
+// Mapping: one warp per cell, a launch-time number of warps per block (1..8,
+// chosen by the autotuner), grid-stride over cells; one launch covers every
+// member of an ensemble.
 // Each warp stages its cell in shared memory and evaluates the tensor-product
 // operators by sum factorisation (1D contractions), one quadrature point,
 // degree of freedom or face point per lane.
@@ -11,8 +13,8 @@
 
 namespace swdg {
 
-constexpr int WPB = 4; // warps per block
-constexpr int TPB = 32 * WPB;
+constexpr int WPB = 4;    // default warps per block
+constexpr int MAXWPB = 8; // largest block the kernels are compiled for
 
 // ---------------------------------------------------------------------------
 // small tensor contractions on a warp (all arrays in shared memory, x fastest)
@@ -288,14 +290,14 @@ __device__ __forceinline__ const B (*tab_or(const double (*d)[MXN], const float 
 // FP64 round-off and the lake at rest exactly); the momentum, friction and
 // flux arithmetic is FP32.
 template <int R, typename Pix, int MODE, typename B>
-__global__ void __launch_bounds__(TPB, 5)
+__global__ void __maxnreg__(96)
     k_residual(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, int buf,
                int stage, double c_stage, int want_dt) {
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NV = S::NV, NVP = S::NVP, NM = S::NM;
     extern __shared__ double smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     double* su = smem + warp * res_smem<R, B>();
     double* tz = su + 4 * ND;           // [2][ND1][NV] x-contractions of zeta: value, d/dxi
     double* Xd = tz + 2 * ND1 * NV;     // [4][NVP]: F_x, F_y, R_x, R_y
@@ -312,10 +314,9 @@ __global__ void __launch_bounds__(TPB, 5)
     const auto BmB = tab_or<B>(tb.Bm, tb.BmF);
     const double g = d.g, eps = d.eps;
     const B gB = (B)g, epsB = (B)eps;
-    const double t = (c_stage == 0.0) ? d.sc->t : d.sc->t + c_stage * get_dt(d);
     const int64_t n = d.n;
 
-    for (int64_t k = (int64_t)blockIdx.x * WPB + warp; k < n; k += (int64_t)gridDim.x * WPB) {
+    for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n; k += (int64_t)gridDim.x * wpb) {
         for (int i = lane; i < 4 * ND; i += 32) {
             const double v = ufield(d, buf, i / ND, ND)[k * ND + (i % ND)];
             su[i] = v;
@@ -326,6 +327,9 @@ __global__ void __launch_bounds__(TPB, 5)
         const double ihx = d.ihxhy ? d.ihxhy[2 * k] : 1.0 / hx;
         const double ihy = d.ihxhy ? d.ihxhy[2 * k + 1] : 1.0 / hy;
         const B manB = (B)d.manning[k];
+        // the member's stage time t^n + c_l dt (boundary data)
+        const int mem = member_of(d, k);
+        const double t = (c_stage == 0.0) ? d.mb[mem].t : d.mb[mem].t + c_stage * get_dt(d, mem);
         __syncwarp();
         // x-contractions: zeta (value, d/dxi) in FP64, qx, qy, c in B
         for (int i = lane; i < 2 * ND1 * NV; i += 32) {
@@ -531,8 +535,12 @@ __global__ void __launch_bounds__(TPB, 5)
                 const int tag = -1 - s0;
                 zp = zm;
                 tp[0] = tm[0]; tp[1] = tm[1]; tp[2] = tm[2];
-                if (d.bc_kind[tag] == 1) {
-                    zp = d.bc_amp[tag] * sin(2.0 * M_PI * t / d.bc_per[tag] + d.bc_ph[tag]);
+                const bool tide = d.mbc ? d.mbc[mem].kind[tag] == 1 : d.bc_kind[tag] == 1;
+                if (tide) {
+                    const double amp = d.mbc ? d.mbc[mem].amp[tag] : d.bc_amp[tag];
+                    const double per = d.mbc ? d.mbc[mem].per[tag] : d.bc_per[tag];
+                    const double ph = d.mbc ? d.mbc[mem].ph[tag] : d.bc_ph[tag];
+                    zp = amp * sin(2.0 * M_PI * t / per + ph);
                 } else {
                     const B qn = tm[0] * (B)nx + tm[1] * (B)ny;
                     tp[0] = tm[0] - B(2) * qn * (B)nx;
@@ -555,7 +563,7 @@ __global__ void __launch_bounds__(TPB, 5)
         }
         if (want_dt) {
             const double m = warp_max(dtl);
-            if (lane == 0) atomic_max_pos(&d.sc->rmax, m);
+            if (lane == 0) atomic_max_pos(&d.mb[mem].rmax, m);
         }
         __syncwarp();
         // lift the face fluxes onto the nodes of each face
@@ -636,13 +644,13 @@ constexpr int begin_smem() {
 }
 
 template <int R, typename Pix, int MODE>
-__global__ void __launch_bounds__(TPB)
+__global__ void __launch_bounds__(32 * MAXWPB)
     k_step_begin(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, int do_switch) {
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
     extern __shared__ double smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     double* su = smem + warp * begin_smem<R>();
     double* pe = su + 4 * ND;    // [NMP] zeta at mass points
     double* pc = pe + NMP;       // [NMP] c at mass points
@@ -652,11 +660,11 @@ __global__ void __launch_bounds__(TPB)
     double* pg = tmp + 2 * NM * NM; // [3][NGP]
     double* out = pg + 3 * NGP;  // [2][ND]
     const int64_t n = d.n;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        d.sc->rmax = 0ull;
-        d.sc->maxits = 0;
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < d.nmemb; i += blockDim.x) d.mb[i].rmax = 0ull;
+        if (threadIdx.x == 0) d.sc->maxits = 0;
     }
-    for (int64_t k = (int64_t)blockIdx.x * WPB + warp; k < n; k += (int64_t)gridDim.x * WPB) {
+    for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n; k += (int64_t)gridDim.x * wpb) {
         for (int i = lane; i < 4 * ND; i += 32) su[i] = ufield(d, 0, i / ND, ND)[k * ND + (i % ND)];
         unsigned cm = d.cmask[k];
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
@@ -1075,13 +1083,13 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
 }
 
 template <int R, typename Pix, int MODE, typename B>
-__global__ void __launch_bounds__(TPB)
+__global__ void __maxnreg__(128)
     k_stage(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, const StageArgs sa) {
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
     extern __shared__ double smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     double* su = smem + warp * stage_smem<R>(); // [4][ND] state v^n
     double* T = su + 4 * ND;                    // [ND]
     double* rq = T + ND;                        // [2][ND]
@@ -1107,17 +1115,17 @@ __global__ void __launch_bounds__(TPB)
     double* mw = (double*)((((uintptr_t)(rf + ND)) + 7) & ~(uintptr_t)7);
     double* mt = mw + ND + 6 * NGP;
     const int64_t n = d.n;
-    const double dt = get_dt(d);
     const double g = d.g, eps = d.eps;
     int its_max = 0;
     int viol = 0, fb = 0, bad = 0;
 
-    for (int64_t k = (int64_t)blockIdx.x * WPB + warp; k < n; k += (int64_t)gridDim.x * WPB) {
+    for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n; k += (int64_t)gridDim.x * wpb) {
         for (int i = lane; i < 4 * ND; i += 32) su[i] = ufield(d, 0, i / ND, ND)[k * ND + (i % ND)];
         const unsigned cm0 = d.cmask[k];
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
         const double man = d.manning[k];
         int flag = d.flag[k];
+        const double dt = get_dt(d, member_of(d, k)); // the member's step
         // right-hand sides of Eqs. algebraic_elevation, algebraic_discharge, algebraic_concentration
         double tsum = 0.0;
         for (int i = lane; i < ND; i += 32) {
@@ -1343,9 +1351,13 @@ __global__ void __launch_bounds__(TPB)
         if (fb) atomicAdd(&d.sc->fallback, fb);
         if (bad) atomicOr(&d.sc->status, ST_NAN);
     }
-    if (sa.final_ && blockIdx.x == 0 && threadIdx.x == 0) {
-        d.sc->dt_last = dt;
-        d.sc->t = d.sc->t + dt;
+    if (sa.final_ && blockIdx.x == 0) {
+        // every member advances by its own step (rmax is not written here)
+        for (int i = threadIdx.x; i < d.nmemb; i += blockDim.x) {
+            const double dti = get_dt(d, i);
+            d.mb[i].dt_last = dti;
+            d.mb[i].t = d.mb[i].t + dti;
+        }
     }
 }
 
@@ -1355,8 +1367,8 @@ __global__ void __launch_bounds__(TPB)
 template <int R>
 __global__ void k_masks(const __grid_constant__ Dev d, int buf) {
     constexpr int ND = Sz<R>::ND;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t k = (int64_t)blockIdx.x * WPB + warp; k < d.n; k += (int64_t)gridDim.x * WPB) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < d.n; k += (int64_t)gridDim.x * wpb) {
         unsigned cm = 0;
         for (int f = 0; f < 4; ++f) {
             const double* u = ufield(d, buf, f, ND) + k * ND;
@@ -1372,17 +1384,17 @@ __global__ void k_masks(const __grid_constant__ Dev d, int buf) {
 // diagnostics: per-cell wet mass (Eq. positivity-7), tracer mass, min depth
 // ---------------------------------------------------------------------------
 template <int R, typename Pix, int MODE>
-__global__ void __launch_bounds__(TPB)
+__global__ void __launch_bounds__(32 * MAXWPB)
     k_cell_diag(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, double* part) {
     using S = Sz<R>;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP;
     extern __shared__ double smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     double* su = smem + warp * (2 * ND + 2 * NMP + 2 * NM * NM);
     double* pe = su + 2 * ND;
     double* pc = pe + NMP;
     double* tmp = pc + NMP;
-    for (int64_t k = (int64_t)blockIdx.x * WPB + warp; k < d.n; k += (int64_t)gridDim.x * WPB) {
+    for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < d.n; k += (int64_t)gridDim.x * wpb) {
         for (int i = lane; i < ND; i += 32) {
             su[i] = ufield(d, 0, 0, ND)[k * ND + i];
             su[ND + i] = ufield(d, 0, 3, ND)[k * ND + i];
@@ -1421,13 +1433,13 @@ __global__ void __launch_bounds__(TPB)
 // ---------------------------------------------------------------------------
 template <int R>
 __global__ void k_gauges(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, int ng,
-                         const double* xy, double* out) {
+                         const double* xy, double* out, int64_t k0, int64_t k1) {
     constexpr int ND1 = R + 1, ND = ND1 * ND1;
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= ng) return;
     const double x = xy[2 * gi], y = xy[2 * gi + 1];
     double v = NAN;
-    for (int64_t k = 0; k < d.n; ++k) {
+    for (int64_t k = k0; k < k1; ++k) { // the cells searched: [k0, k1)
         const double x0 = d.x0y0[2 * k], y0 = d.x0y0[2 * k + 1], hx = d.hxhy[2 * k],
                      hy = d.hxhy[2 * k + 1];
         if (x >= x0 && x <= x0 + hx && y >= y0 && y <= y0 + hy) {

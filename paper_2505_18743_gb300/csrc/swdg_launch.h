@@ -7,14 +7,27 @@ namespace swdg {
 
 struct StageArgs;
 
+// launch shape of one kernel: blocks and warps (cells in flight) per block
+struct Shape {
+    int grid, wpb;
+};
+
+// kernel kinds the autotuner shapes independently
+enum { KK_BEGIN = 0, KK_RESIDUAL = 1, KK_STAGE = 2, KK_AUX = 3, KK_N = 4 };
+
 struct Launch {
     void (*residual)(const Dev&, const Tables&, int buf, int stage, double c_stage, int want_dt,
-                     int grid, cudaStream_t);
-    void (*step_begin)(const Dev&, const Tables&, int do_switch, int grid, cudaStream_t);
-    void (*stage)(const Dev&, const Tables&, const StageArgs&, int grid, cudaStream_t);
-    void (*masks)(const Dev&, int buf, int grid, cudaStream_t);
-    void (*cell_diag)(const Dev&, const Tables&, double* part, int grid, cudaStream_t);
-    void (*gauges)(const Dev&, const Tables&, int ng, const double* xy, double* out, cudaStream_t);
+                     Shape, cudaStream_t);
+    void (*step_begin)(const Dev&, const Tables&, int do_switch, Shape, cudaStream_t);
+    void (*stage)(const Dev&, const Tables&, const StageArgs&, Shape, cudaStream_t);
+    void (*masks)(const Dev&, int buf, Shape, cudaStream_t);
+    void (*cell_diag)(const Dev&, const Tables&, double* part, Shape, cudaStream_t);
+    void (*gauges)(const Dev&, const Tables&, int ng, const double* xy, double* out, int64_t k0,
+                   int64_t k1, cudaStream_t);
+    // opt every kernel in to the shared memory of MAXWPB warps; false on failure
+    bool (*prepare)();
+    // resident blocks per SM of kernel kind KK_* at wpb warps per block (0: cannot launch)
+    int (*occupancy)(int kind, int wpb);
     int nzp; // mode P samples per cell
 };
 

@@ -28,6 +28,10 @@ SWDG_BC_WALL = 0
 SWDG_BC_TIDE = 1
 SWDG_PIX_F32 = 0
 SWDG_PIX_F64 = 1
+SWDG_KIND_BEGIN = 0
+SWDG_KIND_RESIDUAL = 1
+SWDG_KIND_STAGE = 2
+SWDG_KIND_AUX = 3
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -67,6 +71,15 @@ SIGNATURES = {
     "swdg_diagnostics": (_I, [_P, _P]),
     "swdg_residual_noalloc": (_I, [ctypes.POINTER(swdg_config), _I64, _P, _P, _P, _I, _I, _P, _P,
                                    _P, _P, _P, _P, _D, _P, _P, ctypes.c_char_p, _I]),
+    "swdg_set_members": (_I, [_P, _I, _P]),
+    "swdg_upload_bathymetry_members": (_I, [_P, _P, _I, _P, _P]),
+    "swdg_set_boundary_member": (_I, [_P, _I, _I, _I, _D, _D, _D]),
+    "swdg_member_times": (_I, [_P, _P, _P, _I]),
+    "swdg_member_diagnostics": (_I, [_P, _P]),
+    "swdg_gather_gauges_member": (_I, [_P, _I, _I, _P, _P]),
+    "swdg_set_shape": (_I, [_P, _I, _I, _I]),
+    "swdg_get_shapes": (_I, [_P, _P]),
+    "swdg_autotune": (_I, [_P, _I, _P]),
     "swdg_last_error": (ctypes.c_char_p, [_P]),
     "swdg_destroy": (None, [_P]),
 }
@@ -244,12 +257,31 @@ class Context:
                                            out.ctypes.data_as(_P)))
         return out
 
+    DIAG_KEYS = ("mass", "tracer_mass", "min_h", "r_cells", "newton_max",
+                 "positivity_violations", "dt", "t")
+
     def diagnostics(self):
         d = np.empty(8)
         self._ck(load().swdg_diagnostics(self.h, d.ctypes.data_as(_P)))
-        keys = ("mass", "tracer_mass", "min_h", "r_cells", "newton_max", "positivity_violations",
-                "dt", "t")
-        return dict(zip(keys, d.tolist()))
+        return dict(zip(self.DIAG_KEYS, d.tolist()))
+
+    # launch shapes and the autotuner
+    def set_shape(self, kind, grid, warps_per_block):
+        self._ck(load().swdg_set_shape(self.h, kind, grid, warps_per_block))
+
+    def shapes(self):
+        out = np.zeros(8, dtype=np.int32)
+        self._ck(load().swdg_get_shapes(self.h, out.ctypes.data_as(_P)))
+        return {k: (int(out[2 * i]), int(out[2 * i + 1]))
+                for i, k in enumerate(("begin", "residual", "stage", "aux"))}
+
+    def autotune(self, repeats=2):
+        """pick the fastest launch shape per kernel kind on this context's own
+        mesh and state; returns {kind: (grid, warps per block, ms per step)}"""
+        rep = np.zeros(9)
+        self._ck(load().swdg_autotune(self.h, repeats, rep.ctypes.data_as(_P)))
+        return {k: (int(rep[3 * i]), int(rep[3 * i + 1]), float(rep[3 * i + 2]))
+                for i, k in enumerate(("begin", "residual", "stage"))}
 
     @classmethod
     def from_workload(cls, wl, stream=None, **over):
@@ -263,4 +295,89 @@ class Context:
         if wl.manning is not None:
             ctx.set_manning(wl.manning)
         ctx.set_state(*wl.state())
+        return ctx
+
+
+class Ensemble(Context):
+    """Independent members (one Workload each) advanced by the same launches:
+    the context's mesh is the disjoint union of the members' meshes, every
+    member keeps its own CFL step, clock, tide and bathymetry raster."""
+
+    def set_members(self, first_cell):
+        first = np.ascontiguousarray(first_cell, dtype=np.int64)
+        self._ck(load().swdg_set_members(self.h, len(first) - 1, first.ctypes.data_as(_P)))
+        self.first = first
+        self.m = len(first) - 1
+
+    def upload_bathymetry_members(self, rasters):
+        """rasters: list of workloads.Raster, one per member"""
+        zs = [np.ascontiguousarray(r.z) for r in rasters]
+        f32 = all(z.dtype == np.float32 for z in zs)
+        dtype = SWDG_PIX_F32 if f32 else SWDG_PIX_F64
+        zs = [np.ascontiguousarray(z, dtype=np.float32 if f32 else np.float64) for z in zs]
+        ptrs = (_P * len(zs))(*[z.ctypes.data for z in zs])
+        nxny = np.array([[z.shape[1], z.shape[0]] for z in zs], dtype=np.int64)
+        geo = np.array([[r.xo, r.yo, r.dx, r.dy] for r in rasters], dtype=np.float64)
+        self._ck(load().swdg_upload_bathymetry_members(self.h, ctypes.cast(ptrs, _P), dtype,
+                                                       nxny.ctypes.data_as(_P),
+                                                       geo.ctypes.data_as(_P)))
+
+    def set_boundary_member(self, member, tag, kind, amp=0.0, period=1.0, phase=0.0):
+        self._ck(load().swdg_set_boundary_member(self.h, member, tag, kind, amp, period, phase))
+
+    def times(self):
+        t = np.empty(self.m)
+        dt = np.empty(self.m)
+        self._ck(load().swdg_member_times(self.h, t.ctypes.data_as(_P), dt.ctypes.data_as(_P), 0))
+        return t, dt
+
+    def set_times(self, t):
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(t, dtype=np.float64), (self.m,)))
+        self._ck(load().swdg_member_times(self.h, t.ctypes.data_as(_P), None, 1))
+
+    def step(self, n=1, dt=-1.0, t=None):
+        if t is not None:
+            raise ValueError("an ensemble keeps one clock per member: use set_times/times")
+        self._ck(load().swdg_step(self.h, n, dt, None))
+
+    def member_diagnostics(self):
+        d = np.empty((self.m, 8))
+        self._ck(load().swdg_member_diagnostics(self.h, d.ctypes.data_as(_P)))
+        return [dict(zip(self.DIAG_KEYS, row.tolist())) for row in d]
+
+    def member_slice(self, m):
+        return slice(int(self.first[m]), int(self.first[m + 1]))
+
+    def member_state(self, m):
+        return [a[self.member_slice(m)] for a in self.get_state()]
+
+    def gather_gauges_member(self, member, xy):
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        out = np.empty(len(xy))
+        self._ck(load().swdg_gather_gauges_member(self.h, member, len(xy), xy.ctypes.data_as(_P),
+                                                  out.ctypes.data_as(_P)))
+        return out
+
+    @classmethod
+    def from_workloads(cls, wls, stream=None, **over):
+        """one member per workload; the solver settings (degree, tableau, cfl,
+        eps, ...) must agree across the workloads and are taken from the first"""
+        from .workloads import union_mesh
+        cfg = wls[0].config(**over)
+        for w in wls[1:]:
+            if w.config(**over) != cfg:
+                raise ValueError(f"member {w.name}: solver settings differ from {wls[0].name}")
+        ctx = cls(stream=stream, **cfg)
+        x0y0, hxhy, nbr, first = union_mesh([w.mesh for w in wls])
+        ctx.upload_mesh(x0y0, hxhy, nbr)
+        ctx.set_members(first)
+        ctx.upload_bathymetry_members([w.raster for w in wls])
+        for m, w in enumerate(wls):
+            for (tag, kind, amp, per, ph) in w.boundaries:
+                ctx.set_boundary_member(m, tag, kind, amp, per, ph)
+        man = np.concatenate([w.manning if w.manning is not None else np.zeros(w.mesh.n)
+                              for w in wls])
+        ctx.set_manning(man)
+        st = [np.concatenate(parts) for parts in zip(*[w.state() for w in wls])]
+        ctx.set_state(*st)
         return ctx

@@ -140,6 +140,22 @@ def crop_mesh(nx_full: int, i0: int, j0: int, w: int, h: int, hx: float, hy: flo
     return uniform_mesh(w, h, w * hx, h * hy, x0=i0 * hx, y0=j0 * hy, tags=tags)
 
 
+def union_mesh(meshes):
+    """Disjoint union of meshes (one ensemble member each): cells of mesh m
+    follow those of meshes 0..m-1, neighbour indices are shifted by the same
+    offset and boundary tags are kept.  Returns x0y0, hxhy, nbr and
+    ``first`` [M + 1], member m owning cells first[m] .. first[m+1] - 1."""
+    first = np.zeros(len(meshes) + 1, dtype=np.int64)
+    nbrs = []
+    for m, mesh in enumerate(meshes):
+        first[m + 1] = first[m] + mesh.n
+        nb = mesh.nbr.astype(np.int64)
+        nbrs.append(np.where(nb >= 0, nb + first[m], nb).astype(np.int32))
+    x0y0 = np.concatenate([m.x0y0 for m in meshes])
+    hxhy = np.concatenate([m.hxhy for m in meshes])
+    return x0y0, hxhy, np.concatenate(nbrs), first
+
+
 # ----------------------------------------------------------------------------
 # noise helpers
 # ----------------------------------------------------------------------------
@@ -246,6 +262,29 @@ def tidal_beach(seed: int = DEFAULT_SEED, n: int = 256, pix: int = 16, degree: i
                     zero.copy(), zero.copy(), zero.copy(), c, tableau=0, cfl=0.08,
                     eps_vel=0.1, h_lim=0.1, boundaries=[(1, BC_TIDE, 1.0, 44712.0, 0.0)],
                     manning=man, steps=1000)
+
+
+def beach_ensemble(seed: int = DEFAULT_SEED, members: int = 64, sizes=(32, 64, 128, 256),
+                   pix: int = 8, degree: int = 2, L: float = 20000.0, dtype=np.float32):
+    """Ensemble of independent tidal beaches (a parameter sweep): member m,
+    seeded with seed + m, draws its mesh size N x N from ``sizes``, its tide
+    amplitude from U[0.2, 1.5] m and its Manning coefficient from U[0.01,
+    0.04], and builds the beach of ``tidal_beach`` on the same 20 km domain
+    with ``pix`` x ``pix`` pixels per cell (so the rasters differ in
+    resolution).  CFL number 0.12 for r = 2 (0.08 for r = 3)."""
+    wls = []
+    for m in range(members):
+        rng = np.random.default_rng(seed + m)
+        n = int(rng.choice(np.asarray(sizes)))
+        amp = float(rng.uniform(0.2, 1.5))
+        man = float(rng.uniform(0.01, 0.04))
+        wl = tidal_beach(seed=seed + m, n=n, pix=pix, degree=degree, L=L, dtype=dtype)
+        wl.name = f"beach-member{m}-{n}x{n}-r{degree}-p{pix}"
+        wl.boundaries = [(1, BC_TIDE, amp, 44712.0, 0.0)]
+        wl.manning = np.full(wl.mesh.n, man)
+        wl.cfl = {1: 0.2, 2: 0.12, 3: 0.08}[degree]
+        wls.append(wl)
+    return wls
 
 
 # ----------------------------------------------------------------------------
