@@ -350,7 +350,8 @@ def run_gpu(args, rank, world, local):
     flops = sum(table[slot_kind(k)] for k in slots) / len(slots) * wl.mesh.n
     ach = flops / (avg_ms / 1e3) / 1e12
     pk, src = peaks()
-    bpc = algorithmic_bytes_per_cell(slots[0], nres=STAGES)
+    nres = {"stage_2": 1, "stage_3": 2, "stage_4": 3, "final": STAGES}
+    bpc = sum(algorithmic_bytes_per_cell(k, nres=nres.get(k, STAGES)) for k in slots) / len(slots)
     hbm_ach = bpc * wl.mesh.n / (avg_ms / 1e3) / 1e9
     traffic = [(DRAM_BYTES_PER_LAUNCH if prec == 0 else {}).get(slot_kind(k)) for k in slots]
     roof = {"bound": "alu", "kernel": dom_fn, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
