@@ -174,6 +174,24 @@ int swdg_gather_gauges(swdg_ctx* ctx, int n, const double* xy, double* zeta_out)
  * ensemble the first four are over all members and dt, t are member 0's. */
 int swdg_diagnostics(swdg_ctx* ctx, double out[8]);
 
+/* Discrete adjoint of the residual (Sec. 3.2): the vector-Jacobian product
+ * of (F, Gx, Gy, R, Lx, Ly) at the current state and time t.  Inputs: the
+ * cotangents F_b .. Ly_b [n][(r+1)^2] (any may be NULL = 0).  Outputs (any
+ * may be NULL): zeta_b, qx_b, qy_b, c_b [n][(r+1)^2] = sum over every
+ * residual entry of its cotangent times its derivative with respect to each
+ * nodal value; manning_b [n] the same with respect to each cell's Manning
+ * coefficient; delta_b [n] with respect to a bathymetry offset of each cell
+ * (every pixel depth of cell K, or in mode P every sampled depth, deepened by
+ * delta_K), at delta = 0.  Kinks: max(x, 0) in the sub-grid integrals has
+ * derivative [x > 0] (Eq. mask); the reconstruction's min and the wave-speed
+ * max follow the side whose residual is differentiated at ties; |x| and
+ * sqrt(x) have derivative 0 at 0.  Always FP64 (also in an FP32-bulk
+ * context).  The paper states the forward operator only. */
+int swdg_residual_vjp(swdg_ctx* ctx, double t, const double* F_b, const double* Gx_b,
+                      const double* Gy_b, const double* R_b, const double* Lx_b,
+                      const double* Ly_b, double* zeta_b, double* qx_b, double* qy_b,
+                      double* c_b, double* manning_b, double* delta_b, int where);
+
 /* ---- ensembles (the paper has no counterpart: many independent problems,
  * e.g. a parameter sweep of tides, friction and bathymetry, advanced by the
  * same kernel launches) ----

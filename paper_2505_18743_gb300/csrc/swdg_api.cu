@@ -49,6 +49,7 @@ struct swdg_ctx {
     Member* mb = nullptr;
     Bc* bcd = nullptr;
     int64_t* first_d = nullptr; // [nmemb + 1]
+    double* adj = nullptr;      // adjoint scratch: 6 + 4 fields of [n][nd], then 2 [n]
     double* mdiag = nullptr;    // [nmemb][4]
     std::vector<Bc> bch;
     // device allocations
@@ -671,6 +672,8 @@ static void free_mesh(swdg_ctx* c) {
     cudaFree(c->x0y0); cudaFree(c->hxhy); cudaFree(c->ihxhy); cudaFree(c->manning); cudaFree(c->U); cudaFree(c->res);
     cudaFree(c->llin); cudaFree(c->HN); cudaFree(c->CN); cudaFree(c->HNbar); cudaFree(c->CNbar);
     cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->diag); cudaFree(c->finfo);
+    cudaFree(c->adj);
+    c->adj = nullptr;
     c->x0y0 = c->hxhy = c->ihxhy = c->manning = c->U = c->res = c->llin = c->HN = c->CN = c->HNbar =
         c->CNbar = c->diag = nullptr;
     c->nbr = nullptr;
@@ -1391,6 +1394,43 @@ int swdg_diagnostics(swdg_ctx* ctx, double out[8]) {
     if (rc) return rc;
     out[6] = mh[0].dt_last; // member 0 of an ensemble
     out[7] = mh[0].t;
+    return SWDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// discrete adjoint of the residual
+// ---------------------------------------------------------------------------
+int swdg_residual_vjp(swdg_ctx* ctx, double t, const double* Fb, const double* Gxb,
+                      const double* Gyb, const double* Rb, const double* Lxb, const double* Lyb,
+                      double* zeta_b, double* qx_b, double* qy_b, double* c_b, double* manning_b,
+                      double* delta_b, int where) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "residual_vjp: no state");
+    if (where != SWDG_HOST && where != SWDG_DEVICE)
+        return fail(ctx, SWDG_EINVAL, "residual_vjp: bad where");
+    const int64_t n = ctx->n;
+    const size_t f = (size_t)n * ctx->nd, fb = f * sizeof(double);
+    if (!ctx->adj) CK(cudaMalloc(&ctx->adj, (10 * f + 2 * (size_t)n) * sizeof(double)));
+    const cudaMemcpyKind in = where == SWDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind out = where == SWDG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const double* src[6] = {Fb, Gxb, Gyb, Rb, Lxb, Lyb};
+    for (int i = 0; i < 6; ++i) {
+        if (src[i]) CK(cudaMemcpyAsync(ctx->adj + i * f, src[i], fb, in, ctx->st));
+        else CK(cudaMemsetAsync(ctx->adj + i * f, 0, fb, ctx->st));
+    }
+    int rc = put_clocks(ctx, t, 0);
+    if (rc) return rc;
+    double* ub = ctx->adj + 6 * f;
+    double* nb = ctx->adj + 10 * f;
+    double* db = nb + n;
+    ctx->L.residual_vjp(ctx->d, ctx->tb, ctx->adj, ub, nb, db, Shape{grid_for(n), WPB}, ctx->st);
+    CK(cudaGetLastError());
+    double* dst[4] = {zeta_b, qx_b, qy_b, c_b};
+    for (int i = 0; i < 4; ++i)
+        if (dst[i]) CK(cudaMemcpyAsync(dst[i], ub + i * f, fb, out, ctx->st));
+    if (manning_b) CK(cudaMemcpyAsync(manning_b, nb, n * sizeof(double), out, ctx->st));
+    if (delta_b) CK(cudaMemcpyAsync(delta_b, db, n * sizeof(double), out, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
     return SWDG_OK;
 }
 

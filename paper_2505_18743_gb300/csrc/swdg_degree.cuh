@@ -1,6 +1,7 @@
 // swdg_degree.cuh -- launchers of one polynomial degree (included once by each
 // swdg_r{1,2,3}.cu with SWDG_DEGREE defined).
 #pragma once
+#include "swdg_adjoint.cuh"
 #include "swdg_kernels.cuh"
 #include "swdg_launch.h"
 
@@ -13,6 +14,7 @@ struct Launchers {
     static constexpr size_t begin_b = sizeof(double) * begin_smem<R>();
     static constexpr size_t stage_b = sizeof(double) * stage_smem<R>();
     static constexpr size_t diag_b = sizeof(double) * (2 * S::ND + 2 * S::NMP + 2 * S::NM * S::NM);
+    static constexpr size_t vjp_b = sizeof(double) * vjp_smem<R>();
 
     static void residual(const Dev& d, const Tables& tb, int buf, int stage, double c_stage,
                          int want_dt, Shape s, cudaStream_t st) {
@@ -35,6 +37,11 @@ struct Launchers {
                        int64_t k0, int64_t k1, cudaStream_t st) {
         k_gauges<R><<<(ng + 63) / 64, 64, 0, st>>>(d, tb, ng, xy, out, k0, k1);
     }
+    static void residual_vjp(const Dev& d, const Tables& tb, const double* rbar, double* ubar,
+                             double* nbar, double* dbar, Shape s, cudaStream_t st) {
+        k_residual_vjp<R, Pix, MODE><<<s.grid, 32 * s.wpb, vjp_b * s.wpb, st>>>(d, tb, rbar, ubar,
+                                                                              nbar, dbar);
+    }
     template <typename K>
     static bool opt_in(K kern, size_t per_warp) {
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -44,7 +51,8 @@ struct Launchers {
         return opt_in(k_residual<R, Pix, MODE, B>, res_b) &&
                opt_in(k_step_begin<R, Pix, MODE>, begin_b) &&
                opt_in(k_stage<R, Pix, MODE, B>, stage_b) &&
-               opt_in(k_cell_diag<R, Pix, MODE>, diag_b);
+               opt_in(k_cell_diag<R, Pix, MODE>, diag_b) &&
+               opt_in(k_residual_vjp<R, Pix, MODE>, vjp_b);
     }
     template <typename K>
     static int occ(K kern, int wpb, size_t per_warp) {
@@ -70,6 +78,7 @@ struct Launchers {
         L->masks = &masks;
         L->cell_diag = &cell_diag;
         L->gauges = &gauges;
+        L->residual_vjp = &residual_vjp;
         L->prepare = &prepare;
         L->occupancy = &occupancy;
         L->nzp = Sz<R>::NZP;

@@ -24,6 +24,10 @@ struct Launch {
     void (*cell_diag)(const Dev&, const Tables&, double* part, Shape, cudaStream_t);
     void (*gauges)(const Dev&, const Tables&, int ng, const double* xy, double* out, int64_t k0,
                    int64_t k1, cudaStream_t);
+    // discrete adjoint of the residual (FP64): rbar [6][n][nd] -> ubar [4][n][nd],
+    // nbar [n] (Manning), dbar [n] (bathymetry offset)
+    void (*residual_vjp)(const Dev&, const Tables&, const double* rbar, double* ubar, double* nbar,
+                         double* dbar, Shape, cudaStream_t);
     // opt every kernel in to the shared memory of MAXWPB warps; false on failure
     bool (*prepare)();
     // resident blocks per SM of kernel kind KK_* at wpb warps per block (0: cannot launch)

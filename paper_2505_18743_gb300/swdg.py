@@ -71,6 +71,7 @@ SIGNATURES = {
     "swdg_diagnostics": (_I, [_P, _P]),
     "swdg_residual_noalloc": (_I, [ctypes.POINTER(swdg_config), _I64, _P, _P, _P, _I, _I, _P, _P,
                                    _P, _P, _P, _P, _D, _P, _P, ctypes.c_char_p, _I]),
+    "swdg_residual_vjp": (_I, [_P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
     "swdg_set_members": (_I, [_P, _I, _P]),
     "swdg_upload_bathymetry_members": (_I, [_P, _P, _I, _P, _P]),
     "swdg_set_boundary_member": (_I, [_P, _I, _I, _I, _D, _D, _D]),
@@ -226,6 +227,17 @@ class Context:
         bufs = [_buf(v, np.float64) for v in out]
         self._ck(load().swdg_residual(self.h, t, *[b[0] for b in bufs], bufs[0][1]))
         return dict(zip(("F", "Gx", "Gy", "R", "Lx", "Ly"), out))
+
+    def residual_vjp(self, cot, t=0.0):
+        """discrete adjoint of the residual: cotangents of (F, Gx, Gy, R, Lx, Ly)
+        (host arrays [n, nd], None = 0) to those of (zeta, qx, qy, c) [n, nd],
+        the Manning coefficients [n] and per-cell bathymetry offsets [n]"""
+        ins = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in cot]
+        outs = [np.empty((self.n, self.nd)) for _ in range(4)] + [np.empty(self.n), np.empty(self.n)]
+        ptr = [None if a is None else a.ctypes.data_as(_P) for a in ins]
+        self._ck(load().swdg_residual_vjp(self.h, t, *ptr, *[o.ctypes.data_as(_P) for o in outs],
+                                          SWDG_HOST))
+        return dict(zip(("zeta", "qx", "qy", "c", "manning", "delta"), outs))
 
     def cfl_dt(self, t=0.0):
         d = _D(0.0)
