@@ -138,25 +138,8 @@ class TorchResidual:
             self.P, self.Pmax = P, Pmax
             self.tiles = torch.tensor(tiles)
 
-        def rect_w(k, X0, X1, Y0, Y1):
-            # pixel-area fractions of the rectangle over cell k's tile
-            Pk = int(self.P[k])
-            fx = _fractions((X0 - x0[k]) / raster.dx, (X1 - x0[k]) / raster.dx, Pk, self.Pmax)
-            fy = _fractions((Y0 - y0[k]) / raster.dy, (Y1 - y0[k]) / raster.dy, Pk, self.Pmax)
-            return np.outer(fy, fx).ravel()
-
-        def bilinear(x, y):
-            fi = min(max((x - raster.xo) / raster.dx - 0.5, 0.0), z.shape[1] - 1.0)
-            fj = min(max((y - raster.yo) / raster.dy - 0.5, 0.0), z.shape[0] - 1.0)
-            ii, jj = min(int(np.floor(fi)), z.shape[1] - 2), min(int(np.floor(fj)), z.shape[0] - 2)
-            a, b = fi - ii, fj - jj
-            return ((1 - a) * (1 - b) * z[jj, ii] + a * (1 - b) * z[jj, ii + 1] +
-                    (1 - a) * b * z[jj + 1, ii] + a * b * z[jj + 1, ii + 1])
-
-        def site(k, X0, X1, Y0, Y1, px, py):
-            if subgrid_mode == 0:
-                return rect_w(k, X0, X1, Y0, Y1)
-            return bilinear(px, py)
+        self.x0, self.y0, self.z = x0, y0, z
+        site = self.site
 
         # ---- volume points: basis rows and sites
         Bv, Dx, Dy, wts = [], [], [], []
@@ -172,16 +155,7 @@ class TorchResidual:
         self.Dx = torch.tensor(np.array(Dx))
         self.Dy = torch.tensor(np.array(Dy))
         self.wv = torch.tensor(np.array(wts))
-        vs = []
-        for k in range(n):
-            row = []
-            for ib in range(nv):
-                for ia in range(nv):
-                    row.append(site(k, x0[k] + sv[ia] * hx[k], x0[k] + sv[ia + 1] * hx[k],
-                                    y0[k] + sv[ib] * hy[k], y0[k] + sv[ib + 1] * hy[k],
-                                    x0[k] + xv[ia] * hx[k], y0[k] + xv[ib] * hy[k]))
-            vs.append(row)
-        self.vol_site = torch.tensor(np.array(vs))  # [n, npv, Pmax^2] or [n, npv]
+        self.vol_site = self.cell_sites(xv, sv)  # [n, npv, Pmax^2] or [n, npv]
 
         # ---- face points: one item per (cell, face, subface)
         items = []  # (K, f, nb, tag, t0, L)
@@ -250,6 +224,42 @@ class TorchResidual:
         self.site_m = torch.tensor(np.array(s_m))    # [ni, nm, (Pmax^2)]
         self.site_p = torch.tensor(np.array(s_p))
         self.wl = torch.tensor(np.array(wl))         # [ni, nm]
+
+    # -- sampling sites: pixel-area fractions of a rectangle over cell k's tile
+    # (mode S) or the bottom depth at a point (mode P)
+    def _rect_w(self, k, X0, X1, Y0, Y1):
+        ras = self.raster
+        Pk = int(self.P[k])
+        fx = _fractions((X0 - self.x0[k]) / ras.dx, (X1 - self.x0[k]) / ras.dx, Pk, self.Pmax)
+        fy = _fractions((Y0 - self.y0[k]) / ras.dy, (Y1 - self.y0[k]) / ras.dy, Pk, self.Pmax)
+        return np.outer(fy, fx).ravel()
+
+    def _bilinear(self, x, y):
+        ras, z = self.raster, self.z
+        fi = min(max((x - ras.xo) / ras.dx - 0.5, 0.0), z.shape[1] - 1.0)
+        fj = min(max((y - ras.yo) / ras.dy - 0.5, 0.0), z.shape[0] - 1.0)
+        ii, jj = min(int(np.floor(fi)), z.shape[1] - 2), min(int(np.floor(fj)), z.shape[0] - 2)
+        a, b = fi - ii, fj - jj
+        return ((1 - a) * (1 - b) * z[jj, ii] + a * (1 - b) * z[jj, ii + 1] +
+                (1 - a) * b * z[jj + 1, ii] + a * b * z[jj + 1, ii + 1])
+
+    def site(self, k, X0, X1, Y0, Y1, px, py):
+        if self.mode == 0:
+            return self._rect_w(k, X0, X1, Y0, Y1)
+        return self._bilinear(px, py)
+
+    def cell_sites(self, xq, sq):
+        """sites of the tensor rule (nodes xq, breakpoints sq) of every cell,
+        point index ia + len(xq) ib"""
+        m = len(xq)
+        out = []
+        for k in range(self.n):
+            x0, y0, hx, hy = self.x0[k], self.y0[k], self.hx[k], self.hy[k]
+            out.append([self.site(k, x0 + sq[ia] * hx, x0 + sq[ia + 1] * hx,
+                                  y0 + sq[ib] * hy, y0 + sq[ib + 1] * hy,
+                                  x0 + xq[ia] * hx, y0 + xq[ib] * hy)
+                        for ib in range(m) for ia in range(m)])
+        return torch.tensor(np.array(out))
 
     # -- sub-grid wet depth: site [a, q, ...] of cells k [a] at elevations eta [a, q]
     def V(self, site, k, eta, delta):

@@ -1,0 +1,322 @@
+"""PyTorch (CPU, float64) restatement of one IMEX Runge-Kutta time step
+(Sec. 3.1, 3.4) on top of ``torch_residual``, for the discrete adjoint of the
+step.
+
+TEST INFRASTRUCTURE ONLY: only the tests use it.  It follows ``ora_step`` of
+``swdg_oracle.c`` (which it is pinned against, value for value) with a fixed
+time step:
+
+  * degree switch (Eq. criteria_p): r_K = r iff the smallest wet depth over
+    the (r+2)^2 Gauss-Lobatto mass points exceeds h_lim; an r_K = 0 cell is
+    remapped mass-exactly (zeta: H(e) = H(zeta^n) by scalar Newton; q: the
+    Gauss-Legendre mean; c: tracer mass / mass, or the mean when dry);
+  * H(zeta^n), C~^n (Eqs. depth_rhs, concentration_rhs);
+  * each stage l: T = H(zeta^n) + dt sum_m a_lm F^(m), solved for zeta^(l) by
+    Newton with the wet-area matrix M (Eqs. algebraic_elevation, newton; an
+    iterate with a completely dry mass sub-cell turns the cell to r_K = 0 for
+    the rest of the step), the momentum mass system with the implicit
+    friction of the diagonal (Eq. algebraic_discharge) and the depth-weighted
+    tracer system (Eq. algebraic_concentration), then the residual of the
+    stage at t + c_l dt;
+  * the final combination with b, b~, the last stage entering with the
+    linearised friction it solved (the R8 reading of the design notes).
+
+Differentiation: every discrete decision (degree flags, r_K = 0 fallbacks,
+Newton iterations) is taken without gradients, and each converged nonlinear
+solve is then re-expressed as one Newton correction from its detached root,
+e = e* - J(e*)^-1 (G(e*, theta) - target(theta)) with J detached, whose
+derivative is the implicit-function-theorem derivative
+de = J^-1 (d target - dG/d theta d theta).  Linear solves are differentiated
+by autograd.  The result is the exact derivative of the step along the path
+the forward took.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from .oracle import rule, tableau
+from .torch_residual import TorchResidual, _breaks, _lagrange
+
+
+def _basis_rows(xs, xq):
+    rows = []
+    for ib in range(len(xq)):
+        for ia in range(len(xq)):
+            la, _ = _lagrange(xs, xq[ia])
+            lb, _ = _lagrange(xs, xq[ib])
+            rows.append(np.outer(lb, la).ravel())
+    return torch.tensor(np.array(rows))
+
+
+class TorchStep:
+    def __init__(self, wl, **over):
+        cfg = wl.config(**over)
+        self.cfg = cfg
+        r = cfg["degree"]
+        self.res = TorchResidual(wl.mesh, wl.raster, r, cfg["subgrid_mode"], cfg["g"],
+                                 cfg["eps_vel"], wl.boundaries)
+        tr = self.res
+        self.n, self.nd = tr.n, tr.nd
+        xs, _ = rule(1, r + 1)
+        xm, wm = rule(1, r + 2)
+        xg, wg = rule(0, r + 1)
+        self.Bm = _basis_rows(xs, xm)            # [nmp, nd]
+        self.Bg = _basis_rows(xs, xg)            # [ngp, nd]
+        self.wm2 = torch.tensor(np.outer(wm, wm).ravel())
+        self.wg2 = torch.tensor(np.outer(wg, wg).ravel())
+        self.J = torch.tensor(tr.hx * tr.hy)[:, None]
+        self.mass_site = tr.cell_sites(xm, _breaks(wm))
+        self.mom_site = tr.cell_sites(xg, _breaks(wg))
+        # cell bounds of the bathymetry: max z_b (dry start, Eq. initial_guess)
+        # and max |z_b| (Newton tolerance scale)
+        if cfg["subgrid_mode"] == 0:
+            tiles = tr.tiles.numpy().reshape(self.n, tr.Pmax, tr.Pmax)
+            zmax, zabs = np.empty(self.n), np.empty(self.n)
+            for k in range(self.n):
+                t = tiles[k, :tr.P[k], :tr.P[k]]
+                zmax[k], zabs[k] = t.max(), np.abs(t).max()
+        else:
+            zz = self.mass_site.numpy()
+            zmax, zabs = zz.max(1), np.abs(zz).max(1)
+        self.zmax, self.zabs = torch.tensor(zmax), torch.tensor(zabs)
+        self.tab = tableau(cfg["tableau"])
+        self.cells = torch.arange(self.n)
+
+    # ---- sub-grid operators at the mass / momentum points
+    def VA(self, site, eta, delta):
+        tr = self.res
+        V = tr.V(site, self.cells, eta, delta)
+        with torch.no_grad():
+            e = eta + delta[:, None]
+            if tr.mode == 0:
+                A = (site * ((e[:, :, None] + tr.tiles[:, None, :]) > 0)).sum(-1)
+            else:
+                A = ((e + site) > 0).to(eta.dtype)
+        return V, A
+
+    def H(self, zeta, delta):
+        V, A = self.VA(self.mass_site, zeta @ self.Bm.T, delta)
+        w = self.J * self.wm2
+        return (w * V) @ self.Bm, V, A
+
+    def Hbar(self, e, delta):
+        """scalar wet mass and wet area at constant elevations e [n]"""
+        V, A = self.VA(self.mass_site, e[:, None].expand(-1, self.Bm.shape[0]), delta)
+        w = self.J * self.wm2
+        return (w * V).sum(1), (w * A).sum(1)
+
+    def gamma_mom(self, uprev, manning, delta):
+        """Manning gamma at the momentum points from the previous stage"""
+        z = uprev[0] @ self.Bg.T
+        qx, qy = uprev[1] @ self.Bg.T, uprev[2] @ self.Bg.T
+        V, _ = self.VA(self.mom_site, z, delta)
+        return self.res.gamma(manning[:, None], V, qx, qy)
+
+    # ---- scalar Newton for Hbar(e) = target, no gradients (Eqs. newton, initial_guess)
+    def scalar_newton(self, target, e, cells, delta):
+        nd, tol, nmax = self.nd, self.cfg["newton_tol"], self.cfg["newton_max"]
+        e = e.clone()
+        zero = delta.detach()
+        for k in cells.tolist():
+            ek = e[k:k + 1]
+            sel = torch.zeros(self.n, dtype=torch.bool)
+            sel[k] = True
+            Hk, Ak = self._hbar_one(k, ek, zero)
+            if Ak == 0.0:
+                ek = ek * 0 - (self.zmax[k] + zero[k]) + self.cfg["eps0"]
+            for _ in range(nmax):
+                Hk, Ak = self._hbar_one(k, ek, zero)
+                if Ak == 0.0:
+                    break
+                dd = (Hk - target[k]) / Ak
+                ek = ek - dd
+                if nd * abs(float(dd)) <= tol * nd * (1.0 + abs(float(ek)) + float(self.zabs[k])):
+                    break
+            e[k] = ek[0]
+        return e
+
+    def _hbar_one(self, k, ek, delta):
+        tr = self.res
+        site = self.mass_site[k:k + 1]
+        eta = ek[:, None].expand(1, self.Bm.shape[0]) + delta[k]
+        if tr.mode == 0:
+            d = eta[:, :, None] + tr.tiles[k:k + 1][:, None, :]
+            V = (site * torch.where(d > 0, d, torch.zeros_like(d))).sum(-1)
+            A = (site * (d > 0)).sum(-1)
+        else:
+            d = eta + site
+            V = torch.where(d > 0, d, torch.zeros_like(d))
+            A = (d > 0).to(d.dtype)
+        w = self.J[k] * self.wm2
+        return float((w * V).sum()), float((w * A).sum())
+
+    def ift_scalar(self, estar, target, delta, cells):
+        """e = e* + (target - Hbar(e*, delta)) / A(e*) on `cells` (IFT derivative)"""
+        Hb, Ab = self.Hbar(estar.detach(), delta)
+        ok = cells & (Ab > 0)
+        corr = torch.where(ok, (target - Hb) / torch.where(ok, Ab, torch.ones_like(Ab)).detach(),
+                           torch.zeros_like(Hb))
+        return estar.detach() + corr
+
+    # ---- degree switch with the mass-exact remap
+    def degree_switch(self, u, delta):
+        hl = self.cfg["h_lim"]
+        with torch.no_grad():
+            _, V, _ = self.H(u[0], delta.detach())
+            flag = V.min(1).values > hl
+        low = ~flag
+        if not bool(low.any()):
+            return list(u), flag
+        w = self.J * self.wm2
+        zm = u[0] @ self.Bm.T
+        Vm, _ = self.VA(self.mass_site, zm, delta)
+        cm = u[3] @ self.Bm.T
+        m = (w * Vm).sum(1)
+        tracer = (w * Vm * cm).sum(1)
+        means = [(self.wg2 * (u[f] @ self.Bg.T)).sum(1) for f in (1, 2, 3)]
+        J = self.J[:, 0]
+        wet = m > 1e-14 * J * hl
+        cnew = torch.where(wet, tracer / torch.where(wet, m, torch.ones_like(m)), means[2])
+        with torch.no_grad():
+            e0 = zm.max(1).values
+            e0 = torch.where(m > 0, e0, -(self.zmax + delta.detach()))
+            estar = self.scalar_newton(m.detach(), e0, torch.nonzero(low & (m > 0)).flatten(),
+                                       delta)
+        e = torch.where(m > 0, self.ift_scalar(estar, m, delta, low & (m > 0)), estar)
+        one = torch.ones(self.nd, dtype=torch.float64)
+        out = []
+        for f, val in ((0, e), (1, means[0]), (2, means[1]), (3, cnew)):
+            out.append(torch.where(low[:, None], val[:, None] * one, u[f]))
+        return out, flag
+
+    # ---- one stage update (or the final combination)
+    def stage(self, un, uprev, res, wa, wat, add, HN, HNbar, CN, CNbar, flag, dt, manning,
+              delta, make_llin):
+        n, nd = self.n, self.nd
+        J = self.J[:, 0]
+        F = sum(a * r[0] for a, r in zip(wa, res))
+        T = HN + dt * F
+        Tsum = HNbar + dt * F.sum(1)
+        rq = [dt * sum(a * r[1 + f] + b * r[4 + f] for a, b, r in zip(wa, wat, res)) for f in (0, 1)]
+        rc = CN + dt * sum(a * r[3] for a, r in zip(wa, res))
+        # continuity: Newton without gradients (path), then the IFT correction
+        scalar = ~flag
+        with torch.no_grad():
+            z = un[0].clone()
+            active = flag.clone()
+            tol, nmax = self.cfg["newton_tol"], self.cfg["newton_max"]
+            for _ in range(nmax):
+                if not bool(active.any()):
+                    break
+                Hz, V, A = self.H(z, delta.detach())
+                dry = (A == 0).any(1) & active
+                scalar = scalar | dry
+                active = active & ~dry
+                M = torch.einsum("pi,kp,pj->kij", self.Bm, self.J * self.wm2 * A, self.Bm)
+                M = torch.where(active[:, None, None], M, torch.eye(nd, dtype=torch.float64))
+                d = torch.linalg.solve(M, torch.where(active[:, None], Hz - T, torch.zeros_like(T)))
+                z = z - d
+                inc = d.abs().sum(1)
+                s = (1.0 + z.abs() + self.zabs[:, None]).sum(1)
+                active = active & ~(inc <= tol * s)
+            _, _, A = self.H(z, delta.detach())
+            scalar = scalar | ((A == 0).any(1) & ~scalar)
+            zstar = z
+        full = ~scalar
+        Hz, _, A = self.H(zstar, delta)
+        M = torch.einsum("pi,kp,pj->kij", self.Bm, self.J * self.wm2 * A, self.Bm).detach()
+        M = torch.where(full[:, None, None], M, torch.eye(nd, dtype=torch.float64))
+        rhs = torch.where(full[:, None], T - Hz, torch.zeros_like(T))
+        zeta_full = zstar.detach() + torch.linalg.solve(M, rhs)
+        with torch.no_grad():
+            z0 = un[0]
+            const = (z0 == z0[:, :1]).all(1)
+            e0 = torch.where(const, z0[:, 0], (self.wm2 * (z0 @ self.Bm.T)).sum(1))
+            estar = self.scalar_newton(Tsum.detach(), e0, torch.nonzero(scalar).flatten(), delta)
+        e = self.ift_scalar(estar, Tsum, delta, scalar)
+        one = torch.ones(nd, dtype=torch.float64)
+        zeta = torch.where(scalar[:, None], e[:, None] * one, zeta_full)
+        # momentum on the (r+1)^2 Gauss-Legendre points
+        w = self.J * self.wg2
+        gam = self.gamma_mom(uprev, manning, delta) if add != 0.0 else torch.zeros_like(w)
+        Dg = w * (1.0 + add * dt * gam)
+        qn = [un[1 + f] @ self.Bg.T for f in (0, 1)]
+        Am = torch.einsum("pi,kp,pj->kij", self.Bg, Dg, self.Bg)
+        q_full = [torch.linalg.solve(Am, rq[f] + (w * qn[f]) @ self.Bg) for f in (0, 1)]
+        den = Dg.sum(1)
+        q_sc = [((w * qn[f]).sum(1) + rq[f].sum(1)) / den for f in (0, 1)]
+        q = [torch.where(scalar[:, None], q_sc[f][:, None] * one, q_full[f]) for f in (0, 1)]
+        llin = None
+        if make_llin:
+            act = (add != 0.0) & (manning != 0.0)
+            qg = [q[f] @ self.Bg.T for f in (0, 1)]
+            llin = [torch.where(act[:, None], -(w * gam * qg[f]) @ self.Bg, torch.zeros_like(q[f]))
+                    for f in (0, 1)]
+        # tracer: depth-weighted mass matrix
+        Hl, Vl, _ = self.H(zeta, delta)
+        Hc = torch.einsum("pi,kp,pj->kij", self.Bm, self.J * self.wm2 * Vl, self.Bm)
+        Hc = torch.where(full[:, None, None], Hc, torch.eye(nd, dtype=torch.float64))
+        c_full = torch.linalg.solve(Hc, torch.where(full[:, None], rc, torch.zeros_like(rc)))
+        Hs, _ = self.Hbar(e, delta)
+        rsum = CNbar + (rc - CN).sum(1)
+        wet = Hs > 1e-14 * J * self.cfg["h_lim"]
+        c_sc = torch.where(wet[:, None],
+                           (rsum / torch.where(wet, Hs, torch.ones_like(Hs)))[:, None] * one, un[3])
+        c = torch.where(scalar[:, None], c_sc, c_full)
+        return [zeta, q[0], q[1], c], llin, ~scalar
+
+    def step(self, u, manning, delta, t, dt):
+        """one time step of fixed size dt from state u (4 tensors [n, nd])"""
+        tab = self.tab
+        s = tab["s"]
+        un, flag = self.degree_switch(u, delta)
+        HN, V, _ = self.H(un[0], delta)
+        w = self.J * self.wm2
+        HNbar = (w * V).sum(1)
+        cm = un[3] @ self.Bm.T
+        CN = (w * V * cm) @ self.Bm
+        CNbar = (w * V * cm).sum(1)
+        stages, res = [un], []
+        llin = None
+        for l in range(s):
+            if l > 0:
+                add = float(tab["at"][l][l])
+                v, ll, flag = self.stage(un, stages[l - 1], res, tab["a"][l][:l], tab["at"][l][:l],
+                                         add, HN, HNbar, CN, CNbar, flag, dt, manning, delta,
+                                         make_llin=(l == s - 1 and add != 0.0))
+                if ll is not None:
+                    llin = ll
+                stages.append(v)
+            res.append(self.res(*stages[l], manning, delta, t + float(tab["c"][l]) * dt))
+        rr = [list(r) for r in res]
+        if llin is not None and float(tab["at"][s - 1][s - 1]) != 0.0:
+            rr[s - 1][4], rr[s - 1][5] = llin[0], llin[1]
+        out, _, _ = self.stage(un, stages[s - 1], rr, tab["b"], tab["bt"], 0.0, HN, HNbar, CN,
+                               CNbar, flag, dt, manning, delta, make_llin=False)
+        return out
+
+
+def step_value(ts: TorchStep, state, manning, delta, t, dt, nsteps=1):
+    u = [torch.tensor(np.asarray(a, dtype=np.float64)) for a in state]
+    m = torch.tensor(np.asarray(manning, dtype=np.float64))
+    dl = torch.tensor(np.asarray(delta, dtype=np.float64))
+    with torch.no_grad():
+        for i in range(nsteps):
+            u = ts.step(u, m, dl, t + i * dt, dt)
+    return [a.numpy() for a in u]
+
+
+def step_vjp(ts: TorchStep, state, manning, delta, cot, t, dt, nsteps=1):
+    """cotangents of the state after nsteps fixed steps pulled back to the
+    initial state, the Manning coefficients and the bathymetry offsets"""
+    xs = [torch.tensor(np.asarray(a, dtype=np.float64), requires_grad=True) for a in state]
+    m = torch.tensor(np.asarray(manning, dtype=np.float64), requires_grad=True)
+    dl = torch.tensor(np.asarray(delta, dtype=np.float64), requires_grad=True)
+    u = xs
+    for i in range(nsteps):
+        u = ts.step(u, m, dl, t + i * dt, dt)
+    s = sum((a * torch.tensor(np.asarray(b, dtype=np.float64))).sum() for a, b in zip(u, cot))
+    grads = torch.autograd.grad(s, xs + [m, dl], allow_unused=True)
+    return [g.detach().numpy() if g is not None else np.zeros(v.shape)
+            for g, v in zip(grads, xs + [m, dl])]
