@@ -192,6 +192,30 @@ int swdg_residual_vjp(swdg_ctx* ctx, double t, const double* F_b, const double* 
                       const double* Ly_b, double* zeta_b, double* qx_b, double* qy_b,
                       double* c_b, double* manning_b, double* delta_b, int where);
 
+/* Discrete adjoint of one time step (the paper states the forward scheme only).
+ * swdg_step_record advances one step of fixed size dt (> 0) like swdg_step
+ * (t_inout may be NULL: the context's clock) and keeps what the adjoint needs:
+ * the start state, the state after the degree switch, the stage states and
+ * the degree flags after every stage update.  swdg_step_vjp then pulls the
+ * cotangent of the state after that step (zeta_b .. c_b, [n][(r+1)^2], NULL =
+ * 0) back to the state before it (zeta_b_out .. c_b_out), to the Manning
+ * coefficients (manning_b [n]) and to per-cell bathymetry offsets (delta_b
+ * [n], every depth of cell K deepened by delta_K, at delta = 0); any output
+ * may be NULL.  The derivative is taken along the path the forward took:
+ * the time step and every discrete decision (degree flags, r_K = 0 fallbacks,
+ * the tracer's dry guard) are held fixed, each converged nonlinear solve is
+ * differentiated by the implicit function theorem (the continuity Newton
+ * solve by M(zeta^(l))^-1, M symmetric), the remap of an r_K = 0 cell and a
+ * constant field are differentiated as their formulas, and the kinks follow
+ * swdg_residual_vjp.  A multi-step adjoint records and pulls back the steps
+ * in reverse order, re-running each step from a stored (checkpointed) start
+ * state.  FP64 contexts with one member only (SWDG_EINVAL otherwise);
+ * swdg_step_vjp without a recorded step returns SWDG_ESTATE. */
+int swdg_step_record(swdg_ctx* ctx, double dt, double* t_inout);
+int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const double* qy_b,
+                  const double* c_b, double* zeta_b_out, double* qx_b_out, double* qy_b_out,
+                  double* c_b_out, double* manning_b, double* delta_b, int where);
+
 /* ---- ensembles (the paper has no counterpart: many independent problems,
  * e.g. a parameter sweep of tides, friction and bathymetry, advanced by the
  * same kernel launches) ----

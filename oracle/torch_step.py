@@ -183,7 +183,9 @@ class TorchStep:
             e0 = torch.where(m > 0, e0, -(self.zmax + delta.detach()))
             estar = self.scalar_newton(m.detach(), e0, torch.nonzero(low & (m > 0)).flatten(),
                                        delta)
-        e = torch.where(m > 0, self.ift_scalar(estar, m, delta, low & (m > 0)), estar)
+        # a completely dry cell sits at the dry level -max(z_b + delta) of Sec. 3.4
+        e = torch.where(m > 0, self.ift_scalar(estar, m, delta, low & (m > 0)),
+                        -(self.zmax + delta))
         one = torch.ones(self.nd, dtype=torch.float64)
         out = []
         for f, val in ((0, e), (1, means[0]), (2, means[1]), (3, cnew)):

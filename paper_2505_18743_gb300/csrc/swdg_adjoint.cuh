@@ -89,8 +89,9 @@ __device__ __forceinline__ void side_flux(T qxA, T qyA, T cA, T hA, T hsA, T qxB
 template <int R, typename Pix, int MODE>
 __global__ void __launch_bounds__(32 * MAXWPB)
     k_residual_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
+                   const double* __restrict__ u, const uint8_t* __restrict__ cmask,
                    const double* __restrict__ rbar, double* __restrict__ ubar,
-                   double* __restrict__ nbar, double* __restrict__ dbar) {
+                   double* __restrict__ nbar, double* __restrict__ dbar, int accumulate) {
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     using ad::D1;
@@ -110,9 +111,9 @@ __global__ void __launch_bounds__(32 * MAXWPB)
     const size_t fs = (size_t)n * ND;  // field stride of the state and cotangent arrays
 
     for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n; k += (int64_t)gridDim.x * wpb) {
-        for (int i = lane; i < 4 * ND; i += 32) su[i] = ufield(d, 0, i / ND, ND)[k * ND + (i % ND)];
+        for (int i = lane; i < 4 * ND; i += 32) su[i] = u[(i / ND) * fs + k * ND + (i % ND)];
         for (int i = lane; i < 6 * ND; i += 32) rb[i] = rbar[(i / ND) * fs + k * ND + (i % ND)];
-        const unsigned cm = d.cmask[k];
+        const unsigned cm = cmask[k];
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
         const double ihx = 1.0 / hx, ihy = 1.0 / hy;
         const double man = d.manning[k];
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                 const int fo = f ^ 1;
                 const double(*Bnb)[MXN] = fine ? tb.BmH[half] : tb.Bm;
                 double tp[4], yp[4];
-                face_trace<ND1>(ufield(d, 0, 0, ND) + nb * ND, fs, d.cmask[nb], fo, Bnb, al, tp);
+                face_trace<ND1>(u + nb * ND, fs, cmask[nb], fo, Bnb, al, tp);
                 face_trace<ND1>(rbar + nb * ND, fs, 0u, fo, Bnb, al, yp);
 #pragma unroll
                 for (int cf = 0; cf < 4; ++cf) yp[cf] *= -wl;
@@ -395,14 +396,488 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                         for (int al = 0; al < NM; ++al) s += tb.Bm[al][tn] * fp[al];
                     }
                 }
-                ubar[cf * fs + k * ND + i] = s;
+                if (accumulate) ubar[cf * fs + k * ND + i] += s;
+                else ubar[cf * fs + k * ND + i] = s;
             }
         }
         const double ds = warp_sum(dsum), ns = warp_sum(nsum);
         if (lane == 0) {
-            dbar[k] = ds;
-            nbar[k] = ns;
+            dbar[k] = accumulate ? dbar[k] + ds : ds;
+            nbar[k] = accumulate ? nbar[k] + ns : ns;
         }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of one stage update (or of the final combination), Sec. 3.1: the
+// cotangent of the stage output v^(l) pulled back to the residuals of the
+// earlier stages, to H(zeta^n) and C~^n, to v~^n (the start state after the
+// degree switch) through Q~^n, to the previous stage v^(l-1) through the
+// friction coefficient, and to n_K, delta_K.  Each converged solve is
+// differentiated by the implicit function theorem: the continuity solve
+// H(zeta^(l)) = T by M(zeta^(l))^-1 (M symmetric), the tracer solve by
+// H_c(zeta^(l))^-1 and dH_c/dzeta, the momentum solve by A^-1 = S^-1 D^-1 S^-T.
+// Cell-local: every output is accumulated by the cell's own warp.
+// ---------------------------------------------------------------------------
+struct StageVjpArgs {
+    const double* un;     // v~^n [4][n][nd]
+    const uint8_t* cmn;   // its constant-field masks
+    const double* uo;     // stage output v^(l) [4][n][nd]
+    const uint8_t* cmo;
+    const double* up;     // previous stage v^(l-1) [4][n][nd] (friction coefficient)
+    const uint8_t* cmp;
+    const uint8_t* flag;  // degree flags after this stage (0: the r_K = 0 path)
+    const double* vb;     // cotangent of v^(l) [4][n][nd]
+    const double* llb_in; // cotangent of the linearised friction this stage formed [2][n][nd]
+    double* rbar;         // [stage][6][n][nd] (+=, stages m < nres)
+    double* llb_out;      // (+=) cotangent of the linearised friction standing for L of stage nres-1
+    double* HNb;          // [n][nd] (+=)
+    double* CNb;          // [n][nd] (+=)
+    double* ubn;          // cotangent of v~^n [4][n][nd] (+=)
+    double* ubp;          // cotangent of v^(l-1) [4][n][nd] (+=)
+    double* nbar;         // [n] (+=)
+    double* dbar;         // [n] (+=)
+    double wa[MXS], wat[MXS], add, dt;
+    int nres, make_llin, use_llin;
+};
+
+template <int R>
+constexpr int stage_vjp_smem() {
+    using S = Sz<R>;
+    return 4 * S::ND + 5 * S::NMP + S::ND * S::ND + S::ND1 * S::ND1 * S::NM + S::ND +
+           2 * S::NM * S::NM + 3 * S::ND + 9 * S::NGP;
+}
+
+template <int R, typename Pix, int MODE>
+__global__ void __launch_bounds__(32 * MAXWPB)
+    k_stage_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
+                const StageVjpArgs a) {
+    using S = Sz<R>;
+    using ST = Site<R, Pix, MODE>;
+    using ad::D1;
+    constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
+    extern __shared__ double smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    double* vb = smem + warp * stage_vjp_smem<R>(); // [4][ND] cotangent of v^(l)
+    double* pz = vb + 4 * ND;          // [NMP] zeta^(l) at the mass points
+    double* pc = pz + NMP;             // [NMP] c^(l)
+    double* pV = pc + NMP;             // [NMP] J w V
+    double* pA = pV + NMP;             // [NMP] J w A
+    double* pw = pA + NMP;             // [NMP] scratch
+    double* M = pw + NMP;              // [ND][ND]
+    double* Y = M + ND * ND;           // [ND1 ND1 NM]
+    double* inv = Y + ND1 * ND1 * NM;  // [ND]
+    double* tmp = inv + ND;            // [2 NM NM]
+    double* rcb = tmp + 2 * NM * NM;   // [ND] cotangent of the tracer right-hand side
+    double* Tb = rcb + ND;             // [ND] cotangent of T
+    double* x = Tb + ND;               // [ND] scratch
+    double* gam = x + ND;              // [NGP] friction coefficient of v^(l-1)
+    double* gb = gam + NGP;            // [NGP] its cotangent
+    double* g3 = gb + NGP;             // [3][NGP] v^(l-1) at the momentum points
+    double* Xb = g3 + 3 * NGP;         // [2][NGP]
+    double* SQ = Xb + 2 * NGP;         // [2][NGP]
+    const int64_t n = d.n;
+    const size_t fs = (size_t)n * ND;
+    const double g = d.g, eps = d.eps, dt = a.dt;
+
+    // the right-hand-side cotangents spread to the residuals of stages m < nres
+    auto to_res = [&](int field, int i, int64_t k, double v, bool implicit) {
+        for (int m = 0; m < a.nres; ++m) {
+            const double w = implicit ? a.wat[m] : a.wa[m];
+            if (w == 0.0) continue;
+            const int fld = implicit ? field + 3 : field; // L_x, L_y sit 3 after G_x, G_y
+            if (implicit && a.use_llin && m == a.nres - 1)
+                a.llb_out[(size_t)(field - 1) * fs + k * ND + i] += dt * w * v;
+            else
+                a.rbar[((size_t)m * 6 + fld) * fs + k * ND + i] += dt * w * v;
+        }
+    };
+
+    for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n; k += (int64_t)gridDim.x * wpb) {
+        for (int i = lane; i < 4 * ND; i += 32) vb[i] = a.vb[(i / ND) * fs + k * ND + (i % ND)];
+        const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
+        const double man = d.manning[k];
+        const bool scalar = a.flag[k] == 0;
+        const bool need_gam = (a.add != 0.0 || a.make_llin) && man != 0.0;
+        double dsum = 0.0, nsum = 0.0;
+        __syncwarp();
+        // friction coefficient of v^(l-1) on the momentum points (forward values)
+        if (need_gam) {
+            const unsigned cmp = a.cmp[k];
+            for (int f = 0; f < 3; ++f) {
+                tens_interp<ND1, NG>(tb.Bg, a.up + f * fs + k * ND, tmp, g3 + f * NGP, lane);
+                if (cmp & (1u << f))
+                    for (int p = lane; p < NGP; p += 32) g3[f * NGP + p] = a.up[f * fs + k * ND];
+                __syncwarp();
+            }
+            for (int p = lane; p < NGP; p += 32) {
+                double V, A;
+                ST::VA(d, tb, k, SET_MOM, p % NG, p / NG, g3[p], V, A);
+                gam[p] = gamma_manning<double>(man, V, g3[NGP + p], g3[2 * NGP + p], g, eps);
+            }
+        } else {
+            for (int p = lane; p < NGP; p += 32) gam[p] = 0.0;
+        }
+        for (int p = lane; p < NGP; p += 32) gb[p] = 0.0;
+        __syncwarp();
+        if (!scalar) {
+            // linearised friction Llin_f = -S^T (D0 gamma S Q_f) formed by this stage
+            if (a.make_llin && a.llb_in && need_gam) {
+                for (int f = 0; f < 2; ++f) {
+                    tens_interp<ND1, NG>(tb.Bg, a.uo + (1 + f) * fs + k * ND, tmp, SQ + f * NGP, lane);
+                    tens_interp<ND1, NG>(tb.Bg, a.llb_in + f * fs + k * ND, tmp, Xb + f * NGP, lane);
+                }
+                for (int p = lane; p < NGP; p += 32) {
+                    const double D0 = J * tb.wg[p % NG] * tb.wg[p / NG];
+                    gb[p] -= D0 * (SQ[p] * Xb[p] + SQ[NGP + p] * Xb[NGP + p]);
+                    Xb[p] *= -D0 * gam[p];
+                    Xb[NGP + p] *= -D0 * gam[p];
+                }
+                __syncwarp();
+                for (int f = 0; f < 2; ++f) {
+                    tens_test<ND1, NG>(tb.Bg, Xb + f * NGP, tmp, x, lane);
+                    for (int i = lane; i < ND; i += 32) vb[(1 + f) * ND + i] += x[i];
+                    __syncwarp();
+                }
+            }
+            // tracer: rcb = H_c^-1 c_bar, H_c = B^T diag(J w V(zeta^(l))) B
+            const unsigned cmo = a.cmo[k];
+            tens_interp<ND1, NM>(tb.Bm, a.uo + k * ND, tmp, pz, lane);
+            tens_interp<ND1, NM>(tb.Bm, a.uo + 3 * fs + k * ND, tmp, pc, lane);
+            for (int p = lane; p < NMP; p += 32) {
+                if (cmo & 1u) pz[p] = a.uo[k * ND];
+                if (cmo & 8u) pc[p] = a.uo[3 * fs + k * ND];
+                double V, A;
+                ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pz[p], V, A);
+                const double w = J * tb.wm[p % NM] * tb.wm[p / NM];
+                pV[p] = w * V;
+                pA[p] = w * A;
+            }
+            __syncwarp();
+            assemble_mass<ND1, NM>(tb, pV, Y, M, lane);
+            for (int i = lane; i < ND; i += 32) rcb[i] = vb[3 * ND + i];
+            __syncwarp();
+            chol_solve<ND>(M, rcb, inv, lane);
+            // dH_c/dzeta: zeta_bar(p) -= J w A rcb(p) c(p); the same for delta
+            tens_interp<ND1, NM>(tb.Bm, rcb, tmp, pw, lane);
+            for (int p = lane; p < NMP; p += 32) {
+                pw[p] = -pA[p] * pw[p] * pc[p];
+                dsum += pw[p];
+            }
+            __syncwarp();
+            tens_test<ND1, NM>(tb.Bm, pw, tmp, x, lane);
+            for (int i = lane; i < ND; i += 32) {
+                vb[i] += x[i];
+                a.CNb[k * ND + i] += rcb[i];
+                to_res(3, i, k, rcb[i], false);
+            }
+            __syncwarp();
+            // momentum: X_bar = S^-T Q_bar; rq_bar = S^-1 (X_bar / D); q^n part D0 X_bar / D;
+            // D_bar = -X_bar (S Q) / D -> gamma_bar
+            for (int f = 0; f < 2; ++f) {
+                kron_apply<ND1, true, MXP>(tb.Bginv, vb + (1 + f) * ND, tmp, Xb + f * NGP, 1.0, lane);
+                tens_interp<ND1, NG>(tb.Bg, a.uo + (1 + f) * fs + k * ND, tmp, SQ + f * NGP, lane);
+            }
+            for (int p = lane; p < NGP; p += 32) {
+                const double D0 = J * tb.wg[p % NG] * tb.wg[p / NG];
+                const double D = D0 * (1.0 + a.add * dt * gam[p]);
+                gb[p] -= (Xb[p] * SQ[p] + Xb[NGP + p] * SQ[NGP + p]) / D * D0 * a.add * dt;
+                Xb[p] /= D;
+                Xb[NGP + p] /= D;
+                SQ[p] = Xb[p] * D0;           // q^n cotangent at the points
+                SQ[NGP + p] = Xb[NGP + p] * D0;
+            }
+            __syncwarp();
+            for (int f = 0; f < 2; ++f) {
+                kron_apply<ND1, false, MXP>(tb.Bginv, Xb + f * NGP, tmp, x, 1.0, lane);
+                for (int i = lane; i < ND; i += 32) {
+                    to_res(1 + f, i, k, x[i], false);
+                    to_res(1 + f, i, k, x[i], true);
+                }
+                __syncwarp();
+                tens_test<ND1, NG>(tb.Bg, SQ + f * NGP, tmp, x, lane);
+                for (int i = lane; i < ND; i += 32) a.ubn[(1 + f) * fs + k * ND + i] += x[i];
+                __syncwarp();
+            }
+            // continuity: T_bar = M(zeta^(l))^-1 zeta_bar, M = B^T diag(J w A) B; the
+            // offset moves H(zeta^(l)) by J w A: delta_bar -= sum J w A T_bar(p)
+            assemble_mass<ND1, NM>(tb, pA, Y, M, lane);
+            for (int i = lane; i < ND; i += 32) Tb[i] = vb[i];
+            __syncwarp();
+            chol_solve<ND>(M, Tb, inv, lane);
+            tens_interp<ND1, NM>(tb.Bm, Tb, tmp, pw, lane);
+            for (int p = lane; p < NMP; p += 32) dsum -= pA[p] * pw[p];
+            for (int i = lane; i < ND; i += 32) {
+                a.HNb[k * ND + i] += Tb[i];
+                to_res(0, i, k, Tb[i], false);
+            }
+            __syncwarp();
+        } else {
+            // the r_K = 0 path: one value per field, test function 1
+            const double e = a.uo[k * ND], cl = a.uo[3 * fs + k * ND];
+            const double vq[2] = {a.uo[fs + k * ND], a.uo[2 * fs + k * ND]};
+            double ez = 0.0, qs[2] = {0.0, 0.0}, cs = 0.0;
+            for (int i = lane; i < ND; i += 32) {
+                ez += vb[i];
+                qs[0] += vb[ND + i];
+                qs[1] += vb[2 * ND + i];
+                cs += vb[3 * ND + i];
+            }
+            ez = warp_sum(ez);
+            qs[0] = warp_sum(qs[0]);
+            qs[1] = warp_sum(qs[1]);
+            cs = warp_sum(cs);
+            if (a.make_llin && a.llb_in && need_gam) {
+                for (int f = 0; f < 2; ++f)
+                    tens_interp<ND1, NG>(tb.Bg, a.llb_in + f * fs + k * ND, tmp, Xb + f * NGP, lane);
+                double s0 = 0.0, s1 = 0.0;
+                for (int p = lane; p < NGP; p += 32) {
+                    const double D0 = J * tb.wg[p % NG] * tb.wg[p / NG];
+                    gb[p] -= D0 * (vq[0] * Xb[p] + vq[1] * Xb[NGP + p]);
+                    s0 -= D0 * gam[p] * Xb[p];
+                    s1 -= D0 * gam[p] * Xb[NGP + p];
+                }
+                qs[0] += warp_sum(s0);
+                qs[1] += warp_sum(s1);
+            }
+            double Hs, As;
+            mass_scalar<R, Pix, MODE>(d, tb, k, J, e, lane, Hs, As);
+            // tracer: c = (CNbar + dt sum a sum_i R_i) / Hbar(e), or c^n in a dry cell
+            if (Hs > 1e-14 * J * d.hlim) {
+                const double rsb = cs / Hs, Hsb = -cs * cl / Hs;
+                ez += Hsb * As;
+                if (lane == 0) dsum += Hsb * As;
+                for (int i = lane; i < ND; i += 32) {
+                    a.CNb[k * ND + i] += rsb;
+                    to_res(3, i, k, rsb, false);
+                }
+            } else {
+                for (int i = lane; i < ND; i += 32) a.ubn[3 * fs + k * ND + i] += vb[3 * ND + i];
+            }
+            // momentum: q = (sum_p D0 q^n(p) + sum_i rq_i) / sum_p D
+            double den = 0.0;
+            for (int p = lane; p < NGP; p += 32) {
+                const double D0 = J * tb.wg[p % NG] * tb.wg[p / NG];
+                den += D0 * (1.0 + a.add * dt * gam[p]);
+            }
+            den = warp_sum(den);
+            const double denb = -(qs[0] * vq[0] + qs[1] * vq[1]) / den;
+            for (int p = lane; p < NGP; p += 32) {
+                const double D0 = J * tb.wg[p % NG] * tb.wg[p / NG];
+                gb[p] += denb * D0 * a.add * dt;
+                Xb[p] = D0 * qs[0] / den;
+                Xb[NGP + p] = D0 * qs[1] / den;
+            }
+            __syncwarp();
+            for (int f = 0; f < 2; ++f) {
+                tens_test<ND1, NG>(tb.Bg, Xb + f * NGP, tmp, x, lane);
+                for (int i = lane; i < ND; i += 32) {
+                    a.ubn[(1 + f) * fs + k * ND + i] += x[i];
+                    to_res(1 + f, i, k, qs[f] / den, false);
+                    to_res(1 + f, i, k, qs[f] / den, true);
+                }
+                __syncwarp();
+            }
+            // continuity: Hbar(e) = HNbar + dt sum a sum_i F_i (the offset moves Hbar by A)
+            if (As > 0.0) {
+                const double tsb = ez / As;
+                if (lane == 0) dsum -= ez;
+                for (int i = lane; i < ND; i += 32) {
+                    a.HNb[k * ND + i] += tsb;
+                    to_res(0, i, k, tsb, false);
+                }
+            }
+            __syncwarp();
+        }
+        // friction coefficient of v^(l-1): gamma(n, V(zeta), qx, qy) at each point
+        if (need_gam) {
+            for (int p = lane; p < NGP; p += 32) {
+                double V, A;
+                ST::VA(d, tb, k, SET_MOM, p % NG, p / NG, g3[p], V, A);
+                const double qx = g3[NGP + p], qy = g3[2 * NGP + p], gbp = gb[p];
+                double dg[4];
+#pragma unroll 1
+                for (int dir = 0; dir < 4; ++dir) {
+                    const D1 r = gamma_manning<D1>(D1(man, dir == 3 ? 1.0 : 0.0),
+                                                   D1(V, dir == 0 ? 1.0 : 0.0),
+                                                   D1(qx, dir == 1 ? 1.0 : 0.0),
+                                                   D1(qy, dir == 2 ? 1.0 : 0.0), D1(g), D1(eps));
+                    dg[dir] = r.d;
+                }
+                g3[p] = gbp * dg[0] * A;
+                g3[NGP + p] = gbp * dg[1];
+                g3[2 * NGP + p] = gbp * dg[2];
+                dsum += gbp * dg[0] * A;
+                nsum += gbp * dg[3];
+            }
+            __syncwarp();
+            for (int f = 0; f < 3; ++f) {
+                tens_test<ND1, NG>(tb.Bg, g3 + f * NGP, tmp, x, lane);
+                for (int i = lane; i < ND; i += 32) a.ubp[f * fs + k * ND + i] += x[i];
+                __syncwarp();
+            }
+        }
+        const double ds = warp_sum(dsum), ns = warp_sum(nsum);
+        if (lane == 0) {
+            a.dbar[k] += ds;
+            a.nbar[k] += ns;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of the step start: H(zeta~^n), C~^n (Eqs. depth_rhs,
+// concentration_rhs) and the degree switch's mass-exact remap of r_K = 0
+// cells (zeta: Hbar(e) = Hbar(zeta^n); q: Gauss-Legendre means; c: tracer
+// mass / mass, or the mean in a dry cell; a completely dry cell sits at
+// -max(z_b + delta))
+// ---------------------------------------------------------------------------
+struct BeginVjpArgs {
+    const double* upre;   // v^n before the degree switch [4][n][nd]
+    const double* un;     // v~^n [4][n][nd]
+    const uint8_t* cmn;
+    const uint8_t* flag0; // flags of the degree switch
+    const double* HNb;
+    const double* CNb;
+    const double* ubn;    // cotangent of v~^n (all but the H, C~ parts)
+    double* ubpre;        // out: cotangent of v^n [4][n][nd]
+    double* dbar;         // (+=)
+};
+
+template <int R>
+constexpr int begin_vjp_smem() {
+    using S = Sz<R>;
+    return 4 * S::ND + 6 * S::NMP + 2 * S::NM * S::NM + S::ND + S::NGP;
+}
+
+template <int R, typename Pix, int MODE>
+__global__ void __launch_bounds__(32 * MAXWPB)
+    k_begin_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
+                const BeginVjpArgs a) {
+    using S = Sz<R>;
+    using ST = Site<R, Pix, MODE>;
+    constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
+    extern __shared__ double smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    double* ub = smem + warp * begin_vjp_smem<R>(); // [4][ND]
+    double* pz = ub + 4 * ND;   // [NMP]
+    double* pc = pz + NMP;
+    double* h1 = pc + NMP;      // [NMP] H_bar at the points, then zeta~ cotangent
+    double* c1 = h1 + NMP;      // [NMP] C~_bar at the points, then c~ cotangent
+    double* pV = c1 + NMP;      // [NMP]
+    double* pA = pV + NMP;      // [NMP]
+    double* tmp = pA + NMP;     // [2 NM NM]
+    double* x = tmp + 2 * NM * NM; // [ND]
+    double* pg = x + ND;        // [NGP]
+    const int64_t n = d.n;
+    const size_t fs = (size_t)n * ND;
+    for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n; k += (int64_t)gridDim.x * wpb) {
+        for (int i = lane; i < 4 * ND; i += 32) ub[i] = a.ubn[(i / ND) * fs + k * ND + (i % ND)];
+        const double J = d.hxhy[2 * k] * d.hxhy[2 * k + 1];
+        const unsigned cm = a.cmn[k];
+        double dsum = 0.0;
+        __syncwarp();
+        // H_i = sum_p J w V(zeta~) psi_i, C~_i = sum_p J w V c~ psi_i
+        tens_interp<ND1, NM>(tb.Bm, a.un + k * ND, tmp, pz, lane);
+        tens_interp<ND1, NM>(tb.Bm, a.un + 3 * fs + k * ND, tmp, pc, lane);
+        tens_interp<ND1, NM>(tb.Bm, a.HNb + k * ND, tmp, h1, lane);
+        tens_interp<ND1, NM>(tb.Bm, a.CNb + k * ND, tmp, c1, lane);
+        for (int p = lane; p < NMP; p += 32) {
+            if (cm & 1u) pz[p] = a.un[k * ND];
+            if (cm & 8u) pc[p] = a.un[3 * fs + k * ND];
+            double V, A;
+            ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pz[p], V, A);
+            const double w = J * tb.wm[p % NM] * tb.wm[p / NM];
+            const double zt = w * A * (h1[p] + pc[p] * c1[p]);
+            c1[p] = w * V * c1[p];
+            h1[p] = zt;
+            dsum += zt;
+        }
+        __syncwarp();
+        tens_test<ND1, NM>(tb.Bm, h1, tmp, x, lane);
+        for (int i = lane; i < ND; i += 32) ub[i] += x[i];
+        __syncwarp();
+        tens_test<ND1, NM>(tb.Bm, c1, tmp, x, lane);
+        for (int i = lane; i < ND; i += 32) ub[3 * ND + i] += x[i];
+        __syncwarp();
+        if (a.flag0[k] != 0) {
+            for (int i = lane; i < 4 * ND; i += 32) a.ubpre[(i / ND) * fs + k * ND + (i % ND)] = ub[i];
+        } else {
+            // remap of v^n to one value per field
+            tens_interp<ND1, NM>(tb.Bm, a.upre + k * ND, tmp, pz, lane);
+            tens_interp<ND1, NM>(tb.Bm, a.upre + 3 * fs + k * ND, tmp, pc, lane);
+            double m = 0.0, tr = 0.0, Am = 0.0;
+            for (int p = lane; p < NMP; p += 32) {
+                double V, A;
+                ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pz[p], V, A);
+                const double w = J * tb.wm[p % NM] * tb.wm[p / NM];
+                pV[p] = w * V;
+                pA[p] = w * A;
+                m += w * V;
+                tr += w * V * pc[p];
+                Am += w * A;
+            }
+            m = warp_sum(m);
+            tr = warp_sum(tr);
+            Am = warp_sum(Am);
+            double ez = 0.0, qs[2] = {0.0, 0.0}, cs = 0.0;
+            for (int i = lane; i < ND; i += 32) {
+                ez += ub[i];
+                qs[0] += ub[ND + i];
+                qs[1] += ub[2 * ND + i];
+                cs += ub[3 * ND + i];
+            }
+            ez = warp_sum(ez);
+            qs[0] = warp_sum(qs[0]);
+            qs[1] = warp_sum(qs[1]);
+            cs = warp_sum(cs);
+            // q~ = sum_p w_p q(p) on the Gauss-Legendre points
+            for (int f = 0; f < 2; ++f) {
+                for (int p = lane; p < NGP; p += 32) pg[p] = tb.wg[p % NG] * tb.wg[p / NG] * qs[f];
+                __syncwarp();
+                tens_test<ND1, NG>(tb.Bg, pg, tmp, x, lane);
+                for (int i = lane; i < ND; i += 32) a.ubpre[(1 + f) * fs + k * ND + i] = x[i];
+                __syncwarp();
+            }
+            double mb = 0.0;
+            for (int p = lane; p < NMP; p += 32) h1[p] = 0.0;
+            if (m > 1e-14 * J * d.hlim) { // c~ = tracer / m
+                const double tb_ = cs / m;
+                mb -= cs * (tr / m) / m;
+                for (int p = lane; p < NMP; p += 32) {
+                    c1[p] = tb_ * pV[p];
+                    h1[p] += tb_ * pA[p] * pc[p];
+                    dsum += tb_ * pA[p] * pc[p];
+                }
+                __syncwarp();
+                tens_test<ND1, NM>(tb.Bm, c1, tmp, x, lane);
+            } else {                       // c~ = Gauss-Legendre mean
+                for (int p = lane; p < NGP; p += 32) pg[p] = tb.wg[p % NG] * tb.wg[p / NG] * cs;
+                __syncwarp();
+                tens_test<ND1, NG>(tb.Bg, pg, tmp, x, lane);
+            }
+            for (int i = lane; i < ND; i += 32) a.ubpre[3 * fs + k * ND + i] = x[i];
+            __syncwarp();
+            // zeta~ = e with Hbar(e, delta) = m(zeta^n, delta); dry: e = -max(z_b + delta)
+            if (m > 0.0) {
+                double Hs, As;
+                mass_scalar<R, Pix, MODE>(d, tb, k, J, a.un[k * ND], lane, Hs, As);
+                if (As > 0.0) mb += ez / As;
+            }
+            if (lane == 0) dsum -= ez;
+            for (int p = lane; p < NMP; p += 32) {
+                h1[p] += mb * pA[p];
+                dsum += mb * pA[p];
+            }
+            __syncwarp();
+            tens_test<ND1, NM>(tb.Bm, h1, tmp, x, lane);
+            for (int i = lane; i < ND; i += 32) a.ubpre[k * ND + i] = x[i];
+            __syncwarp();
+        }
+        const double ds = warp_sum(dsum);
+        if (lane == 0) a.dbar[k] += ds;
         __syncwarp();
     }
 }

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/swdg.h"
+#include "swdg_adjoint.cuh"
 #include "swdg_kernels.cuh"
 #include "swdg_launch.h"
 
@@ -50,6 +51,15 @@ struct swdg_ctx {
     Bc* bcd = nullptr;
     int64_t* first_d = nullptr; // [nmemb + 1]
     double* adj = nullptr;      // adjoint scratch: 6 + 4 fields of [n][nd], then 2 [n]
+    // step adjoint workspace (swdg_step_record / swdg_step_vjp)
+    struct AdjWs {
+        double *vpre = nullptr, *vtil = nullptr, *ubs = nullptr, *rbar = nullptr, *llb = nullptr,
+               *HNb = nullptr, *CNb = nullptr, *nbar = nullptr, *dbar = nullptr, *vb = nullptr,
+               *ubpre = nullptr;
+        uint8_t *cmtil = nullptr, *flags = nullptr;
+        double t0 = 0.0, dt = 0.0;
+        bool valid = false;
+    } ws;
     double* mdiag = nullptr;    // [nmemb][4]
     std::vector<Bc> bch;
     // device allocations
@@ -674,6 +684,12 @@ static void free_mesh(swdg_ctx* c) {
     cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->diag); cudaFree(c->finfo);
     cudaFree(c->adj);
     c->adj = nullptr;
+    for (double* p : {c->ws.vpre, c->ws.vtil, c->ws.ubs, c->ws.rbar, c->ws.llb, c->ws.HNb, c->ws.CNb,
+                      c->ws.nbar, c->ws.dbar, c->ws.vb, c->ws.ubpre})
+        cudaFree(p);
+    cudaFree(c->ws.cmtil);
+    cudaFree(c->ws.flags);
+    c->ws = swdg_ctx::AdjWs{};
     c->x0y0 = c->hxhy = c->ihxhy = c->manning = c->U = c->res = c->llin = c->HN = c->CN = c->HNbar =
         c->CNbar = c->diag = nullptr;
     c->nbr = nullptr;
@@ -1206,15 +1222,29 @@ int swdg_cfl_dt(swdg_ctx* ctx, double t, double* dt) {
 
 // the kernels of one time step, in stream order; with ev != nullptr an event
 // pair brackets every launch (slot layout of swdg_step_profile)
-static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr) {
+static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr, bool rec = false) {
     const Dev& d = ctx->d;
     const int s = d.s;
+    const int64_t n = ctx->n;
+    const size_t ub = 4 * (size_t)n * ctx->nd * sizeof(double);
     auto mark = [&](int slot, int which) {
         if (ev) cudaEventRecord(ev[slot][which], ctx->st);
     };
+    // recording for the adjoint: v^n, v~^n and its masks, the flags after the
+    // degree switch and after every stage update
+    auto keep_flags = [&](int slot) {
+        if (rec) cudaMemcpyAsync(ctx->ws.flags + (size_t)slot * n, ctx->flag, n,
+                                 cudaMemcpyDeviceToDevice, ctx->st);
+    };
+    if (rec) cudaMemcpyAsync(ctx->ws.vpre, ctx->U, ub, cudaMemcpyDeviceToDevice, ctx->st);
     mark(0, 0);
     ctx->L.step_begin(d, ctx->tb, 1, ctx->shp[KK_BEGIN], ctx->st);
     mark(0, 1);
+    if (rec) {
+        cudaMemcpyAsync(ctx->ws.vtil, ctx->U, ub, cudaMemcpyDeviceToDevice, ctx->st);
+        cudaMemcpyAsync(ctx->ws.cmtil, ctx->cmask, n, cudaMemcpyDeviceToDevice, ctx->st);
+    }
+    keep_flags(0);
     for (int l = 0; l < s; ++l) {
         if (l > 0) {
             StageArgs sa{};
@@ -1232,6 +1262,7 @@ static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr) {
             mark(4 + l, 0);
             ctx->L.stage(d, ctx->tb, sa, ctx->shp[KK_STAGE], ctx->st);
             mark(4 + l, 1);
+            keep_flags(l);
         }
         mark(1 + l, 0);
         ctx->L.residual(d, ctx->tb, l, l, d.c[l], l == 0 ? 1 : 0, ctx->shp[KK_RESIDUAL], ctx->st);
@@ -1252,6 +1283,7 @@ static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr) {
     mark(8, 0);
     ctx->L.stage(d, ctx->tb, sa, ctx->shp[KK_STAGE], ctx->st);
     mark(8, 1);
+    keep_flags(s);
     CK(cudaGetLastError());
     return SWDG_OK;
 }
@@ -1423,13 +1455,183 @@ int swdg_residual_vjp(swdg_ctx* ctx, double t, const double* Fb, const double* G
     double* ub = ctx->adj + 6 * f;
     double* nb = ctx->adj + 10 * f;
     double* db = nb + n;
-    ctx->L.residual_vjp(ctx->d, ctx->tb, ctx->adj, ub, nb, db, Shape{grid_for(n), WPB}, ctx->st);
+    ctx->L.residual_vjp(ctx->d, ctx->tb, ctx->U, ctx->cmask, ctx->adj, ub, nb, db, 0,
+                        Shape{grid_for(n), WPB}, ctx->st);
     CK(cudaGetLastError());
     double* dst[4] = {zeta_b, qx_b, qy_b, c_b};
     for (int i = 0; i < 4; ++i)
         if (dst[i]) CK(cudaMemcpyAsync(dst[i], ub + i * f, fb, out, ctx->st));
     if (manning_b) CK(cudaMemcpyAsync(manning_b, nb, n * sizeof(double), out, ctx->st));
     if (delta_b) CK(cudaMemcpyAsync(delta_b, db, n * sizeof(double), out, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return SWDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// discrete adjoint of a time step
+// ---------------------------------------------------------------------------
+static int adjoint_ready(swdg_ctx* ctx, const char* who) {
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "%s: no state", who);
+    if (ctx->cfg.precision != 0)
+        return fail(ctx, SWDG_EINVAL, "%s: the step adjoint differentiates the FP64 path", who);
+    if (ctx->nmemb != 1) return fail(ctx, SWDG_EINVAL, "%s: not for an ensemble", who);
+    return SWDG_OK;
+}
+
+int swdg_step_record(swdg_ctx* ctx, double dt, double* t_inout) {
+    if (!ctx) return SWDG_EINVAL;
+    int rc = adjoint_ready(ctx, "step_record");
+    if (rc) return rc;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, SWDG_EINVAL, "step_record: dt > 0 required");
+    const int64_t n = ctx->n;
+    const int s = ctx->d.s;
+    const size_t f = (size_t)n * ctx->nd;
+    auto& w = ctx->ws;
+    if (!w.vpre) {
+        CK(cudaMalloc(&w.vpre, 4 * f * sizeof(double)));
+        CK(cudaMalloc(&w.vtil, 4 * f * sizeof(double)));
+        CK(cudaMalloc(&w.ubs, (size_t)MXS * 4 * f * sizeof(double)));
+        CK(cudaMalloc(&w.rbar, (size_t)MXS * 6 * f * sizeof(double)));
+        CK(cudaMalloc(&w.llb, 2 * f * sizeof(double)));
+        CK(cudaMalloc(&w.HNb, f * sizeof(double)));
+        CK(cudaMalloc(&w.CNb, f * sizeof(double)));
+        CK(cudaMalloc(&w.nbar, n * sizeof(double)));
+        CK(cudaMalloc(&w.dbar, n * sizeof(double)));
+        CK(cudaMalloc(&w.vb, 4 * f * sizeof(double)));
+        CK(cudaMalloc(&w.ubpre, 4 * f * sizeof(double)));
+        CK(cudaMalloc(&w.cmtil, n));
+        CK(cudaMalloc(&w.flags, (size_t)(MXS + 1) * n));
+    }
+    std::vector<Member> mh;
+    rc = read_clocks(ctx, mh);
+    if (rc) return rc;
+    const double t0 = t_inout ? *t_inout : mh[0].t;
+    rc = put_time(ctx, t0, dt);
+    if (rc) return rc;
+    rc = enqueue_step(ctx, nullptr, true);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->sc_host, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    (void)s;
+    w.t0 = t0;
+    w.dt = dt;
+    w.valid = true;
+    if (t_inout) *t_inout = ctx->sc_host->m0.t;
+    if (ctx->sc_host->status & ST_NAN) return fail(ctx, SWDG_ENAN, "step_record: non-finite state");
+    return SWDG_OK;
+}
+
+int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const double* qy_b,
+                  const double* c_b, double* zeta_b_out, double* qx_b_out, double* qy_b_out,
+                  double* c_b_out, double* manning_b, double* delta_b, int where) {
+    if (!ctx) return SWDG_EINVAL;
+    int rc = adjoint_ready(ctx, "step_vjp");
+    if (rc) return rc;
+    auto& w = ctx->ws;
+    if (!w.valid) return fail(ctx, SWDG_ESTATE, "step_vjp: no recorded step (swdg_step_record)");
+    if (where != SWDG_HOST && where != SWDG_DEVICE) return fail(ctx, SWDG_EINVAL, "step_vjp: bad where");
+    const Dev& d = ctx->d;
+    const int64_t n = ctx->n;
+    const int s = d.s;
+    const size_t f = (size_t)n * ctx->nd, fb = f * sizeof(double);
+    const cudaMemcpyKind in = where == SWDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind out = where == SWDG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const double* src[4] = {zeta_b, qx_b, qy_b, c_b};
+    for (int i = 0; i < 4; ++i) {
+        if (src[i]) CK(cudaMemcpyAsync(w.vb + i * f, src[i], fb, in, ctx->st));
+        else CK(cudaMemsetAsync(w.vb + i * f, 0, fb, ctx->st));
+    }
+    CK(cudaMemsetAsync(w.ubs, 0, (size_t)s * 4 * fb, ctx->st));
+    CK(cudaMemsetAsync(w.rbar, 0, (size_t)s * 6 * fb, ctx->st));
+    CK(cudaMemsetAsync(w.llb, 0, 2 * fb, ctx->st));
+    CK(cudaMemsetAsync(w.HNb, 0, fb, ctx->st));
+    CK(cudaMemsetAsync(w.CNb, 0, fb, ctx->st));
+    CK(cudaMemsetAsync(w.nbar, 0, n * sizeof(double), ctx->st));
+    CK(cudaMemsetAsync(w.dbar, 0, n * sizeof(double), ctx->st));
+    const Shape shp{grid_for(n), WPB};
+    auto ubuf = [&](int l) { return ctx->U + (size_t)l * 4 * f; };
+    auto cbuf = [&](int l) { return ctx->cmask + (size_t)l * n; };
+    const bool imp = d.at[s - 1][s - 1] != 0.0;
+    // final combination (weights b, b~, no implicit diagonal)
+    StageVjpArgs a{};
+    a.un = w.vtil;
+    a.cmn = w.cmtil;
+    a.rbar = w.rbar;
+    a.HNb = w.HNb;
+    a.CNb = w.CNb;
+    a.ubn = w.ubs;
+    a.nbar = w.nbar;
+    a.dbar = w.dbar;
+    a.dt = w.dt;
+    a.uo = ubuf(0);
+    a.cmo = cbuf(0);
+    a.up = s > 1 ? ubuf(s - 1) : w.vtil;
+    a.cmp = s > 1 ? cbuf(s - 1) : w.cmtil;
+    a.flag = w.flags + (size_t)s * n;
+    a.vb = w.vb;
+    a.llb_in = nullptr;
+    a.llb_out = w.llb;
+    a.ubp = w.ubs + (size_t)(s - 1) * 4 * f;
+    for (int m = 0; m < s; ++m) {
+        a.wa[m] = d.b[m];
+        a.wat[m] = d.bt[m];
+    }
+    a.add = 0.0;
+    a.nres = s;
+    a.make_llin = 0;
+    a.use_llin = imp ? 1 : 0;
+    ctx->L.stage_vjp(d, ctx->tb, a, shp, ctx->st);
+    CK(cudaGetLastError());
+    for (int l = s - 1; l >= 0; --l) {
+        // residual of stage l at t^n + c_l dt
+        rc = put_clocks(ctx, w.t0 + d.c[l] * w.dt, 0);
+        if (rc) return rc;
+        const double* ul = l == 0 ? w.vtil : ubuf(l);
+        const uint8_t* cl = l == 0 ? w.cmtil : cbuf(l);
+        ctx->L.residual_vjp(d, ctx->tb, ul, cl, w.rbar + (size_t)l * 6 * f,
+                            w.ubs + (size_t)l * 4 * f, w.nbar, w.dbar, 1, shp, ctx->st);
+        CK(cudaGetLastError());
+        if (l == 0) break;
+        StageVjpArgs b = a;
+        b.uo = ubuf(l);
+        b.cmo = cbuf(l);
+        b.up = l - 1 == 0 ? w.vtil : ubuf(l - 1);
+        b.cmp = l - 1 == 0 ? w.cmtil : cbuf(l - 1);
+        b.flag = w.flags + (size_t)l * n;
+        b.vb = w.ubs + (size_t)l * 4 * f;
+        b.make_llin = (l == s - 1 && d.at[l][l] != 0.0) ? 1 : 0;
+        b.llb_in = b.make_llin ? w.llb : nullptr;
+        b.llb_out = nullptr;
+        b.use_llin = 0;
+        b.ubp = w.ubs + (size_t)(l - 1) * 4 * f;
+        for (int m = 0; m < MXS; ++m) {
+            b.wa[m] = m < l ? d.a[l][m] : 0.0;
+            b.wat[m] = m < l ? d.at[l][m] : 0.0;
+        }
+        b.add = d.at[l][l];
+        b.nres = l;
+        ctx->L.stage_vjp(d, ctx->tb, b, shp, ctx->st);
+        CK(cudaGetLastError());
+    }
+    BeginVjpArgs bg{};
+    bg.upre = w.vpre;
+    bg.un = w.vtil;
+    bg.cmn = w.cmtil;
+    bg.flag0 = w.flags;
+    bg.HNb = w.HNb;
+    bg.CNb = w.CNb;
+    bg.ubn = w.ubs;
+    bg.ubpre = w.ubpre;
+    bg.dbar = w.dbar;
+    ctx->L.begin_vjp(d, ctx->tb, bg, shp, ctx->st);
+    CK(cudaGetLastError());
+    rc = put_clocks(ctx, w.t0 + w.dt, 0);
+    if (rc) return rc;
+    double* dst[4] = {zeta_b_out, qx_b_out, qy_b_out, c_b_out};
+    for (int i = 0; i < 4; ++i)
+        if (dst[i]) CK(cudaMemcpyAsync(dst[i], w.ubpre + i * f, fb, out, ctx->st));
+    if (manning_b) CK(cudaMemcpyAsync(manning_b, w.nbar, n * sizeof(double), out, ctx->st));
+    if (delta_b) CK(cudaMemcpyAsync(delta_b, w.dbar, n * sizeof(double), out, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return SWDG_OK;
 }

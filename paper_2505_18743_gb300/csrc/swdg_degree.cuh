@@ -15,6 +15,8 @@ struct Launchers {
     static constexpr size_t stage_b = sizeof(double) * stage_smem<R>();
     static constexpr size_t diag_b = sizeof(double) * (2 * S::ND + 2 * S::NMP + 2 * S::NM * S::NM);
     static constexpr size_t vjp_b = sizeof(double) * vjp_smem<R>();
+    static constexpr size_t svjp_b = sizeof(double) * stage_vjp_smem<R>();
+    static constexpr size_t bvjp_b = sizeof(double) * begin_vjp_smem<R>();
 
     static void residual(const Dev& d, const Tables& tb, int buf, int stage, double c_stage,
                          int want_dt, Shape s, cudaStream_t st) {
@@ -37,10 +39,19 @@ struct Launchers {
                        int64_t k0, int64_t k1, cudaStream_t st) {
         k_gauges<R><<<(ng + 63) / 64, 64, 0, st>>>(d, tb, ng, xy, out, k0, k1);
     }
-    static void residual_vjp(const Dev& d, const Tables& tb, const double* rbar, double* ubar,
-                             double* nbar, double* dbar, Shape s, cudaStream_t st) {
-        k_residual_vjp<R, Pix, MODE><<<s.grid, 32 * s.wpb, vjp_b * s.wpb, st>>>(d, tb, rbar, ubar,
-                                                                              nbar, dbar);
+    static void residual_vjp(const Dev& d, const Tables& tb, const double* u, const uint8_t* cm,
+                             const double* rbar, double* ubar, double* nbar, double* dbar,
+                             int accumulate, Shape s, cudaStream_t st) {
+        k_residual_vjp<R, Pix, MODE><<<s.grid, 32 * s.wpb, vjp_b * s.wpb, st>>>(
+            d, tb, u, cm, rbar, ubar, nbar, dbar, accumulate);
+    }
+    static void stage_vjp(const Dev& d, const Tables& tb, const StageVjpArgs& a, Shape s,
+                          cudaStream_t st) {
+        k_stage_vjp<R, Pix, MODE><<<s.grid, 32 * s.wpb, svjp_b * s.wpb, st>>>(d, tb, a);
+    }
+    static void begin_vjp(const Dev& d, const Tables& tb, const BeginVjpArgs& a, Shape s,
+                          cudaStream_t st) {
+        k_begin_vjp<R, Pix, MODE><<<s.grid, 32 * s.wpb, bvjp_b * s.wpb, st>>>(d, tb, a);
     }
     template <typename K>
     static bool opt_in(K kern, size_t per_warp) {
@@ -52,7 +63,9 @@ struct Launchers {
                opt_in(k_step_begin<R, Pix, MODE>, begin_b) &&
                opt_in(k_stage<R, Pix, MODE, B>, stage_b) &&
                opt_in(k_cell_diag<R, Pix, MODE>, diag_b) &&
-               opt_in(k_residual_vjp<R, Pix, MODE>, vjp_b);
+               opt_in(k_residual_vjp<R, Pix, MODE>, vjp_b) &&
+               opt_in(k_stage_vjp<R, Pix, MODE>, svjp_b) &&
+               opt_in(k_begin_vjp<R, Pix, MODE>, bvjp_b);
     }
     template <typename K>
     static int occ(K kern, int wpb, size_t per_warp) {
@@ -79,6 +92,8 @@ struct Launchers {
         L->cell_diag = &cell_diag;
         L->gauges = &gauges;
         L->residual_vjp = &residual_vjp;
+        L->stage_vjp = &stage_vjp;
+        L->begin_vjp = &begin_vjp;
         L->prepare = &prepare;
         L->occupancy = &occupancy;
         L->nzp = Sz<R>::NZP;

@@ -6,6 +6,8 @@
 namespace swdg {
 
 struct StageArgs;
+struct StageVjpArgs;
+struct BeginVjpArgs;
 
 // launch shape of one kernel: blocks and warps (cells in flight) per block
 struct Shape {
@@ -26,8 +28,12 @@ struct Launch {
                    int64_t k1, cudaStream_t);
     // discrete adjoint of the residual (FP64): rbar [6][n][nd] -> ubar [4][n][nd],
     // nbar [n] (Manning), dbar [n] (bathymetry offset)
-    void (*residual_vjp)(const Dev&, const Tables&, const double* rbar, double* ubar, double* nbar,
-                         double* dbar, Shape, cudaStream_t);
+    void (*residual_vjp)(const Dev&, const Tables&, const double* u, const uint8_t* cmask,
+                         const double* rbar, double* ubar, double* nbar, double* dbar,
+                         int accumulate, Shape, cudaStream_t);
+    // adjoints of a stage update / the final combination and of the step start (FP64)
+    void (*stage_vjp)(const Dev&, const Tables&, const StageVjpArgs&, Shape, cudaStream_t);
+    void (*begin_vjp)(const Dev&, const Tables&, const BeginVjpArgs&, Shape, cudaStream_t);
     // opt every kernel in to the shared memory of MAXWPB warps; false on failure
     bool (*prepare)();
     // resident blocks per SM of kernel kind KK_* at wpb warps per block (0: cannot launch)

@@ -72,6 +72,8 @@ SIGNATURES = {
     "swdg_residual_noalloc": (_I, [ctypes.POINTER(swdg_config), _I64, _P, _P, _P, _I, _I, _P, _P,
                                    _P, _P, _P, _P, _D, _P, _P, ctypes.c_char_p, _I]),
     "swdg_residual_vjp": (_I, [_P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
+    "swdg_step_record": (_I, [_P, _D, ctypes.POINTER(_D)]),
+    "swdg_step_vjp": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
     "swdg_set_members": (_I, [_P, _I, _P]),
     "swdg_upload_bathymetry_members": (_I, [_P, _P, _I, _P, _P]),
     "swdg_set_boundary_member": (_I, [_P, _I, _I, _I, _D, _D, _D]),
@@ -237,6 +239,33 @@ class Context:
         ptr = [None if a is None else a.ctypes.data_as(_P) for a in ins]
         self._ck(load().swdg_residual_vjp(self.h, t, *ptr, *[o.ctypes.data_as(_P) for o in outs],
                                           SWDG_HOST))
+        return dict(zip(("zeta", "qx", "qy", "c", "manning", "delta"), outs))
+
+    def step_record(self, dt, t=None):
+        """one fixed step of size dt, recorded for step_vjp; returns the end time"""
+        tt = _D(0.0 if t is None else t)
+        self._ck(load().swdg_step_record(self.h, dt, ctypes.byref(tt) if t is not None else None))
+        return tt.value if t is not None else None
+
+    def step_vjp(self, cot):
+        """adjoint of the recorded step: cotangent of the state after it (4 arrays
+        [n, nd], host numpy or CUDA tensors) -> that of the state before it, the
+        Manning coefficients [n] and the bathymetry offsets [n]"""
+        dev = _torch() is not None and isinstance(cot[0], _torch().Tensor) and cot[0].is_cuda
+        if dev:
+            t = _torch()
+            outs = [t.empty_like(cot[0]) for _ in range(4)] + \
+                [t.empty(self.n, dtype=t.float64, device=cot[0].device) for _ in range(2)]
+            ins = [ctypes.c_void_p(a.contiguous().data_ptr()) for a in cot]
+            self._ck(load().swdg_step_vjp(self.h, *ins,
+                                          *[ctypes.c_void_p(o.data_ptr()) for o in outs],
+                                          SWDG_DEVICE))
+        else:
+            ins = [np.ascontiguousarray(a, dtype=np.float64) for a in cot]
+            outs = [np.empty((self.n, self.nd)) for _ in range(4)] + [np.empty(self.n),
+                                                                        np.empty(self.n)]
+            self._ck(load().swdg_step_vjp(self.h, *[a.ctypes.data_as(_P) for a in ins],
+                                          *[o.ctypes.data_as(_P) for o in outs], SWDG_HOST))
         return dict(zip(("zeta", "qx", "qy", "c", "manning", "delta"), outs))
 
     def cfl_dt(self, t=0.0):
