@@ -212,6 +212,12 @@ int swdg_residual_vjp(swdg_ctx* ctx, double t, const double* F_b, const double* 
  * state.  FP64 contexts with one member only (SWDG_EINVAL otherwise);
  * swdg_step_vjp without a recorded step returns SWDG_ESTATE. */
 int swdg_step_record(swdg_ctx* ctx, double dt, double* t_inout);
+/* Per-cell bathymetry offsets delta [n] (host or device per where; NULL = 0):
+ * every depth of cell K (its pixels in mode S -- rounded to the raster's
+ * precision --, its sampled depths in mode P) becomes the uploaded depth +
+ * delta_K, the parameter whose cotangent swdg_step_vjp returns.  Offsets are
+ * absolute (relative to the uploaded bathymetry), not cumulative. */
+int swdg_set_bathymetry_offset(swdg_ctx* ctx, const double* delta, int where);
 int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const double* qy_b,
                   const double* c_b, double* zeta_b_out, double* qx_b_out, double* qy_b_out,
                   double* c_b_out, double* manning_b, double* delta_b, int where);

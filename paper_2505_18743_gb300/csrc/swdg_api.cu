@@ -72,6 +72,10 @@ struct swdg_ctx {
     OvTab* ov = nullptr;
     double* zhang = nullptr;
     void* tiles = nullptr;
+    // the uploaded depth data, kept once an offset is applied (swdg_set_bathymetry_offset)
+    void* tiles0 = nullptr;
+    double* zpts0 = nullptr;
+    int64_t npix = 0;
     Scalars* sc = nullptr;
     Scalars* sc_host = nullptr; // pinned staging
     double* pin = nullptr;      // pinned staging for small reads
@@ -698,6 +702,9 @@ static void free_mesh(swdg_ctx* c) {
 static void free_bathy(swdg_ctx* c) {
     cudaFree(c->tiles); cudaFree(c->zpts); cudaFree(c->zmax); cudaFree(c->zmin); cudaFree(c->zabs);
     cudaFree(c->zhang); cudaFree(c->tile_off); cudaFree(c->pcls); cudaFree(c->ov);
+    cudaFree(c->tiles0); cudaFree(c->zpts0);
+    c->tiles0 = nullptr;
+    c->zpts0 = nullptr;
     c->tiles = nullptr;
     c->zpts = c->zmax = c->zmin = c->zabs = c->zhang = nullptr;
     c->tile_off = nullptr;
@@ -1041,6 +1048,7 @@ static int upload_bathy(swdg_ctx* ctx, int nseg, const void* const* rasters, int
     d.zmax = ctx->zmax;
     d.zmin = ctx->zmin;
     d.zabs = ctx->zabs;
+    ctx->npix = npix;
     ctx->has_bathy = true;
     return SWDG_OK;
 }
@@ -1633,6 +1641,122 @@ int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const
     if (manning_b) CK(cudaMemcpyAsync(manning_b, w.nbar, n * sizeof(double), out, ctx->st));
     if (delta_b) CK(cudaMemcpyAsync(delta_b, w.dbar, n * sizeof(double), out, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    return SWDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-cell bathymetry offsets (the parameter of the step adjoint)
+// ---------------------------------------------------------------------------
+} // extern "C"
+
+template <typename Pix>
+__global__ void k_offset_tiles(const Pix* __restrict__ base, Pix* tiles, const int64_t* off,
+                               const uint8_t* pcls, const OvTab* ov, const double* delta,
+                               int64_t n) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = warp; k < n; k += nw) {
+        const int P = ov[pcls[k]].P;
+        const double dk = delta ? delta[k] : 0.0;
+        for (int i = lane; i < P * P; i += 32)
+            tiles[off[k] + i] = (Pix)((double)base[off[k] + i] + dk);
+    }
+}
+
+// mode P: every sampled depth of cell k moves by delta_k; bounds from the mass points
+__global__ void k_offset_points(const double* __restrict__ base, double* zpts, double* zhang,
+                                double* zmax, double* zmin, double* zabs, const double* delta,
+                                int nzp, int nv2, int nm2, int zh, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double dk = delta ? delta[k] : 0.0;
+        double m = -INFINITY, mn = INFINITY, a = 0.0;
+        for (int p = 0; p < nzp; ++p) {
+            const double z = base[k * nzp + p] + dk;
+            zpts[k * nzp + p] = z;
+            if (p >= nv2 && p < nv2 + nm2) {
+                m = fmax(m, z);
+                mn = fmin(mn, z);
+                a = fmax(a, fabs(z));
+            }
+        }
+        for (int i = 0; i < zh; ++i) zhang[k * zh + i] = base[n * nzp + k * zh + i] + dk;
+        zmax[k] = m;
+        zmin[k] = mn;
+        zabs[k] = a;
+    }
+}
+
+extern "C" {
+
+int swdg_set_bathymetry_offset(swdg_ctx* ctx, const double* delta, int where) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_bathy) return fail(ctx, SWDG_ESTATE, "set_bathymetry_offset: no bathymetry");
+    if (where != SWDG_HOST && where != SWDG_DEVICE)
+        return fail(ctx, SWDG_EINVAL, "set_bathymetry_offset: bad where");
+    const int64_t n = ctx->n;
+    const int R_ = ctx->R, nv_ = (3 * R_) / 2 + 1, nm_ = R_ + 2, ng_ = R_ + 1;
+    const int nzp_ = nv_ * nv_ + nm_ * nm_ + ng_ * ng_, zh = 8 * nm_;
+    const size_t es = ctx->pix == 0 ? 4 : 8;
+    double* dd = nullptr;
+    if (delta) {
+        if (where == SWDG_HOST) {
+            for (int64_t k = 0; k < n; ++k)
+                if (!std::isfinite(delta[k]))
+                    return fail(ctx, SWDG_EINVAL, "set_bathymetry_offset: bad value at cell %lld",
+                                (long long)k);
+        }
+        CK(cudaMalloc(&dd, n * sizeof(double)));
+        CK(cudaMemcpyAsync(dd, delta, n * sizeof(double),
+                           where == SWDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           ctx->st));
+    }
+    const int gw = (int)std::min<int64_t>(152 * 32, (n * 32 + 255) / 256 + 1);
+    if (ctx->mode == 0) {
+        if (!ctx->tiles0) { // keep the uploaded pixels
+            CK(cudaMalloc(&ctx->tiles0, (size_t)ctx->npix * es));
+            CK(cudaMemcpyAsync(ctx->tiles0, ctx->tiles, (size_t)ctx->npix * es,
+                               cudaMemcpyDeviceToDevice, ctx->st));
+        }
+        if (ctx->pix == 0)
+            k_offset_tiles<float><<<gw, 256, 0, ctx->st>>>((const float*)ctx->tiles0,
+                                                          (float*)ctx->tiles, ctx->tile_off,
+                                                          ctx->pcls, ctx->ov, dd, n);
+        else
+            k_offset_tiles<double><<<gw, 256, 0, ctx->st>>>((const double*)ctx->tiles0,
+                                                           (double*)ctx->tiles, ctx->tile_off,
+                                                           ctx->pcls, ctx->ov, dd, n);
+        // bounds, sub-cell means and coarse-side strips of the moved pixels
+        if (ctx->pix == 0) {
+            k_tile_bounds<float><<<gw, 256, 0, ctx->st>>>((const float*)ctx->tiles, ctx->tile_off,
+                                                         ctx->pcls, ctx->ov, n, ctx->zmax, ctx->zmin,
+                                                         ctx->zabs);
+            k_subcell_means<float><<<gw, 256, 0, ctx->st>>>(
+                (const float*)ctx->tiles, ctx->tile_off, ctx->pcls, ctx->ov, ctx->finfo, nv_, nm_, ng_,
+                ctx->zpts, ctx->zhang, n);
+        } else {
+            k_tile_bounds<double><<<gw, 256, 0, ctx->st>>>((const double*)ctx->tiles, ctx->tile_off,
+                                                          ctx->pcls, ctx->ov, n, ctx->zmax,
+                                                          ctx->zmin, ctx->zabs);
+            k_subcell_means<double><<<gw, 256, 0, ctx->st>>>(
+                (const double*)ctx->tiles, ctx->tile_off, ctx->pcls, ctx->ov, ctx->finfo, nv_, nm_,
+                ng_, ctx->zpts, ctx->zhang, n);
+        }
+    } else {
+        if (!ctx->zpts0) { // keep the uploaded samples: [n][nzp] then [n][8 nm]
+            CK(cudaMalloc(&ctx->zpts0, (size_t)n * (nzp_ + zh) * sizeof(double)));
+            CK(cudaMemcpyAsync(ctx->zpts0, ctx->zpts, (size_t)n * nzp_ * sizeof(double),
+                               cudaMemcpyDeviceToDevice, ctx->st));
+            CK(cudaMemcpyAsync(ctx->zpts0 + (size_t)n * nzp_, ctx->zhang, (size_t)n * zh * sizeof(double),
+                               cudaMemcpyDeviceToDevice, ctx->st));
+        }
+        k_offset_points<<<(int)std::min<int64_t>(152 * 16, (n + 127) / 128), 128, 0, ctx->st>>>(
+            ctx->zpts0, ctx->zpts, ctx->zhang, ctx->zmax, ctx->zmin, ctx->zabs, dd, nzp_,
+            nv_ * nv_, nm_ * nm_, zh, n);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->st));
+    cudaFree(dd);
     return SWDG_OK;
 }
 

@@ -74,6 +74,7 @@ SIGNATURES = {
     "swdg_residual_vjp": (_I, [_P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
     "swdg_step_record": (_I, [_P, _D, ctypes.POINTER(_D)]),
     "swdg_step_vjp": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
+    "swdg_set_bathymetry_offset": (_I, [_P, _P, _I]),
     "swdg_set_members": (_I, [_P, _I, _P]),
     "swdg_upload_bathymetry_members": (_I, [_P, _P, _I, _P, _P]),
     "swdg_set_boundary_member": (_I, [_P, _I, _I, _I, _D, _D, _D]),
@@ -240,6 +241,18 @@ class Context:
         self._ck(load().swdg_residual_vjp(self.h, t, *ptr, *[o.ctypes.data_as(_P) for o in outs],
                                           SWDG_HOST))
         return dict(zip(("zeta", "qx", "qy", "c", "manning", "delta"), outs))
+
+    def clock(self):
+        """(t, last dt) of the context (member 0 of an ensemble)"""
+        m = max(getattr(self, "m", 1), 1)
+        t, dt = np.empty(m), np.empty(m)
+        self._ck(load().swdg_member_times(self.h, t.ctypes.data_as(_P), dt.ctypes.data_as(_P), 0))
+        return float(t[0]), float(dt[0])
+
+    def set_bathymetry_offset(self, delta):
+        """every depth of cell K deepened by delta[K] (absolute, None = 0)"""
+        p, where, keep = _buf(delta, np.float64)
+        self._ck(load().swdg_set_bathymetry_offset(self.h, p, where))
 
     def step_record(self, dt, t=None):
         """one fixed step of size dt, recorded for step_vjp; returns the end time"""
