@@ -303,6 +303,64 @@ def ensemble_variant(args, stream, dev, world, members=64):
     return out
 
 
+def adjoint_variant(args, stream, dev, world, nsteps=40, every=20):
+    """Gradient of a functional of the final state with respect to the start
+    state, the Manning coefficients and per-cell bathymetry offsets, through
+    nsteps CFL steps of a 128 x 128-cell, r = 2 crop of the beach (16 x 16 px
+    per cell, the shoreline band included), checkpoint every 20 steps: the
+    forward run, the backward run (re-run of each block, recorded steps,
+    step adjoints), and the plain forward (one CUDA graph per step) for
+    comparison."""
+    import torch
+    from paper_2505_18743_gb300 import adjoint, swdg
+    wl = W.tidal_beach(window=(128, 64, 128, 128), degree=2, pix=16)
+    Xn, Yn = W.nodal_coordinates(wl.mesh, wl.degree)
+    # a 0.3 m flood with a 0.2 m hump offshore: wet, wet-dry and dry cells in motion
+    wl.zeta = 0.3 + 0.2 * np.exp(-((Xn - 16000.0) ** 2 + (Yn - 7000.0) ** 2) / 1500.0 ** 2)
+    ctx = swdg.Context.from_workload(wl, stream=stream.cuda_stream)
+    nd = (wl.degree + 1) ** 2
+    units = wl.mesh.n * 4 * nd * STAGES * nsteps
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    mk = lambda a: torch.tensor(np.asarray(a, dtype=np.float64), device=dev, requires_grad=True)
+    state = [mk(a) for a in wl.state()]
+    man, delta = mk(wl.manning), mk(np.zeros(wl.mesh.n))
+    w = [torch.randn((wl.mesh.n, nd), dtype=torch.float64, device=dev,
+                     generator=torch.Generator(device=dev).manual_seed(5)) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        s0, s1, s2 = ev(), ev(), ev()
+        torch.cuda.synchronize(dev)
+        s0.record(stream)
+        outs = adjoint.solve(ctx, *state, man, delta, nsteps=nsteps, checkpoint_every=every)
+        loss = sum((o * wi).sum() for o, wi in zip(outs, w))
+        s1.record(stream)
+        loss.backward()
+        s2.record(stream)
+        torch.cuda.synchronize(dev)
+    t_fwd, t_bwd = s0.elapsed_time(s1), s1.elapsed_time(s2)
+    plain = swdg.Context.from_workload(wl, stream=stream.cuda_stream)
+    plain.step(2, -1.0, 0.0)
+    p0, p1 = ev(), ev()
+    torch.cuda.synchronize(dev)
+    p0.record(stream)
+    plain.step(nsteps, -1.0, 0.0)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_plain = p0.elapsed_time(p1)
+    ok = all(bool(torch.isfinite(g).all()) for g in [s.grad for s in state] + [man.grad, delta.grad])
+    ctx.close()
+    plain.close()
+    return {"workload": "tidal beach crop 128x128 cells (cells 128..255 x 64..191), r=2, "
+                        "16x16 px/cell, RK32-IMEX, 0.3 m flood with an offshore hump",
+            "steps": nsteps, "checkpoint_every": every,
+            "forward_ms": t_fwd, "backward_ms": t_bwd, "plain_forward_ms": t_plain,
+            "backward_over_plain_forward": t_bwd / t_plain,
+            "gradient_updates_per_s": units * world / (t_bwd / 1e3), "unit": "updates/s",
+            "gradients_finite": ok}
+
+
 def run_gpu(args, rank, world, local):
     import torch
     from paper_2505_18743_gb300 import swdg
@@ -419,6 +477,7 @@ def run_gpu(args, rank, world, local):
 
     if not args.no_variants and prec == 0:
         variants["ensemble"] = ensemble_variant(args, stream, dev, world)
+        variants["adjoint"] = adjoint_variant(args, stream, dev, world)
 
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
