@@ -212,6 +212,18 @@ int swdg_residual_vjp(swdg_ctx* ctx, double t, const double* F_b, const double* 
  * state.  FP64 contexts with one member only (SWDG_EINVAL otherwise);
  * swdg_step_vjp without a recorded step returns SWDG_ESTATE. */
 int swdg_step_record(swdg_ctx* ctx, double dt, double* t_inout);
+/* Record slots, so that a block of steps is run forward once and then pulled
+ * back from its records: swdg_adjoint_slots reserves n_slots records (each
+ * (s + 2) states of [4][n][(r+1)^2] float64 plus 2 (s + 1) n bytes, s the
+ * stages of the tableau); swdg_step_record_slot / swdg_step_vjp_slot are
+ * swdg_step_record / swdg_step_vjp on slot `slot` (the plain calls use slot
+ * 0).  SWDG_EINVAL for a slot out of range, SWDG_ESTATE for an empty one. */
+int swdg_adjoint_slots(swdg_ctx* ctx, int n_slots);
+int swdg_step_record_slot(swdg_ctx* ctx, int slot, double dt, double* t_inout);
+int swdg_step_vjp_slot(swdg_ctx* ctx, int slot, const double* zeta_b, const double* qx_b,
+                       const double* qy_b, const double* c_b, double* zeta_b_out,
+                       double* qx_b_out, double* qy_b_out, double* c_b_out, double* manning_b,
+                       double* delta_b, int where);
 /* Per-cell bathymetry offsets delta [n] (host or device per where; NULL = 0):
  * every depth of cell K (its pixels in mode S -- rounded to the raster's
  * precision --, its sampled depths in mode P) becomes the uploaded depth +

@@ -11,7 +11,8 @@ per cell: every depth of cell K deepened by delta_K) and the start state are
 CUDA float64 tensors.  The forward run keeps the state every
 ``checkpoint_every`` steps and the time step of every step (the CFL step,
 ``dt < 0``, or a fixed one); the backward pass re-runs each block of steps
-from its checkpoint, then records and pulls back its steps in reverse order.
+from its checkpoint once, keeping a record of every step of the block, then
+pulls the steps back in reverse order from their records.
 The time steps and every discrete decision of the forward run are held fixed
 in the adjoint (the derivative along the forward's path).  All arithmetic
 runs in the library's kernels; this module only orders the calls.
@@ -69,20 +70,15 @@ class _Solve(torch.autograd.Function):
         db = torch.zeros(ctx.n, dtype=torch.float64, device=dev)
         ctx.set_manning(manning.contiguous())
         ctx.set_bathymetry_offset(delta.contiguous())
+        ctx.adjoint_slots(min(spec.every, spec.nsteps))
         for i0 in sorted(ckpt, reverse=True):
             i1 = min(i0 + spec.every, spec.nsteps)
             state, t = ckpt[i0]
             ctx.set_state(*state)
-            starts = []
-            for i in range(i0, i1):
-                starts.append((ctx.get_state(_empty_state(ctx, manning)), t))
-                if i + 1 < i1:
-                    t = ctx.step(1, dts[i], t)
+            for i in range(i0, i1):  # re-run the block, recording every step
+                t = ctx.step_record(dts[i], t, slot=i - i0)
             for i in reversed(range(i0, i1)):
-                st, ti = starts[i - i0]
-                ctx.set_state(*st)
-                ctx.step_record(dts[i], ti)
-                r = ctx.step_vjp(ub)
+                r = ctx.step_vjp(ub, slot=i - i0)
                 ub = [r["zeta"], r["qx"], r["qy"], r["c"]]
                 nb += r["manning"]
                 db += r["delta"]

@@ -10,8 +10,8 @@
 // parts are the transposes of the forward contractions (interpolation <->
 // test integration, trace <-> lift); the pointwise parts (velocity, friction,
 // reconstruction, Rusanov flux) are differentiated by forward-mode dual
-// numbers through the same templates the forward residual runs, one input
-// direction per pass.  The sub-grid operator enters through V and its exact
+// numbers through the same templates the forward residual runs, every input
+// direction of a point carried in one evaluation.  The sub-grid operator enters through V and its exact
 // derivative A = dV/d(eta) = dV/d(delta).
 //
 // Derivative conventions at the kinks: max(x, 0) -> [x > 0] (Eq. mask); the
@@ -61,6 +61,105 @@ __device__ __forceinline__ D1 fabs(D1 a) {
 __device__ __forceinline__ D1 fmax(D1 a, D1 b) { return a.v >= b.v ? a : b; }
 __device__ __forceinline__ D1 fmin(D1 a, D1 b) { return a.v <= b.v ? a : b; }
 
+// value and W directional derivatives (all directions in one evaluation)
+template <int W>
+struct DN {
+    double v, d[W];
+    __device__ __forceinline__ DN() : v(0.0) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) d[i] = 0.0;
+    }
+    __device__ __forceinline__ DN(double x) : v(x) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) d[i] = 0.0;
+    }
+    // x with unit derivative along direction dir
+    __device__ __forceinline__ static DN seed(double x, int dir) {
+        DN r(x);
+#pragma unroll
+        for (int i = 0; i < W; ++i) r.d[i] = (i == dir) ? 1.0 : 0.0;
+        return r;
+    }
+};
+template <int W>
+__device__ __forceinline__ DN<W> operator+(const DN<W>& a, const DN<W>& b) {
+    DN<W> r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int i = 0; i < W; ++i) r.d[i] = a.d[i] + b.d[i];
+    return r;
+}
+template <int W>
+__device__ __forceinline__ DN<W> operator-(const DN<W>& a, const DN<W>& b) {
+    DN<W> r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int i = 0; i < W; ++i) r.d[i] = a.d[i] - b.d[i];
+    return r;
+}
+template <int W>
+__device__ __forceinline__ DN<W> operator-(const DN<W>& a) {
+    DN<W> r;
+    r.v = -a.v;
+#pragma unroll
+    for (int i = 0; i < W; ++i) r.d[i] = -a.d[i];
+    return r;
+}
+template <int W>
+__device__ __forceinline__ DN<W> operator*(const DN<W>& a, const DN<W>& b) {
+    DN<W> r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int i = 0; i < W; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+    return r;
+}
+template <int W>
+__device__ __forceinline__ DN<W> operator/(const DN<W>& a, const DN<W>& b) {
+    DN<W> r;
+    r.v = a.v / b.v;
+    const double ib = 1.0 / b.v;
+#pragma unroll
+    for (int i = 0; i < W; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+    return r;
+}
+template <int W>
+__device__ __forceinline__ DN<W>& operator+=(DN<W>& a, const DN<W>& b) { return a = a + b; }
+template <int W>
+__device__ __forceinline__ bool operator<(const DN<W>& a, const DN<W>& b) { return a.v < b.v; }
+template <int W>
+__device__ __forceinline__ bool operator<=(const DN<W>& a, const DN<W>& b) { return a.v <= b.v; }
+template <int W>
+__device__ __forceinline__ bool operator>(const DN<W>& a, const DN<W>& b) { return a.v > b.v; }
+template <int W>
+__device__ __forceinline__ bool operator>=(const DN<W>& a, const DN<W>& b) { return a.v >= b.v; }
+template <int W>
+__device__ __forceinline__ bool operator==(const DN<W>& a, const DN<W>& b) { return a.v == b.v; }
+template <int W>
+__device__ __forceinline__ DN<W> scale_d(double v, const DN<W>& a, double f) {
+    DN<W> r(v);
+#pragma unroll
+    for (int i = 0; i < W; ++i) r.d[i] = a.d[i] * f;
+    return r;
+}
+template <int W>
+__device__ __forceinline__ DN<W> sqrt(const DN<W>& a) {
+    const double s = ::sqrt(a.v);
+    return scale_d(s, a, a.v > 0.0 ? 0.5 / s : 0.0);
+}
+template <int W>
+__device__ __forceinline__ DN<W> cbrt(const DN<W>& a) {
+    const double s = ::cbrt(a.v);
+    return scale_d(s, a, a.v != 0.0 ? 1.0 / (3.0 * s * s) : 0.0);
+}
+template <int W>
+__device__ __forceinline__ DN<W> fabs(const DN<W>& a) {
+    return scale_d(::fabs(a.v), a, a.v > 0.0 ? 1.0 : (a.v < 0.0 ? -1.0 : 0.0));
+}
+template <int W>
+__device__ __forceinline__ DN<W> fmax(const DN<W>& a, const DN<W>& b) { return a.v >= b.v ? a : b; }
+template <int W>
+__device__ __forceinline__ DN<W> fmin(const DN<W>& a, const DN<W>& b) { return a.v <= b.v ? a : b; }
+
 } // namespace ad
 
 template <int R>
@@ -94,7 +193,6 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                    double* __restrict__ nbar, double* __restrict__ dbar, int accumulate) {
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
-    using ad::D1;
     constexpr int ND1 = S::ND1, ND = S::ND, NV = S::NV, NVP = S::NVP, NM = S::NM;
     extern __shared__ double smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -185,28 +283,31 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                                    cb[2][1], cb[2][2], cb[2][0],               // Gy x, y, v
                                    cb[4][0], cb[5][0]};                        // Lx, Ly
             double xb[8];
-            // input directions: 0 z, 1 z_xi, 2 z_eta, 3 qx, 4 qy, 5 c, 6 delta, 7 n
-#pragma unroll 1
-            for (int dir = 0; dir < 8; ++dir) {
-                const D1 zz(z, dir == 0 ? 1.0 : 0.0);
-                const D1 zx = D1(zxd, dir == 1 ? 1.0 : 0.0) * D1(ihx);
-                const D1 zy = D1(zyd, dir == 2 ? 1.0 : 0.0) * D1(ihy);
-                const D1 vqx(qx, dir == 3 ? 1.0 : 0.0), vqy(qy, dir == 4 ? 1.0 : 0.0);
-                const D1 vc(c, dir == 5 ? 1.0 : 0.0);
-                const D1 h(V, A * (zz.d + (dir == 6 ? 1.0 : 0.0)));
-                const D1 nn(man, dir == 7 ? 1.0 : 0.0);
-                const D1 fv = vel_factor<D1>(h, D1(eps));
-                const D1 ux = fv * vqx, uy = fv * vqy;
-                const D1 gam = gamma_manning<D1>(nn, h, vqx, vqy, D1(g), D1(eps));
-                const D1 W(w), wx(w * ihx), wy(w * ihy), gg(g);
-                const D1 X[12] = {wx * vqx, wy * vqy, wx * vc * vqx, wy * vc * vqy,
+            {
+                // input directions: 0 z, 1 z_xi, 2 z_eta, 3 qx, 4 qy, 5 c, 6 delta, 7 n
+                using DV = ad::DN<8>;
+                const DV zx = DV::seed(zxd, 1) * DV(ihx);
+                const DV zy = DV::seed(zyd, 2) * DV(ihy);
+                const DV vqx = DV::seed(qx, 3), vqy = DV::seed(qy, 4), vc = DV::seed(c, 5);
+                DV h(V);
+                h.d[0] = A;
+                h.d[6] = A;
+                const DV nn = DV::seed(man, 7);
+                const DV fv = vel_factor<DV>(h, DV(eps));
+                const DV ux = fv * vqx, uy = fv * vqy;
+                const DV gam = gamma_manning<DV>(nn, h, vqx, vqy, DV(g), DV(eps));
+                const DV W(w), wx(w * ihx), wy(w * ihy), gg(g);
+                const DV X[12] = {wx * vqx, wy * vqy, wx * vc * vqx, wy * vc * vqy,
                                   wx * vqx * ux, wy * vqx * uy, -(W * gg * h * zx),
                                   wx * vqy * ux, wy * vqy * uy, -(W * gg * h * zy),
                                   -(W * gam * vqx), -(W * gam * vqy)};
-                double s = 0.0;
 #pragma unroll
-                for (int o = 0; o < 12; ++o) s += Xb[o] * X[o].d;
-                xb[dir] = s;
+                for (int dir = 0; dir < 8; ++dir) {
+                    double s_ = 0.0;
+#pragma unroll
+                    for (int o = 0; o < 12; ++o) s_ += Xb[o] * X[o].d[dir];
+                    xb[dir] = s_;
+                }
             }
             for (int q = 0; q < 6; ++q) xv[q * NVP + p] = xb[q];
             dsum += xb[6];
@@ -267,25 +368,29 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                 nb_VA(tp[0], hp, Ap);
                 nb_VA(tm[0], Vnm, Anm);
                 own_VA(tp[0], Vop, Aop);
-#pragma unroll 1
-                for (int dir = 0; dir < 5; ++dir) {
+                {
                     // directions of the own side: 0 zeta, 1 qx, 2 qy, 3 c, 4 delta
-                    const double dz = dir == 0 ? 1.0 : 0.0, dd = dir == 4 ? 1.0 : 0.0;
-                    const D1 qxm(tm[1], dir == 1 ? 1.0 : 0.0), qym(tm[2], dir == 2 ? 1.0 : 0.0);
-                    const D1 cmv(tm[3], dir == 3 ? 1.0 : 0.0);
-                    const D1 hmD(hm, Am * (dz + dd));         // own operator at own zeta
-                    const D1 vnmD(Vnm, Anm * dz);              // neighbour's operator at own zeta
-                    const D1 vopD(Vop, Aop * dd);              // own operator at neighbour's zeta
-                    const D1 hpD(hp);
-                    const D1 hsm = ad::fmin(hmD, vnmD), hsp = ad::fmin(hpD, vopD);
-                    const D1 qxp(tp[1]), qyp(tp[2]), cpv(tp[3]);
-                    D1 oo[4], on[4];
-                    side_flux<D1>(qxm, qym, cmv, hmD, hsm, qxp, qyp, cpv, hpD, hsp, nx, ny, g, eps, oo);
-                    side_flux<D1>(qxp, qyp, cpv, hpD, hsp, qxm, qym, cmv, hmD, hsm, -nx, -ny, g, eps, on);
-                    double s = 0.0;
+                    using DF = ad::DN<5>;
+                    const DF qxm = DF::seed(tm[1], 1), qym = DF::seed(tm[2], 2);
+                    const DF cmv = DF::seed(tm[3], 3);
+                    DF hmD(hm), vnmD(Vnm), vopD(Vop);
+                    hmD.d[0] = Am;   // own operator at own zeta
+                    hmD.d[4] = Am;
+                    vnmD.d[0] = Anm; // neighbour's operator at own zeta
+                    vopD.d[4] = Aop; // own operator at neighbour's zeta
+                    const DF hpD(hp);
+                    const DF hsm = ad::fmin(hmD, vnmD), hsp = ad::fmin(hpD, vopD);
+                    const DF qxp(tp[1]), qyp(tp[2]), cpv(tp[3]);
+                    DF oo[4], on[4];
+                    side_flux<DF>(qxm, qym, cmv, hmD, hsm, qxp, qyp, cpv, hpD, hsp, nx, ny, g, eps, oo);
+                    side_flux<DF>(qxp, qyp, cpv, hpD, hsp, qxm, qym, cmv, hmD, hsm, -nx, -ny, g, eps, on);
 #pragma unroll
-                    for (int cf = 0; cf < 4; ++cf) s += ym[cf] * oo[cf].d + yp[cf] * on[cf].d;
-                    xb[dir] = s;
+                    for (int dir = 0; dir < 5; ++dir) {
+                        double s_ = 0.0;
+#pragma unroll
+                        for (int cf = 0; cf < 4; ++cf) s_ += ym[cf] * oo[cf].d[dir] + yp[cf] * on[cf].d[dir];
+                        xb[dir] = s_;
+                    }
                 }
             } else {
                 const int tag = -1 - s0;
@@ -300,26 +405,31 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                     zt = amp * sin(2.0 * M_PI * t / per + ph);
                     own_VA(zt, Vt, At);
                 }
-#pragma unroll 1
-                for (int dir = 0; dir < 5; ++dir) {
-                    const double dz = dir == 0 ? 1.0 : 0.0, dd = dir == 4 ? 1.0 : 0.0;
-                    const D1 qxm(tm[1], dir == 1 ? 1.0 : 0.0), qym(tm[2], dir == 2 ? 1.0 : 0.0);
-                    const D1 cmv(tm[3], dir == 3 ? 1.0 : 0.0);
-                    const D1 hmD(hm, Am * (dz + dd));
-                    D1 qxp = qxm, qyp = qym, hpD = hmD;
+                {
+                    using DF = ad::DN<5>;
+                    const DF qxm = DF::seed(tm[1], 1), qym = DF::seed(tm[2], 2);
+                    const DF cmv = DF::seed(tm[3], 3);
+                    DF hmD(hm);
+                    hmD.d[0] = Am;
+                    hmD.d[4] = Am;
+                    DF qxp = qxm, qyp = qym, hpD = hmD;
                     if (tide) {
-                        hpD = D1(Vt, At * dd); // ghost elevation fixed, same operator
+                        hpD = DF(Vt); // ghost elevation fixed, same operator
+                        hpD.d[4] = At;
                     } else {
-                        const D1 qn = qxm * D1(nx) + qym * D1(ny);
-                        qxp = qxm - D1(2.0) * qn * D1(nx);
-                        qyp = qym - D1(2.0) * qn * D1(ny);
+                        const DF qn = qxm * DF(nx) + qym * DF(ny);
+                        qxp = qxm - DF(2.0) * qn * DF(nx);
+                        qyp = qym - DF(2.0) * qn * DF(ny);
                     }
-                    D1 oo[4];
-                    side_flux<D1>(qxm, qym, cmv, hmD, hmD, qxp, qyp, cmv, hpD, hpD, nx, ny, g, eps, oo);
-                    double s = 0.0;
+                    DF oo[4];
+                    side_flux<DF>(qxm, qym, cmv, hmD, hmD, qxp, qyp, cmv, hpD, hpD, nx, ny, g, eps, oo);
 #pragma unroll
-                    for (int cf = 0; cf < 4; ++cf) s += ym[cf] * oo[cf].d;
-                    xb[dir] = s;
+                    for (int dir = 0; dir < 5; ++dir) {
+                        double s_ = 0.0;
+#pragma unroll
+                        for (int cf = 0; cf < 4; ++cf) s_ += ym[cf] * oo[cf].d[dir];
+                        xb[dir] = s_;
+                    }
                 }
             }
 #pragma unroll
@@ -450,12 +560,11 @@ constexpr int stage_vjp_smem() {
 }
 
 template <int R, typename Pix, int MODE>
-__global__ void __launch_bounds__(32 * MAXWPB)
+__global__ void __maxnreg__(128)
     k_stage_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
                 const StageVjpArgs a) {
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
-    using ad::D1;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
     extern __shared__ double smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -696,15 +805,11 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                 double V, A;
                 ST::VA(d, tb, k, SET_MOM, p % NG, p / NG, g3[p], V, A);
                 const double qx = g3[NGP + p], qy = g3[2 * NGP + p], gbp = gb[p];
-                double dg[4];
-#pragma unroll 1
-                for (int dir = 0; dir < 4; ++dir) {
-                    const D1 r = gamma_manning<D1>(D1(man, dir == 3 ? 1.0 : 0.0),
-                                                   D1(V, dir == 0 ? 1.0 : 0.0),
-                                                   D1(qx, dir == 1 ? 1.0 : 0.0),
-                                                   D1(qy, dir == 2 ? 1.0 : 0.0), D1(g), D1(eps));
-                    dg[dir] = r.d;
-                }
+                // directions: 0 h, 1 qx, 2 qy, 3 n
+                using DG = ad::DN<4>;
+                const DG r = gamma_manning<DG>(DG::seed(man, 3), DG::seed(V, 0), DG::seed(qx, 1),
+                                               DG::seed(qy, 2), DG(g), DG(eps));
+                const double* dg = r.d;
                 g3[p] = gbp * dg[0] * A;
                 g3[NGP + p] = gbp * dg[1];
                 g3[2 * NGP + p] = gbp * dg[2];
@@ -753,7 +858,7 @@ constexpr int begin_vjp_smem() {
 }
 
 template <int R, typename Pix, int MODE>
-__global__ void __launch_bounds__(32 * MAXWPB)
+__global__ void __maxnreg__(96)
     k_begin_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
                 const BeginVjpArgs a) {
     using S = Sz<R>;

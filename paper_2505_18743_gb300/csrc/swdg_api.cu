@@ -53,12 +53,17 @@ struct swdg_ctx {
     double* adj = nullptr;      // adjoint scratch: 6 + 4 fields of [n][nd], then 2 [n]
     // step adjoint workspace (swdg_step_record / swdg_step_vjp)
     struct AdjWs {
-        double *vpre = nullptr, *vtil = nullptr, *ubs = nullptr, *rbar = nullptr, *llb = nullptr,
-               *HNb = nullptr, *CNb = nullptr, *nbar = nullptr, *dbar = nullptr, *vb = nullptr,
-               *ubpre = nullptr;
-        uint8_t *cmtil = nullptr, *flags = nullptr;
-        double t0 = 0.0, dt = 0.0;
-        bool valid = false;
+        // per record slot: v^n, v~^n, the stage states 1..s-1 and v^{n+1} ([s+2][4][n][nd]),
+        // the masks of v~^n, the stages and v^{n+1} ([s+1][n]), the flags after the degree
+        // switch, each stage and the final combination ([s+1][n])
+        int nslots = 0;
+        double* rec_u = nullptr;
+        uint8_t *rec_cm = nullptr, *rec_flags = nullptr;
+        std::vector<double> t0, dt;
+        std::vector<char> valid;
+        // adjoint scratch
+        double *ubs = nullptr, *rbar = nullptr, *llb = nullptr, *HNb = nullptr, *CNb = nullptr,
+               *nbar = nullptr, *dbar = nullptr, *vb = nullptr, *ubpre = nullptr;
     } ws;
     double* mdiag = nullptr;    // [nmemb][4]
     std::vector<Bc> bch;
@@ -688,11 +693,11 @@ static void free_mesh(swdg_ctx* c) {
     cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->diag); cudaFree(c->finfo);
     cudaFree(c->adj);
     c->adj = nullptr;
-    for (double* p : {c->ws.vpre, c->ws.vtil, c->ws.ubs, c->ws.rbar, c->ws.llb, c->ws.HNb, c->ws.CNb,
+    for (double* p : {c->ws.rec_u, c->ws.ubs, c->ws.rbar, c->ws.llb, c->ws.HNb, c->ws.CNb,
                       c->ws.nbar, c->ws.dbar, c->ws.vb, c->ws.ubpre})
         cudaFree(p);
-    cudaFree(c->ws.cmtil);
-    cudaFree(c->ws.flags);
+    cudaFree(c->ws.rec_cm);
+    cudaFree(c->ws.rec_flags);
     c->ws = swdg_ctx::AdjWs{};
     c->x0y0 = c->hxhy = c->ihxhy = c->manning = c->U = c->res = c->llin = c->HN = c->CN = c->HNbar =
         c->CNbar = c->diag = nullptr;
@@ -1230,28 +1235,48 @@ int swdg_cfl_dt(swdg_ctx* ctx, double t, double* dt) {
 
 // the kernels of one time step, in stream order; with ev != nullptr an event
 // pair brackets every launch (slot layout of swdg_step_profile)
-static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr, bool rec = false) {
+// views of record slot `slot` (see AdjWs): state k = 0 v^n, 1 v~^n, 1 + l stage l, s + 1 v^{n+1};
+// masks / flags k = 0 v~^n (degree switch), l stage l, s final
+static double* rec_state(swdg_ctx* c, int slot, int k) {
+    const size_t f4 = 4 * (size_t)c->n * c->nd;
+    return c->ws.rec_u + ((size_t)slot * (c->d.s + 2) + k) * f4;
+}
+static uint8_t* rec_mask(swdg_ctx* c, int slot, int k) {
+    return c->ws.rec_cm + ((size_t)slot * (c->d.s + 1) + k) * (size_t)c->n;
+}
+static uint8_t* rec_flag(swdg_ctx* c, int slot, int k) {
+    return c->ws.rec_flags + ((size_t)slot * (c->d.s + 1) + k) * (size_t)c->n;
+}
+
+static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr, int rec_slot = -1) {
     const Dev& d = ctx->d;
     const int s = d.s;
     const int64_t n = ctx->n;
     const size_t ub = 4 * (size_t)n * ctx->nd * sizeof(double);
+    const bool rec = rec_slot >= 0;
     auto mark = [&](int slot, int which) {
         if (ev) cudaEventRecord(ev[slot][which], ctx->st);
     };
     // recording for the adjoint: v^n, v~^n and its masks, the flags after the
     // degree switch and after every stage update
-    auto keep_flags = [&](int slot) {
-        if (rec) cudaMemcpyAsync(ctx->ws.flags + (size_t)slot * n, ctx->flag, n,
-                                 cudaMemcpyDeviceToDevice, ctx->st);
+    // keep the state of buffer `buf` as record state k with its masks (mask slot km)
+    auto keep = [&](int buf, int k, int km) {
+        if (!rec) return;
+        cudaMemcpyAsync(rec_state(ctx, rec_slot, k), ctx->U + (size_t)buf * 4 * n * ctx->nd, ub,
+                        cudaMemcpyDeviceToDevice, ctx->st);
+        if (km >= 0)
+            cudaMemcpyAsync(rec_mask(ctx, rec_slot, km), ctx->cmask + (size_t)buf * n, n,
+                            cudaMemcpyDeviceToDevice, ctx->st);
     };
-    if (rec) cudaMemcpyAsync(ctx->ws.vpre, ctx->U, ub, cudaMemcpyDeviceToDevice, ctx->st);
+    auto keep_flags = [&](int k) {
+        if (rec) cudaMemcpyAsync(rec_flag(ctx, rec_slot, k), ctx->flag, n, cudaMemcpyDeviceToDevice,
+                                 ctx->st);
+    };
+    keep(0, 0, -1);
     mark(0, 0);
     ctx->L.step_begin(d, ctx->tb, 1, ctx->shp[KK_BEGIN], ctx->st);
     mark(0, 1);
-    if (rec) {
-        cudaMemcpyAsync(ctx->ws.vtil, ctx->U, ub, cudaMemcpyDeviceToDevice, ctx->st);
-        cudaMemcpyAsync(ctx->ws.cmtil, ctx->cmask, n, cudaMemcpyDeviceToDevice, ctx->st);
-    }
+    keep(0, 1, 0);
     keep_flags(0);
     for (int l = 0; l < s; ++l) {
         if (l > 0) {
@@ -1270,6 +1295,7 @@ static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr, bool rec 
             mark(4 + l, 0);
             ctx->L.stage(d, ctx->tb, sa, ctx->shp[KK_STAGE], ctx->st);
             mark(4 + l, 1);
+            keep(l, 1 + l, l);
             keep_flags(l);
         }
         mark(1 + l, 0);
@@ -1291,6 +1317,7 @@ static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr, bool rec 
     mark(8, 0);
     ctx->L.stage(d, ctx->tb, sa, ctx->shp[KK_STAGE], ctx->st);
     mark(8, 1);
+    keep(0, s + 1, s);
     keep_flags(s);
     CK(cudaGetLastError());
     return SWDG_OK;
@@ -1486,62 +1513,99 @@ static int adjoint_ready(swdg_ctx* ctx, const char* who) {
     return SWDG_OK;
 }
 
-int swdg_step_record(swdg_ctx* ctx, double dt, double* t_inout) {
+static int alloc_scratch(swdg_ctx* ctx) {
+    auto& w = ctx->ws;
+    if (w.ubs) return SWDG_OK;
+    const int64_t n = ctx->n;
+    const size_t f = (size_t)n * ctx->nd;
+    CK(cudaMalloc(&w.ubs, (size_t)MXS * 4 * f * sizeof(double)));
+    CK(cudaMalloc(&w.rbar, (size_t)MXS * 6 * f * sizeof(double)));
+    CK(cudaMalloc(&w.llb, 2 * f * sizeof(double)));
+    CK(cudaMalloc(&w.HNb, f * sizeof(double)));
+    CK(cudaMalloc(&w.CNb, f * sizeof(double)));
+    CK(cudaMalloc(&w.nbar, n * sizeof(double)));
+    CK(cudaMalloc(&w.dbar, n * sizeof(double)));
+    CK(cudaMalloc(&w.vb, 4 * f * sizeof(double)));
+    CK(cudaMalloc(&w.ubpre, 4 * f * sizeof(double)));
+    return SWDG_OK;
+}
+
+int swdg_adjoint_slots(swdg_ctx* ctx, int nslots) {
+    if (!ctx) return SWDG_EINVAL;
+    int rc = adjoint_ready(ctx, "adjoint_slots");
+    if (rc) return rc;
+    if (nslots < 1 || nslots > 4096) return fail(ctx, SWDG_EINVAL, "adjoint_slots: 1..4096 slots");
+    auto& w = ctx->ws;
+    if (nslots == w.nslots) return SWDG_OK;
+    cudaFree(w.rec_u);
+    cudaFree(w.rec_cm);
+    cudaFree(w.rec_flags);
+    w.rec_u = nullptr;
+    w.rec_cm = w.rec_flags = nullptr;
+    w.nslots = 0;
+    const int s = ctx->d.s;
+    const size_t f4 = 4 * (size_t)ctx->n * ctx->nd;
+    CK(cudaMalloc(&w.rec_u, (size_t)nslots * (s + 2) * f4 * sizeof(double)));
+    CK(cudaMalloc(&w.rec_cm, (size_t)nslots * (s + 1) * ctx->n));
+    CK(cudaMalloc(&w.rec_flags, (size_t)nslots * (s + 1) * ctx->n));
+    w.nslots = nslots;
+    w.t0.assign(nslots, 0.0);
+    w.dt.assign(nslots, 0.0);
+    w.valid.assign(nslots, 0);
+    return alloc_scratch(ctx);
+}
+
+int swdg_step_record_slot(swdg_ctx* ctx, int slot, double dt, double* t_inout) {
     if (!ctx) return SWDG_EINVAL;
     int rc = adjoint_ready(ctx, "step_record");
     if (rc) return rc;
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, SWDG_EINVAL, "step_record: dt > 0 required");
-    const int64_t n = ctx->n;
-    const int s = ctx->d.s;
-    const size_t f = (size_t)n * ctx->nd;
     auto& w = ctx->ws;
-    if (!w.vpre) {
-        CK(cudaMalloc(&w.vpre, 4 * f * sizeof(double)));
-        CK(cudaMalloc(&w.vtil, 4 * f * sizeof(double)));
-        CK(cudaMalloc(&w.ubs, (size_t)MXS * 4 * f * sizeof(double)));
-        CK(cudaMalloc(&w.rbar, (size_t)MXS * 6 * f * sizeof(double)));
-        CK(cudaMalloc(&w.llb, 2 * f * sizeof(double)));
-        CK(cudaMalloc(&w.HNb, f * sizeof(double)));
-        CK(cudaMalloc(&w.CNb, f * sizeof(double)));
-        CK(cudaMalloc(&w.nbar, n * sizeof(double)));
-        CK(cudaMalloc(&w.dbar, n * sizeof(double)));
-        CK(cudaMalloc(&w.vb, 4 * f * sizeof(double)));
-        CK(cudaMalloc(&w.ubpre, 4 * f * sizeof(double)));
-        CK(cudaMalloc(&w.cmtil, n));
-        CK(cudaMalloc(&w.flags, (size_t)(MXS + 1) * n));
-    }
+    if (slot < 0 || slot >= w.nslots) return fail(ctx, SWDG_EINVAL, "step_record: bad slot %d", slot);
     std::vector<Member> mh;
     rc = read_clocks(ctx, mh);
     if (rc) return rc;
     const double t0 = t_inout ? *t_inout : mh[0].t;
     rc = put_time(ctx, t0, dt);
     if (rc) return rc;
-    rc = enqueue_step(ctx, nullptr, true);
+    rc = enqueue_step(ctx, nullptr, slot);
     if (rc) return rc;
+    CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ctx->sc_host, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    (void)s;
-    w.t0 = t0;
-    w.dt = dt;
-    w.valid = true;
+    w.t0[slot] = t0;
+    w.dt[slot] = dt;
+    w.valid[slot] = 1;
     if (t_inout) *t_inout = ctx->sc_host->m0.t;
     if (ctx->sc_host->status & ST_NAN) return fail(ctx, SWDG_ENAN, "step_record: non-finite state");
     return SWDG_OK;
 }
 
-int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const double* qy_b,
-                  const double* c_b, double* zeta_b_out, double* qx_b_out, double* qy_b_out,
-                  double* c_b_out, double* manning_b, double* delta_b, int where) {
+int swdg_step_record(swdg_ctx* ctx, double dt, double* t_inout) {
+    if (!ctx) return SWDG_EINVAL;
+    if (ctx->ws.nslots < 1) {
+        int rc = swdg_adjoint_slots(ctx, 1);
+        if (rc) return rc;
+    }
+    return swdg_step_record_slot(ctx, 0, dt, t_inout);
+}
+
+int swdg_step_vjp_slot(swdg_ctx* ctx, int slot, const double* zeta_b, const double* qx_b,
+                       const double* qy_b, const double* c_b, double* zeta_b_out, double* qx_b_out,
+                       double* qy_b_out, double* c_b_out, double* manning_b, double* delta_b,
+                       int where) {
     if (!ctx) return SWDG_EINVAL;
     int rc = adjoint_ready(ctx, "step_vjp");
     if (rc) return rc;
     auto& w = ctx->ws;
-    if (!w.valid) return fail(ctx, SWDG_ESTATE, "step_vjp: no recorded step (swdg_step_record)");
+    if (slot < 0 || slot >= w.nslots || !w.valid[slot])
+        return fail(ctx, SWDG_ESTATE, "step_vjp: no recorded step in slot %d (swdg_step_record)", slot);
     if (where != SWDG_HOST && where != SWDG_DEVICE) return fail(ctx, SWDG_EINVAL, "step_vjp: bad where");
     const Dev& d = ctx->d;
     const int64_t n = ctx->n;
     const int s = d.s;
     const size_t f = (size_t)n * ctx->nd, fb = f * sizeof(double);
+    const double t0 = w.t0[slot], dt = w.dt[slot];
     const cudaMemcpyKind in = where == SWDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind out = where == SWDG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     const double* src[4] = {zeta_b, qx_b, qy_b, c_b};
@@ -1557,25 +1621,28 @@ int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const
     CK(cudaMemsetAsync(w.nbar, 0, n * sizeof(double), ctx->st));
     CK(cudaMemsetAsync(w.dbar, 0, n * sizeof(double), ctx->st));
     const Shape shp{grid_for(n), WPB};
-    auto ubuf = [&](int l) { return ctx->U + (size_t)l * 4 * f; };
-    auto cbuf = [&](int l) { return ctx->cmask + (size_t)l * n; };
+    // stage l state and masks of the recorded step (l = 0: v~^n)
+    auto ust = [&](int l) { return rec_state(ctx, slot, 1 + l); };
+    auto cst = [&](int l) { return rec_mask(ctx, slot, l); };
+    const double* vtil = ust(0);
+    const uint8_t* cmtil = cst(0);
     const bool imp = d.at[s - 1][s - 1] != 0.0;
     // final combination (weights b, b~, no implicit diagonal)
     StageVjpArgs a{};
-    a.un = w.vtil;
-    a.cmn = w.cmtil;
+    a.un = vtil;
+    a.cmn = cmtil;
     a.rbar = w.rbar;
     a.HNb = w.HNb;
     a.CNb = w.CNb;
     a.ubn = w.ubs;
     a.nbar = w.nbar;
     a.dbar = w.dbar;
-    a.dt = w.dt;
-    a.uo = ubuf(0);
-    a.cmo = cbuf(0);
-    a.up = s > 1 ? ubuf(s - 1) : w.vtil;
-    a.cmp = s > 1 ? cbuf(s - 1) : w.cmtil;
-    a.flag = w.flags + (size_t)s * n;
+    a.dt = dt;
+    a.uo = rec_state(ctx, slot, s + 1);
+    a.cmo = rec_mask(ctx, slot, s);
+    a.up = ust(s - 1);
+    a.cmp = cst(s - 1);
+    a.flag = rec_flag(ctx, slot, s);
     a.vb = w.vb;
     a.llb_in = nullptr;
     a.llb_out = w.llb;
@@ -1592,20 +1659,18 @@ int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const
     CK(cudaGetLastError());
     for (int l = s - 1; l >= 0; --l) {
         // residual of stage l at t^n + c_l dt
-        rc = put_clocks(ctx, w.t0 + d.c[l] * w.dt, 0);
+        rc = put_clocks(ctx, t0 + d.c[l] * dt, 0);
         if (rc) return rc;
-        const double* ul = l == 0 ? w.vtil : ubuf(l);
-        const uint8_t* cl = l == 0 ? w.cmtil : cbuf(l);
-        ctx->L.residual_vjp(d, ctx->tb, ul, cl, w.rbar + (size_t)l * 6 * f,
+        ctx->L.residual_vjp(d, ctx->tb, ust(l), cst(l), w.rbar + (size_t)l * 6 * f,
                             w.ubs + (size_t)l * 4 * f, w.nbar, w.dbar, 1, shp, ctx->st);
         CK(cudaGetLastError());
         if (l == 0) break;
         StageVjpArgs b = a;
-        b.uo = ubuf(l);
-        b.cmo = cbuf(l);
-        b.up = l - 1 == 0 ? w.vtil : ubuf(l - 1);
-        b.cmp = l - 1 == 0 ? w.cmtil : cbuf(l - 1);
-        b.flag = w.flags + (size_t)l * n;
+        b.uo = ust(l);
+        b.cmo = cst(l);
+        b.up = ust(l - 1);
+        b.cmp = cst(l - 1);
+        b.flag = rec_flag(ctx, slot, l);
         b.vb = w.ubs + (size_t)l * 4 * f;
         b.make_llin = (l == s - 1 && d.at[l][l] != 0.0) ? 1 : 0;
         b.llb_in = b.make_llin ? w.llb : nullptr;
@@ -1622,10 +1687,10 @@ int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const
         CK(cudaGetLastError());
     }
     BeginVjpArgs bg{};
-    bg.upre = w.vpre;
-    bg.un = w.vtil;
-    bg.cmn = w.cmtil;
-    bg.flag0 = w.flags;
+    bg.upre = rec_state(ctx, slot, 0);
+    bg.un = vtil;
+    bg.cmn = cmtil;
+    bg.flag0 = rec_flag(ctx, slot, 0);
     bg.HNb = w.HNb;
     bg.CNb = w.CNb;
     bg.ubn = w.ubs;
@@ -1633,7 +1698,7 @@ int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const
     bg.dbar = w.dbar;
     ctx->L.begin_vjp(d, ctx->tb, bg, shp, ctx->st);
     CK(cudaGetLastError());
-    rc = put_clocks(ctx, w.t0 + w.dt, 0);
+    rc = put_clocks(ctx, t0 + dt, 0);
     if (rc) return rc;
     double* dst[4] = {zeta_b_out, qx_b_out, qy_b_out, c_b_out};
     for (int i = 0; i < 4; ++i)
@@ -1642,6 +1707,15 @@ int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const
     if (delta_b) CK(cudaMemcpyAsync(delta_b, w.dbar, n * sizeof(double), out, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return SWDG_OK;
+}
+
+int swdg_step_vjp(swdg_ctx* ctx, const double* zeta_b, const double* qx_b, const double* qy_b,
+                  const double* c_b, double* zeta_b_out, double* qx_b_out, double* qy_b_out,
+                  double* c_b_out, double* manning_b, double* delta_b, int where) {
+    if (!ctx) return SWDG_EINVAL;
+    if (ctx->ws.nslots < 1) return fail(ctx, SWDG_ESTATE, "step_vjp: no recorded step (swdg_step_record)");
+    return swdg_step_vjp_slot(ctx, 0, zeta_b, qx_b, qy_b, c_b, zeta_b_out, qx_b_out, qy_b_out,
+                              c_b_out, manning_b, delta_b, where);
 }
 
 // ---------------------------------------------------------------------------

@@ -75,6 +75,9 @@ SIGNATURES = {
     "swdg_step_record": (_I, [_P, _D, ctypes.POINTER(_D)]),
     "swdg_step_vjp": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
     "swdg_set_bathymetry_offset": (_I, [_P, _P, _I]),
+    "swdg_adjoint_slots": (_I, [_P, _I]),
+    "swdg_step_record_slot": (_I, [_P, _I, _D, ctypes.POINTER(_D)]),
+    "swdg_step_vjp_slot": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
     "swdg_set_members": (_I, [_P, _I, _P]),
     "swdg_upload_bathymetry_members": (_I, [_P, _P, _I, _P, _P]),
     "swdg_set_boundary_member": (_I, [_P, _I, _I, _I, _D, _D, _D]),
@@ -254,13 +257,21 @@ class Context:
         p, where, keep = _buf(delta, np.float64)
         self._ck(load().swdg_set_bathymetry_offset(self.h, p, where))
 
-    def step_record(self, dt, t=None):
+    def adjoint_slots(self, n):
+        """reserve n step records (see swdg_adjoint_slots)"""
+        self._ck(load().swdg_adjoint_slots(self.h, n))
+
+    def step_record(self, dt, t=None, slot=None):
         """one fixed step of size dt, recorded for step_vjp; returns the end time"""
         tt = _D(0.0 if t is None else t)
-        self._ck(load().swdg_step_record(self.h, dt, ctypes.byref(tt) if t is not None else None))
+        pt = ctypes.byref(tt) if t is not None else None
+        if slot is None:
+            self._ck(load().swdg_step_record(self.h, dt, pt))
+        else:
+            self._ck(load().swdg_step_record_slot(self.h, slot, dt, pt))
         return tt.value if t is not None else None
 
-    def step_vjp(self, cot):
+    def step_vjp(self, cot, slot=None):
         """adjoint of the recorded step: cotangent of the state after it (4 arrays
         [n, nd], host numpy or CUDA tensors) -> that of the state before it, the
         Manning coefficients [n] and the bathymetry offsets [n]"""
@@ -269,16 +280,20 @@ class Context:
             t = _torch()
             outs = [t.empty_like(cot[0]) for _ in range(4)] + \
                 [t.empty(self.n, dtype=t.float64, device=cot[0].device) for _ in range(2)]
-            ins = [ctypes.c_void_p(a.contiguous().data_ptr()) for a in cot]
-            self._ck(load().swdg_step_vjp(self.h, *ins,
-                                          *[ctypes.c_void_p(o.data_ptr()) for o in outs],
-                                          SWDG_DEVICE))
+            keep = [a.contiguous() for a in cot]
+            ptrs = [ctypes.c_void_p(a.data_ptr()) for a in keep] + \
+                [ctypes.c_void_p(o.data_ptr()) for o in outs]
+            where = SWDG_DEVICE
         else:
-            ins = [np.ascontiguousarray(a, dtype=np.float64) for a in cot]
+            keep = [np.ascontiguousarray(a, dtype=np.float64) for a in cot]
             outs = [np.empty((self.n, self.nd)) for _ in range(4)] + [np.empty(self.n),
                                                                         np.empty(self.n)]
-            self._ck(load().swdg_step_vjp(self.h, *[a.ctypes.data_as(_P) for a in ins],
-                                          *[o.ctypes.data_as(_P) for o in outs], SWDG_HOST))
+            ptrs = [a.ctypes.data_as(_P) for a in keep] + [o.ctypes.data_as(_P) for o in outs]
+            where = SWDG_HOST
+        if slot is None:
+            self._ck(load().swdg_step_vjp(self.h, *ptrs, where))
+        else:
+            self._ck(load().swdg_step_vjp_slot(self.h, slot, *ptrs, where))
         return dict(zip(("zeta", "qx", "qy", "c", "manning", "delta"), outs))
 
     def cfl_dt(self, t=0.0):
