@@ -71,6 +71,7 @@ def lib():
         L.ora_zb_point.argtypes = [_P, _c_double, _c_double]
         L.ora_face_flux_p.argtypes = [_P, _P, _P]
         L.ora_tableau.argtypes = [_c_int, _P, _P, _P, _P, _P, _P]
+        L.ora_set_tracer_diffusivity.argtypes = [_P, _P]
     return _lib
 
 
@@ -124,6 +125,8 @@ class Oracle:
             o.set_boundary(tag, kind, amp, per, ph)
         if wl.manning is not None:
             o.set_manning(wl.manning)
+        if getattr(wl, "tracer_diffusivity", None) is not None:
+            o.set_tracer_diffusivity(wl.tracer_diffusivity)
         o.set_state(*wl.state())
         return o
 
@@ -135,6 +138,13 @@ class Oracle:
     def set_boundary(self, tag, kind, amp=0.0, period=1.0, phase=0.0):
         if lib().ora_set_boundary(self.h, tag, kind, amp, period, phase):
             raise ValueError(lib().ora_error().decode())
+
+    def set_tracer_diffusivity(self, nu):
+        if nu is None:
+            lib().ora_set_tracer_diffusivity(self.h, None)
+            return
+        a = np.ascontiguousarray(nu, dtype=np.float64)
+        lib().ora_set_tracer_diffusivity(self.h, _ptr(a))
 
     def set_manning(self, n):
         a = np.ascontiguousarray(n, dtype=np.float64)

@@ -189,6 +189,7 @@ struct ora {
     int bc_kind[MAXTAG];
     double bc_amp[MAXTAG], bc_per[MAXTAG], bc_ph[MAXTAG];
     double* manning;
+    double* nu_c; /* tracer numerical diffusivity per cell (Eq. numdiff), NULL: none */
     double* u[4]; /* zeta, qx, qy, c: [n][nd] */
     uint8_t* flag;
     double* zmax; /* per cell: dry-start level (Eq. initial_guess) */
@@ -500,6 +501,7 @@ void ora_destroy(ora* o) {
     if (!o) return;
     free(o->x0); free(o->y0); free(o->hx); free(o->hy); free(o->nbr); free(o->ras);
     free(o->manning);
+    free(o->nu_c);
     for (int f = 0; f < 4; f++) free(o->u[f]);
     free(o->flag); free(o->zmax); free(o->zabs);
     free(o);
@@ -516,6 +518,15 @@ int ora_set_boundary(ora* o, int tag, int kind, double amp, double period, doubl
     o->bc_ph[tag] = phase;
     return 0;
 }
+int ora_set_tracer_diffusivity(ora* o, const double* nu) {
+    free(o->nu_c);
+    o->nu_c = NULL;
+    if (!nu) return 0;
+    o->nu_c = malloc(o->n * sizeof(double));
+    for (int64_t k = 0; k < o->n; k++) o->nu_c[k] = nu[k];
+    return 0;
+}
+
 int ora_set_manning(ora* o, const double* n) {
     for (int64_t k = 0; k < o->n; k++) o->manning[k] = n ? n[k] : 0.0;
     return 0;
@@ -668,13 +679,17 @@ static void cell_residual(const ora* o, int64_t K, double t, double* F, double* 
     for (int ib = 0; ib < o->nv; ib++)
         for (int ia = 0; ia < o->nv; ia++) {
             double xi = o->xv[ia], eta = o->xv[ib], w = o->wv[ia] * o->wv[ib];
-            double z, zx, zy, qx, qy, c;
+            double z, zx, zy, qx, qy, c, cx, cy;
             field_at(o, o->u[0] + K * nd, xi, eta, &z, &zx, &zy);
             field_at(o, o->u[1] + K * nd, xi, eta, &qx, NULL, NULL);
             field_at(o, o->u[2] + K * nd, xi, eta, &qy, NULL, NULL);
-            field_at(o, o->u[3] + K * nd, xi, eta, &c, NULL, NULL);
+            field_at(o, o->u[3] + K * nd, xi, eta, &c, &cx, &cy);
             zx /= hx;
             zy /= hy;
+            cx /= hx;
+            cy /= hy;
+            /* tracer numerical diffusion nu_c h grad c (Eq. numdiff) */
+            double nuh = o->nu_c ? o->nu_c[K] : 0.0;
             site s = cell_site(o, K, o->sv, o->xv, ia, ib);
             double h = site_V(o, &s, z);
             double ux, uy;
@@ -689,6 +704,7 @@ static void cell_residual(const ora* o, int64_t K, double t, double* F, double* 
                 Gx[i] += J * w * (qx * ux * px + qx * uy * py - g * h * zx * ps);
                 Gy[i] += J * w * (qy * ux * px + qy * uy * py - g * h * zy * ps);
                 R[i] += J * w * c * (qx * px + qy * py);
+                if (nuh != 0.0) R[i] -= J * w * nuh * h * (cx * px + cy * py);
                 Lx[i] -= J * w * gam * qx * ps;
                 Ly[i] -= J * w * gam * qy * ps;
             }

@@ -52,6 +52,9 @@ const char* ora_error(void);
 
 int ora_set_boundary(ora* o, int tag, int kind, double amp, double period, double phase);
 int ora_set_manning(ora* o, const double* n_per_cell);
+/* tracer numerical diffusivity nu_c per cell (Eq. numdiff: -sum_K int nu_c h
+ * grad c . grad psi_i added to R); NULL: none (the default) */
+int ora_set_tracer_diffusivity(ora* o, const double* nu);
 int ora_set_state(ora* o, const double* zeta, const double* qx, const double* qy, const double* c);
 int ora_get_state(const ora* o, double* zeta, double* qx, double* qy, double* c);
 int ora_get_flags(const ora* o, uint8_t* flags);

@@ -23,7 +23,9 @@ Definitions (each evaluated directly, no sum factorisation):
     hydro_rec_vars), the non-conservative pressure term (Eq.
     pressure_tumolo), the desingularised velocity (Eq. velocity) and Manning
     friction (Eq. manning);
-  * wall and tidal-elevation ghost states on boundary faces.
+  * wall and tidal-elevation ghost states on boundary faces;
+  * optionally the tracer numerical diffusion -int nu_c h grad c . grad psi_i
+    (Eq. numdiff).
 
 Derivative conventions at the kinks (the reading the adjoint takes):
   * max(x, 0) inside V has derivative [x > 0] (Eq. mask's strict inequality);
@@ -102,7 +104,7 @@ class TorchResidual:
     differentiable function of (zeta, qx, qy, c, manning, delta)."""
 
     def __init__(self, mesh, raster, degree, subgrid_mode=0, g=9.81, eps_vel=0.01,
-                 boundaries=()):
+                 boundaries=(), tracer_diffusivity=None):
         self.r = degree
         self.nd1 = degree + 1
         self.nd = self.nd1 ** 2
@@ -110,6 +112,8 @@ class TorchResidual:
         self.g = g
         self.eps = eps_vel
         self.bc = {tag: (kind, amp, per, ph) for (tag, kind, amp, per, ph) in boundaries}
+        self.nu = None if tracer_diffusivity is None else \
+            torch.tensor(np.asarray(tracer_diffusivity, dtype=np.float64))[:, None]
         n = mesh.n
         self.n = n
         x0, y0 = mesh.x0y0[:, 0], mesh.x0y0[:, 1]
@@ -323,6 +327,9 @@ class TorchResidual:
         Gx = integ(vqx * ux, vqx * uy, -g * h * zx)
         Gy = integ(vqy * ux, vqy * uy, -g * h * zy)
         R = integ(vc * vqx, vc * vqy, None)
+        if self.nu is not None:  # tracer numerical diffusion (Eq. numdiff)
+            cx, cy = (c @ self.Dx.T) / hx, (c @ self.Dy.T) / hy
+            R = R - integ(self.nu * h * cx, self.nu * h * cy, None)
         Lx = integ(None, None, -gam * vqx)
         Ly = integ(None, None, -gam * vqy)
         # ---- face terms

@@ -55,7 +55,8 @@ class TorchStep:
         self.cfg = cfg
         r = cfg["degree"]
         self.res = TorchResidual(wl.mesh, wl.raster, r, cfg["subgrid_mode"], cfg["g"],
-                                 cfg["eps_vel"], wl.boundaries)
+                                 cfg["eps_vel"], wl.boundaries,
+                                 getattr(wl, "tracer_diffusivity", None))
         tr = self.res
         self.n, self.nd = tr.n, tr.nd
         xs, _ = rule(1, r + 1)

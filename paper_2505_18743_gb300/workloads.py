@@ -69,6 +69,7 @@ class Workload:
     subgrid_mode: int = 0  # 0 S, 1 P
     boundaries: list = field(default_factory=list)  # (tag, kind, amp, period, phase)
     manning: np.ndarray | None = None
+    tracer_diffusivity: np.ndarray | None = None  # nu_c per cell (Eq. numdiff), None: none
     steps: int = 100
 
     def config(self, **over):

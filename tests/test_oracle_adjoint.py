@@ -54,7 +54,13 @@ def forest(degree=1):
 
 def torch_res(wl):
     return TorchResidual(wl.mesh, wl.raster, wl.degree, wl.subgrid_mode, wl.g, wl.eps_vel,
-                         wl.boundaries)
+                         wl.boundaries, wl.tracer_diffusivity)
+
+
+def diffusive_beach():
+    wl = beach(2)
+    wl.tracer_diffusivity = np.linspace(0.5, 3.0, wl.mesh.n)
+    return wl
 
 
 def shifted_raster(wl, delta):
@@ -75,13 +81,17 @@ def c_residual(wl, state, manning, delta, t):
     for (tag, kind, amp, per, ph) in wl.boundaries:
         o.set_boundary(tag, kind, amp, per, ph)
     o.set_manning(manning)
+    if wl.tracer_diffusivity is not None:
+        o.set_tracer_diffusivity(wl.tracer_diffusivity)
     o.set_state(*state)
     return o.residual(t)
 
 
-@pytest.mark.parametrize("case", ["basin", "beach_r2", "beach_r3", "beach_P", "forest_r1", "forest_r2"])
+@pytest.mark.parametrize("case", ["basin", "beach_r2", "beach_r3", "beach_P", "forest_r1", "forest_r2",
+                                  "diffusion"])
 def test_torch_residual_matches_the_c_oracle(case):
     wl = {"basin": lambda: W.closed_basin(), "beach_r2": lambda: beach(2),
+          "diffusion": diffusive_beach,
           "beach_r3": lambda: beach(3), "beach_P": lambda: beach(2, mode=1),
           "forest_r1": lambda: forest(1), "forest_r2": lambda: forest(2)}[case]()
     t = 1000.0
@@ -125,6 +135,10 @@ def test_vjp_matches_central_differences_mode_S_with_bathymetry_offset():
 
 def test_vjp_matches_central_differences_r3():
     directional_check(beach(3, window=(236, 120, 4, 3)), 5, True, seed=5)
+
+
+def test_vjp_matches_central_differences_with_tracer_diffusion():
+    directional_check(diffusive_beach(), 5, True, seed=19)
 
 
 def test_vjp_matches_central_differences_mode_P():

@@ -40,6 +40,7 @@ CASES = {
     "beach_P": lambda: A.beach(2, mode=1),
     "wetdry": wetdry_beach,
     "forest_r1": lambda: A.forest(1),
+    "diffusion": A.diffusive_beach,
 }
 
 
@@ -49,6 +50,8 @@ def oracle_steps(wl, state, manning, delta, dt, nsteps):
     for (tag, kind, amp, per, ph) in wl.boundaries:
         o.set_boundary(tag, kind, amp, per, ph)
     o.set_manning(manning)
+    if wl.tracer_diffusivity is not None:
+        o.set_tracer_diffusivity(wl.tracer_diffusivity)
     o.set_state(*state)
     o.step(nsteps, dt, 0.0)
     return o.get_state()
