@@ -119,6 +119,14 @@ int swdg_set_boundary(swdg_ctx* ctx, int tag, int kind, double amp, double perio
 /* Per-cell Manning coefficient n (Eq. manning), [n] float64; NULL sets 0. */
 int swdg_set_manning(swdg_ctx* ctx, const double* n_per_cell, int where);
 
+/* Tracer numerical diffusion (Eq. numdiff): with a diffusivity nu_c [n] per
+ * cell (>= 0; host or device per where), the term -sum_K int_K nu_c h grad c
+ * . grad psi_i joins the tracer residual R (volume points, h the sub-grid
+ * depth); the paper sets nu_c = C |K| r^-2 S with a case-dependent strain
+ * rate S, which the caller computes.  NULL turns it off (the default).  It
+ * moves no tracer mass and is dissipative. */
+int swdg_set_tracer_diffusivity(swdg_ctx* ctx, const double* nu, int where);
+
 /* Set the state (zeta, qx, qy, c), each [n][(r+1)^2] float64.  Resets the
  * per-cell degree flags to r. */
 int swdg_set_state(swdg_ctx* ctx, const double* zeta, const double* qx, const double* qy,

@@ -165,11 +165,12 @@ __device__ __forceinline__ DN<W> fmin(const DN<W>& a, const DN<W>& b) { return a
 template <int R>
 constexpr int vjp_smem() {
     // su [4 ND] state, rb [6 ND] own cotangents, tz [2 ND1 NV], tq [3 ND1 NV],
-    // tc [12 ND1 NV] cotangent x-contractions, xv [6 NVP] point cotangents,
-    // xf [4 * 4 * 2 NM] face-point cotangents, tt [3 NV ND1] transposes
+    // tc [12 ND1 NV] cotangent x-contractions, xv [8 NVP] point cotangents,
+    // xf [4 * 4 * 2 NM] face-point cotangents, tt [3 NV ND1] transposes,
+    // tcd [ND1 NV] d/dxi x-contraction of c (tracer diffusion)
     using S = Sz<R>;
     return 4 * S::ND + 6 * S::ND + 2 * S::ND1 * S::NV + 3 * S::ND1 * S::NV +
-           12 * S::ND1 * S::NV + 6 * S::NVP + 32 * S::NM + 3 * S::NV * S::ND1;
+           12 * S::ND1 * S::NV + 8 * S::NVP + 32 * S::NM + 3 * S::NV * S::ND1 + S::ND1 * S::NV;
 }
 
 // the face fluxes of one face point seen from side A (outward normal n_A):
@@ -201,9 +202,10 @@ __global__ void __launch_bounds__(32 * MAXWPB)
     double* tz = rb + 6 * ND;          // [2][ND1][NV] zeta: x-value, x-derivative
     double* tq = tz + 2 * ND1 * NV;    // [3][ND1][NV] qx, qy, c: x-value
     double* tc = tq + 3 * ND1 * NV;    // [6 fields][2: value, d/dxi][ND1][NV]
-    double* xv = tc + 12 * ND1 * NV;   // [6][NVP]: bars of z, z_xi, z_eta, qx, qy, c at points
-    double* xf = xv + 6 * NVP;         // [4 fields][4 faces][2 halves][NM]
+    double* xv = tc + 12 * ND1 * NV;   // [8][NVP]: bars of z, z_xi, z_eta, qx, qy, c, c_xi, c_eta
+    double* xf = xv + 8 * NVP;         // [4 fields][4 faces][2 halves][NM]
     double* tt = xf + 32 * NM;         // [3][NV][ND1]
+    double* tcd = tt + 3 * NV * ND1;   // [ND1][NV] c: x-derivative
     const double g = d.g, eps = d.eps;
     const int64_t n = d.n;
     const size_t fs = (size_t)n * ND;  // field stride of the state and cotangent arrays
@@ -215,7 +217,16 @@ __global__ void __launch_bounds__(32 * MAXWPB)
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
         const double ihx = 1.0 / hx, ihy = 1.0 / hy;
         const double man = d.manning[k];
+        const double nu = d.nu_c ? d.nu_c[k] : 0.0;
         __syncwarp();
+        if (nu != 0.0)
+            for (int i = lane; i < ND1 * NV; i += 32) {
+                const int b = i / NV, al = i % NV;
+                double s = 0.0;
+#pragma unroll
+                for (int a = 0; a < ND1; ++a) s += tb.Dv[al][a] * su[3 * ND + ND1 * b + a];
+                tcd[i] = s;
+            }
         // x-contractions of the state (values at points) and of the cotangents
         // (value and d/dxi: the transposed test functions)
         for (int i = lane; i < 2 * ND1 * NV; i += 32) {
@@ -309,7 +320,26 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                     xb[dir] = s_;
                 }
             }
+            // tracer numerical diffusion (Eq. numdiff): X_2 -= w nu h c_xi / hx^2,
+            // X_3 -= w nu h c_eta / hy^2 (linear in grad c; h = V(z + delta))
+            double xcx = 0.0, xcy = 0.0;
+            if (nu != 0.0) {
+                double cxd = 0.0, cyd = 0.0;
+#pragma unroll
+                for (int b = 0; b < ND1; ++b) {
+                    cxd += tb.Bv[be][b] * tcd[b * NV + al];
+                    cyd += tb.Dv[be][b] * tq[(2 * ND1 + b) * NV + al];
+                }
+                const double kx = w * nu * ihx * ihx, ky = w * nu * ihy * ihy;
+                xcx = -Xb[2] * kx * V;
+                xcy = -Xb[3] * ky * V;
+                const double xh = -(Xb[2] * kx * cxd + Xb[3] * ky * cyd);
+                xb[0] += A * xh;
+                xb[6] += A * xh;
+            }
             for (int q = 0; q < 6; ++q) xv[q * NVP + p] = xb[q];
+            xv[6 * NVP + p] = xcx;
+            xv[7 * NVP + p] = xcy;
             dsum += xb[6];
             nsum += xb[7];
         }
@@ -467,21 +497,29 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             ub[c_] = s;
         }
         __syncwarp();
-        // qx, qy, c: (Bv, Bv) transposes
+        // qx, qy, c: (Bv, Bv) transposes; c also (Dv, Bv) c_xi and (Bv, Dv) c_eta
         for (int fl = 0; fl < 3; ++fl) {
+            const bool grad = fl == 2 && nu != 0.0;
             for (int i = lane; i < NV * ND1; i += 32) {
                 const int al = i / ND1, b = i % ND1;
-                double s = 0.0;
+                double s = 0.0, s1 = 0.0;
 #pragma unroll
-                for (int be = 0; be < NV; ++be) s += tb.Bv[be][b] * xv[(3 + fl) * NVP + al + NV * be];
+                for (int be = 0; be < NV; ++be) {
+                    s += tb.Bv[be][b] * xv[(3 + fl) * NVP + al + NV * be];
+                    if (grad)
+                        s += tb.Dv[be][b] * xv[7 * NVP + al + NV * be],
+                            s1 += tb.Bv[be][b] * xv[6 * NVP + al + NV * be];
+                }
                 tt[i] = s;
+                tt[NV * ND1 + i] = s1;
             }
             __syncwarp();
             for (int i = lane, c_ = 0; i < ND; i += 32, ++c_) {
                 const int a = i % ND1, b = i / ND1;
                 double s = 0.0;
 #pragma unroll
-                for (int al = 0; al < NV; ++al) s += tb.Bv[al][a] * tt[al * ND1 + b];
+                for (int al = 0; al < NV; ++al)
+                    s += tb.Bv[al][a] * tt[al * ND1 + b] + tb.Dv[al][a] * tt[NV * ND1 + al * ND1 + b];
                 ub[(1 + fl) * NC + c_] = s;
             }
             __syncwarp();

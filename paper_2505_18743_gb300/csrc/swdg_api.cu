@@ -68,6 +68,7 @@ struct swdg_ctx {
     double* mdiag = nullptr;    // [nmemb][4]
     std::vector<Bc> bch;
     // device allocations
+    double* nu_c = nullptr; // tracer numerical diffusivity per cell
     double *x0y0 = nullptr, *hxhy = nullptr, *ihxhy = nullptr, *manning = nullptr, *U = nullptr, *res = nullptr,
            *llin = nullptr, *HN = nullptr, *CN = nullptr, *HNbar = nullptr, *CNbar = nullptr,
            *zpts = nullptr, *zmax = nullptr, *zmin = nullptr, *zabs = nullptr, *diag = nullptr;
@@ -693,6 +694,9 @@ static void free_mesh(swdg_ctx* c) {
     cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->diag); cudaFree(c->finfo);
     cudaFree(c->adj);
     c->adj = nullptr;
+    cudaFree(c->nu_c);
+    c->nu_c = nullptr;
+    c->d.nu_c = nullptr;
     for (double* p : {c->ws.rec_u, c->ws.ubs, c->ws.rbar, c->ws.llb, c->ws.HNb, c->ws.CNb,
                       c->ws.nbar, c->ws.dbar, c->ws.vb, c->ws.ubpre})
         cudaFree(p);
@@ -1099,6 +1103,32 @@ int swdg_set_boundary(swdg_ctx* ctx, int tag, int kind, double amp, double perio
                            cudaMemcpyHostToDevice, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
     }
+    return SWDG_OK;
+}
+
+int swdg_set_tracer_diffusivity(swdg_ctx* ctx, const double* nu, int where) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_mesh) return fail(ctx, SWDG_ESTATE, "set_tracer_diffusivity: no mesh");
+    const int64_t n = ctx->n;
+    if (!nu) {
+        cudaFree(ctx->nu_c);
+        ctx->nu_c = nullptr;
+        ctx->d.nu_c = nullptr;
+        invalidate_graph(ctx);
+        return SWDG_OK;
+    }
+    if (where == SWDG_HOST)
+        for (int64_t k = 0; k < n; ++k)
+            if (!(nu[k] >= 0) || !std::isfinite(nu[k]))
+                return fail(ctx, SWDG_EINVAL, "set_tracer_diffusivity: bad value at cell %lld",
+                            (long long)k);
+    if (!ctx->nu_c) CK(cudaMalloc(&ctx->nu_c, n * sizeof(double)));
+    CK(cudaMemcpyAsync(ctx->nu_c, nu, n * sizeof(double),
+                       where == SWDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->d.nu_c = ctx->nu_c;
+    invalidate_graph(ctx);
     return SWDG_OK;
 }
 

@@ -111,6 +111,7 @@ struct Dev {
     const double* zmin; // min z_b of the cell: every pixel is wet when eta > -zmin
     const double* zabs; // max |z_b| of the cell (Newton tolerance scale)
     const double* manning;
+    const double* nu_c; // tracer numerical diffusivity per cell (Eq. numdiff); null: none
     double* U;
     uint8_t* cmask;
     double* res;

@@ -244,10 +244,11 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
 template <int R, typename B>
 constexpr int res_smem() {
     // in doubles: su [4 ND], tz [2 ND1 NV], Xd [4 NVP], sd [4 NV ND1], fh [32 NM], rs [6 ND],
-    // then B-typed: suB [4 ND], tB [3 ND1 NV], XB [8 NVP], sB [8 NV ND1]
+    // tc [2 ND1 NV] (tracer diffusion), then B-typed: suB [4 ND], tB [3 ND1 NV], XB [8 NVP],
+    // sB [8 NV ND1]
     using S = Sz<R>;
     constexpr int nd = 4 * S::ND + 2 * S::ND1 * S::NV + 4 * S::NVP + 4 * S::NV * S::ND1 +
-                       32 * S::NM + 6 * S::ND;
+                       32 * S::NM + 6 * S::ND + 2 * S::ND1 * S::NV;
     constexpr int nb = 4 * S::ND + 3 * S::ND1 * S::NV + 8 * S::NVP + 8 * S::NV * S::ND1;
     return nd + (nb * (int)sizeof(B) + 7) / 8;
 }
@@ -304,9 +305,10 @@ __global__ void __maxnreg__(96)
     double* sd = Xd + 4 * NVP;          // [4][NV][ND1]
     double* fh = sd + 4 * NV * ND1;     // [4 fields][4 faces][2 halves][NM]
     double* rs = fh + 32 * NM;          // [6][ND]
+    double* tc = rs + 6 * ND;           // [2][ND1][NV] x-contractions of c (value, d/dxi), FP64
     constexpr bool F64 = sizeof(B) == sizeof(double);
-    B* suB = F64 ? (B*)su : (B*)(rs + 6 * ND); // [4][ND] (the FP64 state itself when B = double)
-    B* tB = (B*)(rs + 6 * ND) + 4 * ND;        // [3][ND1][NV]: qx, qy, c
+    B* suB = F64 ? (B*)su : (B*)(tc + 2 * ND1 * NV); // [4][ND] (the FP64 state itself when B = double)
+    B* tB = (B*)(tc + 2 * ND1 * NV) + 4 * ND;        // [3][ND1][NV]: qx, qy, c
     B* XB = tB + 3 * ND1 * NV;          // [8][NVP]: Gx (x, y, v), Gy (x, y, v), Lx, Ly
     B* sB = XB + 8 * NVP;               // [8][NV][ND1]
     const auto BvB = tab_or<B>(tb.Bv, tb.BvF);
@@ -352,6 +354,18 @@ __global__ void __maxnreg__(96)
             for (int a = 0; a < ND1; ++a) s += BvB[al][a] * u[a];
             tB[i] = s;
         }
+        // tracer numerical diffusion (Eq. numdiff): grad c in FP64
+        const double nu = d.nu_c ? d.nu_c[k] : 0.0;
+        if (nu != 0.0) {
+            for (int i = lane; i < 2 * ND1 * NV; i += 32) {
+                const int f = i / (ND1 * NV), r_ = i % (ND1 * NV), b = r_ / NV, al = r_ % NV;
+                double s = 0.0;
+#pragma unroll
+                for (int a = 0; a < ND1; ++a)
+                    s += (f ? tb.Dv[al][a] : tb.Bv[al][a]) * su[3 * ND + ND1 * b + a];
+                tc[i] = s;
+            }
+        }
         __syncwarp();
         // y-contraction and pointwise physics, one volume point per lane
         for (int p = lane; p < NVP; p += 32) {
@@ -385,6 +399,17 @@ __global__ void __maxnreg__(96)
             Xd[1 * NVP + p] = (double)(wy * qy);
             Xd[2 * NVP + p] = (double)(wx * c * qx);
             Xd[3 * NVP + p] = (double)(wy * c * qy);
+            if (nu != 0.0 && !(cm & 8u)) {
+                // -nu h grad c . grad psi: the reference derivatives of c at the point
+                double cxd = 0.0, cyd = 0.0;
+#pragma unroll
+                for (int b = 0; b < ND1; ++b) {
+                    cxd += tb.Bv[be][b] * tc[(ND1 + b) * NV + al];
+                    cyd += tb.Dv[be][b] * tc[b * NV + al];
+                }
+                Xd[2 * NVP + p] -= w * nu * h * cxd * ihx * ihx;
+                Xd[3 * NVP + p] -= w * nu * h * cyd * ihy * ihy;
+            }
             XB[0 * NVP + p] = wx * qx * ux;
             XB[1 * NVP + p] = wy * qx * uy;
             XB[2 * NVP + p] = -wB * gB * hB * zx;

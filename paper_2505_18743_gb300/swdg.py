@@ -60,6 +60,7 @@ SIGNATURES = {
     "swdg_upload_bathymetry": (_I, [_P, _P, _I, _I64, _I64, _D, _D, _D, _D]),
     "swdg_set_boundary": (_I, [_P, _I, _I, _D, _D, _D]),
     "swdg_set_manning": (_I, [_P, _P, _I]),
+    "swdg_set_tracer_diffusivity": (_I, [_P, _P, _I]),
     "swdg_set_state": (_I, [_P, _P, _P, _P, _P, _I]),
     "swdg_get_state": (_I, [_P, _P, _P, _P, _P, _I]),
     "swdg_residual": (_I, [_P, _D, _P, _P, _P, _P, _P, _P, _I]),
@@ -215,6 +216,11 @@ class Context:
         p, where, keep = _buf(n, np.float64)
         self._ck(load().swdg_set_manning(self.h, p, where))
 
+    def set_tracer_diffusivity(self, nu):
+        """tracer numerical diffusivity nu_c per cell (Eq. numdiff); None: off"""
+        p, where, keep = _buf(nu, np.float64)
+        self._ck(load().swdg_set_tracer_diffusivity(self.h, p, where))
+
     def set_state(self, zeta, qx, qy, c):
         bufs = [_buf(v, np.float64) for v in (zeta, qx, qy, c)]
         where = bufs[0][1]
@@ -363,6 +369,8 @@ class Context:
             ctx.set_boundary(tag, kind, amp, per, ph)
         if wl.manning is not None:
             ctx.set_manning(wl.manning)
+        if getattr(wl, "tracer_diffusivity", None) is not None:
+            ctx.set_tracer_diffusivity(wl.tracer_diffusivity)
         ctx.set_state(*wl.state())
         return ctx
 
@@ -447,6 +455,10 @@ class Ensemble(Context):
         man = np.concatenate([w.manning if w.manning is not None else np.zeros(w.mesh.n)
                               for w in wls])
         ctx.set_manning(man)
+        if any(getattr(w, "tracer_diffusivity", None) is not None for w in wls):
+            ctx.set_tracer_diffusivity(np.concatenate(
+                [w.tracer_diffusivity if w.tracer_diffusivity is not None else np.zeros(w.mesh.n)
+                 for w in wls]))
         st = [np.concatenate(parts) for parts in zip(*[w.state() for w in wls])]
         ctx.set_state(*st)
         return ctx

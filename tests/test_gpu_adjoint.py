@@ -40,7 +40,7 @@ def compare(wl, t=1000.0, seed=2, precision=0, check_delta=True):
     cot = [rng.standard_normal((n, nd)) for _ in range(6)]
     man = wl.manning if wl.manning is not None else np.zeros(n)
     tr = TorchResidual(wl.mesh, wl.raster, wl.degree, wl.subgrid_mode, wl.g, wl.eps_vel,
-                       wl.boundaries)
+                       wl.boundaries, wl.tracer_diffusivity)
     ref = residual_vjp(tr, wl.state(), man, np.zeros(n), cot, t)
     ctx = swdg.Context.from_workload(wl, precision=precision)
     got = ctx.residual_vjp(cot, t)
@@ -56,12 +56,12 @@ def compare(wl, t=1000.0, seed=2, precision=0, check_delta=True):
 
 
 @pytest.mark.parametrize("case", ["basin", "beach_r1", "beach_r2", "beach_r3", "beach_P",
-                                  "forest_r1", "forest_r2"])
+                                  "forest_r1", "forest_r2", "diffusion"])
 def test_residual_vjp_matches_the_adjoint_oracle(case):
     wl = {"basin": lambda: W.closed_basin(), "beach_r1": lambda: A.beach(1),
           "beach_r2": lambda: A.beach(2), "beach_r3": lambda: A.beach(3),
           "beach_P": lambda: A.beach(2, mode=1), "forest_r1": lambda: A.forest(1),
-          "forest_r2": lambda: A.forest(2)}[case]()
+          "forest_r2": lambda: A.forest(2), "diffusion": A.diffusive_beach}[case]()
     compare(wl, check_delta=case != "basin")  # the basin's bottom is flat in places
 
 

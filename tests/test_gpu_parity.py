@@ -383,3 +383,25 @@ def test_errors_are_reported():
     with pytest.raises(swdg.SwdgError) as e:
         ctx.step(1, -1.0, 0.0)
     assert e.value.code == swdg.SWDG_ENAN
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_residual_and_steps_with_tracer_diffusion(degree):
+    # Eq. numdiff with a per-cell diffusivity, on the shoreline crop (wet, dry, partly wet)
+    wl = W.tidal_beach(window=(232, 118, 8, 6), degree=degree, pix=16)
+    Xn, Yn = W.nodal_coordinates(wl.mesh, degree)
+    wl.zeta = 0.2 + 0.1 * np.sin(Xn / 300.0) * np.cos(Yn / 250.0)  # every field carries signal
+    wl.qx = 0.1 * np.cos(Yn / 200.0) + 0.0 * Xn
+    wl.qy = 0.05 * np.sin(Xn / 170.0)
+    wl.c = 0.5 + 0.4 * np.sin(Xn / 150.0) * np.cos(Yn / 120.0)
+    wl.tracer_diffusivity = np.linspace(0.5, 4.0, wl.mesh.n)
+    ctx, ora = pair(wl)
+    check_residual(ctx, ora, t=500.0)
+    ctx.step(6, -1.0, 0.0)
+    ora.step(6, -1.0, 0.0)
+    check_state(ctx, ora)
+    # without diffusion the tracer differs: the term is active
+    plain, _ = pair(W.tidal_beach(window=(232, 118, 8, 6), degree=degree, pix=16))
+    plain.set_state(*wl.state())
+    plain.step(6, -1.0, 0.0)
+    assert np.abs(plain.get_state()[3] - ctx.get_state()[3]).max() > 1e-8
