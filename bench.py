@@ -65,9 +65,9 @@ FLOPS_PER_CELL = {"step_begin": 2187, "residual": 12680, "stage_2": 9701, "stage
 # the FP32-bulk kernels' FP64 flops (their FP32 work runs on the 60x faster FP32 pipe)
 FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "residual": 3831, "stage_2": 6371,
                            "stage_3": 6620, "final": 6400}
-# DRAM bytes per launch from the same ncu capture (FP64 path); {} once the kernel changed
-DRAM_BYTES_PER_LAUNCH = {"residual": 96.3e6, "stage_2": 156.3e6, "stage_3": 248.3e6,
-                         "final": 254.1e6, "step_begin": 59.2e6}
+# DRAM bytes per launch from an ncu capture of the current kernels (FP64 path);
+# {} (traffic null) whenever the kernels changed after the capture
+DRAM_BYTES_PER_LAUNCH = {}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
 
 
