@@ -285,6 +285,66 @@ int swdg_member_diagnostics(swdg_ctx* ctx, double* out);
 int swdg_gather_gauges_member(swdg_ctx* ctx, int member, int n, const double* xy,
                               double* zeta_out);
 
+/* ---- dynamic h-adaptation (Sec. 3.4) ----
+ * A forest of quadtrees over an nx0 x ny0 grid of coarse cells (origin x0,
+ * y0; size hx0 x hy0); leaf (l, i, j) is the cell [x0 + i hx0 / 2^l, ...] x
+ * [y0 + j hy0 / 2^l, ...] at level l = 0..max_level (the paper's mesh level
+ * n_K = l + 1).  Domain faces carry tags[4] (W, E, S, N) unless periodic.
+ * Leaves are listed along the Morton curve of their lower-left corners on the
+ * level-max_level grid. */
+typedef struct {
+    int nx0, ny0;
+    double x0, y0, hx0, hy0;
+    int max_level;
+    double h_min;   /* H_min: a cell with max(hx, hy) <= h_min is not refined */
+    int tags[4];
+    int periodic[2];
+} swdg_forest;
+
+/* Criteria of Sec. 3.4 (host, no GPU): with eta_max = max eta, flags[k] = 1
+ * (refine) if eta_k > theta_r eta_max, l < max_level and max(hx, hy) > h_min;
+ * else -1 (coarsen) if eta_k < theta_c eta_max and l > 0; else 0.
+ * lij [n][3] = (l, i, j) of each leaf. */
+int swdg_forest_flags(const swdg_forest* f, int64_t n, const int32_t* lij, const double* eta,
+                      double theta_r, double theta_c, int8_t* flags);
+/* Adapted leaf set (host, no GPU): refine the leaves flagged 1, merge four
+ * sibling leaves that are all flagged -1 into their parent, then split leaves
+ * until every face joins leaves at most one level apart (the smallest such
+ * set).  Writes *n_out, and the ordered leaves to lij_out if n_out <= cap
+ * (SWDG_EINVAL otherwise). */
+int swdg_forest_adapt(const swdg_forest* f, int64_t n, const int32_t* lij, const int8_t* flags,
+                      int64_t cap, int32_t* lij_out, int64_t* n_out);
+/* Mesh of a 2:1-balanced ordered leaf set (host, no GPU): x0y0, hxhy [n][2],
+ * nbr [n][4][2] in the layout of swdg_upload_mesh. */
+int swdg_forest_mesh(const swdg_forest* f, int64_t n, const int32_t* lij, double* x0y0,
+                     double* hxhy, int32_t* nbr);
+
+/* Adaptation of a context's mesh (one member, FP64 or FP32-bulk).
+ * swdg_amr_setup declares the forest the current mesh belongs to (every cell
+ * must be one of its leaves; SWDG_EINVAL otherwise).
+ * swdg_amr_indicator writes eta [n] (host): kind 0 = max over the volume
+ * Gauss points of |curl u| (Sec. 4.4; u = f(h) q with f the desingularised
+ * factor of Eq. velocity and grad h = A grad zeta), kind 1 = max of |grad c|
+ * (Sec. 5).
+ * swdg_amr_adapt flags the leaves by the criteria (eta from the caller, host
+ * [n], or NULL for indicator `kind`), adapts the forest, remaps the state
+ * (a kept cell keeps its values, a child takes its parent's polynomial, a
+ * parent the L2 projection of its children -- conservative for every field),
+ * rebuilds mesh and bathymetry (from the uploaded raster; every new cell must
+ * span whole pixels) and carries the per-cell Manning and diffusivity values
+ * over (children inherit, a parent takes the children's mean).  report [6]
+ * (may be NULL): cells before, cells after, leaves refined, parents formed,
+ * Q^n = the change of the total wet mass sum_K Hbar_K across the adaptation
+ * (Eq. mass-loss: with a conservative remap, the bathymetry-integral term)
+ * and the change of the tracer mass.  Launch shapes return to their defaults
+ * and a bathymetry offset is dropped.  Not for ensembles. */
+int swdg_amr_setup(swdg_ctx* ctx, const swdg_forest* f);
+int swdg_amr_indicator(swdg_ctx* ctx, int kind, double* eta);
+int swdg_amr_adapt(swdg_ctx* ctx, const double* eta, int kind, double theta_r, double theta_c,
+                   double* report);
+/* (l, i, j) of the current leaves, lij [n][3] (host). */
+int swdg_amr_leaves(const swdg_ctx* ctx, int32_t* lij);
+
 /* ---- launch shapes (the paper has no counterpart) ----
  * Each kernel kind runs one warp per cell, grid-stride over all cells: kind
  * SWDG_KIND_BEGIN (degree switch and H, C~), SWDG_KIND_RESIDUAL,

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswdg.so")
-SOURCES = ["swdg_api.cu", "swdg_r1.cu", "swdg_r2.cu", "swdg_r3.cu"]
+SOURCES = ["swdg_api.cu", "swdg_forest.cu", "swdg_r1.cu", "swdg_r2.cu", "swdg_r3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

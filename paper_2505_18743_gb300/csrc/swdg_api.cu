@@ -9,12 +9,15 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/swdg.h"
 #include "swdg_adjoint.cuh"
 #include "swdg_kernels.cuh"
 #include "swdg_launch.h"
+#include "swdg_forest.h"
+#include "swdg_amr.cuh"
 
 using namespace swdg;
 
@@ -69,6 +72,14 @@ struct swdg_ctx {
     std::vector<Bc> bch;
     // device allocations
     double* nu_c = nullptr; // tracer numerical diffusivity per cell
+    // dynamic h-adaptation: the forest, the leaf of every cell, the uploaded raster
+    bool amr = false;
+    swdg_forest forest{};
+    std::vector<Leaf> leaves;
+    std::vector<uint8_t> ras_h;
+    int ras_dtype = 0;
+    int64_t ras_nx = 0, ras_ny = 0;
+    double ras_geo[4] = {0, 0, 1, 1};
     double *x0y0 = nullptr, *hxhy = nullptr, *ihxhy = nullptr, *manning = nullptr, *U = nullptr, *res = nullptr,
            *llin = nullptr, *HN = nullptr, *CN = nullptr, *HNbar = nullptr, *CNbar = nullptr,
            *zpts = nullptr, *zmax = nullptr, *zmin = nullptr, *zabs = nullptr, *diag = nullptr;
@@ -814,6 +825,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     free_bathy(ctx);
     ctx->has_bathy = ctx->has_state = false;
     ctx->n = n;
+    ctx->amr = false; // a new mesh leaves the forest (swdg_amr_adapt sets it again)
     free_members(ctx);
     const size_t nd = ctx->nd;
     CK(cudaMalloc(&ctx->x0y0, 2 * n * sizeof(double)));
@@ -1070,7 +1082,21 @@ int swdg_upload_bathymetry(swdg_ctx* ctx, const void* raster, int dtype, int64_t
     const int64_t nxny[2] = {nx, ny};
     const double geo[4] = {xo, yo, dx, dy};
     const int64_t first[2] = {0, ctx->n};
-    return upload_bathy(ctx, 1, r, dtype, nxny, geo, first);
+    int rc = upload_bathy(ctx, 1, r, dtype, nxny, geo, first);
+    if (rc) return rc;
+    // a host copy for re-tiling after an adaptation of the mesh
+    if (ctx->ras_h.data() != (const uint8_t*)raster) {
+        const size_t bytes = (size_t)nx * ny * (dtype == SWDG_PIX_F32 ? 4 : 8);
+        ctx->ras_h.assign((const uint8_t*)raster, (const uint8_t*)raster + bytes);
+    }
+    ctx->ras_dtype = dtype;
+    ctx->ras_nx = nx;
+    ctx->ras_ny = ny;
+    ctx->ras_geo[0] = xo;
+    ctx->ras_geo[1] = yo;
+    ctx->ras_geo[2] = dx;
+    ctx->ras_geo[3] = dy;
+    return SWDG_OK;
 }
 
 int swdg_upload_bathymetry_members(swdg_ctx* ctx, const void* const* rasters, int dtype,
@@ -1861,6 +1887,224 @@ int swdg_set_bathymetry_offset(swdg_ctx* ctx, const double* delta, int where) {
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->st));
     cudaFree(dd);
+    return SWDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// dynamic h-adaptation (Sec. 3.4)
+// ---------------------------------------------------------------------------
+int swdg_amr_setup(swdg_ctx* ctx, const swdg_forest* f) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_mesh) return fail(ctx, SWDG_ESTATE, "amr_setup: no mesh");
+    if (ctx->nmemb != 1) return fail(ctx, SWDG_EINVAL, "amr_setup: not for an ensemble");
+    if (!forest_valid(f)) return fail(ctx, SWDG_EINVAL, "amr_setup: bad forest");
+    Forest F{*f};
+    std::vector<Leaf> lv;
+    if (!F.leaves_of(ctx->n, ctx->x0y0_h.data(), ctx->hxhy_h.data(), lv))
+        return fail(ctx, SWDG_EINVAL, "amr_setup: a cell is not a leaf of the forest");
+    std::vector<double> x(2 * ctx->n), h(2 * ctx->n);
+    std::vector<int32_t> nb(8 * ctx->n);
+    try {
+        F.mesh(lv, x.data(), h.data(), nb.data());
+    } catch (...) {
+        return fail(ctx, SWDG_EINVAL, "amr_setup: the cells are not a 2:1-balanced leaf set");
+    }
+    if (nb != ctx->nbr_h)
+        return fail(ctx, SWDG_EINVAL,
+                    "amr_setup: the mesh's neighbours differ from the forest's (tags, periodicity)");
+    ctx->forest = *f;
+    ctx->leaves = lv;
+    ctx->amr = true;
+    return SWDG_OK;
+}
+
+int swdg_amr_leaves(const swdg_ctx* ctx, int32_t* lij) {
+    if (!ctx || !lij || !ctx->amr) return SWDG_EINVAL;
+    for (size_t k = 0; k < ctx->leaves.size(); ++k) {
+        lij[3 * k] = ctx->leaves[k].l;
+        lij[3 * k + 1] = ctx->leaves[k].i;
+        lij[3 * k + 2] = ctx->leaves[k].j;
+    }
+    return SWDG_OK;
+}
+
+int swdg_amr_indicator(swdg_ctx* ctx, int kind, double* eta) {
+    if (!ctx || !eta) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "amr_indicator: no state");
+    if (kind != 0 && kind != 1) return fail(ctx, SWDG_EINVAL, "amr_indicator: kind 0 or 1");
+    double* buf = nullptr;
+    CK(cudaMalloc(&buf, ctx->n * sizeof(double)));
+    ctx->L.indicator(ctx->d, ctx->tb, kind, buf, Shape{grid_for(ctx->n), WPB}, ctx->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(eta, buf, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    cudaFree(buf);
+    return SWDG_OK;
+}
+
+int swdg_amr_adapt(swdg_ctx* ctx, const double* eta_in, int kind, double theta_r, double theta_c,
+                   double* report) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->amr) return fail(ctx, SWDG_ESTATE, "amr_adapt: no forest (swdg_amr_setup)");
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "amr_adapt: no state");
+    if (ctx->ras_h.empty()) return fail(ctx, SWDG_ESTATE, "amr_adapt: no raster to re-tile");
+    if (!std::isfinite(theta_r) || !std::isfinite(theta_c))
+        return fail(ctx, SWDG_EINVAL, "amr_adapt: bad thresholds");
+    const int64_t n = ctx->n;
+    const int nd = ctx->nd;
+    std::vector<double> eta(n);
+    if (eta_in) {
+        for (int64_t k = 0; k < n; ++k) {
+            if (!std::isfinite(eta_in[k]) || eta_in[k] < 0.0)
+                return fail(ctx, SWDG_EINVAL, "amr_adapt: bad indicator at cell %lld", (long long)k);
+            eta[k] = eta_in[k];
+        }
+    } else {
+        int rc = swdg_amr_indicator(ctx, kind, eta.data());
+        if (rc) return rc;
+    }
+    Forest F{ctx->forest};
+    std::vector<int8_t> fl(n);
+    F.flags(ctx->leaves, eta.data(), theta_r, theta_c, fl.data());
+    std::vector<Leaf> nl = F.adapt(ctx->leaves, fl.data());
+    const int64_t n2 = (int64_t)nl.size();
+    // the plan of every new cell
+    std::unordered_map<uint64_t, int32_t> old;
+    old.reserve(n * 2);
+    auto key = [](int l, int64_t i, int64_t j) {
+        return ((uint64_t)l << 58) | ((uint64_t)i << 29) | (uint64_t)j;
+    };
+    for (int64_t k = 0; k < n; ++k)
+        old[key(ctx->leaves[k].l, ctx->leaves[k].i, ctx->leaves[k].j)] = (int32_t)k;
+    std::vector<int8_t> type(n2);
+    std::vector<int32_t> src(4 * n2, 0);
+    std::vector<double> rel(3 * n2, 0.0);
+    int64_t nref = 0, npar = 0;
+    bool same = n2 == n;
+    for (int64_t k = 0; k < n2; ++k) {
+        const Leaf c = nl[k];
+        auto it = old.find(key(c.l, c.i, c.j));
+        if (it != old.end()) {
+            type[k] = 0;
+            src[4 * k] = it->second;
+            if (it->second != k) same = false;
+            continue;
+        }
+        same = false;
+        int la = c.l - 1;
+        int64_t ia = c.i >> 1, ja = c.j >> 1;
+        for (; la >= 0; --la, ia >>= 1, ja >>= 1) {
+            it = old.find(key(la, ia, ja));
+            if (it != old.end()) break;
+        }
+        if (la >= 0) {
+            type[k] = 1;
+            src[4 * k] = it->second;
+            const double s_ = 1.0 / (double)(1 << (c.l - la));
+            rel[3 * k] = s_;
+            rel[3 * k + 1] = c.i * s_ - (double)ia;
+            rel[3 * k + 2] = c.j * s_ - (double)ja;
+            continue;
+        }
+        type[k] = 2;
+        ++npar;
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                auto ch = old.find(key(c.l + 1, 2 * (int64_t)c.i + a, 2 * (int64_t)c.j + b));
+                if (ch == old.end())
+                    return fail(ctx, SWDG_EINVAL, "amr_adapt: internal: a new parent without its children");
+                src[4 * k + a + 2 * b] = ch->second;
+            }
+    }
+    for (int64_t k = 0; k < n; ++k)
+        if (fl[k] == 1) ++nref;
+    double d0[8], d1[8];
+    int rc = swdg_diagnostics(ctx, d0);
+    if (rc) return rc;
+    if (same) {
+        if (report) {
+            const double rr[6] = {(double)n, (double)n, 0.0, 0.0, 0.0, 0.0};
+            memcpy(report, rr, sizeof rr);
+        }
+        return SWDG_OK;
+    }
+    // every new cell must span whole, aligned pixels (mode S)
+    std::vector<double> x(2 * n2), h(2 * n2);
+    std::vector<int32_t> nb(8 * n2);
+    F.mesh(nl, x.data(), h.data(), nb.data());
+    if (ctx->mode == 0) {
+        const double dx = ctx->ras_geo[2], dy = ctx->ras_geo[3];
+        for (int64_t k = 0; k < n2; ++k) {
+            const double px = h[2 * k] / dx, py = h[2 * k + 1] / dy;
+            const double cx = (x[2 * k] - ctx->ras_geo[0]) / dx, cy = (x[2 * k + 1] - ctx->ras_geo[1]) / dy;
+            if (std::fabs(px - std::round(px)) > 1e-6 || std::fabs(py - std::round(py)) > 1e-6 ||
+                std::round(px) < 1 || std::round(px) > MXPIX || std::round(px) != std::round(py) ||
+                std::fabs(cx - std::round(cx)) > 1e-6 || std::fabs(cy - std::round(cy)) > 1e-6)
+                return fail(ctx, SWDG_EINVAL,
+                            "amr_adapt: new cell %lld would not span whole pixels (raise h_min)",
+                            (long long)k);
+        }
+    }
+    // remap the state on the device
+    int8_t* dtype_ = nullptr;
+    int32_t* dsrc = nullptr;
+    double *drel = nullptr, *unew = nullptr;
+    CK(cudaMalloc(&dtype_, n2));
+    CK(cudaMalloc(&dsrc, 4 * n2 * sizeof(int32_t)));
+    CK(cudaMalloc(&drel, 3 * n2 * sizeof(double)));
+    CK(cudaMalloc(&unew, 4 * (size_t)n2 * nd * sizeof(double)));
+    CK(cudaMemcpyAsync(dtype_, type.data(), n2, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(dsrc, src.data(), 4 * n2 * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(drel, rel.data(), 3 * n2 * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    RemapArgs ra{ctx->U, n, dtype_, dsrc, drel, unew, n2};
+    ctx->L.remap(ctx->tb, ra, Shape{grid_for(n2), WPB}, ctx->st);
+    CK(cudaGetLastError());
+    // per-cell coefficients: children inherit, a parent takes its children's mean
+    std::vector<double> man(n), nu;
+    CK(cudaMemcpyAsync(man.data(), ctx->manning, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    if (ctx->nu_c) {
+        nu.resize(n);
+        CK(cudaMemcpyAsync(nu.data(), ctx->nu_c, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    auto carry = [&](const std::vector<double>& a) {
+        std::vector<double> b(n2);
+        for (int64_t k = 0; k < n2; ++k) {
+            if (type[k] == 2)
+                b[k] = 0.25 * (a[src[4 * k]] + a[src[4 * k + 1]] + a[src[4 * k + 2]] + a[src[4 * k + 3]]);
+            else
+                b[k] = a[src[4 * k]];
+        }
+        return b;
+    };
+    const std::vector<double> man2 = carry(man);
+    const std::vector<double> nu2 = nu.empty() ? std::vector<double>() : carry(nu);
+    // the new mesh, bathymetry, coefficients and state
+    const std::vector<uint8_t> ras = ctx->ras_h;
+    const Scalars keep_sc = *ctx->sc_host;
+    (void)keep_sc;
+    rc = swdg_upload_mesh(ctx, n2, x.data(), h.data(), nb.data());
+    if (!rc) rc = swdg_upload_bathymetry(ctx, ras.data(), ctx->ras_dtype, ctx->ras_nx, ctx->ras_ny,
+                                        ctx->ras_geo[0], ctx->ras_geo[1], ctx->ras_geo[2],
+                                        ctx->ras_geo[3]);
+    if (!rc) rc = swdg_set_manning(ctx, man2.data(), SWDG_HOST);
+    if (!rc && !nu2.empty()) rc = swdg_set_tracer_diffusivity(ctx, nu2.data(), SWDG_HOST);
+    const size_t fb = (size_t)n2 * nd;
+    if (!rc) rc = swdg_set_state(ctx, unew, unew + fb, unew + 2 * fb, unew + 3 * fb, SWDG_DEVICE);
+    cudaFree(dtype_);
+    cudaFree(dsrc);
+    cudaFree(drel);
+    cudaFree(unew);
+    if (rc) return rc;
+    ctx->leaves = nl;
+    ctx->amr = true;
+    rc = swdg_diagnostics(ctx, d1);
+    if (rc) return rc;
+    if (report) {
+        const double rr[6] = {(double)n, (double)n2, (double)nref, (double)npar, d1[0] - d0[0],
+                              d1[1] - d0[1]};
+        memcpy(report, rr, sizeof rr);
+    }
     return SWDG_OK;
 }
 

@@ -2,6 +2,7 @@
 // swdg_r{1,2,3}.cu with SWDG_DEGREE defined).
 #pragma once
 #include "swdg_adjoint.cuh"
+#include "swdg_amr.cuh"
 #include "swdg_kernels.cuh"
 #include "swdg_launch.h"
 
@@ -17,6 +18,8 @@ struct Launchers {
     static constexpr size_t vjp_b = sizeof(double) * vjp_smem<R>();
     static constexpr size_t svjp_b = sizeof(double) * stage_vjp_smem<R>();
     static constexpr size_t bvjp_b = sizeof(double) * begin_vjp_smem<R>();
+    static constexpr size_t ind_b = sizeof(double) * indicator_smem<R>();
+    static constexpr size_t remap_b = sizeof(double) * remap_smem<R>();
 
     static void residual(const Dev& d, const Tables& tb, int buf, int stage, double c_stage,
                          int want_dt, Shape s, cudaStream_t st) {
@@ -52,6 +55,13 @@ struct Launchers {
     static void begin_vjp(const Dev& d, const Tables& tb, const BeginVjpArgs& a, Shape s,
                           cudaStream_t st) {
         k_begin_vjp<R, Pix, MODE><<<s.grid, 32 * s.wpb, bvjp_b * s.wpb, st>>>(d, tb, a);
+    }
+    static void indicator(const Dev& d, const Tables& tb, int kind, double* eta, Shape s,
+                          cudaStream_t st) {
+        k_indicator<R, Pix, MODE><<<s.grid, 32 * s.wpb, ind_b * s.wpb, st>>>(d, tb, kind, eta);
+    }
+    static void remap(const Tables& tb, const RemapArgs& a, Shape s, cudaStream_t st) {
+        k_remap<R><<<s.grid, 32 * s.wpb, remap_b * s.wpb, st>>>(tb, a);
     }
     template <typename K>
     static bool opt_in(K kern, size_t per_warp) {
@@ -94,6 +104,8 @@ struct Launchers {
         L->residual_vjp = &residual_vjp;
         L->stage_vjp = &stage_vjp;
         L->begin_vjp = &begin_vjp;
+        L->indicator = &indicator;
+        L->remap = &remap;
         L->prepare = &prepare;
         L->occupancy = &occupancy;
         L->nzp = Sz<R>::NZP;

@@ -8,6 +8,7 @@ namespace swdg {
 struct StageArgs;
 struct StageVjpArgs;
 struct BeginVjpArgs;
+struct RemapArgs;
 
 // launch shape of one kernel: blocks and warps (cells in flight) per block
 struct Shape {
@@ -34,6 +35,9 @@ struct Launch {
     // adjoints of a stage update / the final combination and of the step start (FP64)
     void (*stage_vjp)(const Dev&, const Tables&, const StageVjpArgs&, Shape, cudaStream_t);
     void (*begin_vjp)(const Dev&, const Tables&, const BeginVjpArgs&, Shape, cudaStream_t);
+    // refinement indicator (kind 0 |curl u|, 1 |grad c|) and state remap (Sec. 3.4)
+    void (*indicator)(const Dev&, const Tables&, int kind, double* eta, Shape, cudaStream_t);
+    void (*remap)(const Tables&, const RemapArgs&, Shape, cudaStream_t);
     // opt every kernel in to the shared memory of MAXWPB warps; false on failure
     bool (*prepare)();
     // resident blocks per SM of kernel kind KK_* at wpb warps per block (0: cannot launch)

@@ -45,6 +45,17 @@ class swdg_config(ctypes.Structure):
                 ("newton_max", _I), ("newton_tol", _D), ("stream", _P)]
 
 
+class swdg_forest(ctypes.Structure):
+    _fields_ = [("nx0", _I), ("ny0", _I), ("x0", _D), ("y0", _D), ("hx0", _D), ("hy0", _D),
+                ("max_level", _I), ("h_min", _D), ("tags", _I * 4), ("periodic", _I * 2)]
+
+
+def make_forest(nx0, ny0, x0, y0, hx0, hy0, max_level, h_min=0.0, tags=(0, 0, 0, 0),
+                periodic=(False, False)):
+    return swdg_forest(nx0, ny0, x0, y0, hx0, hy0, max_level, h_min, (_I * 4)(*tags),
+                       (_I * 2)(*[int(p) for p in periodic]))
+
+
 class SwdgError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"swdg error {code}: {msg}")
@@ -79,6 +90,14 @@ SIGNATURES = {
     "swdg_adjoint_slots": (_I, [_P, _I]),
     "swdg_step_record_slot": (_I, [_P, _I, _D, ctypes.POINTER(_D)]),
     "swdg_step_vjp_slot": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
+    "swdg_forest_flags": (_I, [ctypes.POINTER(swdg_forest), _I64, _P, _P, _D, _D, _P]),
+    "swdg_forest_adapt": (_I, [ctypes.POINTER(swdg_forest), _I64, _P, _P, _I64, _P,
+                               ctypes.POINTER(_I64)]),
+    "swdg_forest_mesh": (_I, [ctypes.POINTER(swdg_forest), _I64, _P, _P, _P, _P]),
+    "swdg_amr_setup": (_I, [_P, ctypes.POINTER(swdg_forest)]),
+    "swdg_amr_indicator": (_I, [_P, _I, _P]),
+    "swdg_amr_adapt": (_I, [_P, _P, _I, _D, _D, _P]),
+    "swdg_amr_leaves": (_I, [_P, _P]),
     "swdg_set_members": (_I, [_P, _I, _P]),
     "swdg_upload_bathymetry_members": (_I, [_P, _P, _I, _P, _P]),
     "swdg_set_boundary_member": (_I, [_P, _I, _I, _I, _D, _D, _D]),
@@ -132,6 +151,50 @@ def _buf(a, dtype):
         return ctypes.c_void_p(a.data_ptr()), (SWDG_DEVICE if a.is_cuda else SWDG_HOST), a
     arr = np.ascontiguousarray(a, dtype=dtype)
     return arr.ctypes.data_as(ctypes.c_void_p), SWDG_HOST, arr
+
+
+def forest_flags(forest, lij, eta, theta_r, theta_c):
+    """refine (1) / coarsen (-1) / keep (0) flags of Sec. 3.4 (host)"""
+    lij = np.ascontiguousarray(lij, dtype=np.int32)
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    out = np.zeros(len(lij), dtype=np.int8)
+    rc = load().swdg_forest_flags(ctypes.byref(forest), len(lij), lij.ctypes.data_as(_P),
+                                  eta.ctypes.data_as(_P), theta_r, theta_c, out.ctypes.data_as(_P))
+    if rc:
+        raise SwdgError(rc, "swdg_forest_flags failed")
+    return out
+
+
+def forest_adapt(forest, lij, flags):
+    """the adapted, 2:1-balanced, Morton-ordered leaf set (host)"""
+    lij = np.ascontiguousarray(lij, dtype=np.int32)
+    flags = np.ascontiguousarray(flags, dtype=np.int8)
+    nout = _I64(0)
+    cap = 4 * len(lij) + 64
+    while True:
+        out = np.zeros((cap, 3), dtype=np.int32)
+        rc = load().swdg_forest_adapt(ctypes.byref(forest), len(lij), lij.ctypes.data_as(_P),
+                                      flags.ctypes.data_as(_P), cap, out.ctypes.data_as(_P),
+                                      ctypes.byref(nout))
+        if rc == 0:
+            return out[:nout.value]
+        if nout.value <= cap:
+            raise SwdgError(rc, "swdg_forest_adapt failed")
+        cap = nout.value
+
+
+def forest_mesh(forest, lij):
+    """x0y0 [n, 2], hxhy [n, 2], nbr [n, 4, 2] of an ordered leaf set (host)"""
+    lij = np.ascontiguousarray(lij, dtype=np.int32)
+    n = len(lij)
+    x0y0, hxhy = np.zeros((n, 2)), np.zeros((n, 2))
+    nbr = np.zeros((n, 4, 2), dtype=np.int32)
+    rc = load().swdg_forest_mesh(ctypes.byref(forest), n, lij.ctypes.data_as(_P),
+                                 x0y0.ctypes.data_as(_P), hxhy.ctypes.data_as(_P),
+                                 nbr.ctypes.data_as(_P))
+    if rc:
+        raise SwdgError(rc, "swdg_forest_mesh failed")
+    return x0y0, hxhy, nbr
 
 
 def residual_noalloc(cfg, n_cells, hxhy, nbr, tiles, pixels_per_side, pix_dtype, manning, state,
@@ -262,6 +325,31 @@ class Context:
         """every depth of cell K deepened by delta[K] (absolute, None = 0)"""
         p, where, keep = _buf(delta, np.float64)
         self._ck(load().swdg_set_bathymetry_offset(self.h, p, where))
+
+    # dynamic h-adaptation
+    def amr_setup(self, forest):
+        self.forest = forest
+        self._ck(load().swdg_amr_setup(self.h, ctypes.byref(forest)))
+
+    def amr_indicator(self, kind):
+        eta = np.empty(self.n)
+        self._ck(load().swdg_amr_indicator(self.h, kind, eta.ctypes.data_as(_P)))
+        return eta
+
+    def amr_adapt(self, theta_r, theta_c, eta=None, kind=0):
+        """adapt the mesh (Sec. 3.4); returns the report of swdg_amr_adapt"""
+        e = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
+        rep = np.zeros(6)
+        self._ck(load().swdg_amr_adapt(self.h, None if e is None else e.ctypes.data_as(_P), kind,
+                                       theta_r, theta_c, rep.ctypes.data_as(_P)))
+        self.n = int(rep[1])
+        return dict(zip(("cells_before", "cells_after", "refined", "coarsened", "Q", "tracer_Q"),
+                        rep.tolist()))
+
+    def amr_leaves(self):
+        out = np.zeros((self.n, 3), dtype=np.int32)
+        self._ck(load().swdg_amr_leaves(self.h, out.ctypes.data_as(_P)))
+        return out
 
     def adjoint_slots(self, n):
         """reserve n step records (see swdg_adjoint_slots)"""
