@@ -361,6 +361,50 @@ def adjoint_variant(args, stream, dev, world, nsteps=40, every=20):
             "gradients_finite": ok}
 
 
+def amr_variant(args, stream, dev, world, cycles=4, every=5):
+    """Dynamic h-adaptation on the lagoon (256 x 128 coarse cells of
+    195 x 234 m, two refinement levels, r = 2, 8192 x 4096 f32 raster, tide
+    on the south): every 5 steps the |grad c| indicator (Sec. 5), the
+    criteria of Sec. 3.4 (theta_r = 0.3, theta_c = 0.05), the forest
+    adaptation, the remap and the re-upload; the share of the adaptation in
+    the wall time and the accumulated |Q^n| relative to the initial mass."""
+    import torch
+    from paper_2505_18743_gb300 import swdg
+    wl = W.lagoon()
+    Xn, Yn = W.nodal_coordinates(wl.mesh, wl.degree)
+    wl.c = 0.5 + 0.5 * np.tanh((Xn - 25000.0) / 2000.0)  # a tracer front across the lagoon
+    ctx = swdg.Context.from_workload(wl, stream=stream.cuda_stream)
+    ctx.amr_setup(swdg.make_forest(256, 128, 0.0, 0.0, 50000.0 / 256, 30000.0 / 128, 2, 0.0,
+                                   (0, 0, 1, 0), (False, False)))
+    h0 = ctx.diagnostics()["mass"]
+    t = 0.0
+    t = ctx.step(2, -1.0, t)  # warm-up
+    step_ms, adapt_ms, cells, qsum, split = [], [], [wl.mesh.n], 0.0, []
+    for _ in range(cycles):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        t = ctx.step(every, -1.0, t)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        rep = ctx.amr_adapt(0.3, 0.05, kind=1)
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        step_ms.append(1e3 * (t1 - t0) / every)
+        adapt_ms.append(1e3 * (t2 - t1))
+        split.append([round(rep[k], 2) for k in ("indicator_ms", "forest_ms", "rebuild_ms")])
+        cells.append(int(rep["cells_after"]))
+        qsum += abs(rep["Q"])
+    ctx.close()
+    steps_total = sum(step_ms) * every
+    return {"workload": "lagoon 256x128 coarse cells, 2 levels, r=2, |grad c| indicator, "
+                        "adaptation every 5 steps",
+            "cells": cells, "step_ms": [round(x, 3) for x in step_ms],
+            "adapt_ms": [round(x, 2) for x in adapt_ms],
+            "adapt_split_ms_indicator_forest_rebuild": split,
+            "adaptation_share_of_wall_time": sum(adapt_ms) / (steps_total + sum(adapt_ms)),
+            "sum_abs_Q_over_initial_mass": qsum / h0}
+
+
 def run_gpu(args, rank, world, local):
     import torch
     from paper_2505_18743_gb300 import swdg
@@ -478,6 +522,7 @@ def run_gpu(args, rank, world, local):
     if not args.no_variants and prec == 0:
         variants["ensemble"] = ensemble_variant(args, stream, dev, world)
         variants["adjoint"] = adjoint_variant(args, stream, dev, world)
+        variants["amr"] = amr_variant(args, stream, dev, world)
 
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -332,11 +332,13 @@ int swdg_forest_mesh(const swdg_forest* f, int64_t n, const int32_t* lij, double
  * parent the L2 projection of its children -- conservative for every field),
  * rebuilds mesh and bathymetry (from the uploaded raster; every new cell must
  * span whole pixels) and carries the per-cell Manning and diffusivity values
- * over (children inherit, a parent takes the children's mean).  report [6]
+ * over (children inherit, a parent takes the children's mean).  report [9]
  * (may be NULL): cells before, cells after, leaves refined, parents formed,
  * Q^n = the change of the total wet mass sum_K Hbar_K across the adaptation
- * (Eq. mass-loss: with a conservative remap, the bathymetry-integral term)
- * and the change of the tracer mass.  Launch shapes return to their defaults
+ * (Eq. mass-loss: with a conservative remap, the bathymetry-integral term),
+ * the change of the tracer mass, and the milliseconds spent on the
+ * indicator, on the forest (host) and on the remap and rebuild.  Launch
+ * shapes return to their defaults
  * and a bathymetry offset is dropped.  Not for ensembles. */
 int swdg_amr_setup(swdg_ctx* ctx, const swdg_forest* f);
 int swdg_amr_indicator(swdg_ctx* ctx, int kind, double* eta);

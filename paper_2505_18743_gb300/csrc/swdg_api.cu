@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1952,6 +1953,11 @@ int swdg_amr_adapt(swdg_ctx* ctx, const double* eta_in, int kind, double theta_r
         return fail(ctx, SWDG_EINVAL, "amr_adapt: bad thresholds");
     const int64_t n = ctx->n;
     const int nd = ctx->nd;
+    using clk = std::chrono::steady_clock;
+    auto ms = [](clk::time_point a, clk::time_point b) {
+        return std::chrono::duration<double, std::milli>(b - a).count();
+    };
+    const clk::time_point c0 = clk::now();
     std::vector<double> eta(n);
     if (eta_in) {
         for (int64_t k = 0; k < n; ++k) {
@@ -1963,19 +1969,16 @@ int swdg_amr_adapt(swdg_ctx* ctx, const double* eta_in, int kind, double theta_r
         int rc = swdg_amr_indicator(ctx, kind, eta.data());
         if (rc) return rc;
     }
+    const clk::time_point c1 = clk::now();
     Forest F{ctx->forest};
     std::vector<int8_t> fl(n);
     F.flags(ctx->leaves, eta.data(), theta_r, theta_c, fl.data());
     std::vector<Leaf> nl = F.adapt(ctx->leaves, fl.data());
     const int64_t n2 = (int64_t)nl.size();
     // the plan of every new cell
-    std::unordered_map<uint64_t, int32_t> old;
-    old.reserve(n * 2);
-    auto key = [](int l, int64_t i, int64_t j) {
-        return ((uint64_t)l << 58) | ((uint64_t)i << 29) | (uint64_t)j;
-    };
+    CellIndex old(ctx->forest);
     for (int64_t k = 0; k < n; ++k)
-        old[key(ctx->leaves[k].l, ctx->leaves[k].i, ctx->leaves[k].j)] = (int32_t)k;
+        old.set(ctx->leaves[k].l, ctx->leaves[k].i, ctx->leaves[k].j, (int32_t)k);
     std::vector<int8_t> type(n2);
     std::vector<int32_t> src(4 * n2, 0);
     std::vector<double> rel(3 * n2, 0.0);
@@ -1983,23 +1986,23 @@ int swdg_amr_adapt(swdg_ctx* ctx, const double* eta_in, int kind, double theta_r
     bool same = n2 == n;
     for (int64_t k = 0; k < n2; ++k) {
         const Leaf c = nl[k];
-        auto it = old.find(key(c.l, c.i, c.j));
-        if (it != old.end()) {
+        int32_t v = old.get(c.l, c.i, c.j);
+        if (v >= 0) {
             type[k] = 0;
-            src[4 * k] = it->second;
-            if (it->second != k) same = false;
+            src[4 * k] = v;
+            if (v != k) same = false;
             continue;
         }
         same = false;
         int la = c.l - 1;
         int64_t ia = c.i >> 1, ja = c.j >> 1;
         for (; la >= 0; --la, ia >>= 1, ja >>= 1) {
-            it = old.find(key(la, ia, ja));
-            if (it != old.end()) break;
+            v = old.get(la, ia, ja);
+            if (v >= 0) break;
         }
         if (la >= 0) {
             type[k] = 1;
-            src[4 * k] = it->second;
+            src[4 * k] = v;
             const double s_ = 1.0 / (double)(1 << (c.l - la));
             rel[3 * k] = s_;
             rel[3 * k + 1] = c.i * s_ - (double)ia;
@@ -2010,10 +2013,12 @@ int swdg_amr_adapt(swdg_ctx* ctx, const double* eta_in, int kind, double theta_r
         ++npar;
         for (int b = 0; b < 2; ++b)
             for (int a = 0; a < 2; ++a) {
-                auto ch = old.find(key(c.l + 1, 2 * (int64_t)c.i + a, 2 * (int64_t)c.j + b));
-                if (ch == old.end())
+                const int32_t ch = c.l + 1 <= ctx->forest.max_level
+                                       ? old.get(c.l + 1, 2 * (int64_t)c.i + a, 2 * (int64_t)c.j + b)
+                                       : -1;
+                if (ch < 0)
                     return fail(ctx, SWDG_EINVAL, "amr_adapt: internal: a new parent without its children");
-                src[4 * k + a + 2 * b] = ch->second;
+                src[4 * k + a + 2 * b] = ch;
             }
     }
     for (int64_t k = 0; k < n; ++k)
@@ -2023,7 +2028,8 @@ int swdg_amr_adapt(swdg_ctx* ctx, const double* eta_in, int kind, double theta_r
     if (rc) return rc;
     if (same) {
         if (report) {
-            const double rr[6] = {(double)n, (double)n, 0.0, 0.0, 0.0, 0.0};
+            const double rr[9] = {(double)n, (double)n, 0.0, 0.0, 0.0, 0.0, ms(c0, c1),
+                                  ms(c1, clk::now()), 0.0};
             memcpy(report, rr, sizeof rr);
         }
         return SWDG_OK;
@@ -2045,6 +2051,7 @@ int swdg_amr_adapt(swdg_ctx* ctx, const double* eta_in, int kind, double theta_r
                             (long long)k);
         }
     }
+    const clk::time_point c2 = clk::now();
     // remap the state on the device
     int8_t* dtype_ = nullptr;
     int32_t* dsrc = nullptr;
@@ -2101,8 +2108,8 @@ int swdg_amr_adapt(swdg_ctx* ctx, const double* eta_in, int kind, double theta_r
     rc = swdg_diagnostics(ctx, d1);
     if (rc) return rc;
     if (report) {
-        const double rr[6] = {(double)n, (double)n2, (double)nref, (double)npar, d1[0] - d0[0],
-                              d1[1] - d0[1]};
+        const double rr[9] = {(double)n, (double)n2, (double)nref, (double)npar, d1[0] - d0[0],
+                              d1[1] - d0[1], ms(c0, c1), ms(c1, c2), ms(c2, clk::now())};
         memcpy(report, rr, sizeof rr);
     }
     return SWDG_OK;

@@ -28,8 +28,87 @@ bool Forest::wrap(int l, int64_t i, int64_t j, int64_t& ii, int64_t& jj) const {
     return true;
 }
 
+// a set of cells of the forest: one occupancy byte per cell of every level
+// while the levels fit in 256 MB (the usual case), else a hash set
+class CellSet {
+  public:
+    explicit CellSet(const swdg_forest& f) {
+        int64_t tot = 0;
+        for (int l = 0; l <= f.max_level; ++l) tot += ((int64_t)f.nx0 << l) * ((int64_t)f.ny0 << l);
+        dense_ = tot <= (int64_t)1 << 28;
+        if (dense_) {
+            grid_.resize(f.max_level + 1);
+            nx_.resize(f.max_level + 1);
+            for (int l = 0; l <= f.max_level; ++l) {
+                nx_[l] = (int64_t)f.nx0 << l;
+                grid_[l].assign((size_t)nx_[l] * ((int64_t)f.ny0 << l), 0);
+            }
+        }
+    }
+    bool count(uint64_t key) const {
+        if (!dense_) return hash_.count(key) != 0;
+        const int l = (int)(key >> 58);
+        if (l < 0 || l >= (int)grid_.size()) return false;
+        const int64_t i = (int64_t)((key >> 29) & ((1ull << 29) - 1)), j = (int64_t)(key & ((1ull << 29) - 1));
+        return grid_[l][(size_t)(i + nx_[l] * j)] != 0;
+    }
+    void insert(uint64_t key) {
+        if (!dense_) {
+            hash_.insert(key);
+            return;
+        }
+        const int l = (int)(key >> 58);
+        const int64_t i = (int64_t)((key >> 29) & ((1ull << 29) - 1)), j = (int64_t)(key & ((1ull << 29) - 1));
+        grid_[l][(size_t)(i + nx_[l] * j)] = 1;
+    }
+    void erase(uint64_t key) {
+        if (!dense_) {
+            hash_.erase(key);
+            return;
+        }
+        const int l = (int)(key >> 58);
+        const int64_t i = (int64_t)((key >> 29) & ((1ull << 29) - 1)), j = (int64_t)(key & ((1ull << 29) - 1));
+        grid_[l][(size_t)(i + nx_[l] * j)] = 0;
+    }
+
+  private:
+    bool dense_ = false;
+    std::vector<std::vector<uint8_t>> grid_;
+    std::vector<int64_t> nx_;
+    std::unordered_set<uint64_t> hash_;
+};
+
+CellIndex::CellIndex(const swdg_forest& f) {
+    int64_t tot = 0;
+    for (int l = 0; l <= f.max_level; ++l) tot += ((int64_t)f.nx0 << l) * ((int64_t)f.ny0 << l);
+    dense_ = tot <= (int64_t)1 << 26;
+    if (dense_) {
+        grid_.resize(f.max_level + 1);
+        nx_.resize(f.max_level + 1);
+        for (int l = 0; l <= f.max_level; ++l) {
+            nx_[l] = (int64_t)f.nx0 << l;
+            grid_[l].assign((size_t)nx_[l] * ((int64_t)f.ny0 << l), -1);
+        }
+    }
+}
+
+void CellIndex::set(int l, int64_t i, int64_t j, int32_t v) {
+    if (dense_) grid_[l][(size_t)(i + nx_[l] * j)] = v;
+    else hash_[pack(l, i, j)] = v;
+}
+
+int32_t CellIndex::get(int l, int64_t i, int64_t j) const {
+    if (l < 0) return -1;
+    if (dense_) {
+        if (l >= (int)grid_.size()) return -1;
+        return grid_[l][(size_t)(i + nx_[l] * j)];
+    }
+    auto it = hash_.find(pack(l, i, j));
+    return it == hash_.end() ? -1 : it->second;
+}
+
 // the leaf covering cell (l, i, j) if it is that cell or an ancestor
-static bool covering(const std::unordered_set<uint64_t>& S, int l, int64_t i, int64_t j, Leaf* out) {
+static bool covering(const CellSet& S, int l, int64_t i, int64_t j, Leaf* out) {
     while (l >= 0) {
         if (S.count(pack(l, i, j))) {
             if (out) *out = Leaf{l, (int32_t)i, (int32_t)j};
@@ -72,28 +151,33 @@ void Forest::flags(const std::vector<Leaf>& leaves, const double* eta, double th
 }
 
 std::vector<Leaf> Forest::adapt(const std::vector<Leaf>& leaves, const int8_t* fl) const {
-    std::unordered_set<uint64_t> S, marked;
-    S.reserve(leaves.size() * 2);
+    CellSet S(f), marked(f);
+    std::vector<uint64_t> live; // every key ever inserted into S (removed ones are skipped)
+    live.reserve(leaves.size() * 2);
+    auto add = [&](uint64_t key) {
+        S.insert(key);
+        live.push_back(key);
+    };
     for (size_t k = 0; k < leaves.size(); ++k) {
         const Leaf c = leaves[k];
         if (fl[k] == 1) {
             for (int b = 0; b < 2; ++b)
-                for (int a = 0; a < 2; ++a) S.insert(pack(c.l + 1, 2 * c.i + a, 2 * c.j + b));
+                for (int a = 0; a < 2; ++a) add(pack(c.l + 1, 2 * c.i + a, 2 * c.j + b));
         } else {
-            S.insert(pack(c.l, c.i, c.j));
+            add(pack(c.l, c.i, c.j));
         }
         if (fl[k] == -1) marked.insert(pack(c.l, c.i, c.j));
     }
     // four siblings, all leaves and all marked, merge into their parent
-    std::vector<uint64_t> done;
+    CellSet done(f);
     for (size_t k = 0; k < leaves.size(); ++k) {
         if (fl[k] != -1) continue;
         const Leaf c = leaves[k];
         const int l = c.l - 1;
         const int64_t pi = c.i >> 1, pj = c.j >> 1;
         const uint64_t pk = pack(l, pi, pj);
-        if (std::find(done.begin(), done.end(), pk) != done.end()) continue;
-        done.push_back(pk);
+        if (done.count(pk)) continue;
+        done.insert(pk);
         bool all = true;
         for (int b = 0; b < 2 && all; ++b)
             for (int a = 0; a < 2 && all; ++a) {
@@ -103,15 +187,16 @@ std::vector<Leaf> Forest::adapt(const std::vector<Leaf>& leaves, const int8_t* f
         if (!all) continue;
         for (int b = 0; b < 2; ++b)
             for (int a = 0; a < 2; ++a) S.erase(pack(l + 1, 2 * pi + a, 2 * pj + b));
-        S.insert(pk);
+        add(pk);
     }
     // 2:1 balance: split every leaf whose face neighbour region holds leaves
     // two or more levels finer, until none does
     bool changed = true;
     while (changed) {
         changed = false;
-        std::vector<uint64_t> cur(S.begin(), S.end());
-        for (uint64_t key : cur) {
+        const size_t nlive = live.size();
+        for (size_t q = 0; q < nlive; ++q) {
+            const uint64_t key = live[q];
             if (!S.count(key)) continue;
             const int l = (int)(key >> 58);
             const int64_t i = (int64_t)((key >> 29) & ((1ull << 29) - 1)), j = (int64_t)(key & ((1ull << 29) - 1));
@@ -124,17 +209,20 @@ std::vector<Leaf> Forest::adapt(const std::vector<Leaf>& leaves, const int8_t* f
                 if (S.count(al[0]) && S.count(al[1])) continue;
                 S.erase(key);
                 for (int b = 0; b < 2; ++b)
-                    for (int a = 0; a < 2; ++a) S.insert(pack(l + 1, 2 * i + a, 2 * j + b));
+                    for (int a = 0; a < 2; ++a) add(pack(l + 1, 2 * i + a, 2 * j + b));
                 changed = true;
                 break;
             }
         }
     }
     std::vector<Leaf> out;
-    out.reserve(S.size());
-    for (uint64_t key : S)
+    CellSet seen(f);
+    for (uint64_t key : live) {
+        if (!S.count(key) || seen.count(key)) continue;
+        seen.insert(key);
         out.push_back(Leaf{(int)(key >> 58), (int32_t)((key >> 29) & ((1ull << 29) - 1)),
                            (int32_t)(key & ((1ull << 29) - 1))});
+    }
     order(out);
     return out;
 }
@@ -149,15 +237,19 @@ uint64_t Forest::morton(const Leaf& c) const {
 }
 
 void Forest::order(std::vector<Leaf>& leaves) const {
-    std::sort(leaves.begin(), leaves.end(),
-              [&](const Leaf& a, const Leaf& b) { return morton(a) < morton(b); });
+    std::vector<std::pair<uint64_t, Leaf>> kl(leaves.size());
+    for (size_t k = 0; k < leaves.size(); ++k) kl[k] = {morton(leaves[k]), leaves[k]};
+    std::sort(kl.begin(), kl.end(),
+              [](const std::pair<uint64_t, Leaf>& a, const std::pair<uint64_t, Leaf>& b) {
+                  return a.first < b.first;
+              });
+    for (size_t k = 0; k < leaves.size(); ++k) leaves[k] = kl[k].second;
 }
 
 void Forest::mesh(const std::vector<Leaf>& leaves, double* x0y0, double* hxhy, int32_t* nbr) const {
-    std::unordered_map<uint64_t, int32_t> index;
-    index.reserve(leaves.size() * 2);
+    CellIndex index(f);
     for (size_t k = 0; k < leaves.size(); ++k)
-        index[pack(leaves[k].l, leaves[k].i, leaves[k].j)] = (int32_t)k;
+        index.set(leaves[k].l, leaves[k].i, leaves[k].j, (int32_t)k);
     for (size_t k = 0; k < leaves.size(); ++k) {
         const Leaf c = leaves[k];
         const double hx = f.hx0 / (double)(1 << c.l), hy = f.hy0 / (double)(1 << c.l);
@@ -173,22 +265,30 @@ void Forest::mesh(const std::vector<Leaf>& leaves, double* x0y0, double* hxhy, i
                 s[0] = -1 - f.tags[d];
                 continue;
             }
-            auto it = index.find(pack(c.l, ii, jj));
-            if (it != index.end()) {
-                s[0] = it->second;
+            int32_t v = index.get(c.l, ii, jj);
+            if (v >= 0) {
+                s[0] = v;
                 continue;
             }
-            if (c.l > 0) {
-                it = index.find(pack(c.l - 1, ii >> 1, jj >> 1));
-                if (it != index.end()) {
-                    s[0] = it->second;
-                    continue;
-                }
+            v = index.get(c.l - 1, ii >> 1, jj >> 1);
+            if (v >= 0) {
+                s[0] = v;
+                continue;
             }
-            uint64_t al[2];
-            along(c.l, ii, jj, DIR[d][0], DIR[d][1], al);
-            s[0] = index.at(al[0]);
-            s[1] = index.at(al[1]);
+            if (c.l + 1 > f.max_level) throw 1; // no finer leaves can exist: not balanced
+            int32_t v0, v1;
+            if (DIR[d][0] != 0) {
+                const int a = DIR[d][0] > 0 ? 0 : 1;
+                v0 = index.get(c.l + 1, 2 * ii + a, 2 * jj);
+                v1 = index.get(c.l + 1, 2 * ii + a, 2 * jj + 1);
+            } else {
+                const int b = DIR[d][1] > 0 ? 0 : 1;
+                v0 = index.get(c.l + 1, 2 * ii, 2 * jj + b);
+                v1 = index.get(c.l + 1, 2 * ii + 1, 2 * jj + b);
+            }
+            if (v0 < 0 || v1 < 0) throw 1; // the face is not 2:1 balanced
+            s[0] = v0;
+            s[1] = v1;
         }
     }
 }

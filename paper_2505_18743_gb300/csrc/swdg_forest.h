@@ -3,6 +3,7 @@
 // adaptation step.
 #pragma once
 #include <cstdint>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/swdg.h"
@@ -11,6 +12,21 @@ namespace swdg {
 
 struct Leaf {
     int32_t l, i, j; // level, column and row on the grid of that level
+};
+
+// index of the leaf that is cell (l, i, j), -1 if none: one int32 per cell
+// of every level while they fit in 256 MB, else a hash map
+class CellIndex {
+  public:
+    explicit CellIndex(const swdg_forest& f);
+    void set(int l, int64_t i, int64_t j, int32_t v);
+    int32_t get(int l, int64_t i, int64_t j) const;
+
+  private:
+    bool dense_ = false;
+    std::vector<std::vector<int32_t>> grid_;
+    std::vector<int64_t> nx_;
+    std::unordered_map<uint64_t, int32_t> hash_;
 };
 
 struct Forest {

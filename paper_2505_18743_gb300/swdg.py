@@ -339,12 +339,12 @@ class Context:
     def amr_adapt(self, theta_r, theta_c, eta=None, kind=0):
         """adapt the mesh (Sec. 3.4); returns the report of swdg_amr_adapt"""
         e = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
-        rep = np.zeros(6)
+        rep = np.zeros(9)
         self._ck(load().swdg_amr_adapt(self.h, None if e is None else e.ctypes.data_as(_P), kind,
                                        theta_r, theta_c, rep.ctypes.data_as(_P)))
         self.n = int(rep[1])
-        return dict(zip(("cells_before", "cells_after", "refined", "coarsened", "Q", "tracer_Q"),
-                        rep.tolist()))
+        return dict(zip(("cells_before", "cells_after", "refined", "coarsened", "Q", "tracer_Q",
+                         "indicator_ms", "forest_ms", "rebuild_ms"), rep.tolist()))
 
     def amr_leaves(self):
         out = np.zeros((self.n, 3), dtype=np.int32)
