@@ -176,6 +176,17 @@ int swdg_degree_switch(swdg_ctx* ctx, uint8_t* flags_out);
  * order) containing the point answers; see swdg_gather_gauges_member. */
 int swdg_gather_gauges(swdg_ctx* ctx, int n, const double* xy, double* zeta_out);
 
+/* Transpose of swdg_gather_gauges, for losses over gauge time series (the
+ * paper has no counterpart): adds gbar[g] times the derivative of the gauge
+ * value zeta(xy[g]) with respect to each nodal zeta value of its cell to
+ * zeta_b [n_cells][(r+1)^2] (host or device per where; xy [n][2] and gbar [n]
+ * are host arrays).  A constant (r_K = 0) cell is differentiated as its
+ * polynomial; a point outside the mesh adds nothing.  Both gauge calls locate
+ * the points on the host once and reuse the cells while the points and the
+ * mesh stay the same. */
+int swdg_gauges_vjp(swdg_ctx* ctx, int n, const double* xy, const double* gbar, double* zeta_b,
+                    int where);
+
 /* out[8] = total mass sum_K Hbar_K (Eq. positivity-7), tracer mass, min wet
  * depth over mass points, number of r_K = r cells, max Newton iterations of
  * the last step, positivity violations (cumulative), last dt, t.  On an

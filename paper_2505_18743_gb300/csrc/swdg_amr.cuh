@@ -181,4 +181,35 @@ __global__ void __launch_bounds__(32 * MAXWPB)
     }
 }
 
+// transpose of k_gauges: zb[k][a + (R+1) b] += gbar[g] lx_a(xi) ly_b(eta) for
+// the cell k holding gauge g (cell[g], or the first containing cell when cell
+// is null); a constant (r_K = 0) cell is differentiated as its polynomial.
+// One thread per gauge; gauges sharing a cell add atomically.
+template <int R>
+__global__ void k_gauges_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, int ng,
+                             const double* xy, const double* gbar, double* zb, const int32_t* cell) {
+    constexpr int ND1 = R + 1;
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ng) return;
+    const double x = xy[2 * gi], y = xy[2 * gi + 1];
+    int64_t k0 = 0, k1 = d.n;
+    if (cell) {
+        k0 = cell[gi];
+        k1 = k0 < 0 ? k0 : k0 + 1;
+    }
+    for (int64_t k = k0; k < k1; ++k) {
+        const double x0 = d.x0y0[2 * k], y0 = d.x0y0[2 * k + 1], hx = d.hxhy[2 * k],
+                     hy = d.hxhy[2 * k + 1];
+        if (x >= x0 && x <= x0 + hx && y >= y0 && y <= y0 + hy) {
+            const double xi = (x - x0) / hx, eta = (y - y0) / hy, g = gbar[gi];
+            for (int b = 0; b < ND1; ++b) {
+                const double ly = g * lagrange_at(tb.xs, ND1, b, eta);
+                for (int a = 0; a < ND1; ++a)
+                    atomicAdd(zb + k * ND1 * ND1 + a + ND1 * b, ly * lagrange_at(tb.xs, ND1, a, xi));
+            }
+            break;
+        }
+    }
+}
+
 } // namespace swdg

@@ -74,6 +74,13 @@ struct swdg_ctx {
     // device allocations
     double* nu_c = nullptr; // tracer numerical diffusivity per cell
     // dynamic h-adaptation: the forest, the leaf of every cell, the uploaded raster
+    // gauges: the cells of the last gauge set (located on the host once) and a
+    // device scratch for its points, values and cells
+    std::vector<double> gxy;
+    int64_t gk0 = 0, gk1 = 0;
+    double* gdev = nullptr;
+    int32_t* gcell = nullptr;
+    int gcap = 0;
     bool amr = false;
     swdg_forest forest{};
     std::vector<Leaf> leaves;
@@ -706,6 +713,12 @@ static void free_mesh(swdg_ctx* c) {
     cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->diag); cudaFree(c->finfo);
     cudaFree(c->adj);
     c->adj = nullptr;
+    cudaFree(c->gdev);
+    cudaFree(c->gcell);
+    c->gdev = nullptr;
+    c->gcell = nullptr;
+    c->gcap = 0;
+    c->gxy.clear();
     cudaFree(c->nu_c);
     c->nu_c = nullptr;
     c->d.nu_c = nullptr;
@@ -1481,19 +1494,86 @@ int swdg_degree_switch(swdg_ctx* ctx, uint8_t* flags_out) {
     return SWDG_OK;
 }
 
+// device copies of the gauge points xy [n][2] and of the cell holding each
+// (the first containing cell of [k0, k1), -1 outside); the points are located
+// again only when they or the range change
+static int gauges_prepare(swdg_ctx* ctx, int n, const double* xy, int64_t k0, int64_t k1) {
+    if (n > ctx->gcap) {
+        cudaFree(ctx->gdev);
+        cudaFree(ctx->gcell);
+        ctx->gdev = nullptr;
+        ctx->gcell = nullptr;
+        ctx->gcap = 0;
+        ctx->gxy.clear();
+        CK(cudaMalloc(&ctx->gdev, 3 * (size_t)n * sizeof(double)));
+        CK(cudaMalloc(&ctx->gcell, (size_t)n * sizeof(int32_t)));
+        ctx->gcap = n;
+    }
+    if ((int64_t)ctx->gxy.size() == 2 * (int64_t)n && ctx->gk0 == k0 && ctx->gk1 == k1 &&
+        memcmp(ctx->gxy.data(), xy, 2 * (size_t)n * sizeof(double)) == 0)
+        return SWDG_OK;
+    std::vector<int32_t> cell(n, -1);
+    for (int g = 0; g < n; ++g) {
+        const double x = xy[2 * g], y = xy[2 * g + 1];
+        for (int64_t k = k0; k < k1; ++k) {
+            const double x0 = ctx->x0y0_h[2 * k], y0 = ctx->x0y0_h[2 * k + 1];
+            if (x >= x0 && x <= x0 + ctx->hxhy_h[2 * k] && y >= y0 &&
+                y <= y0 + ctx->hxhy_h[2 * k + 1]) {
+                cell[g] = (int32_t)k;
+                break;
+            }
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->gdev, xy, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->st));
+    CK(cudaMemcpyAsync(ctx->gcell, cell.data(), (size_t)n * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->gxy.assign(xy, xy + 2 * (size_t)n);
+    ctx->gk0 = k0;
+    ctx->gk1 = k1;
+    return SWDG_OK;
+}
+
 int swdg_gather_gauges(swdg_ctx* ctx, int n, const double* xy, double* out) {
     if (!ctx) return SWDG_EINVAL;
     if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "gather_gauges: no state");
     if (n < 0 || (n > 0 && (!xy || !out))) return fail(ctx, SWDG_EINVAL, "gather_gauges: bad arguments");
     if (n == 0) return SWDG_OK;
-    double* buf = nullptr;
-    CK(cudaMalloc(&buf, 3 * (size_t)n * sizeof(double)));
-    CK(cudaMemcpyAsync(buf, xy, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-    ctx->L.gauges(ctx->d, ctx->tb, n, buf, buf + 2 * n, 0, ctx->n, ctx->st);
+    int rc = gauges_prepare(ctx, n, xy, 0, ctx->n);
+    if (rc) return rc;
+    ctx->L.gauges(ctx->d, ctx->tb, n, ctx->gdev, ctx->gdev + 2 * n, 0, ctx->n, ctx->gcell, ctx->st);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(out, buf + 2 * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(out, ctx->gdev + 2 * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    cudaFree(buf);
+    return SWDG_OK;
+}
+
+int swdg_gauges_vjp(swdg_ctx* ctx, int n, const double* xy, const double* gbar, double* zeta_b,
+                    int where) {
+    if (!ctx) return SWDG_EINVAL;
+    if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "gauges_vjp: no state");
+    if (n < 0 || (n > 0 && (!xy || !gbar || !zeta_b)) || (where != SWDG_HOST && where != SWDG_DEVICE))
+        return fail(ctx, SWDG_EINVAL, "gauges_vjp: bad arguments");
+    if (n == 0) return SWDG_OK;
+    const size_t fb = (size_t)ctx->n * ctx->nd * sizeof(double);
+    int rc = gauges_prepare(ctx, n, xy, 0, ctx->n);
+    if (rc) return rc;
+    double* gb = ctx->gdev + 2 * n;
+    CK(cudaMemcpyAsync(gb, gbar, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    double* zb = zeta_b;
+    double* tmp = nullptr;
+    if (where == SWDG_HOST) {
+        CK(cudaMalloc(&tmp, fb));
+        zb = tmp;
+        CK(cudaMemcpyAsync(zb, zeta_b, fb, cudaMemcpyHostToDevice, ctx->st));
+    }
+    ctx->L.gauges_vjp(ctx->d, ctx->tb, n, ctx->gdev, gb, zb, ctx->gcell, ctx->st);
+    CK(cudaGetLastError());
+    if (where == SWDG_HOST) CK(cudaMemcpyAsync(zeta_b, zb, fb, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    cudaFree(tmp);
     return SWDG_OK;
 }
 
@@ -2248,15 +2328,14 @@ int swdg_gather_gauges_member(swdg_ctx* ctx, int member, int n, const double* xy
     if (member < 0 || member >= ctx->nmemb || n < 0 || (n > 0 && (!xy || !out)))
         return fail(ctx, SWDG_EINVAL, "gather_gauges_member: bad arguments");
     if (n == 0) return SWDG_OK;
-    double* buf = nullptr;
-    CK(cudaMalloc(&buf, 3 * (size_t)n * sizeof(double)));
-    CK(cudaMemcpyAsync(buf, xy, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-    ctx->L.gauges(ctx->d, ctx->tb, n, buf, buf + 2 * n, ctx->first[member], ctx->first[member + 1],
-                  ctx->st);
+    int rc = gauges_prepare(ctx, n, xy, ctx->first[member], ctx->first[member + 1]);
+    if (rc) return rc;
+    ctx->L.gauges(ctx->d, ctx->tb, n, ctx->gdev, ctx->gdev + 2 * n, ctx->first[member],
+                  ctx->first[member + 1], ctx->gcell, ctx->st);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(out, buf + 2 * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(out, ctx->gdev + 2 * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    cudaFree(buf);
     return SWDG_OK;
 }
 

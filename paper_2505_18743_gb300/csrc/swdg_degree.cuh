@@ -39,8 +39,12 @@ struct Launchers {
         k_cell_diag<R, Pix, MODE><<<s.grid, 32 * s.wpb, diag_b * s.wpb, st>>>(d, tb, part);
     }
     static void gauges(const Dev& d, const Tables& tb, int ng, const double* xy, double* out,
-                       int64_t k0, int64_t k1, cudaStream_t st) {
-        k_gauges<R><<<(ng + 63) / 64, 64, 0, st>>>(d, tb, ng, xy, out, k0, k1);
+                       int64_t k0, int64_t k1, const int32_t* cell, cudaStream_t st) {
+        k_gauges<R><<<(ng + 63) / 64, 64, 0, st>>>(d, tb, ng, xy, out, k0, k1, cell);
+    }
+    static void gauges_vjp(const Dev& d, const Tables& tb, int ng, const double* xy,
+                           const double* gbar, double* zb, const int32_t* cell, cudaStream_t st) {
+        k_gauges_vjp<R><<<(ng + 63) / 64, 64, 0, st>>>(d, tb, ng, xy, gbar, zb, cell);
     }
     static void residual_vjp(const Dev& d, const Tables& tb, const double* u, const uint8_t* cm,
                              const double* rbar, double* ubar, double* nbar, double* dbar,
@@ -101,6 +105,7 @@ struct Launchers {
         L->masks = &masks;
         L->cell_diag = &cell_diag;
         L->gauges = &gauges;
+        L->gauges_vjp = &gauges_vjp;
         L->residual_vjp = &residual_vjp;
         L->stage_vjp = &stage_vjp;
         L->begin_vjp = &begin_vjp;

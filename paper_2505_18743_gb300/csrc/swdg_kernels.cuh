@@ -1458,13 +1458,19 @@ __global__ void __launch_bounds__(32 * MAXWPB)
 // ---------------------------------------------------------------------------
 template <int R>
 __global__ void k_gauges(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, int ng,
-                         const double* xy, double* out, int64_t k0, int64_t k1) {
+                         const double* xy, double* out, int64_t k0, int64_t k1,
+                         const int32_t* cell) {
     constexpr int ND1 = R + 1, ND = ND1 * ND1;
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= ng) return;
     const double x = xy[2 * gi], y = xy[2 * gi + 1];
     double v = NAN;
-    for (int64_t k = k0; k < k1; ++k) { // the cells searched: [k0, k1)
+    // the cells searched: [k0, k1), or only the one located on the host (cell[gi], -1: none)
+    if (cell) {
+        k0 = cell[gi];
+        k1 = k0 < 0 ? k0 : k0 + 1;
+    }
+    for (int64_t k = k0; k < k1; ++k) {
         const double x0 = d.x0y0[2 * k], y0 = d.x0y0[2 * k + 1], hx = d.hxhy[2 * k],
                      hy = d.hxhy[2 * k + 1];
         if (x >= x0 && x <= x0 + hx && y >= y0 && y <= y0 + hy) {

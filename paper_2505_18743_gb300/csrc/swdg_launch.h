@@ -25,8 +25,12 @@ struct Launch {
     void (*stage)(const Dev&, const Tables&, const StageArgs&, Shape, cudaStream_t);
     void (*masks)(const Dev&, int buf, Shape, cudaStream_t);
     void (*cell_diag)(const Dev&, const Tables&, double* part, Shape, cudaStream_t);
+    // zeta at gauge points (cell: the cell of each point, -1 none; null: search [k0, k1))
     void (*gauges)(const Dev&, const Tables&, int ng, const double* xy, double* out, int64_t k0,
-                   int64_t k1, cudaStream_t);
+                   int64_t k1, const int32_t* cell, cudaStream_t);
+    // its transpose: zb [n][nd] += gbar [ng] times the interpolation weights
+    void (*gauges_vjp)(const Dev&, const Tables&, int ng, const double* xy, const double* gbar,
+                       double* zb, const int32_t* cell, cudaStream_t);
     // discrete adjoint of the residual (FP64): rbar [6][n][nd] -> ubar [4][n][nd],
     // nbar [n] (Manning), dbar [n] (bathymetry offset)
     void (*residual_vjp)(const Dev&, const Tables&, const double* u, const uint8_t* cmask,

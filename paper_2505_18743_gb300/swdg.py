@@ -80,6 +80,7 @@ SIGNATURES = {
     "swdg_step_profile": (_I, [_P, _I, _D, ctypes.POINTER(_D), _P]),
     "swdg_degree_switch": (_I, [_P, _P]),
     "swdg_gather_gauges": (_I, [_P, _I, _P, _P]),
+    "swdg_gauges_vjp": (_I, [_P, _I, _P, _P, _P, _I]),
     "swdg_diagnostics": (_I, [_P, _P]),
     "swdg_residual_noalloc": (_I, [ctypes.POINTER(swdg_config), _I64, _P, _P, _P, _I, _I, _P, _P,
                                    _P, _P, _P, _P, _D, _P, _P, ctypes.c_char_p, _I]),
@@ -419,6 +420,19 @@ class Context:
         self._ck(load().swdg_gather_gauges(self.h, len(xy), xy.ctypes.data_as(_P),
                                            out.ctypes.data_as(_P)))
         return out
+
+    def gauges_vjp(self, xy, gbar, zeta_b):
+        """zeta_b (host array or CUDA tensor [n, nd], updated in place) += the
+        transpose of the gauge interpolation at xy [ng, 2] applied to gbar [ng]"""
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        g = np.ascontiguousarray(gbar, dtype=np.float64)
+        if g.shape != (len(xy),):
+            raise ValueError("gbar must have one value per gauge")
+        p, where, keep = _buf(zeta_b, np.float64)
+        if keep is not zeta_b:
+            raise ValueError("zeta_b must be a contiguous float64 array or tensor")
+        self._ck(load().swdg_gauges_vjp(self.h, len(xy), xy.ctypes.data_as(_P),
+                                        g.ctypes.data_as(_P), p, where))
 
     DIAG_KEYS = ("mass", "tracer_mass", "min_h", "r_cells", "newton_max",
                  "positivity_violations", "dt", "t")

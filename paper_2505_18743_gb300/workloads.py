@@ -265,6 +265,29 @@ def tidal_beach(seed: int = DEFAULT_SEED, n: int = 256, pix: int = 16, degree: i
                     manning=man, steps=1000)
 
 
+def gauge_misfit_case(seed: int = DEFAULT_SEED, ngauges: int = 50, window=(128, 64, 128, 128),
+                      pix: int = 16, dtype=np.float64):
+    """The adjoint case: a 128 x 128-cell, r = 2 crop of the beach (16 x 16 px
+    per cell, cells 128..255 x 64..191, the shoreline band included) flooded
+    0.3 m with a 0.2 m hump offshore, ``ngauges`` seeded gauges in wet cells
+    (offshore of x = 18.5 km, one per cell, at uniform offsets within the
+    cell's middle 80 %), and a truth Manning field 0.02 (1 + 0.3 (2 s - 1))
+    with s a smooth field in [0, 1] (a +-30 % perturbation).  The pixel depths
+    are the beach's float32 values held as float64, so that a per-cell
+    bathymetry offset moves them without rounding.
+    Returns (workload, gauge xy [ngauges, 2], truth Manning [n])."""
+    wl = tidal_beach(seed, window=window, degree=2, pix=pix, dtype=dtype)
+    Xn, Yn = nodal_coordinates(wl.mesh, wl.degree)
+    wl.zeta = 0.3 + 0.2 * np.exp(-((Xn - 16000.0) ** 2 + (Yn - 7000.0) ** 2) / 1500.0 ** 2)
+    rng = np.random.default_rng(seed + 5)
+    xc = wl.mesh.x0y0 + 0.5 * wl.mesh.hxhy
+    wet = np.nonzero(xc[:, 0] < 18500.0)[0]
+    cells = rng.choice(wet, ngauges, replace=False)
+    xy = wl.mesh.x0y0[cells] + rng.uniform(0.1, 0.9, (ngauges, 2)) * wl.mesh.hxhy[cells]
+    pert = smooth_field(np.random.default_rng(seed + 6), xc[:, 0], xc[:, 1], 20000.0)
+    return wl, xy, wl.manning * (1.0 + 0.3 * (2.0 * pert - 1.0))
+
+
 def beach_ensemble(seed: int = DEFAULT_SEED, members: int = 64, sizes=(32, 64, 128, 256),
                    pix: int = 8, degree: int = 2, L: float = 20000.0, dtype=np.float32):
     """Ensemble of independent tidal beaches (a parameter sweep): member m,
