@@ -60,19 +60,17 @@ def units_per_step(wl):
 # FP64 flops one launch performs per cell on this workload: active-lane
 # 2 DFMA + DMUL + DADD counted by ncu (profiles/fp64_ops_tidal_beach_256x256_r3.md).
 # These kernels are bound by the FP64 pipe: GB300's FP64 rate is the roofline.
-FLOPS_PER_CELL = {"step_begin": 2187, "residual": 12680, "stage_2": 9701, "stage_3": 10485,
-                  "final": 8181}
+FLOPS_PER_CELL = {"step_begin": 2187, "residual_1": 12467, "residual_2": 13009,
+                  "residual_3": 13010, "stage_2": 9858, "stage_3": 10642, "final": 8338}
 # the FP32-bulk kernels' FP64 flops (their FP32 work runs on the 60x faster FP32 pipe)
-FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "residual": 3831, "stage_2": 6371,
-                           "stage_3": 6620, "final": 6400}
+FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "residual_1": 3618, "residual_2": 4160,
+                           "residual_3": 4161, "stage_2": 6566, "stage_3": 6815, "final": 6595}
 # DRAM bytes per launch from an ncu capture of the current kernels (FP64 path);
 # {} (traffic null) whenever the kernels changed after the capture
-DRAM_BYTES_PER_LAUNCH = {}
+DRAM_BYTES_PER_LAUNCH = {"step_begin": 59226112, "residual_1": 95480576, "residual_2": 96324096,
+                         "residual_3": 96815872, "stage_2": 156174336, "stage_3": 248689920,
+                         "final": 253510400}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
-
-
-def slot_kind(slot):
-    return "residual" if slot.startswith("residual") else slot
 
 
 def algorithmic_bytes_per_cell(kernel, r=3, P=16, pix_bytes=4, nres=3):
@@ -463,13 +461,13 @@ def run_gpu(args, rank, world, local):
              (dom_fn == "k_step_begin" and k == "step_begin")]
     avg_ms = sum(per_launch[k] for k in slots) / len(slots)
     table = FLOPS_PER_CELL if prec == 0 else FLOPS_PER_CELL_FP32BULK
-    flops = sum(table[slot_kind(k)] for k in slots) / len(slots) * wl.mesh.n
+    flops = sum(table[k] for k in slots) / len(slots) * wl.mesh.n
     ach = flops / (avg_ms / 1e3) / 1e12
     pk, src = peaks()
     nres = {"stage_2": 1, "stage_3": 2, "stage_4": 3, "final": STAGES}
     bpc = sum(algorithmic_bytes_per_cell(k, nres=nres.get(k, STAGES)) for k in slots) / len(slots)
     hbm_ach = bpc * wl.mesh.n / (avg_ms / 1e3) / 1e9
-    traffic = [(DRAM_BYTES_PER_LAUNCH if prec == 0 else {}).get(slot_kind(k)) for k in slots]
+    traffic = [(DRAM_BYTES_PER_LAUNCH if prec == 0 else {}).get(k) for k in slots]
     roof = {"bound": "alu", "kernel": dom_fn, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
             "traffic": (sum(traffic) / len(traffic)) if all(x is not None for x in traffic) else None,
