@@ -910,16 +910,21 @@ __device__ void chol_subst_f(const float* M, const float* inv, float* b, int lan
 }
 
 // FP32 copy of M_(a,b),(c,d) = sum c_{al,be} Bm[al][a] Bm[al][c] Bm[be][b] Bm[be][d]
+// from the FP32 basis table and one FP32 copy of the weights cw (conversions
+// run on the FP64 pipe: converting inside the sums would cost one per term)
 template <int ND1, int NM>
 __device__ __forceinline__ void assemble_mass_f(const Tables& tb, const double* cw, float* Y,
                                                 float* M, int lane) {
     constexpr int ND = ND1 * ND1;
+    static_assert(NM * NM <= ND * ND, "the weights are staged in M");
+    float* cwf = M; // M is written only by the second pass
+    for (int p = lane; p < NM * NM; p += 32) cwf[p] = (float)cw[p];
+    __syncwarp();
     for (int i = lane; i < ND1 * ND1 * NM; i += 32) {
         const int a = i / (ND1 * NM), r_ = i % (ND1 * NM), c = r_ / NM, be = r_ % NM;
         float s = 0.0f;
 #pragma unroll
-        for (int al = 0; al < NM; ++al)
-            s += (float)cw[al + NM * be] * (float)tb.Bm[al][a] * (float)tb.Bm[al][c];
+        for (int al = 0; al < NM; ++al) s += cwf[al + NM * be] * tb.BmF[al][a] * tb.BmF[al][c];
         Y[i] = s;
     }
     __syncwarp();
@@ -929,7 +934,7 @@ __device__ __forceinline__ void assemble_mass_f(const Tables& tb, const double* 
         float s = 0.0f;
 #pragma unroll
         for (int be = 0; be < NM; ++be)
-            s += Y[(a * ND1 + c) * NM + be] * (float)tb.Bm[be][b] * (float)tb.Bm[be][dd];
+            s += Y[(a * ND1 + c) * NM + be] * tb.BmF[be][b] * tb.BmF[be][dd];
         M[i] = s;
     }
     __syncwarp();
