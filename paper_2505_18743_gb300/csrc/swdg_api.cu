@@ -81,6 +81,11 @@ struct swdg_ctx {
     double* gdev = nullptr;
     int32_t* gcell = nullptr;
     int gcap = 0;
+    // face points of the residual, each evaluated once (k_faces): the job
+    // list and the per-cell flux slots
+    int64_t* fjobs = nullptr;
+    double* fflux = nullptr;
+    int64_t njobs = 0;
     bool amr = false;
     swdg_forest forest{};
     std::vector<Leaf> leaves;
@@ -719,6 +724,14 @@ static void free_mesh(swdg_ctx* c) {
     c->gcell = nullptr;
     c->gcap = 0;
     c->gxy.clear();
+    cudaFree(c->fjobs);
+    cudaFree(c->fflux);
+    c->fjobs = nullptr;
+    c->fflux = nullptr;
+    c->njobs = 0;
+    c->d.fjobs = nullptr;
+    c->d.fflux = nullptr;
+    c->d.njobs = 0;
     cudaFree(c->nu_c);
     c->nu_c = nullptr;
     c->d.nu_c = nullptr;
@@ -875,6 +888,32 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     ctx->hxhy_h.assign(hxhy, hxhy + 2 * n);
     ctx->finfo_h = fi;
     ctx->nbr_h.assign(nbr, nbr + 8 * n);
+    {
+        // face jobs: every (cell, face, half, GLL point) whose cell is the lower
+        // index of the face, or whose face is on the boundary (or is its own
+        // neighbour), in cell order
+        const int NM = ctx->R + 2;
+        std::vector<int64_t> jobs;
+        jobs.reserve((size_t)n * 2 * NM + 64);
+        for (int64_t k = 0; k < n; ++k)
+            for (int f = 0; f < 4; ++f) {
+                const bool coarse = (fi[k * 4 + f] & 3) == FI_COARSE;
+                for (int h = 0; h < (coarse ? 2 : 1); ++h) {
+                    const int32_t s0 = nbr[k * 8 + f * 2];
+                    const int64_t nb = s0 < 0 ? -1 : (coarse && h ? nbr[k * 8 + f * 2 + 1] : s0);
+                    if (nb >= 0 && nb < k) continue;
+                    for (int al = 0; al < NM; ++al)
+                        jobs.push_back((k << 8) | (int64_t)f | ((int64_t)h << 2) | ((int64_t)al << 3));
+                }
+            }
+        ctx->njobs = (int64_t)jobs.size();
+        CK(cudaMalloc(&ctx->fjobs, jobs.size() * sizeof(int64_t)));
+        CK(cudaMalloc(&ctx->fflux, (size_t)n * 32 * NM * sizeof(double)));
+        CK(cudaMemcpyAsync(ctx->fjobs, jobs.data(), jobs.size() * sizeof(int64_t),
+                           cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemsetAsync(ctx->fflux, 0, (size_t)n * 32 * NM * sizeof(double), ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
     Dev& d = ctx->d;
     d.n = n;
     d.x0y0 = ctx->x0y0;
@@ -882,6 +921,9 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     d.ihxhy = ctx->ihxhy;
     d.nbr = ctx->nbr;
     d.finfo = ctx->finfo;
+    d.fflux = ctx->fflux;
+    d.fjobs = ctx->fjobs;
+    d.njobs = ctx->njobs;
     d.manning = ctx->manning;
     d.U = ctx->U;
     d.cmask = ctx->cmask;
@@ -1268,6 +1310,7 @@ int swdg_residual(swdg_ctx* ctx, double t, double* F, double* Gx, double* Gy, do
     if (!ctx->has_state) return fail(ctx, SWDG_ESTATE, "residual: no state");
     int rc = put_time(ctx, t, -1.0);
     if (rc) return rc;
+    if (ctx->d.fflux) ctx->L.faces(ctx->d, ctx->tb, 0, 0.0, 0, ctx->st);
     ctx->L.residual(ctx->d, ctx->tb, 0, 0, 0.0, 0, ctx->shp[KK_RESIDUAL], ctx->st);
     CK(cudaGetLastError());
     double* dst[6] = {F, Gx, Gy, R, Lx, Ly};
@@ -1287,6 +1330,7 @@ int swdg_cfl_dt(swdg_ctx* ctx, double t, double* dt) {
     int rc = put_clocks(ctx, t, 1);
     if (!rc) rc = put_fixed_dt(ctx, -1.0);
     if (rc) return rc;
+    if (ctx->d.fflux) ctx->L.faces(ctx->d, ctx->tb, 0, 0.0, 1, ctx->st);
     ctx->L.residual(ctx->d, ctx->tb, 0, 0, 0.0, 1, ctx->shp[KK_RESIDUAL], ctx->st);
     CK(cudaGetLastError());
     std::vector<Member> mh;
@@ -1369,6 +1413,7 @@ static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr, int rec_s
             keep_flags(l);
         }
         mark(1 + l, 0);
+        if (d.fflux) ctx->L.faces(d, ctx->tb, l, d.c[l], l == 0 ? 1 : 0, ctx->st);
         ctx->L.residual(d, ctx->tb, l, l, d.c[l], l == 0 ? 1 : 0, ctx->shp[KK_RESIDUAL], ctx->st);
         mark(1 + l, 1);
     }

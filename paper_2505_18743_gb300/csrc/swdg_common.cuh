@@ -134,6 +134,11 @@ struct Dev {
     int bc_kind[MXTAG];
     double bc_amp[MXTAG], bc_per[MXTAG], bc_ph[MXTAG];
     double a[MXS][MXS], at[MXS][MXS], b[MXS], bt[MXS], c[MXS];
+    // face points evaluated once by k_faces (null fflux: the residual
+    // integrates its faces itself)
+    double* fflux;        // [cell][4 fields][4 faces][2 halves][NM]
+    const int64_t* fjobs; // k << 8 | f | h << 2 | al << 3, k the lower index of the face
+    int64_t njobs;
 };
 
 // ---------------------------------------------------------------------------

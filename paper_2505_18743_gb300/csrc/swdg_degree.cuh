@@ -26,6 +26,12 @@ struct Launchers {
         k_residual<R, Pix, MODE, B><<<s.grid, 32 * s.wpb, res_b * s.wpb, st>>>(d, tb, buf, stage,
                                                                               c_stage, want_dt);
     }
+    static void faces(const Dev& d, const Tables& tb, int buf, double c_stage, int want_dt,
+                      cudaStream_t st) {
+        if (d.njobs <= 0) return;
+        const int64_t blocks = std::min<int64_t>((d.njobs + 255) / 256, 152 * 16);
+        k_faces<R, Pix, MODE, B><<<(int)blocks, 256, 0, st>>>(d, tb, buf, c_stage, want_dt);
+    }
     static void step_begin(const Dev& d, const Tables& tb, int do_switch, Shape s, cudaStream_t st) {
         k_step_begin<R, Pix, MODE><<<s.grid, 32 * s.wpb, begin_b * s.wpb, st>>>(d, tb, do_switch);
     }
@@ -100,6 +106,7 @@ struct Launchers {
     }
     static void fill(Launch* L) {
         L->residual = &residual;
+        L->faces = &faces;
         L->step_begin = &step_begin;
         L->stage = &stage;
         L->masks = &masks;

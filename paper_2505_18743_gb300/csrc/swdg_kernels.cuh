@@ -290,6 +290,116 @@ __device__ __forceinline__ const B (*tab_or(const double (*d)[MXN], const float 
 // tracer test integrals stay FP64 (so mass, tracer mass and c = 1 are kept to
 // FP64 round-off and the lake at rest exactly); the momentum, friction and
 // flux arithmetic is FP32.
+// one face point (Sec. 3.2): the Rusanov flux with the hydrostatic
+// reconstruction at GLL point al of half h of face f of cell k, whose state
+// (4 fields, stride ustride) is uk with constant-field mask cm.  An interior
+// point returns the flux of the canonical side order (the lower cell index is
+// side A, so both cells of a face get bit-identical values) in raw, with the
+// pressure term pres, own_first = (k is side A) and the neighbour nb; a
+// boundary point returns k's final flux in raw (bnd = true, nb = -1).  lam is
+// the wave speed bound of the point.
+template <int R, typename Pix, int MODE, typename B>
+__device__ __forceinline__ void face_point(const Dev& d, const Tables& tb, int64_t k, const double* uk,
+                                           size_t ustride, unsigned cm, int buf, int f, int h, int al,
+                                           unsigned info, double hx, double hy, int mem, double t,
+                                           B raw[4], B& pres, B& lam, bool& own_first, bool& bnd,
+                                           int64_t& nb_out) {
+    using S = Sz<R>;
+    using ST = Site<R, Pix, MODE>;
+    constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM;
+    const int64_t n = d.n;
+    const B gB = (B)d.g, epsB = (B)d.eps;
+    const auto BmB = tab_or<B>(tb.Bm, tb.BmF);
+    const bool coarse = (info & 3) == FI_COARSE, fine = (info & 3) == FI_FINE;
+    const int half = (int)(info >> 2);
+    const double nx = (f == 0) ? -1.0 : (f == 1) ? 1.0 : 0.0;
+    const double ny = (f == 2) ? -1.0 : (f == 3) ? 1.0 : 0.0;
+    double zm;
+    B tm[3];
+    face_trace_mixed<ND1, B>(uk, ustride, cm, f, coarse ? tb.BmH[h] : tb.Bm,
+                             coarse ? tab_or<B>(tb.BmH[h], tb.BmHF[h]) : BmB, al, zm, tm);
+    int ia, ib;
+    face_site_index<NM>(f, al, ia, ib);
+    auto own_V = [&](double eta) {
+        double V, A;
+        if (coarse) ST::VA_half(d, k, f, h, al, eta, V, A);
+        else ST::VA(d, tb, k, SET_MASS, ia, ib, eta, V, A);
+        return V;
+    };
+    const int32_t s0 = d.nbr[k * 8 + f * 2];
+    const double hm = own_V(zm);
+    double zp, hp, hsm, hsp;
+    B tp[3];
+    if (s0 >= 0) {
+        const int64_t nb = coarse ? (int64_t)(h ? d.nbr[k * 8 + f * 2 + 1] : s0) : (int64_t)s0;
+        const int fo = f ^ 1;
+        face_trace_mixed<ND1, B>(ufield(d, buf, 0, ND) + nb * ND, (size_t)n * ND,
+                                 d.cmask[(size_t)buf * n + nb], fo, fine ? tb.BmH[half] : tb.Bm,
+                                 fine ? tab_or<B>(tb.BmH[half], tb.BmHF[half]) : BmB, al, zp, tp);
+        int ja, jb;
+        face_site_index<NM>(fo, al, ja, jb);
+        auto nb_V = [&](double eta) {
+            double V, A;
+            if (fine) ST::VA_half(d, nb, fo, half, al, eta, V, A);
+            else ST::VA(d, tb, nb, SET_MASS, ja, jb, eta, V, A);
+            return V;
+        };
+        hp = nb_V(zp);
+        hsm = fmin(hm, nb_V(zm)); // min(V-(zeta-), V+(zeta-)), FP64
+        hsp = fmin(hp, own_V(zp)); // min(V+(zeta+), V-(zeta+)), FP64
+        own_first = k < nb;
+        if (own_first)
+            rusanov<B>(tm[0], tm[1], tm[2], (B)hm, (B)hsm, tp[0], tp[1], tp[2], (B)hp, (B)hsp,
+                       (B)(hsm - hsp), (B)nx, (B)ny, gB, epsB, raw, pres, lam);
+        else
+            rusanov<B>(tp[0], tp[1], tp[2], (B)hp, (B)hsp, tm[0], tm[1], tm[2], (B)hm, (B)hsm,
+                       (B)(hsp - hsm), (B)(-nx), (B)(-ny), gB, epsB, raw, pres, lam);
+        bnd = false;
+        nb_out = nb;
+    } else {
+        const int tag = -1 - s0;
+        zp = zm;
+        tp[0] = tm[0]; tp[1] = tm[1]; tp[2] = tm[2];
+        const bool tide = d.mbc ? d.mbc[mem].kind[tag] == 1 : d.bc_kind[tag] == 1;
+        if (tide) {
+            const double amp = d.mbc ? d.mbc[mem].amp[tag] : d.bc_amp[tag];
+            const double per = d.mbc ? d.mbc[mem].per[tag] : d.bc_per[tag];
+            const double ph = d.mbc ? d.mbc[mem].ph[tag] : d.bc_ph[tag];
+            zp = amp * sin(2.0 * M_PI * t / per + ph);
+        } else {
+            const B qn = tm[0] * (B)nx + tm[1] * (B)ny;
+            tp[0] = tm[0] - B(2) * qn * (B)nx;
+            tp[1] = tm[1] - B(2) * qn * (B)ny;
+        }
+        hp = own_V(zp); // ghost: same sub-grid operator
+        hsm = hm;
+        hsp = hp;
+        rusanov<B>(tm[0], tm[1], tm[2], (B)hm, (B)hsm, tp[0], tp[1], tp[2], (B)hp, (B)hsp,
+                   (B)(hsm - hsp), (B)nx, (B)ny, gB, epsB, raw, pres, lam);
+        raw[1] -= pres * (B)nx;
+        raw[2] -= pres * (B)ny;
+        own_first = true;
+        bnd = true;
+        nb_out = -1;
+    }
+}
+
+// the flux of an interior face point as seen from the cell whose face f it
+// is: the canonical flux with the sign of that side, and the pressure vector
+// g {{h*}} (h*A - h*B)/2 n_A, which is the same for both sides
+template <typename B>
+__device__ __forceinline__ void side_flux(const B raw[4], B pres, bool own_first, int f, B out[4]) {
+    const double nx = (f == 0) ? -1.0 : (f == 1) ? 1.0 : 0.0;
+    const double ny = (f == 2) ? -1.0 : (f == 3) ? 1.0 : 0.0;
+    const B sg = own_first ? B(1) : B(-1);
+    const B pnx = own_first ? pres * (B)nx : pres * (B)(-nx);
+    const B pny = own_first ? pres * (B)ny : pres * (B)(-ny);
+    out[0] = raw[0] * sg;
+    out[1] = sg * raw[1] - pnx;
+    out[2] = sg * raw[2] - pny;
+    out[3] = raw[3] * sg;
+}
+
 template <int R, typename Pix, int MODE, typename B>
 __global__ void __maxnreg__(96)
     k_residual(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, int buf,
@@ -495,98 +605,37 @@ __global__ void __maxnreg__(96)
             fi[f] = d.finfo ? d.finfo[k * 4 + f] : 0;
             base[f + 1] = base[f] + (((fi[f] & 3) == FI_COARSE) ? 2 : 1) * NM;
         }
-        for (int it = lane; it < base[4]; it += 32) {
-            const int f = (it >= base[1]) + (it >= base[2]) + (it >= base[3]);
-            const int r_ = it - base[f], h = r_ / NM, al = r_ % NM;
-            const unsigned info = fi[f];
-            const bool coarse = (info & 3) == FI_COARSE, fine = (info & 3) == FI_FINE;
-            const int half = (int)(info >> 2);
-            const double nx = (f == 0) ? -1.0 : (f == 1) ? 1.0 : 0.0;
-            const double ny = (f == 2) ? -1.0 : (f == 3) ? 1.0 : 0.0;
-            const double L = ((f < 2) ? hy : hx) * (coarse ? 0.5 : 1.0);
-            double zm;
-            B tm[3];
-            face_trace_mixed<ND1, B>(su, ND, cm, f, coarse ? tb.BmH[h] : tb.Bm,
-                                     coarse ? tab_or<B>(tb.BmH[h], tb.BmHF[h]) : BmB, al, zm, tm);
-            int ia, ib;
-            face_site_index<NM>(f, al, ia, ib);
-            auto own_V = [&](double eta) {
-                double V, A;
-                if (coarse) ST::VA_half(d, k, f, h, al, eta, V, A);
-                else ST::VA(d, tb, k, SET_MASS, ia, ib, eta, V, A);
-                return V;
-            };
-            const int32_t s0 = d.nbr[k * 8 + f * 2];
-            const double hm = own_V(zm);
-            double zp, hp, hsm, hsp;
-            B tp[3], out[4], pres, lam;
-            if (s0 >= 0) {
-                const int64_t nb = coarse ? (int64_t)(h ? d.nbr[k * 8 + f * 2 + 1] : s0) : (int64_t)s0;
-                const int fo = f ^ 1;
-                face_trace_mixed<ND1, B>(ufield(d, buf, 0, ND) + nb * ND, (size_t)n * ND,
-                                         d.cmask[(size_t)buf * n + nb], fo,
-                                         fine ? tb.BmH[half] : tb.Bm,
-                                         fine ? tab_or<B>(tb.BmH[half], tb.BmHF[half]) : BmB, al, zp,
-                                         tp);
-                int ja, jb;
-                face_site_index<NM>(fo, al, ja, jb);
-                auto nb_V = [&](double eta) {
-                    double V, A;
-                    if (fine) ST::VA_half(d, nb, fo, half, al, eta, V, A);
-                    else ST::VA(d, tb, nb, SET_MASS, ja, jb, eta, V, A);
-                    return V;
-                };
-                hp = nb_V(zp);
-                hsm = fmin(hm, nb_V(zm)); // min(V-(zeta-), V+(zeta-)), FP64
-                hsp = fmin(hp, own_V(zp)); // min(V+(zeta+), V-(zeta+)), FP64
-                // canonical side order: the lower cell index is side A, so both
-                // cells of the face compute bit-identical fluxes
-                const bool own_first = k < nb;
-                if (own_first)
-                    rusanov<B>(tm[0], tm[1], tm[2], (B)hm, (B)hsm, tp[0], tp[1], tp[2], (B)hp, (B)hsp,
-                               (B)(hsm - hsp), (B)nx, (B)ny, gB, epsB, out, pres, lam);
-                else
-                    rusanov<B>(tp[0], tp[1], tp[2], (B)hp, (B)hsp, tm[0], tm[1], tm[2], (B)hm, (B)hsm,
-                               (B)(hsp - hsm), (B)(-nx), (B)(-ny), gB, epsB, out, pres, lam);
-                const B sg = own_first ? B(1) : B(-1);
-                // the pressure vector g {{h*}} (h*A - h*B)/2 n_A is the same for both sides
-                const B pnx = own_first ? pres * (B)nx : pres * (B)(-nx);
-                const B pny = own_first ? pres * (B)ny : pres * (B)(-ny);
-                out[0] *= sg;
-                out[1] = sg * out[1] - pnx;
-                out[2] = sg * out[2] - pny;
-                out[3] *= sg;
-            } else {
-                const int tag = -1 - s0;
-                zp = zm;
-                tp[0] = tm[0]; tp[1] = tm[1]; tp[2] = tm[2];
-                const bool tide = d.mbc ? d.mbc[mem].kind[tag] == 1 : d.bc_kind[tag] == 1;
-                if (tide) {
-                    const double amp = d.mbc ? d.mbc[mem].amp[tag] : d.bc_amp[tag];
-                    const double per = d.mbc ? d.mbc[mem].per[tag] : d.bc_per[tag];
-                    const double ph = d.mbc ? d.mbc[mem].ph[tag] : d.bc_ph[tag];
-                    zp = amp * sin(2.0 * M_PI * t / per + ph);
-                } else {
-                    const B qn = tm[0] * (B)nx + tm[1] * (B)ny;
-                    tp[0] = tm[0] - B(2) * qn * (B)nx;
-                    tp[1] = tm[1] - B(2) * qn * (B)ny;
-                }
-                hp = own_V(zp); // ghost: same sub-grid operator
-                hsm = hm;
-                hsp = hp;
-                rusanov<B>(tm[0], tm[1], tm[2], (B)hm, (B)hsm, tp[0], tp[1], tp[2], (B)hp, (B)hsp,
-                           (B)(hsm - hsp), (B)nx, (B)ny, gB, epsB, out, pres, lam);
-                out[1] -= pres * (B)nx;
-                out[2] -= pres * (B)ny;
-            }
-            const double wl = L * tb.wm[al];
+        if (d.fflux) {
+            // the face fluxes of this cell, computed once per face point by k_faces
+            const double* F = d.fflux + k * (32 * NM);
+            for (int i = lane; i < 32 * NM; i += 32) fh[i] = F[i];
+        } else {
+            for (int it = lane; it < base[4]; it += 32) {
+                const int f = (it >= base[1]) + (it >= base[2]) + (it >= base[3]);
+                const int r_ = it - base[f], h = r_ / NM, al = r_ % NM;
+                const unsigned info = fi[f];
+                const bool coarse = (info & 3) == FI_COARSE;
+                B raw[4], pres, lam, out[4];
+                bool own_first, bnd;
+                int64_t nb;
+                face_point<R, Pix, MODE, B>(d, tb, k, su, ND, cm, buf, f, h, al, info, hx, hy, mem, t,
+                                            raw, pres, lam, own_first, bnd, nb);
+                if (bnd) {
 #pragma unroll
-            for (int cf = 0; cf < 4; ++cf)
-                fh[((cf * 4 + f) * 2 + h) * NM + al] = wl * (double)out[cf];
-            // lambda l / J for the positivity step (l = L, J = hx hy)
-            dtl = fmax(dtl, fmax((double)lam, 1e-12) * ((f < 2) ? ihx : ihy) * (coarse ? 0.5 : 1.0));
+                    for (int cf = 0; cf < 4; ++cf) out[cf] = raw[cf];
+                } else {
+                    side_flux<B>(raw, pres, own_first, f, out);
+                }
+                const double L = ((f < 2) ? hy : hx) * (coarse ? 0.5 : 1.0);
+                const double wl = L * tb.wm[al];
+#pragma unroll
+                for (int cf = 0; cf < 4; ++cf)
+                    fh[((cf * 4 + f) * 2 + h) * NM + al] = wl * (double)out[cf];
+                // lambda l / J for the positivity step (l = L, J = hx hy)
+                dtl = fmax(dtl, fmax((double)lam, 1e-12) * ((f < 2) ? ihx : ihy) * (coarse ? 0.5 : 1.0));
+            }
         }
-        if (want_dt) {
+        if (want_dt && !d.fflux) {
             const double m = warp_max(dtl);
             if (lane == 0) atomic_max_pos(&d.mb[mem].rmax, m);
         }
@@ -615,6 +664,91 @@ __global__ void __maxnreg__(96)
         for (int i = lane; i < 6 * ND; i += 32)
             rfield(d, stage, i / ND, ND)[k * ND + (i % ND)] = rs[i];
         __syncwarp();
+    }
+}
+
+// every face point of the mesh once (the residual's face integrals, Sec. 3.2):
+// job j of d.fjobs is cell k = job >> 8 with face f, half h and GLL point al
+// packed as f | h << 2 | al << 3, k the lower cell index of the face (or the
+// cell of a boundary face).  The flux as seen from each side, times that
+// side's quadrature weight, goes to the side's slots of d.fflux
+// ([cell][4 fields][4 faces][2 halves][NM], the residual's fh layout);
+// with want_dt the wave speed bound of each side (lambda l / J) raises its
+// member's rmax, as the residual does when it integrates the faces itself.
+// One job per lane.
+template <int R, typename Pix, int MODE, typename B>
+__global__ void __maxnreg__(128)
+    k_faces(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, int buf, double c_stage,
+            int want_dt) {
+    using S = Sz<R>;
+    constexpr int ND = S::ND, NM = S::NM, SL = 32 * NM;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t n = d.n;
+    for (int64_t j0 = gw * 32; j0 < d.njobs; j0 += nw * 32) { // warp-uniform bounds
+        const int64_t j = j0 + lane;
+        double v = 0.0;
+        int mem = -1;
+        if (j < d.njobs) {
+            const int64_t job = d.fjobs[j];
+            const int64_t k = job >> 8;
+            const int f = (int)(job & 3), h = (int)((job >> 2) & 1), al = (int)((job >> 3) & 31);
+            const unsigned info = d.finfo ? d.finfo[k * 4 + f] : 0;
+            const bool coarse = (info & 3) == FI_COARSE;
+            const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1];
+            const double ihx = d.ihxhy ? d.ihxhy[2 * k] : 1.0 / hx;
+            const double ihy = d.ihxhy ? d.ihxhy[2 * k + 1] : 1.0 / hy;
+            mem = member_of(d, k);
+            const double t = (c_stage == 0.0) ? d.mb[mem].t : d.mb[mem].t + c_stage * get_dt(d, mem);
+            B raw[4], pres, lam, out[4];
+            bool own_first, bnd;
+            int64_t nb;
+            face_point<R, Pix, MODE, B>(d, tb, k, ufield(d, buf, 0, ND) + k * ND, (size_t)n * ND,
+                                        d.cmask[(size_t)buf * n + k], buf, f, h, al, info, hx, hy,
+                                        mem, t, raw, pres, lam, own_first, bnd, nb);
+            if (bnd) {
+#pragma unroll
+                for (int cf = 0; cf < 4; ++cf) out[cf] = raw[cf];
+            } else {
+                side_flux<B>(raw, pres, own_first, f, out);
+            }
+            const double L = ((f < 2) ? hy : hx) * (coarse ? 0.5 : 1.0);
+            const double wl = L * tb.wm[al];
+            double* F = d.fflux + k * SL;
+#pragma unroll
+            for (int cf = 0; cf < 4; ++cf) F[((cf * 4 + f) * 2 + h) * NM + al] = wl * (double)out[cf];
+            v = fmax((double)lam, 1e-12) * ((f < 2) ? ihx : ihy) * (coarse ? 0.5 : 1.0);
+            if (!bnd && nb != k) {
+                // the other side: its face fo, its half (the fine side of a 2:1
+                // face has one) and its own weight
+                const int fo = f ^ 1;
+                const unsigned ninfo = d.finfo ? d.finfo[nb * 4 + fo] : 0;
+                const bool ncoarse = (ninfo & 3) == FI_COARSE;
+                const int hn = ((info & 3) == FI_FINE) ? (int)(info >> 2) : 0;
+                const double nhx = d.hxhy[2 * nb], nhy = d.hxhy[2 * nb + 1];
+                const double nihx = d.ihxhy ? d.ihxhy[2 * nb] : 1.0 / nhx;
+                const double nihy = d.ihxhy ? d.ihxhy[2 * nb + 1] : 1.0 / nhy;
+                side_flux<B>(raw, pres, !own_first, fo, out);
+                const double Ln = ((fo < 2) ? nhy : nhx) * (ncoarse ? 0.5 : 1.0);
+                const double wln = Ln * tb.wm[al];
+                double* Fn = d.fflux + nb * SL;
+#pragma unroll
+                for (int cf = 0; cf < 4; ++cf)
+                    Fn[((cf * 4 + fo) * 2 + hn) * NM + al] = wln * (double)out[cf];
+                v = fmax(v, fmax((double)lam, 1e-12) * ((fo < 2) ? nihx : nihy) * (ncoarse ? 0.5 : 1.0));
+            }
+        }
+        if (want_dt) {
+            // one atomic per warp when its jobs share a member, else per job
+            const int m0 = __shfl_sync(0xffffffffu, mem, 0);
+            if (__all_sync(0xffffffffu, mem == m0 || mem < 0)) {
+                const double m = warp_max(v);
+                if (lane == 0 && m0 >= 0) atomic_max_pos(&d.mb[m0].rmax, m);
+            } else if (mem >= 0) {
+                atomic_max_pos(&d.mb[mem].rmax, v);
+            }
+        }
     }
 }
 

@@ -21,6 +21,8 @@ enum { KK_BEGIN = 0, KK_RESIDUAL = 1, KK_STAGE = 2, KK_AUX = 3, KK_N = 4 };
 struct Launch {
     void (*residual)(const Dev&, const Tables&, int buf, int stage, double c_stage, int want_dt,
                      Shape, cudaStream_t);
+    // the face points of the residual, each once, into d.fflux (before residual)
+    void (*faces)(const Dev&, const Tables&, int buf, double c_stage, int want_dt, cudaStream_t);
     void (*step_begin)(const Dev&, const Tables&, int do_switch, Shape, cudaStream_t);
     void (*stage)(const Dev&, const Tables&, const StageArgs&, Shape, cudaStream_t);
     void (*masks)(const Dev&, int buf, Shape, cudaStream_t);
