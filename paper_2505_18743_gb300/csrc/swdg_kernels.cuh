@@ -85,6 +85,86 @@ __device__ __forceinline__ void kron_apply(const E (*M)[LD], const E* in, E* tmp
     __syncwarp();
 }
 
+// the contractions above for two inputs at once (each output by the same sum,
+// the two halves of the work side by side on the lanes)
+template <int NI, int NO, typename T = double>
+__device__ __forceinline__ void tens_interp2(const T (*B)[MXN], const T* in0, const T* in1, T* tmp0,
+                                             T* tmp1, T* out0, T* out1, int lane) {
+    constexpr int M1 = NI * NO, M2 = NO * NO;
+    for (int i = lane; i < 2 * M1; i += 32) {
+        const int j = i < M1 ? i : i - M1;
+        const T* in = i < M1 ? in0 : in1;
+        const int b = j / NO, q0 = j % NO;
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a < NI; ++a) s += B[q0][a] * in[b * NI + a];
+        (i < M1 ? tmp0 : tmp1)[j] = s;
+    }
+    __syncwarp();
+    for (int i = lane; i < 2 * M2; i += 32) {
+        const int j = i < M2 ? i : i - M2;
+        const T* tmp = i < M2 ? tmp0 : tmp1;
+        const int q1 = j / NO, q0 = j % NO;
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < NI; ++b) s += B[q1][b] * tmp[b * NO + q0];
+        (i < M2 ? out0 : out1)[j] = s;
+    }
+    __syncwarp();
+}
+
+template <int NI, int NO, typename T = double>
+__device__ __forceinline__ void tens_test2(const T (*B)[MXN], const T* in0, const T* in1, T* tmp0,
+                                           T* tmp1, T* out0, T* out1, int lane) {
+    constexpr int M1 = NO * NI, M2 = NI * NI;
+    for (int i = lane; i < 2 * M1; i += 32) {
+        const int j = i < M1 ? i : i - M1;
+        const T* in = i < M1 ? in0 : in1;
+        const int q1 = j / NI, a = j % NI;
+        T s = T(0);
+#pragma unroll
+        for (int q0 = 0; q0 < NO; ++q0) s += B[q0][a] * in[q1 * NO + q0];
+        (i < M1 ? tmp0 : tmp1)[j] = s;
+    }
+    __syncwarp();
+    for (int i = lane; i < 2 * M2; i += 32) {
+        const int j = i < M2 ? i : i - M2;
+        const T* tmp = i < M2 ? tmp0 : tmp1;
+        const int b = j / NI, a = j % NI;
+        T s = T(0);
+#pragma unroll
+        for (int q1 = 0; q1 < NO; ++q1) s += B[q1][b] * tmp[q1 * NI + a];
+        (i < M2 ? out0 : out1)[j] = s;
+    }
+    __syncwarp();
+}
+
+template <int N, bool T, int LD, typename E = double>
+__device__ __forceinline__ void kron_apply2(const E (*M)[LD], const E* in0, const E* in1, E* tmp0,
+                                            E* tmp1, E* out0, E* out1, E scale, int lane) {
+    constexpr int MM = N * N;
+    for (int i = lane; i < 2 * MM; i += 32) {
+        const int j = i < MM ? i : i - MM;
+        const E* in = i < MM ? in0 : in1;
+        const int d = j / N, a = j % N;
+        E s = E(0);
+#pragma unroll
+        for (int c = 0; c < N; ++c) s += (T ? M[c][a] : M[a][c]) * in[d * N + c];
+        (i < MM ? tmp0 : tmp1)[j] = s;
+    }
+    __syncwarp();
+    for (int i = lane; i < 2 * MM; i += 32) {
+        const int j = i < MM ? i : i - MM;
+        const E* tmp = i < MM ? tmp0 : tmp1;
+        const int b = j / N, a = j % N;
+        E s = E(0);
+#pragma unroll
+        for (int d = 0; d < N; ++d) s += (T ? M[d][b] : M[b][d]) * tmp[d * N + a];
+        (i < MM ? out0 : out1)[j] = scale * s;
+    }
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // bathymetry sampling sites
 // ---------------------------------------------------------------------------
@@ -950,8 +1030,8 @@ constexpr int stage_smem() {
            S::ND * S::ND + 6 * S::NGP + 4 * S::ND + S::ND +
            // mixed-precision solve: x, r (ND), q (NMP), float M, Y, inv, r
            2 * S::ND + S::NMP + (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 2 * S::ND + 1) / 2 + 1 +
-           // momentum block scratch (B-typed, sized in doubles)
-           S::ND + 6 * S::NGP + S::ND1 * S::NG;
+           // momentum block scratch (B-typed, sized in doubles): nodal pair, points, tmp pair
+           2 * S::ND + 6 * S::NGP + 2 * S::ND1 * S::NG;
 }
 
 // Cholesky of the SPD matrix M (ND x ND, row-major, lower part used) on a
@@ -1127,14 +1207,21 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
             for (int i = lane; i < ND; i += 32) rf[i] = (float)r[i];
             __syncwarp();
             chol_subst_f<ND>(Mf, invf, rf, lane);
-            double dmax = 0.0, xmax = 0.0;
-            for (int i = lane; i < ND; i += 32) {
-                x[i] += (double)rf[i];
-                dmax = fmax(dmax, fabs((double)rf[i]));
-                xmax = fmax(xmax, fabs(x[i]));
+            // max |correction| and max |x| (a NaN counts as 0, as under fmax),
+            // reduced on their bit patterns
+            static_assert(ND <= 32, "one unknown per lane");
+            float da = 0.0f;
+            double xa = 0.0;
+            if (lane < ND) {
+                const float v = rf[lane];
+                x[lane] += (double)v;
+                da = (v == v) ? fabsf(v) : 0.0f;
+                const unsigned long long xb =
+                    (unsigned long long)__double_as_longlong(x[lane]) & 0x7fffffffffffffffull;
+                xa = __longlong_as_double((long long)(xb > 0x7ff0000000000000ull ? 0ull : xb));
             }
-            dmax = warp_max(dmax);
-            xmax = warp_max(xmax);
+            const double dmax = (double)warp_max_nonneg(da);
+            const double xmax = warp_max_nonneg(xa);
             if (!(dmax <= 1e-15 * xmax) && !(dmax == 0.0)) {
                 // r = b - H x, H x = B^T (cw * (B x))
                 __syncwarp();
@@ -1178,10 +1265,12 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
     const T(*Bginv)[MXP] = nullptr;
     if constexpr (sizeof(T) == sizeof(double)) Bginv = (const T(*)[MXP])tb.Bginv;
     else Bginv = (const T(*)[MXP])tb.BginvF;
-    // w0: [ND] scratch nodal, [NGP x 6] point arrays; w1: [ND1 NG] tmp
-    T* nod = w0;              // [ND]
-    T* pg = w0 + ND;          // [6][NGP]: 0,1 S^-T rq / point values; 2 gamma; 3,4 q^n; 5 spare
+    // w0: [2][ND] nodal pair, [6][NGP] point arrays; w1: [2][ND1 NG] tmp pair.
+    // The two discharge components are contracted side by side.
+    T* nod = w0;              // [2][ND]
+    T* pg = w0 + 2 * ND;      // [6][NGP]: 0,1 S^-T rq / point values; 2 gamma; 3,4 q^n; 5 spare
     T* tmp = w1;
+    T* tmp1 = w1 + ND1 * NG;
     T* gam = pg + 2 * NGP;
     const int64_t n = d.n;
     if (need_gam) {
@@ -1190,15 +1279,16 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
         tens_interp<ND1, NG>(tb.Bg, uz, tmpd, zp, lane); // zeta of v^(l-1), FP64
         if (cmp & 1u)
             for (int p = lane; p < NGP; p += 32) zp[p] = uz[0];
-        for (int f = 0; f < 2; ++f) {
-            const double* up = ufield(d, prev_buf, 1 + f, ND) + k * ND;
-            for (int i = lane; i < ND; i += 32) nod[i] = (T)up[i];
-            __syncwarp();
-            tens_interp<ND1, NG, T>(Bg, nod, tmp, pg + (3 + f) * NGP, lane);
-            if (cmp & (2u << f))
-                for (int p = lane; p < NGP; p += 32) pg[(3 + f) * NGP + p] = (T)up[0];
-            __syncwarp();
-        }
+        const double* up0 = ufield(d, prev_buf, 1, ND) + k * ND;
+        const double* up1 = ufield(d, prev_buf, 2, ND) + k * ND;
+        for (int i = lane; i < 2 * ND; i += 32) nod[i] = (T)(i < ND ? up0[i] : up1[i - ND]);
+        __syncwarp();
+        tens_interp2<ND1, NG, T>(Bg, nod, nod + ND, tmp, tmp1, pg + 3 * NGP, pg + 4 * NGP, lane);
+        if (cmp & 2u)
+            for (int p = lane; p < NGP; p += 32) pg[3 * NGP + p] = (T)up0[0];
+        if (cmp & 4u)
+            for (int p = lane; p < NGP; p += 32) pg[4 * NGP + p] = (T)up1[0];
+        __syncwarp();
         for (int p = lane; p < NGP; p += 32) {
             double V, A;
             Site<R, Pix, MODE>::VA(d, tb, k, SET_MOM, p % NG, p / NG, zp[p], V, A);
@@ -1209,16 +1299,16 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
         for (int p = lane; p < NGP; p += 32) gam[p] = T(0);
     }
     __syncwarp();
-    for (int f = 0; f < 2; ++f) {
-        for (int i = lane; i < ND; i += 32) nod[i] = (T)su[(1 + f) * ND + i];
-        __syncwarp();
-        tens_interp<ND1, NG, T>(Bg, nod, tmp, pg + (3 + f) * NGP, lane);
-        if (cm0 & (2u << f))
-            for (int p = lane; p < NGP; p += 32) pg[(3 + f) * NGP + p] = (T)su[(1 + f) * ND];
-        for (int i = lane; i < ND; i += 32) nod[i] = (T)rq[f * ND + i];
-        __syncwarp();
-        kron_apply<ND1, true, MXP, T>(Bginv, nod, tmp, pg + f * NGP, T(1), lane);
-    }
+    for (int i = lane; i < 2 * ND; i += 32) nod[i] = (T)su[ND + i];
+    __syncwarp();
+    tens_interp2<ND1, NG, T>(Bg, nod, nod + ND, tmp, tmp1, pg + 3 * NGP, pg + 4 * NGP, lane);
+    if (cm0 & 2u)
+        for (int p = lane; p < NGP; p += 32) pg[3 * NGP + p] = (T)su[ND];
+    if (cm0 & 4u)
+        for (int p = lane; p < NGP; p += 32) pg[4 * NGP + p] = (T)su[2 * ND];
+    for (int i = lane; i < 2 * ND; i += 32) nod[i] = (T)rq[i];
+    __syncwarp();
+    kron_apply2<ND1, true, MXP, T>(Bginv, nod, nod + ND, tmp, tmp1, pg, pg + NGP, T(1), lane);
     for (int p = lane; p < NGP; p += 32) {
         const T w = (T)(J * tb.wg[p % NG] * tb.wg[p / NG]);
         const T rD = T(1) / (w * (T(1) + (T)(add * dt) * gam[p]));
@@ -1226,11 +1316,9 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
         pg[1 * NGP + p] = (w * pg[4 * NGP + p] + pg[1 * NGP + p]) * rD;
     }
     __syncwarp();
-    for (int f = 0; f < 2; ++f) {
-        kron_apply<ND1, false, MXP, T>(Bginv, pg + f * NGP, tmp, nod, T(1), lane);
-        for (int i = lane; i < ND; i += 32) Q[f * ND + i] = (double)nod[i];
-        __syncwarp();
-    }
+    kron_apply2<ND1, false, MXP, T>(Bginv, pg, pg + NGP, tmp, tmp1, nod, nod + ND, T(1), lane);
+    for (int i = lane; i < 2 * ND; i += 32) Q[i] = (double)nod[i];
+    __syncwarp();
     if (make_llin) {
         for (int p = lane; p < NGP; p += 32) {
             const T w = (T)(J * tb.wg[p % NG] * tb.wg[p / NG]) * gam[p];
@@ -1238,11 +1326,9 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
             pg[4 * NGP + p] = -w * pg[NGP + p];
         }
         __syncwarp();
-        for (int f = 0; f < 2; ++f) {
-            tens_test<ND1, NG, T>(Bg, pg + (3 + f) * NGP, tmp, nod, lane);
-            for (int i = lane; i < ND; i += 32) llin[f * ND + i] = (double)nod[i];
-            __syncwarp();
-        }
+        tens_test2<ND1, NG, T>(Bg, pg + 3 * NGP, pg + 4 * NGP, tmp, tmp1, nod, nod + ND, lane);
+        for (int i = lane; i < 2 * ND; i += 32) llin[i] = (double)nod[i];
+        __syncwarp();
     }
 }
 
@@ -1277,7 +1363,7 @@ __global__ void __maxnreg__(128)
     float* rf = invf + ND;                      // [ND]
     // momentum scratch, 8-byte aligned after the float arrays
     double* mw = (double*)((((uintptr_t)(rf + ND)) + 7) & ~(uintptr_t)7);
-    double* mt = mw + ND + 6 * NGP;
+    double* mt = mw + 2 * ND + 6 * NGP;
     const int64_t n = d.n;
     const double g = d.g, eps = d.eps;
     int its_max = 0;
