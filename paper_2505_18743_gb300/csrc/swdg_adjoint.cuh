@@ -73,12 +73,18 @@ struct DN {
 #pragma unroll
         for (int i = 0; i < W; ++i) d[i] = 0.0;
     }
-    // x with unit derivative along direction dir
+    // x with unit derivative along direction dir (none when dir is outside [0, W))
     __device__ __forceinline__ static DN seed(double x, int dir) {
         DN r(x);
 #pragma unroll
         for (int i = 0; i < W; ++i) r.d[i] = (i == dir) ? 1.0 : 0.0;
         return r;
+    }
+    // derivative v along direction dir, if dir is one of this value's
+    __device__ __forceinline__ void set(int dir, double v) {
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+            if (i == dir) d[i] = v;
     }
 };
 template <int W>
@@ -253,9 +259,19 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             tc[i] = s;
         }
         __syncwarp();
-        // volume points: one per lane
+        // volume points: one per lane.  When the points fit in half a warp the
+        // two halves take the same point, each with half of the 8 input
+        // directions (lane + 16 hands its four to lane), so the dual
+        // arithmetic runs on all 32 lanes
+        constexpr bool VSPLIT = NVP <= 16;
+        constexpr int VW = VSPLIT ? 4 : 8;         // directions per lane
+        const int vb0 = VSPLIT ? (lane >> 4) * VW : 0; // first direction of this lane
+        constexpr int VSTEP = VSPLIT ? 16 : 32;
         double dsum = 0.0, nsum = 0.0;
-        for (int p = lane; p < NVP; p += 32) {
+        for (int p0 = 0; p0 < NVP; p0 += VSTEP) {
+            const int pl = p0 + (VSPLIT ? (lane & 15) : lane);
+            const bool pv = pl < NVP;    // a lane past the last point computes point 0, unused
+            const int p = pv ? pl : 0;
             const int al = p % NV, be = p / NV;
             double z = 0.0, zxd = 0.0, zyd = 0.0, qx = 0.0, qy = 0.0, c = 0.0;
             // cotangent interpolations: [field][0: (Bv x, Bv y), 1: (Dv x, Bv y), 2: (Bv x, Dv y)]
@@ -296,14 +312,16 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             double xb[8];
             {
                 // input directions: 0 z, 1 z_xi, 2 z_eta, 3 qx, 4 qy, 5 c, 6 delta, 7 n
-                using DV = ad::DN<8>;
-                const DV zx = DV::seed(zxd, 1) * DV(ihx);
-                const DV zy = DV::seed(zyd, 2) * DV(ihy);
-                const DV vqx = DV::seed(qx, 3), vqy = DV::seed(qy, 4), vc = DV::seed(c, 5);
+                // (this lane: vb0 .. vb0 + VW - 1)
+                using DV = ad::DN<VW>;
+                const DV zx = DV::seed(zxd, 1 - vb0) * DV(ihx);
+                const DV zy = DV::seed(zyd, 2 - vb0) * DV(ihy);
+                const DV vqx = DV::seed(qx, 3 - vb0), vqy = DV::seed(qy, 4 - vb0);
+                const DV vc = DV::seed(c, 5 - vb0);
                 DV h(V);
-                h.d[0] = A;
-                h.d[6] = A;
-                const DV nn = DV::seed(man, 7);
+                h.set(0 - vb0, A);
+                h.set(6 - vb0, A);
+                const DV nn = DV::seed(man, 7 - vb0);
                 const DV fv = vel_factor<DV>(h, DV(eps));
                 const DV ux = fv * vqx, uy = fv * vqy;
                 const DV gam = gamma_manning<DV>(nn, h, vqx, vqy, DV(g), DV(eps));
@@ -313,11 +331,16 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                                   wx * vqy * ux, wy * vqy * uy, -(W * gg * h * zy),
                                   -(W * gam * vqx), -(W * gam * vqy)};
 #pragma unroll
-                for (int dir = 0; dir < 8; ++dir) {
+                for (int dir = 0; dir < VW; ++dir) {
                     double s_ = 0.0;
 #pragma unroll
                     for (int o = 0; o < 12; ++o) s_ += Xb[o] * X[o].d[dir];
                     xb[dir] = s_;
+                }
+                if constexpr (VSPLIT) {
+#pragma unroll
+                    for (int dir = 0; dir < VW; ++dir)
+                        xb[VW + dir] = __shfl_down_sync(0xffffffffu, xb[dir], 16);
                 }
             }
             // tracer numerical diffusion (Eq. numdiff): X_2 -= w nu h c_xi / hx^2,
@@ -337,11 +360,13 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                 xb[0] += A * xh;
                 xb[6] += A * xh;
             }
-            for (int q = 0; q < 6; ++q) xv[q * NVP + p] = xb[q];
-            xv[6 * NVP + p] = xcx;
-            xv[7 * NVP + p] = xcy;
-            dsum += xb[6];
-            nsum += xb[7];
+            if (pv && (!VSPLIT || lane < 16)) {
+                for (int q = 0; q < 6; ++q) xv[q * NVP + p] = xb[q];
+                xv[6 * NVP + p] = xcx;
+                xv[7 * NVP + p] = xcy;
+                dsum += xb[6];
+                nsum += xb[7];
+            }
         }
         __syncwarp();
         // faces: one (sub)face point per lane, as the forward
@@ -353,7 +378,16 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             fi[f] = d.finfo ? d.finfo[k * 4 + f] : 0;
             base[f + 1] = base[f] + (((fi[f] & 3) == FI_COARSE) ? 2 : 1) * NM;
         }
-        for (int it = lane; it < base[4]; it += 32) {
+        // as for the volume points: with at most 16 face points per conforming
+        // cell the two halves share a point, directions 0-2 and 3-4
+        constexpr bool FSPLIT = 4 * NM <= 16;
+        constexpr int FW = FSPLIT ? 3 : 5;
+        const int fb0 = FSPLIT ? (lane >> 4) * FW : 0;
+        constexpr int FSTEP = FSPLIT ? 16 : 32;
+        for (int it0 = 0; it0 < base[4]; it0 += FSTEP) {
+            const int il = it0 + (FSPLIT ? (lane & 15) : lane);
+            const bool iv = il < base[4]; // a lane past the last point computes point 0, unused
+            const int it = iv ? il : 0;
             const int f = (it >= base[1]) + (it >= base[2]) + (it >= base[3]);
             const int r_ = it - base[f], h = r_ / NM, al = r_ % NM;
             const unsigned info = fi[f];
@@ -378,7 +412,7 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             const int32_t s0 = d.nbr[k * 8 + f * 2];
             double hm, Am;
             own_VA(tm[0], hm, Am);
-            double xb[5];
+            double xb[5], xl[FW];
             if (s0 >= 0) {
                 const int64_t nb = coarse ? (int64_t)(h ? d.nbr[k * 8 + f * 2 + 1] : s0) : (int64_t)s0;
                 const int fo = f ^ 1;
@@ -400,14 +434,15 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                 own_VA(tp[0], Vop, Aop);
                 {
                     // directions of the own side: 0 zeta, 1 qx, 2 qy, 3 c, 4 delta
-                    using DF = ad::DN<5>;
-                    const DF qxm = DF::seed(tm[1], 1), qym = DF::seed(tm[2], 2);
-                    const DF cmv = DF::seed(tm[3], 3);
+                    // (this lane: fb0 .. fb0 + FW - 1)
+                    using DF = ad::DN<FW>;
+                    const DF qxm = DF::seed(tm[1], 1 - fb0), qym = DF::seed(tm[2], 2 - fb0);
+                    const DF cmv = DF::seed(tm[3], 3 - fb0);
                     DF hmD(hm), vnmD(Vnm), vopD(Vop);
-                    hmD.d[0] = Am;   // own operator at own zeta
-                    hmD.d[4] = Am;
-                    vnmD.d[0] = Anm; // neighbour's operator at own zeta
-                    vopD.d[4] = Aop; // own operator at neighbour's zeta
+                    hmD.set(0 - fb0, Am);   // own operator at own zeta
+                    hmD.set(4 - fb0, Am);
+                    vnmD.set(0 - fb0, Anm); // neighbour's operator at own zeta
+                    vopD.set(4 - fb0, Aop); // own operator at neighbour's zeta
                     const DF hpD(hp);
                     const DF hsm = ad::fmin(hmD, vnmD), hsp = ad::fmin(hpD, vopD);
                     const DF qxp(tp[1]), qyp(tp[2]), cpv(tp[3]);
@@ -415,11 +450,11 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                     side_flux<DF>(qxm, qym, cmv, hmD, hsm, qxp, qyp, cpv, hpD, hsp, nx, ny, g, eps, oo);
                     side_flux<DF>(qxp, qyp, cpv, hpD, hsp, qxm, qym, cmv, hmD, hsm, -nx, -ny, g, eps, on);
 #pragma unroll
-                    for (int dir = 0; dir < 5; ++dir) {
+                    for (int dir = 0; dir < FW; ++dir) {
                         double s_ = 0.0;
 #pragma unroll
                         for (int cf = 0; cf < 4; ++cf) s_ += ym[cf] * oo[cf].d[dir] + yp[cf] * on[cf].d[dir];
-                        xb[dir] = s_;
+                        xl[dir] = s_;
                     }
                 }
             } else {
@@ -436,16 +471,16 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                     own_VA(zt, Vt, At);
                 }
                 {
-                    using DF = ad::DN<5>;
-                    const DF qxm = DF::seed(tm[1], 1), qym = DF::seed(tm[2], 2);
-                    const DF cmv = DF::seed(tm[3], 3);
+                    using DF = ad::DN<FW>;
+                    const DF qxm = DF::seed(tm[1], 1 - fb0), qym = DF::seed(tm[2], 2 - fb0);
+                    const DF cmv = DF::seed(tm[3], 3 - fb0);
                     DF hmD(hm);
-                    hmD.d[0] = Am;
-                    hmD.d[4] = Am;
+                    hmD.set(0 - fb0, Am);
+                    hmD.set(4 - fb0, Am);
                     DF qxp = qxm, qyp = qym, hpD = hmD;
                     if (tide) {
                         hpD = DF(Vt); // ghost elevation fixed, same operator
-                        hpD.d[4] = At;
+                        hpD.set(4 - fb0, At);
                     } else {
                         const DF qn = qxm * DF(nx) + qym * DF(ny);
                         qxp = qxm - DF(2.0) * qn * DF(nx);
@@ -454,17 +489,26 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                     DF oo[4];
                     side_flux<DF>(qxm, qym, cmv, hmD, hmD, qxp, qyp, cmv, hpD, hpD, nx, ny, g, eps, oo);
 #pragma unroll
-                    for (int dir = 0; dir < 5; ++dir) {
+                    for (int dir = 0; dir < FW; ++dir) {
                         double s_ = 0.0;
 #pragma unroll
                         for (int cf = 0; cf < 4; ++cf) s_ += ym[cf] * oo[cf].d[dir];
-                        xb[dir] = s_;
+                        xl[dir] = s_;
                     }
                 }
             }
+            // all lanes (the branches have joined): gather the five directions
 #pragma unroll
-            for (int cf = 0; cf < 4; ++cf) xf[((cf * 4 + f) * 2 + h) * NM + al] = xb[cf];
-            dsum += xb[4];
+            for (int dir = 0; dir < FW; ++dir) xb[dir] = xl[dir];
+            if constexpr (FSPLIT) {
+                xb[3] = __shfl_down_sync(0xffffffffu, xl[0], 16);
+                xb[4] = __shfl_down_sync(0xffffffffu, xl[1], 16);
+            }
+            if (iv && (!FSPLIT || lane < 16)) {
+#pragma unroll
+                for (int cf = 0; cf < 4; ++cf) xf[((cf * 4 + f) * 2 + h) * NM + al] = xb[cf];
+                dsum += xb[4];
+            }
         }
         __syncwarp();
         // transposed interpolation of the volume-point cotangents: y, then x

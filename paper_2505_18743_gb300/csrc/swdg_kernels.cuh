@@ -1183,9 +1183,10 @@ __device__ __forceinline__ void assemble_mass(const Tables& tb, const double* cw
 // tracer matrix of Eq. mass_matrix_concentration, or the masked Jacobian of
 // Eq. mass_matrix) by mixed-precision iterative refinement: H is assembled and
 // factored in FP32, each correction is solved in FP32, and the residual
-// b - H x is formed in FP64 matrix-free by sum factorisation.  If the
-// corrections do not fall below 1e-15 of x within 6 sweeps (an ill-conditioned
-// near-dry cell), the FP64 Cholesky decides.  x (FP64, in place of b on
+// b - H x is formed in FP64 matrix-free by sum factorisation.  The sweeps stop
+// when a correction, or the next one as predicted from the contraction of
+// the last two, is below 1e-15 of x; if that does not happen within 6 sweeps
+// (an ill-conditioned near-dry cell), the FP64 Cholesky decides.  x (FP64, in place of b on
 // return).  Scratch: Mf, Yf (float), r, t (ND doubles), q (NMP doubles),
 // tmp (2 NM NM doubles), M, Y (double, fallback).
 template <int ND1, int NM>
@@ -1203,6 +1204,7 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
         }
         __syncwarp();
         ok = false;
+        double dprev = 0.0; // max |correction| of the previous sweep
         for (int sweep = 0; sweep < 6; ++sweep) {
             for (int i = lane; i < ND; i += 32) rf[i] = (float)r[i];
             __syncwarp();
@@ -1222,7 +1224,13 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
             }
             const double dmax = (double)warp_max_nonneg(da);
             const double xmax = warp_max_nonneg(xa);
-            if (!(dmax <= 1e-15 * xmax) && !(dmax == 0.0)) {
+            // converged when this correction is below 1e-15 of x, or when the
+            // next one is, as predicted from the contraction of the last two
+            // (dmax / dprev, at most 1/2)
+            const bool next_small =
+                sweep > 0 && dmax <= 0.5 * dprev && dmax * dmax <= 1e-15 * xmax * dprev;
+            if (!(dmax <= 1e-15 * xmax) && !(dmax == 0.0) && !next_small) {
+                dprev = dmax;
                 // r = b - H x, H x = B^T (cw * (B x))
                 __syncwarp();
                 tens_interp<ND1, NM>(tb.Bm, x, tmp, q, lane);
