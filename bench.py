@@ -58,18 +58,20 @@ def units_per_step(wl):
 
 
 # FP64 flops one launch performs per cell on this workload: active-lane
-# 2 DFMA + DMUL + DADD counted by ncu (profiles/fp64_ops_tidal_beach_256x256_r3.md).
-# These kernels are bound by the FP64 pipe: GB300's FP64 rate is the roofline.
-FLOPS_PER_CELL = {"step_begin": 2187, "residual_1": 12467, "residual_2": 13009,
-                  "residual_3": 13010, "stage_2": 9858, "stage_3": 10642, "final": 8338}
+# 2 DFMA + DMUL + DADD counted by ncu (profiles/fp64_ops_tidal_beach_256x256_r3.md);
+# a residual slot is k_faces + k_residual.  These kernels are bound by the FP64
+# pipe: GB300's FP64 rate is the roofline.
+FLOPS_PER_CELL = {"step_begin": 2187, "residual_1": 11085, "residual_2": 11800,
+                  "residual_3": 11799, "stage_2": 9284, "stage_3": 10070, "final": 7770}
 # the FP32-bulk kernels' FP64 flops (their FP32 work runs on the 60x faster FP32 pipe)
-FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "residual_1": 3618, "residual_2": 4160,
-                           "residual_3": 4161, "stage_2": 6566, "stage_3": 6815, "final": 6595}
-# DRAM bytes per launch from an ncu capture of the current kernels (FP64 path);
-# {} (traffic null) whenever the kernels changed after the capture
-DRAM_BYTES_PER_LAUNCH = {"step_begin": 59226112, "residual_1": 95480576, "residual_2": 96324096,
-                         "residual_3": 96815872, "stage_2": 156174336, "stage_3": 248689920,
-                         "final": 253510400}
+FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "residual_1": 3529, "residual_2": 4243,
+                           "residual_3": 4243, "stage_2": 5992, "stage_3": 6244, "final": 6024}
+# DRAM bytes per launch (a residual slot: both kernels) from an ncu capture of
+# the current kernels (FP64 path); {} (traffic null) whenever the kernels
+# changed after the capture
+DRAM_BYTES_PER_LAUNCH = {"step_begin": 58996736, "residual_1": 326781696,
+                         "residual_2": 328875264, "residual_3": 328519424,
+                         "stage_2": 155726848, "stage_3": 248966656, "final": 253807104}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
 
 
@@ -553,7 +555,10 @@ def run_gpu(args, rank, world, local):
                        "l2": "inputs larger than L2 (about 0.5 GB working set), no flush",
                        "parallelism": f"replicas x{world}"},
             "clocks": clocks, "roofline": roof, "e2e": e2e, "variants": variants,
-            "gpu_launches": (2 * STAGES + 1) * args.steps}
+            # per step: step_begin, per stage k_faces + k_residual, the stage
+            # updates and the final combination (3 STAGES + 1); plus the clock
+            # upload of the step call
+            "gpu_launches": (3 * STAGES + 1) * args.steps + 1}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": rate, "unit": "updates/s", "cores": cores,
