@@ -29,8 +29,10 @@ Definitions (each evaluated directly, no sum factorisation):
 
 Derivative conventions at the kinks (the reading the adjoint takes):
   * max(x, 0) inside V has derivative [x > 0] (Eq. mask's strict inequality);
-  * the min of the reconstruction and the max of the wave speeds follow
-    their first argument at ties (own side's operator; side "-");
+  * the min of the reconstruction follows its first argument at ties (the
+    side's own operator); the max of the wave speeds follows the side with
+    the lower cell index (the forward evaluates each face once, in that
+    order);
   * |x| and sqrt(x) have derivative 0 at x = 0;
   * the constant-field rule (a field with equal nodal values is evaluated as
     that constant) is a rounding device: the polynomial is differentiated.
@@ -369,7 +371,11 @@ class TorchResidual:
         fm, fp = self.vel(hm), self.vel(hp)
         umx, umy, upx, upy = fm * qxm, fm * qym, fp * qxp, fp * qyp
         unm, unp = umx * nx + umy * ny, upx * nx + upy * ny
-        lam = _max_first(torch.abs(unm) + _sqrt0(g * hm), torch.abs(unp) + _sqrt0(g * hp))
+        # wave speed bound: at a tie the side with the lower cell index decides
+        # (the face is evaluated once, lower index first)
+        lm_, lp_ = torch.abs(unm) + _sqrt0(g * hm), torch.abs(unp) + _sqrt0(g * hp)
+        own_low = (~self.has_nb | (iK < iN))[:, None]
+        lam = torch.where(own_low, _max_first(lm_, lp_), _max_first(lp_, lm_))
         qsmx, qsmy, qspx, qspy = hsm * umx, hsm * umy, hsp * upx, hsp * upy
         fF = 0.5 * ((qsmx + qspx) * nx + (qsmy + qspy) * ny) + 0.5 * lam * (hsm - hsp)
         pres = g * 0.5 * (hsm + hsp) * 0.5 * (hsm - hsp)
