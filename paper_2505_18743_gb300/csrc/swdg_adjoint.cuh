@@ -446,9 +446,32 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                     const DF hpD(hp);
                     const DF hsm = ad::fmin(hmD, vnmD), hsp = ad::fmin(hpD, vopD);
                     const DF qxp(tp[1]), qyp(tp[2]), cpv(tp[3]);
-                    DF oo[4], on[4];
-                    side_flux<DF>(qxm, qym, cmv, hmD, hsm, qxp, qyp, cpv, hpD, hsp, nx, ny, g, eps, oo);
-                    side_flux<DF>(qxp, qyp, cpv, hpD, hsp, qxm, qym, cmv, hmD, hsm, -nx, -ny, g, eps, on);
+                    // the face is evaluated once, the lower cell index as side A
+                    // (as the forward does); the flux of each side follows from it:
+                    // F_side = s raw - pres n_A (momentum), s = +1 for side A, -1 for B
+                    // (one call with the sides selected, so the warp does not split)
+                    const bool own_low = k < nb;
+                    const DF aqx = own_low ? qxm : qxp, aqy = own_low ? qym : qyp;
+                    const DF ac = own_low ? cmv : cpv, ah = own_low ? hmD : hpD;
+                    const DF ahs = own_low ? hsm : hsp;
+                    const DF bqx = own_low ? qxp : qxm, bqy = own_low ? qyp : qym;
+                    const DF bc = own_low ? cpv : cmv, bh = own_low ? hpD : hmD;
+                    const DF bhs = own_low ? hsp : hsm;
+                    const double nAx = own_low ? nx : -nx, nAy = own_low ? ny : -ny;
+                    DF raw[4], pres, lam;
+                    rusanov<DF>(aqx, aqy, ac, ah, ahs, bqx, bqy, bc, bh, bhs, ahs - bhs, DF(nAx), DF(nAy),
+                                DF(g), DF(eps), raw, pres, lam);
+                    const DF pnx = pres * DF(nAx), pny = pres * DF(nAy);
+                    const DF so(own_low ? 1.0 : -1.0), sn(own_low ? -1.0 : 1.0);
+                    DF oo[4], on[4]; // own side's flux, the neighbour's (its own normal)
+                    oo[0] = so * raw[0];
+                    oo[1] = so * raw[1] - pnx;
+                    oo[2] = so * raw[2] - pny;
+                    oo[3] = so * raw[3];
+                    on[0] = sn * raw[0];
+                    on[1] = sn * raw[1] - pnx;
+                    on[2] = sn * raw[2] - pny;
+                    on[3] = sn * raw[3];
 #pragma unroll
                     for (int dir = 0; dir < FW; ++dir) {
                         double s_ = 0.0;
