@@ -90,6 +90,11 @@ struct swdg_ctx {
     swdg_forest forest{};
     std::vector<Leaf> leaves;
     std::vector<uint8_t> ras_h;
+    // with adaptation set up, the raster also stays on the device for the
+    // re-tiling of every rebuild (reuse_raster: this upload is such a rebuild)
+    bool keep_raster = false, reuse_raster = false;
+    void* ras_dev = nullptr;
+    size_t ras_dev_bytes = 0;
     int ras_dtype = 0;
     int64_t ras_nx = 0, ras_ny = 0;
     double ras_geo[4] = {0, 0, 1, 1};
@@ -766,6 +771,7 @@ void swdg_destroy(swdg_ctx* c) {
     invalidate_graph(c);
     free_mesh(c);
     free_bathy(c);
+    cudaFree(c->ras_dev);
     cudaFree(c->memb); cudaFree(c->mb); cudaFree(c->bcd); cudaFree(c->first_d); cudaFree(c->mdiag);
     cudaFree(c->sc);
     if (c->sc_host) cudaFreeHost(c->sc_host);
@@ -1016,10 +1022,26 @@ static int upload_bathy(swdg_ctx* ctx, int nseg, const void* const* rasters, int
     CK(cudaMalloc(&ctx->zabs, n * sizeof(double)));
     CK(cudaMalloc(&ctx->zpts, (size_t)n * nzp_ * sizeof(double)));
     CK(cudaMalloc(&ctx->zhang, (size_t)n * 8 * nm_ * sizeof(double)));
-    // one raster on the device at a time
+    // one raster on the device at a time; a single raster of an adaptive
+    // context stays there (and a rebuild re-tiles from it)
+    const bool keep = nseg == 1 && ctx->keep_raster;
     auto put_raster = [&](int sg, void** ras) -> int {
         const size_t bytes = (size_t)nxny[2 * sg] * nxny[2 * sg + 1] * es;
-        CK(cudaMalloc(ras, bytes));
+        if (keep && ctx->ras_dev && ctx->ras_dev_bytes == bytes) {
+            *ras = ctx->ras_dev;
+            if (ctx->reuse_raster) return SWDG_OK;
+        } else {
+            if (keep) {
+                cudaFree(ctx->ras_dev);
+                ctx->ras_dev = nullptr;
+                ctx->ras_dev_bytes = 0;
+            }
+            CK(cudaMalloc(ras, bytes));
+            if (keep) {
+                ctx->ras_dev = *ras;
+                ctx->ras_dev_bytes = bytes;
+            }
+        }
         CK(cudaMemcpyAsync(*ras, rasters[sg], bytes, cudaMemcpyHostToDevice, ctx->st));
         return SWDG_OK;
     };
@@ -1060,7 +1082,7 @@ static int upload_bathy(swdg_ctx* ctx, int nseg, const void* const* rasters, int
                                                          (double*)ctx->tiles, nk);
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(ctx->st));
-            cudaFree(ras);
+            if (!keep) cudaFree(ras);
         }
         const int gw = (int)std::min<int64_t>(152 * 32, (n * 32 + 255) / 256 + 1); // warp per cell
         if (dtype == SWDG_PIX_F32) {
@@ -1107,7 +1129,7 @@ static int upload_bathy(swdg_ctx* ctx, int nseg, const void* const* rasters, int
                     ctx->zmin + k0, ctx->zabs + k0, nk);
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(ctx->st));
-            cudaFree(ras);
+            if (!keep) cudaFree(ras);
         }
     }
     ctx->pix = dtype == SWDG_PIX_F32 ? 0 : 1;
@@ -2041,6 +2063,7 @@ int swdg_amr_setup(swdg_ctx* ctx, const swdg_forest* f) {
     ctx->forest = *f;
     ctx->leaves = lv;
     ctx->amr = true;
+    ctx->keep_raster = true;
     return SWDG_OK;
 }
 
@@ -2212,13 +2235,13 @@ int swdg_amr_adapt(swdg_ctx* ctx, const double* eta_in, int kind, double theta_r
     const std::vector<double> man2 = carry(man);
     const std::vector<double> nu2 = nu.empty() ? std::vector<double>() : carry(nu);
     // the new mesh, bathymetry, coefficients and state
-    const std::vector<uint8_t> ras = ctx->ras_h;
-    const Scalars keep_sc = *ctx->sc_host;
-    (void)keep_sc;
     rc = swdg_upload_mesh(ctx, n2, x.data(), h.data(), nb.data());
-    if (!rc) rc = swdg_upload_bathymetry(ctx, ras.data(), ctx->ras_dtype, ctx->ras_nx, ctx->ras_ny,
-                                        ctx->ras_geo[0], ctx->ras_geo[1], ctx->ras_geo[2],
-                                        ctx->ras_geo[3]);
+    // the kept raster (its host copy is the same data: nothing is copied)
+    ctx->reuse_raster = true;
+    if (!rc) rc = swdg_upload_bathymetry(ctx, ctx->ras_h.data(), ctx->ras_dtype, ctx->ras_nx,
+                                        ctx->ras_ny, ctx->ras_geo[0], ctx->ras_geo[1],
+                                        ctx->ras_geo[2], ctx->ras_geo[3]);
+    ctx->reuse_raster = false;
     if (!rc) rc = swdg_set_manning(ctx, man2.data(), SWDG_HOST);
     if (!rc && !nu2.empty()) rc = swdg_set_tracer_diffusivity(ctx, nu2.data(), SWDG_HOST);
     const size_t fb = (size_t)n2 * nd;
