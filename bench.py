@@ -41,7 +41,7 @@ WORKLOAD = "tidal-beach 256x256 cells, r=3, 16x16 px/cell (4096^2 f32 raster), R
 STAGES = 3
 # kernel-slot names of swdg_step_profile
 SLOTS = ["step_begin", "residual_1", "residual_2", "residual_3", "residual_4", "stage_2",
-         "stage_3", "stage_4", "final"]
+         "stage_3", "stage_4", "final", "faces_1", "faces_2", "faces_3", "faces_4"]
 
 
 def peaks():
@@ -58,20 +58,22 @@ def units_per_step(wl):
 
 
 # FP64 flops one launch performs per cell on this workload: active-lane
-# 2 DFMA + DMUL + DADD counted by ncu (profiles/fp64_ops_tidal_beach_256x256_r3.md);
-# a residual slot is k_faces + k_residual.  These kernels are bound by the FP64
-# pipe: GB300's FP64 rate is the roofline.
-FLOPS_PER_CELL = {"step_begin": 2187, "residual_1": 11085, "residual_2": 11800,
-                  "residual_3": 11799, "stage_2": 9284, "stage_3": 10070, "final": 7770}
+# 2 DFMA + DMUL + DADD counted by ncu (profiles/fp64_ops_tidal_beach_256x256_r3.md;
+# faces_l: k_faces of stage l, residual_l: k_residual).  These kernels are
+# bound by the FP64 pipe: GB300's FP64 rate is the roofline.
+FLOPS_PER_CELL = {"step_begin": 2187, "faces_1": 1683, "faces_2": 1850, "faces_3": 1851,
+                  "residual_1": 9452, "residual_2": 10000, "residual_3": 9998,
+                  "stage_2": 9284, "stage_3": 10070, "final": 7770}
 # the FP32-bulk kernels' FP64 flops (their FP32 work runs on the 60x faster FP32 pipe)
-FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "residual_1": 3529, "residual_2": 4243,
-                           "residual_3": 4243, "stage_2": 5992, "stage_3": 6244, "final": 6024}
-# DRAM bytes per launch (a residual slot: both kernels) from an ncu capture of
-# the current kernels (FP64 path); {} (traffic null) whenever the kernels
-# changed after the capture
-DRAM_BYTES_PER_LAUNCH = {"step_begin": 58996736, "residual_1": 326781696,
-                         "residual_2": 328875264, "residual_3": 328519424,
-                         "stage_2": 155726848, "stage_3": 248966656, "final": 253807104}
+FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "faces_1": 230, "faces_2": 400, "faces_3": 400,
+                           "residual_1": 3299, "residual_2": 3843, "residual_3": 3843,
+                           "stage_2": 5992, "stage_3": 6244, "final": 6024}
+# DRAM bytes per launch from an ncu capture of the current kernels (FP64
+# path); {} (traffic null) whenever the kernels changed after the capture
+DRAM_BYTES_PER_LAUNCH = {"step_begin": 59139072, "faces_1": 154420736, "faces_2": 154474752,
+                         "faces_3": 154984704, "residual_1": 171870208, "residual_2": 174084096,
+                         "residual_3": 173044224, "stage_2": 156064768, "stage_3": 248926208,
+                         "final": 254206976}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
 
 
@@ -83,6 +85,8 @@ def algorithmic_bytes_per_cell(kernel, r=3, P=16, pix_bytes=4, nres=3):
     geo = 16 + 32 + 8 + 1
     if kernel.startswith("residual"):
         return 4 * nd * 8 + 6 * nd * 8 + P * P * pix_bytes + geo
+    if kernel.startswith("faces"):  # the state once; the face slots are an intermediate
+        return 4 * nd * 8 + geo
     if kernel.startswith("stage") or kernel == "final":
         return 4 * nd * 8 + 2 * nd * 8 + 16 + nres * 6 * nd * 8 + 4 * nd * 8 + geo
     return 4 * nd * 8 + 2 * nd * 8 + 16 + P * P * pix_bytes + geo
@@ -459,13 +463,14 @@ def run_gpu(args, rank, world, local):
     per_launch = {SLOTS[i]: kms[i] / nprof for i in range(len(SLOTS)) if kms[i] > 0}
     total = sum(per_launch.values())
     # the dominant kernel: the kernel function with the largest share of the step
-    share = {"k_residual": sum(v for k, v in per_launch.items() if k.startswith("residual")),
-             "k_stage": sum(v for k, v in per_launch.items() if k.startswith("stage") or k == "final"),
-             "k_step_begin": per_launch.get("step_begin", 0.0)}
+    fn_of = lambda k: ("k_residual" if k.startswith("residual") else "k_faces" if
+                       k.startswith("faces") else "k_stage" if (k.startswith("stage") or
+                                                                k == "final") else "k_step_begin")
+    share = {}
+    for k, v in per_launch.items():
+        share[fn_of(k)] = share.get(fn_of(k), 0.0) + v
     dom_fn = max(share, key=share.get)
-    slots = [k for k in per_launch if (dom_fn == "k_residual" and k.startswith("residual")) or
-             (dom_fn == "k_stage" and (k.startswith("stage") or k == "final")) or
-             (dom_fn == "k_step_begin" and k == "step_begin")]
+    slots = [k for k in per_launch if fn_of(k) == dom_fn]
     avg_ms = sum(per_launch[k] for k in slots) / len(slots)
     table = FLOPS_PER_CELL if prec == 0 else FLOPS_PER_CELL_FP32BULK
     flops = sum(table[k] for k in slots) / len(slots) * wl.mesh.n

@@ -160,10 +160,11 @@ int swdg_step(swdg_ctx* ctx, int n_steps, double dt_or_neg, double* t_inout);
 /* Profiling variant of swdg_step: runs n_steps with the kernels launched one
  * by one (no graph), a CUDA event pair around each launch on the context's
  * stream.  ms_out[SWDG_PROF_SLOTS] receives the summed time per kernel slot:
- * 0 step start (degree switch + H(zeta^n)), 1..4 residual of stage 1..4,
- * 5..7 stage update 2..4, 8 final combination.  Unused slots are 0.  Same
- * numerics and status handling as swdg_step. */
-#define SWDG_PROF_SLOTS 9
+ * 0 step start (degree switch + H(zeta^n)), 1..4 residual of stage 1..4
+ * (the cell kernel), 5..7 stage update 2..4, 8 final combination, 9..12 the
+ * face points of stage 1..4 (the face kernel of that residual).  Unused
+ * slots are 0.  Same numerics and status handling as swdg_step. */
+#define SWDG_PROF_SLOTS 13
 int swdg_step_profile(swdg_ctx* ctx, int n_steps, double dt_or_neg, double* t_inout,
                       double* ms_out);
 

@@ -1434,8 +1434,10 @@ static int enqueue_step(swdg_ctx* ctx, cudaEvent_t (*ev)[2] = nullptr, int rec_s
             keep(l, 1 + l, l);
             keep_flags(l);
         }
-        mark(1 + l, 0);
+        mark(9 + l, 0);
         if (d.fflux) ctx->L.faces(d, ctx->tb, l, d.c[l], l == 0 ? 1 : 0, ctx->st);
+        mark(9 + l, 1);
+        mark(1 + l, 0);
         ctx->L.residual(d, ctx->tb, l, l, d.c[l], l == 0 ? 1 : 0, ctx->shp[KK_RESIDUAL], ctx->st);
         mark(1 + l, 1);
     }
@@ -1526,6 +1528,7 @@ int swdg_step_profile(swdg_ctx* ctx, int n_steps, double dt, double* t_inout, do
     used[0] = used[8] = true;
     for (int l = 0; l < ctx->d.s; ++l) {
         used[1 + l] = true;
+        used[9 + l] = ctx->d.fflux != nullptr;
         if (l > 0) used[4 + l] = true;
     }
     for (int i = 0; i < n_steps; ++i) {

@@ -757,7 +757,7 @@ __global__ void __maxnreg__(96)
 // member's rmax, as the residual does when it integrates the faces itself.
 // One job per lane.
 template <int R, typename Pix, int MODE, typename B>
-__global__ void __maxnreg__(128)
+__global__ void __maxnreg__(80)
     k_faces(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, int buf, double c_stage,
             int want_dt) {
     using S = Sz<R>;
@@ -1341,7 +1341,7 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
 }
 
 template <int R, typename Pix, int MODE, typename B>
-__global__ void __maxnreg__(128)
+__global__ void __maxnreg__(96)
     k_stage(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, const StageArgs sa) {
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;

@@ -404,7 +404,7 @@ class Context:
     def step_profile(self, n=1, dt=-1.0, t=None):
         """per-kernel-slot milliseconds (CUDA events) summed over n eager steps"""
         tt = _D(0.0 if t is None else t)
-        ms = np.zeros(9)
+        ms = np.zeros(13)
         self._ck(load().swdg_step_profile(self.h, n, dt, ctypes.byref(tt) if t is not None else None,
                                           ms.ctypes.data_as(_P)))
         return ms, (tt.value if t is not None else None)
