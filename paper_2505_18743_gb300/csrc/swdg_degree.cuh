@@ -13,7 +13,8 @@ struct Launchers {
     using S = Sz<R>;
     static constexpr size_t res_b = sizeof(double) * res_smem<R, B>();   // per warp
     static constexpr size_t begin_b = sizeof(double) * begin_smem<R>();
-    static constexpr size_t stage_b = sizeof(double) * stage_smem<R>();
+    // k_stage runs two cells per warp (a team of 16 lanes each)
+    static constexpr size_t stage_b = 2 * sizeof(double) * stage_smem<R>();
     static constexpr size_t diag_b = sizeof(double) * (2 * S::ND + 2 * S::NMP + 2 * S::NM * S::NM);
     static constexpr size_t vjp_b = sizeof(double) * vjp_smem<R>();
     static constexpr size_t svjp_b = sizeof(double) * stage_vjp_smem<R>();
@@ -36,7 +37,10 @@ struct Launchers {
         k_step_begin<R, Pix, MODE><<<s.grid, 32 * s.wpb, begin_b * s.wpb, st>>>(d, tb, do_switch);
     }
     static void stage(const Dev& d, const Tables& tb, const StageArgs& sa, Shape s, cudaStream_t st) {
-        k_stage<R, Pix, MODE, B><<<s.grid, 32 * s.wpb, stage_b * s.wpb, st>>>(d, tb, sa);
+        // two cells per warp: no more blocks than 2 wpb cells each
+        const int64_t need = (d.n + 2 * s.wpb - 1) / (2 * s.wpb);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(s.grid, need));
+        k_stage<R, Pix, MODE, B><<<grid, 32 * s.wpb, stage_b * s.wpb, st>>>(d, tb, sa);
     }
     static void masks(const Dev& d, int buf, Shape s, cudaStream_t st) {
         k_masks<R><<<s.grid, 32 * s.wpb, 0, st>>>(d, buf);

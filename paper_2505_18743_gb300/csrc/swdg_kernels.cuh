@@ -20,78 +20,78 @@ constexpr int MAXWPB = 8; // largest block the kernels are compiled for
 // small tensor contractions on a warp (all arrays in shared memory, x fastest)
 // ---------------------------------------------------------------------------
 // out[q1 NO + q0] = sum_b B[q1][b] sum_a B[q0][a] in[b NI + a]
-template <int NI, int NO, typename T = double>
+template <int NI, int NO, typename T = double, int TL = 32>
 __device__ __forceinline__ void tens_interp(const T (*B)[MXN], const T* in, T* tmp, T* out,
-                                            int lane) {
-    for (int i = lane; i < NI * NO; i += 32) {
+                                            int lane, unsigned tm = 0xffffffffu) {
+    for (int i = lane; i < NI * NO; i += TL) {
         int b = i / NO, q0 = i % NO;
         T s = T(0);
 #pragma unroll
         for (int a = 0; a < NI; ++a) s += B[q0][a] * in[b * NI + a];
         tmp[i] = s;
     }
-    __syncwarp();
-    for (int i = lane; i < NO * NO; i += 32) {
+    __syncwarp(tm);
+    for (int i = lane; i < NO * NO; i += TL) {
         int q1 = i / NO, q0 = i % NO;
         T s = T(0);
 #pragma unroll
         for (int b = 0; b < NI; ++b) s += B[q1][b] * tmp[b * NO + q0];
         out[i] = s;
     }
-    __syncwarp();
+    __syncwarp(tm);
 }
 
 // out[b NI + a] = sum_q1 B[q1][b] sum_q0 B[q0][a] in[q1 NO + q0]   (transpose)
-template <int NI, int NO, typename T = double>
+template <int NI, int NO, typename T = double, int TL = 32>
 __device__ __forceinline__ void tens_test(const T (*B)[MXN], const T* in, T* tmp, T* out,
-                                          int lane) {
-    for (int i = lane; i < NO * NI; i += 32) {
+                                          int lane, unsigned tm = 0xffffffffu) {
+    for (int i = lane; i < NO * NI; i += TL) {
         int q1 = i / NI, a = i % NI;
         T s = T(0);
 #pragma unroll
         for (int q0 = 0; q0 < NO; ++q0) s += B[q0][a] * in[q1 * NO + q0];
         tmp[i] = s;
     }
-    __syncwarp();
-    for (int i = lane; i < NI * NI; i += 32) {
+    __syncwarp(tm);
+    for (int i = lane; i < NI * NI; i += TL) {
         int b = i / NI, a = i % NI;
         T s = T(0);
 #pragma unroll
         for (int q1 = 0; q1 < NO; ++q1) s += B[q1][b] * tmp[q1 * NI + a];
         out[i] = s;
     }
-    __syncwarp();
+    __syncwarp(tm);
 }
 
 // out[b N + a] = scale * sum_d C(b,d) sum_c C(a,c) in[d N + c], C(i,j) = T ? M[j][i] : M[i][j]
-template <int N, bool T, int LD, typename E = double>
+template <int N, bool T, int LD, typename E = double, int TL = 32>
 __device__ __forceinline__ void kron_apply(const E (*M)[LD], const E* in, E* tmp, E* out, E scale,
-                                           int lane) {
-    for (int i = lane; i < N * N; i += 32) {
+                                           int lane, unsigned tm = 0xffffffffu) {
+    for (int i = lane; i < N * N; i += TL) {
         int d = i / N, a = i % N;
         E s = E(0);
 #pragma unroll
         for (int c = 0; c < N; ++c) s += (T ? M[c][a] : M[a][c]) * in[d * N + c];
         tmp[i] = s;
     }
-    __syncwarp();
-    for (int i = lane; i < N * N; i += 32) {
+    __syncwarp(tm);
+    for (int i = lane; i < N * N; i += TL) {
         int b = i / N, a = i % N;
         E s = E(0);
 #pragma unroll
         for (int d = 0; d < N; ++d) s += (T ? M[d][b] : M[b][d]) * tmp[d * N + a];
         out[i] = scale * s;
     }
-    __syncwarp();
+    __syncwarp(tm);
 }
 
 // the contractions above for two inputs at once (each output by the same sum,
 // the two halves of the work side by side on the lanes)
-template <int NI, int NO, typename T = double>
+template <int NI, int NO, typename T = double, int TL = 32>
 __device__ __forceinline__ void tens_interp2(const T (*B)[MXN], const T* in0, const T* in1, T* tmp0,
-                                             T* tmp1, T* out0, T* out1, int lane) {
+                                             T* tmp1, T* out0, T* out1, int lane, unsigned tm = 0xffffffffu) {
     constexpr int M1 = NI * NO, M2 = NO * NO;
-    for (int i = lane; i < 2 * M1; i += 32) {
+    for (int i = lane; i < 2 * M1; i += TL) {
         const int j = i < M1 ? i : i - M1;
         const T* in = i < M1 ? in0 : in1;
         const int b = j / NO, q0 = j % NO;
@@ -100,8 +100,8 @@ __device__ __forceinline__ void tens_interp2(const T (*B)[MXN], const T* in0, co
         for (int a = 0; a < NI; ++a) s += B[q0][a] * in[b * NI + a];
         (i < M1 ? tmp0 : tmp1)[j] = s;
     }
-    __syncwarp();
-    for (int i = lane; i < 2 * M2; i += 32) {
+    __syncwarp(tm);
+    for (int i = lane; i < 2 * M2; i += TL) {
         const int j = i < M2 ? i : i - M2;
         const T* tmp = i < M2 ? tmp0 : tmp1;
         const int q1 = j / NO, q0 = j % NO;
@@ -110,14 +110,14 @@ __device__ __forceinline__ void tens_interp2(const T (*B)[MXN], const T* in0, co
         for (int b = 0; b < NI; ++b) s += B[q1][b] * tmp[b * NO + q0];
         (i < M2 ? out0 : out1)[j] = s;
     }
-    __syncwarp();
+    __syncwarp(tm);
 }
 
-template <int NI, int NO, typename T = double>
+template <int NI, int NO, typename T = double, int TL = 32>
 __device__ __forceinline__ void tens_test2(const T (*B)[MXN], const T* in0, const T* in1, T* tmp0,
-                                           T* tmp1, T* out0, T* out1, int lane) {
+                                           T* tmp1, T* out0, T* out1, int lane, unsigned tm = 0xffffffffu) {
     constexpr int M1 = NO * NI, M2 = NI * NI;
-    for (int i = lane; i < 2 * M1; i += 32) {
+    for (int i = lane; i < 2 * M1; i += TL) {
         const int j = i < M1 ? i : i - M1;
         const T* in = i < M1 ? in0 : in1;
         const int q1 = j / NI, a = j % NI;
@@ -126,8 +126,8 @@ __device__ __forceinline__ void tens_test2(const T (*B)[MXN], const T* in0, cons
         for (int q0 = 0; q0 < NO; ++q0) s += B[q0][a] * in[q1 * NO + q0];
         (i < M1 ? tmp0 : tmp1)[j] = s;
     }
-    __syncwarp();
-    for (int i = lane; i < 2 * M2; i += 32) {
+    __syncwarp(tm);
+    for (int i = lane; i < 2 * M2; i += TL) {
         const int j = i < M2 ? i : i - M2;
         const T* tmp = i < M2 ? tmp0 : tmp1;
         const int b = j / NI, a = j % NI;
@@ -136,14 +136,14 @@ __device__ __forceinline__ void tens_test2(const T (*B)[MXN], const T* in0, cons
         for (int q1 = 0; q1 < NO; ++q1) s += B[q1][b] * tmp[q1 * NI + a];
         (i < M2 ? out0 : out1)[j] = s;
     }
-    __syncwarp();
+    __syncwarp(tm);
 }
 
-template <int N, bool T, int LD, typename E = double>
+template <int N, bool T, int LD, typename E = double, int TL = 32>
 __device__ __forceinline__ void kron_apply2(const E (*M)[LD], const E* in0, const E* in1, E* tmp0,
-                                            E* tmp1, E* out0, E* out1, E scale, int lane) {
+                                            E* tmp1, E* out0, E* out1, E scale, int lane, unsigned tm = 0xffffffffu) {
     constexpr int MM = N * N;
-    for (int i = lane; i < 2 * MM; i += 32) {
+    for (int i = lane; i < 2 * MM; i += TL) {
         const int j = i < MM ? i : i - MM;
         const E* in = i < MM ? in0 : in1;
         const int d = j / N, a = j % N;
@@ -152,8 +152,8 @@ __device__ __forceinline__ void kron_apply2(const E (*M)[LD], const E* in0, cons
         for (int c = 0; c < N; ++c) s += (T ? M[c][a] : M[a][c]) * in[d * N + c];
         (i < MM ? tmp0 : tmp1)[j] = s;
     }
-    __syncwarp();
-    for (int i = lane; i < 2 * MM; i += 32) {
+    __syncwarp(tm);
+    for (int i = lane; i < 2 * MM; i += TL) {
         const int j = i < MM ? i : i - MM;
         const E* tmp = i < MM ? tmp0 : tmp1;
         const int b = j / N, a = j % N;
@@ -162,7 +162,7 @@ __device__ __forceinline__ void kron_apply2(const E (*M)[LD], const E* in0, cons
         for (int d = 0; d < N; ++d) s += (T ? M[d][b] : M[b][d]) * tmp[d * N + a];
         (i < MM ? out0 : out1)[j] = scale * s;
     }
-    __syncwarp();
+    __syncwarp(tm);
 }
 
 // ---------------------------------------------------------------------------
@@ -836,12 +836,13 @@ __global__ void __maxnreg__(80)
 // warp-cooperative scalar Newton for Hbar(e) = target (r_K = 0 cells,
 // Eqs. newton, initial_guess); returns iterations
 // ---------------------------------------------------------------------------
-template <int R, typename Pix, int MODE>
+template <int R, typename Pix, int MODE, int TL = 32>
 __device__ __forceinline__ void mass_scalar(const Dev& d, const Tables& tb, int64_t k, double J,
-                                            double e, int lane, double& H, double& A) {
+                                            double e, int lane, double& H, double& A,
+                                            unsigned tm = 0xffffffffu) {
     using S = Sz<R>;
     double h = 0.0, a = 0.0;
-    for (int p = lane; p < S::NMP; p += 32) {
+    for (int p = lane; p < S::NMP; p += TL) {
         const int ia = p % S::NM, ib = p / S::NM;
         double V, Ap;
         Site<R, Pix, MODE>::VA(d, tb, k, SET_MASS, ia, ib, e, V, Ap);
@@ -849,20 +850,20 @@ __device__ __forceinline__ void mass_scalar(const Dev& d, const Tables& tb, int6
         h += w * V;
         a += w * Ap;
     }
-    H = warp_sum(h);
-    A = warp_sum(a);
+    H = team_sum<TL>(h, tm);
+    A = team_sum<TL>(a, tm);
 }
 
-template <int R, typename Pix, int MODE>
+template <int R, typename Pix, int MODE, int TL = 32>
 __device__ int scalar_newton(const Dev& d, const Tables& tb, int64_t k, double J, double target,
-                             double& e, int lane) {
+                             double& e, int lane, unsigned tm = 0xffffffffu) {
     constexpr int ND = Sz<R>::ND;
     double H, A;
-    mass_scalar<R, Pix, MODE>(d, tb, k, J, e, lane, H, A);
+    mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, H, A, tm);
     if (A == 0.0) e = -d.zmax[k] + d.eps0;
     int it = 0;
     for (int kk = 0; kk < d.newton_max; ++kk) {
-        mass_scalar<R, Pix, MODE>(d, tb, k, J, e, lane, H, A);
+        mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, H, A, tm);
         if (A == 0.0) break;
         const double dd = (H - target) / A;
         e -= dd;
@@ -1038,111 +1039,111 @@ constexpr int stage_smem() {
 // warp, then M x = b in place by column-oriented forward and back
 // substitution (one reciprocal per column, the updates spread over lanes);
 // returns false on a non-positive pivot
-template <int ND>
-__device__ bool chol_solve(double* M, double* b, double* inv, int lane) {
+template <int ND, int TL = 32>
+__device__ bool chol_solve(double* M, double* b, double* inv, int lane, unsigned tm = 0xffffffffu) {
     for (int j = 0; j < ND; ++j) {
-        __syncwarp();
+        __syncwarp(tm);
         const double djj = M[j * ND + j];
         if (!(djj > 0.0)) return false;
         const double ljj = sqrt(djj);
         const double r = 1.0 / ljj;
-        __syncwarp();
-        for (int i = j + 1 + lane; i < ND; i += 32) M[i * ND + j] *= r;
+        __syncwarp(tm);
+        for (int i = j + 1 + lane; i < ND; i += TL) M[i * ND + j] *= r;
         if (lane == 0) {
             M[j * ND + j] = ljj;
             inv[j] = r;
         }
-        __syncwarp();
+        __syncwarp(tm);
         const int m = ND - j - 1;
-        for (int idx = lane; idx < m * m; idx += 32) {
+        for (int idx = lane; idx < m * m; idx += TL) {
             const int i = j + 1 + idx / m, l = j + 1 + idx % m;
             if (l <= i) M[i * ND + l] -= M[i * ND + j] * M[l * ND + j];
         }
     }
-    __syncwarp();
+    __syncwarp(tm);
     for (int j = 0; j < ND; ++j) { // L y = b
         const double yj = b[j] * inv[j];
-        __syncwarp();
-        for (int i = j + 1 + lane; i < ND; i += 32) b[i] -= M[i * ND + j] * yj;
+        __syncwarp(tm);
+        for (int i = j + 1 + lane; i < ND; i += TL) b[i] -= M[i * ND + j] * yj;
         if (lane == 0) b[j] = yj;
-        __syncwarp();
+        __syncwarp(tm);
     }
     for (int j = ND - 1; j >= 0; --j) { // L^T x = y
         const double xj = b[j] * inv[j];
-        __syncwarp();
-        for (int i = lane; i < j; i += 32) b[i] -= M[j * ND + i] * xj;
+        __syncwarp(tm);
+        for (int i = lane; i < j; i += TL) b[i] -= M[j * ND + i] * xj;
         if (lane == 0) b[j] = xj;
-        __syncwarp();
+        __syncwarp(tm);
     }
     return true;
 }
 
 // FP32 Cholesky factorisation (lower part of M, reciprocal pivots in inv);
 // returns false on a non-positive pivot
-template <int ND>
-__device__ bool chol_factor_f(float* M, float* inv, int lane) {
+template <int ND, int TL = 32>
+__device__ bool chol_factor_f(float* M, float* inv, int lane, unsigned tm = 0xffffffffu) {
     for (int j = 0; j < ND; ++j) {
-        __syncwarp();
+        __syncwarp(tm);
         const float djj = M[j * ND + j];
         if (!(djj > 0.0f)) return false;
         const float ljj = sqrtf(djj);
         const float r = 1.0f / ljj;
-        __syncwarp();
-        for (int i = j + 1 + lane; i < ND; i += 32) M[i * ND + j] *= r;
+        __syncwarp(tm);
+        for (int i = j + 1 + lane; i < ND; i += TL) M[i * ND + j] *= r;
         if (lane == 0) {
             M[j * ND + j] = ljj;
             inv[j] = r;
         }
-        __syncwarp();
+        __syncwarp(tm);
         const int m = ND - j - 1;
-        for (int idx = lane; idx < m * m; idx += 32) {
+        for (int idx = lane; idx < m * m; idx += TL) {
             const int i = j + 1 + idx / m, l = j + 1 + idx % m;
             if (l <= i) M[i * ND + l] -= M[i * ND + j] * M[l * ND + j];
         }
     }
-    __syncwarp();
+    __syncwarp(tm);
     return true;
 }
 
 // (L L^T)^-1 b in FP32 with the factor of chol_factor_f, in place
-template <int ND>
-__device__ void chol_subst_f(const float* M, const float* inv, float* b, int lane) {
+template <int ND, int TL = 32>
+__device__ void chol_subst_f(const float* M, const float* inv, float* b, int lane, unsigned tm = 0xffffffffu) {
     for (int j = 0; j < ND; ++j) {
         const float yj = b[j] * inv[j];
-        __syncwarp();
-        for (int i = j + 1 + lane; i < ND; i += 32) b[i] -= M[i * ND + j] * yj;
+        __syncwarp(tm);
+        for (int i = j + 1 + lane; i < ND; i += TL) b[i] -= M[i * ND + j] * yj;
         if (lane == 0) b[j] = yj;
-        __syncwarp();
+        __syncwarp(tm);
     }
     for (int j = ND - 1; j >= 0; --j) {
         const float xj = b[j] * inv[j];
-        __syncwarp();
-        for (int i = lane; i < j; i += 32) b[i] -= M[j * ND + i] * xj;
+        __syncwarp(tm);
+        for (int i = lane; i < j; i += TL) b[i] -= M[j * ND + i] * xj;
         if (lane == 0) b[j] = xj;
-        __syncwarp();
+        __syncwarp(tm);
     }
 }
 
 // FP32 copy of M_(a,b),(c,d) = sum c_{al,be} Bm[al][a] Bm[al][c] Bm[be][b] Bm[be][d]
 // from the FP32 basis table and one FP32 copy of the weights cw (conversions
 // run on the FP64 pipe: converting inside the sums would cost one per term)
-template <int ND1, int NM>
+template <int ND1, int NM, int TL = 32>
 __device__ __forceinline__ void assemble_mass_f(const Tables& tb, const double* cw, float* Y,
-                                                float* M, int lane) {
+                                                float* M, int lane, unsigned tm = 0xffffffffu) {
     constexpr int ND = ND1 * ND1;
     static_assert(NM * NM <= ND * ND, "the weights are staged in M");
     float* cwf = M; // M is written only by the second pass
-    for (int p = lane; p < NM * NM; p += 32) cwf[p] = (float)cw[p];
-    __syncwarp();
-    for (int i = lane; i < ND1 * ND1 * NM; i += 32) {
+    for (int p = lane; p < NM * NM; p += TL) cwf[p] = (float)cw[p];
+    __syncwarp(tm);
+    for (int i = lane; i < ND1 * ND1 * NM; i += TL) {
         const int a = i / (ND1 * NM), r_ = i % (ND1 * NM), c = r_ / NM, be = r_ % NM;
         float s = 0.0f;
 #pragma unroll
         for (int al = 0; al < NM; ++al) s += cwf[al + NM * be] * tb.BmF[al][a] * tb.BmF[al][c];
         Y[i] = s;
     }
-    __syncwarp();
-    for (int i = lane; i < ND * ND; i += 32) {
+    __syncwarp(tm);
+    for (int i = lane; i < ND * ND; i += TL) {
         const int r_ = i / ND, s_ = i % ND;
         const int a = r_ % ND1, b = r_ / ND1, c = s_ % ND1, dd = s_ / ND1;
         float s = 0.0f;
@@ -1151,23 +1152,23 @@ __device__ __forceinline__ void assemble_mass_f(const Tables& tb, const double* 
             s += Y[(a * ND1 + c) * NM + be] * tb.BmF[be][b] * tb.BmF[be][dd];
         M[i] = s;
     }
-    __syncwarp();
+    __syncwarp(tm);
 }
 
 // M_(a,b),(c,d) = sum_{al,be} c_{al,be} Bm[al][a] Bm[al][c] Bm[be][b] Bm[be][d]
-template <int ND1, int NM>
+template <int ND1, int NM, int TL = 32>
 __device__ __forceinline__ void assemble_mass(const Tables& tb, const double* cw, double* Y,
-                                              double* M, int lane) {
+                                              double* M, int lane, unsigned tm = 0xffffffffu) {
     constexpr int ND = ND1 * ND1;
-    for (int i = lane; i < ND1 * ND1 * NM; i += 32) {
+    for (int i = lane; i < ND1 * ND1 * NM; i += TL) {
         const int a = i / (ND1 * NM), r_ = i % (ND1 * NM), c = r_ / NM, be = r_ % NM;
         double s = 0.0;
 #pragma unroll
         for (int al = 0; al < NM; ++al) s += cw[al + NM * be] * tb.Bm[al][a] * tb.Bm[al][c];
         Y[i] = s;
     }
-    __syncwarp();
-    for (int i = lane; i < ND * ND; i += 32) {
+    __syncwarp(tm);
+    for (int i = lane; i < ND * ND; i += TL) {
         const int r_ = i / ND, s_ = i % ND;
         const int a = r_ % ND1, b = r_ / ND1, c = s_ % ND1, dd = s_ / ND1;
         double s = 0.0;
@@ -1176,7 +1177,7 @@ __device__ __forceinline__ void assemble_mass(const Tables& tb, const double* cw
             s += Y[(a * ND1 + c) * NM + be] * tb.Bm[be][b] * tb.Bm[be][dd];
         M[i] = s;
     }
-    __syncwarp();
+    __syncwarp(tm);
 }
 
 // Solve H x = b for the depth-weighted mass matrix H = B^T diag(cw) B (the
@@ -1189,29 +1190,29 @@ __device__ __forceinline__ void assemble_mass(const Tables& tb, const double* cw
 // (an ill-conditioned near-dry cell), the FP64 Cholesky decides.  x (FP64, in place of b on
 // return).  Scratch: Mf, Yf (float), r, t (ND doubles), q (NMP doubles),
 // tmp (2 NM NM doubles), M, Y (double, fallback).
-template <int ND1, int NM>
+template <int ND1, int NM, int TL = 32>
 __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, float* Mf,
                                  float* Yf, float* invf, float* rf, double* x, double* r,
                                  double* q, double* tmp, double* M, double* Y, double* inv,
-                                 int lane) {
+                                 int lane, unsigned tm = 0xffffffffu) {
     constexpr int ND = ND1 * ND1, NMP = NM * NM;
-    assemble_mass_f<ND1, NM>(tb, cw, Yf, Mf, lane);
-    bool ok = chol_factor_f<ND>(Mf, invf, lane);
+    assemble_mass_f<ND1, NM, TL>(tb, cw, Yf, Mf, lane, tm);
+    bool ok = chol_factor_f<ND, TL>(Mf, invf, lane, tm);
     if (ok) {
-        for (int i = lane; i < ND; i += 32) {
+        for (int i = lane; i < ND; i += TL) {
             x[i] = 0.0;
             r[i] = b[i];
         }
-        __syncwarp();
+        __syncwarp(tm);
         ok = false;
         double dprev = 0.0; // max |correction| of the previous sweep
         for (int sweep = 0; sweep < 6; ++sweep) {
-            for (int i = lane; i < ND; i += 32) rf[i] = (float)r[i];
-            __syncwarp();
-            chol_subst_f<ND>(Mf, invf, rf, lane);
+            for (int i = lane; i < ND; i += TL) rf[i] = (float)r[i];
+            __syncwarp(tm);
+            chol_subst_f<ND, TL>(Mf, invf, rf, lane, tm);
             // max |correction| and max |x| (a NaN counts as 0, as under fmax),
             // reduced on their bit patterns
-            static_assert(ND <= 32, "one unknown per lane");
+            static_assert(ND <= TL, "one unknown per lane");
             float da = 0.0f;
             double xa = 0.0;
             if (lane < ND) {
@@ -1222,8 +1223,8 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
                     (unsigned long long)__double_as_longlong(x[lane]) & 0x7fffffffffffffffull;
                 xa = __longlong_as_double((long long)(xb > 0x7ff0000000000000ull ? 0ull : xb));
             }
-            const double dmax = (double)warp_max_nonneg(da);
-            const double xmax = warp_max_nonneg(xa);
+            const double dmax = (double)team_max_nonneg(da, tm);
+            const double xmax = team_max_nonneg(xa, tm);
             // converged when this correction is below 1e-15 of x, or when the
             // next one is, as predicted from the contraction of the last two
             // (dmax / dprev, at most 1/2)
@@ -1232,13 +1233,13 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
             if (!(dmax <= 1e-15 * xmax) && !(dmax == 0.0) && !next_small) {
                 dprev = dmax;
                 // r = b - H x, H x = B^T (cw * (B x))
-                __syncwarp();
-                tens_interp<ND1, NM>(tb.Bm, x, tmp, q, lane);
-                for (int p = lane; p < NMP; p += 32) q[p] *= cw[p];
-                __syncwarp();
-                tens_test<ND1, NM>(tb.Bm, q, tmp, r, lane);
-                for (int i = lane; i < ND; i += 32) r[i] = b[i] - r[i];
-                __syncwarp();
+                __syncwarp(tm);
+                tens_interp<ND1, NM, double, TL>(tb.Bm, x, tmp, q, lane, tm);
+                for (int p = lane; p < NMP; p += TL) q[p] *= cw[p];
+                __syncwarp(tm);
+                tens_test<ND1, NM, double, TL>(tb.Bm, q, tmp, r, lane, tm);
+                for (int i = lane; i < ND; i += TL) r[i] = b[i] - r[i];
+                __syncwarp(tm);
             } else {
                 ok = true;
                 break;
@@ -1246,12 +1247,12 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
         }
     }
     if (ok) {
-        for (int i = lane; i < ND; i += 32) b[i] = x[i];
-        __syncwarp();
+        for (int i = lane; i < ND; i += TL) b[i] = x[i];
+        __syncwarp(tm);
         return true;
     }
-    assemble_mass<ND1, NM>(tb, cw, Y, M, lane);
-    return chol_solve<ND>(M, b, inv, lane);
+    assemble_mass<ND1, NM, TL>(tb, cw, Y, M, lane, tm);
+    return chol_solve<ND, TL>(M, b, inv, lane, tm);
 }
 
 // Momentum stage solve of an r_K = r cell in arithmetic T (Eq. algebraic_discharge
@@ -1262,11 +1263,11 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
 // sub-grid depth, q in T).  Optionally the linearised friction term
 // Llin = -S^T (J w gamma S Q).  Inputs su (v^n, FP64), rq [2][ND] (FP64);
 // outputs Q [2][ND] (FP64) and llin [2][ND] (FP64).
-template <int R, typename Pix, int MODE, typename T>
+template <int R, typename Pix, int MODE, typename T, int TL = 32>
 __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double J, double man,
                                double dt, double add, bool need_gam, bool make_llin, int prev_buf,
                                const double* su, unsigned cm0, const double* rq, T* w0, T* w1,
-                               double* zp, double* tmpd, double* Q, double* llin, int lane) {
+                               double* zp, double* tmpd, double* Q, double* llin, int lane, unsigned tm = 0xffffffffu) {
     using S = Sz<R>;
     constexpr int ND1 = S::ND1, ND = S::ND, NG = S::NG, NGP = S::NGP;
     const auto Bg = tab_or<T>(tb.Bg, tb.BgF);
@@ -1284,59 +1285,59 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
     if (need_gam) {
         const unsigned cmp = d.cmask[(size_t)prev_buf * n + k];
         const double* uz = ufield(d, prev_buf, 0, ND) + k * ND;
-        tens_interp<ND1, NG>(tb.Bg, uz, tmpd, zp, lane); // zeta of v^(l-1), FP64
+        tens_interp<ND1, NG, double, TL>(tb.Bg, uz, tmpd, zp, lane, tm); // zeta of v^(l-1), FP64
         if (cmp & 1u)
-            for (int p = lane; p < NGP; p += 32) zp[p] = uz[0];
+            for (int p = lane; p < NGP; p += TL) zp[p] = uz[0];
         const double* up0 = ufield(d, prev_buf, 1, ND) + k * ND;
         const double* up1 = ufield(d, prev_buf, 2, ND) + k * ND;
-        for (int i = lane; i < 2 * ND; i += 32) nod[i] = (T)(i < ND ? up0[i] : up1[i - ND]);
-        __syncwarp();
-        tens_interp2<ND1, NG, T>(Bg, nod, nod + ND, tmp, tmp1, pg + 3 * NGP, pg + 4 * NGP, lane);
+        for (int i = lane; i < 2 * ND; i += TL) nod[i] = (T)(i < ND ? up0[i] : up1[i - ND]);
+        __syncwarp(tm);
+        tens_interp2<ND1, NG, T, TL>(Bg, nod, nod + ND, tmp, tmp1, pg + 3 * NGP, pg + 4 * NGP, lane, tm);
         if (cmp & 2u)
-            for (int p = lane; p < NGP; p += 32) pg[3 * NGP + p] = (T)up0[0];
+            for (int p = lane; p < NGP; p += TL) pg[3 * NGP + p] = (T)up0[0];
         if (cmp & 4u)
-            for (int p = lane; p < NGP; p += 32) pg[4 * NGP + p] = (T)up1[0];
-        __syncwarp();
-        for (int p = lane; p < NGP; p += 32) {
+            for (int p = lane; p < NGP; p += TL) pg[4 * NGP + p] = (T)up1[0];
+        __syncwarp(tm);
+        for (int p = lane; p < NGP; p += TL) {
             double V, A;
             Site<R, Pix, MODE>::VA(d, tb, k, SET_MOM, p % NG, p / NG, zp[p], V, A);
             gam[p] = gamma_manning<T>((T)man, (T)V, pg[3 * NGP + p], pg[4 * NGP + p], (T)d.g,
                                       (T)d.eps);
         }
     } else {
-        for (int p = lane; p < NGP; p += 32) gam[p] = T(0);
+        for (int p = lane; p < NGP; p += TL) gam[p] = T(0);
     }
-    __syncwarp();
-    for (int i = lane; i < 2 * ND; i += 32) nod[i] = (T)su[ND + i];
-    __syncwarp();
-    tens_interp2<ND1, NG, T>(Bg, nod, nod + ND, tmp, tmp1, pg + 3 * NGP, pg + 4 * NGP, lane);
+    __syncwarp(tm);
+    for (int i = lane; i < 2 * ND; i += TL) nod[i] = (T)su[ND + i];
+    __syncwarp(tm);
+    tens_interp2<ND1, NG, T, TL>(Bg, nod, nod + ND, tmp, tmp1, pg + 3 * NGP, pg + 4 * NGP, lane, tm);
     if (cm0 & 2u)
-        for (int p = lane; p < NGP; p += 32) pg[3 * NGP + p] = (T)su[ND];
+        for (int p = lane; p < NGP; p += TL) pg[3 * NGP + p] = (T)su[ND];
     if (cm0 & 4u)
-        for (int p = lane; p < NGP; p += 32) pg[4 * NGP + p] = (T)su[2 * ND];
-    for (int i = lane; i < 2 * ND; i += 32) nod[i] = (T)rq[i];
-    __syncwarp();
-    kron_apply2<ND1, true, MXP, T>(Bginv, nod, nod + ND, tmp, tmp1, pg, pg + NGP, T(1), lane);
-    for (int p = lane; p < NGP; p += 32) {
+        for (int p = lane; p < NGP; p += TL) pg[4 * NGP + p] = (T)su[2 * ND];
+    for (int i = lane; i < 2 * ND; i += TL) nod[i] = (T)rq[i];
+    __syncwarp(tm);
+    kron_apply2<ND1, true, MXP, T, TL>(Bginv, nod, nod + ND, tmp, tmp1, pg, pg + NGP, T(1), lane, tm);
+    for (int p = lane; p < NGP; p += TL) {
         const T w = (T)(J * tb.wg[p % NG] * tb.wg[p / NG]);
         const T rD = T(1) / (w * (T(1) + (T)(add * dt) * gam[p]));
         pg[0 * NGP + p] = (w * pg[3 * NGP + p] + pg[0 * NGP + p]) * rD;
         pg[1 * NGP + p] = (w * pg[4 * NGP + p] + pg[1 * NGP + p]) * rD;
     }
-    __syncwarp();
-    kron_apply2<ND1, false, MXP, T>(Bginv, pg, pg + NGP, tmp, tmp1, nod, nod + ND, T(1), lane);
-    for (int i = lane; i < 2 * ND; i += 32) Q[i] = (double)nod[i];
-    __syncwarp();
+    __syncwarp(tm);
+    kron_apply2<ND1, false, MXP, T, TL>(Bginv, pg, pg + NGP, tmp, tmp1, nod, nod + ND, T(1), lane, tm);
+    for (int i = lane; i < 2 * ND; i += TL) Q[i] = (double)nod[i];
+    __syncwarp(tm);
     if (make_llin) {
-        for (int p = lane; p < NGP; p += 32) {
+        for (int p = lane; p < NGP; p += TL) {
             const T w = (T)(J * tb.wg[p % NG] * tb.wg[p / NG]) * gam[p];
             pg[3 * NGP + p] = -w * pg[p];
             pg[4 * NGP + p] = -w * pg[NGP + p];
         }
-        __syncwarp();
-        tens_test2<ND1, NG, T>(Bg, pg + 3 * NGP, pg + 4 * NGP, tmp, tmp1, nod, nod + ND, lane);
-        for (int i = lane; i < 2 * ND; i += 32) llin[i] = (double)nod[i];
-        __syncwarp();
+        __syncwarp(tm);
+        tens_test2<ND1, NG, T, TL>(Bg, pg + 3 * NGP, pg + 4 * NGP, tmp, tmp1, nod, nod + ND, lane, tm);
+        for (int i = lane; i < 2 * ND; i += TL) llin[i] = (double)nod[i];
+        __syncwarp(tm);
     }
 }
 
@@ -1347,7 +1348,12 @@ __global__ void __maxnreg__(96)
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
     extern __shared__ double smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    // two cells per warp, one per team of 16 lanes (a cell's loops run over 16
+    // nodes and 16 momentum points): "warp" is the team within the block,
+    // "lane" the lane within the team, wpb the teams per block
+    constexpr int TL = 16;
+    const int warp = threadIdx.x / TL, lane = threadIdx.x % TL, wpb = blockDim.x / TL;
+    const unsigned tm = 0xFFFFu << (threadIdx.x & 16); // the team's lanes
     double* su = smem + warp * stage_smem<R>(); // [4][ND] state v^n
     double* T = su + 4 * ND;                    // [ND]
     double* rq = T + ND;                        // [2][ND]
@@ -1378,7 +1384,7 @@ __global__ void __maxnreg__(96)
     int viol = 0, fb = 0, bad = 0;
 
     for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n; k += (int64_t)gridDim.x * wpb) {
-        for (int i = lane; i < 4 * ND; i += 32) su[i] = ufield(d, 0, i / ND, ND)[k * ND + (i % ND)];
+        for (int i = lane; i < 4 * ND; i += TL) su[i] = ufield(d, 0, i / ND, ND)[k * ND + (i % ND)];
         const unsigned cm0 = d.cmask[k];
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
         const double man = d.manning[k];
@@ -1386,7 +1392,7 @@ __global__ void __maxnreg__(96)
         const double dt = get_dt(d, member_of(d, k)); // the member's step
         // right-hand sides of Eqs. algebraic_elevation, algebraic_discharge, algebraic_concentration
         double tsum = 0.0;
-        for (int i = lane; i < ND; i += 32) {
+        for (int i = lane; i < ND; i += TL) {
             double sf = 0.0, sgx = 0.0, sgy = 0.0, sr = 0.0;
             for (int m = 0; m < sa.nres; ++m) {
                 const size_t idx = (size_t)k * ND + i;
@@ -1404,23 +1410,23 @@ __global__ void __maxnreg__(96)
             rq[ND + i] = dt * sgy;
             rc[i] = d.CN[k * ND + i] + dt * sr;
         }
-        const double Tbar = d.HNbar[k] + warp_sum(tsum);
+        const double Tbar = d.HNbar[k] + team_sum<TL>(tsum, tm);
         if (Tbar < 0.0) viol++;
         bool scalar = (flag == 0);
         int its = 0;
-        __syncwarp();
+        __syncwarp(tm);
         if (!scalar) {
-            for (int i = lane; i < ND; i += 32) z[i] = su[i];
+            for (int i = lane; i < ND; i += TL) z[i] = su[i];
             bool zc = (cm0 & 1u) != 0;
             bool prev_full = false;
-            __syncwarp();
+            __syncwarp(tm);
             // each pass evaluates V, A at the current iterate; the last pass is
             // the evaluation at the result (for the tracer matrix and the
             // completely-dry test)
             for (int kk = 0;; ++kk) {
-                tens_interp<ND1, NM>(tb.Bm, z, tmp, pe, lane);
+                tens_interp<ND1, NM, double, TL>(tb.Bm, z, tmp, pe, lane, tm);
                 int ndry = 0, npart = 0;
-                for (int p = lane; p < NMP; p += 32) {
+                for (int p = lane; p < NMP; p += TL) {
                     if (zc) pe[p] = z[0];
                     double V, A;
                     bool full;
@@ -1430,8 +1436,8 @@ __global__ void __maxnreg__(96)
                     if (A == 0.0) ndry++;
                     else if (!full) npart++;
                 }
-                ndry = __reduce_add_sync(0xffffffffu, ndry);
-                npart = __reduce_add_sync(0xffffffffu, npart);
+                ndry = __reduce_add_sync(tm, ndry);
+                npart = __reduce_add_sync(tm, npart);
                 if (ndry) { scalar = true; break; }
                 // every pixel wet at the previous and at this iterate: H is affine
                 // on the segment between them and M(previous) is its exact
@@ -1439,37 +1445,37 @@ __global__ void __maxnreg__(96)
                 // Sec. 3.4); no verification step is needed
                 if (kk > 0 && prev_full && npart == 0) break;
                 if (kk == d.newton_max) break;
-                __syncwarp();
-                tens_test<ND1, NM>(tb.Bm, pV, tmp, o, lane); // H_i(zeta_k)
-                for (int i = lane; i < ND; i += 32) o[i] -= T[i];
-                __syncwarp();
+                __syncwarp(tm);
+                tens_test<ND1, NM, double, TL>(tb.Bm, pV, tmp, o, lane, tm); // H_i(zeta_k)
+                for (int i = lane; i < ND; i += TL) o[i] -= T[i];
+                __syncwarp(tm);
                 if (npart == 0) {
                     // M is the constant mass matrix, inverted by its tensor factors
-                    kron_apply<ND1, false, MXN>(tb.M1inv, o, tmp, o + ND, 1.0 / J, lane);
+                    kron_apply<ND1, false, MXN, double, TL>(tb.M1inv, o, tmp, o + ND, 1.0 / J, lane, tm);
                 } else {
-                    for (int i = lane; i < ND; i += 32) o[ND + i] = o[i];
-                    __syncwarp();
-                    if (!solve_mass_mixed<ND1, NM>(tb, pA, o + ND, Mf, Yf, invf, rf, xs, rs, qs, tmp, M,
-                                                   Y, pinv, lane)) {
+                    for (int i = lane; i < ND; i += TL) o[ND + i] = o[i];
+                    __syncwarp(tm);
+                    if (!solve_mass_mixed<ND1, NM, TL>(tb, pA, o + ND, Mf, Yf, invf, rf, xs, rs, qs,
+                                                       tmp, M, Y, pinv, lane, tm)) {
                         scalar = true;
                         break;
                     }
                 }
                 double inc = 0.0, scale = 0.0;
-                for (int i = lane; i < ND; i += 32) {
+                for (int i = lane; i < ND; i += TL) {
                     z[i] -= o[ND + i];
                     inc += fabs(o[ND + i]);
                     scale += 1.0 + fabs(z[i]) + d.zabs[k];
                 }
-                inc = warp_sum(inc);
-                scale = warp_sum(scale);
+                inc = team_sum<TL>(inc, tm);
+                scale = team_sum<TL>(scale, tm);
                 its++;
                 prev_full = (npart == 0);
-                __syncwarp();
+                __syncwarp(tm);
                 {
                     bool eq = true;
-                    for (int i = lane; i < ND; i += 32) eq = eq && (z[i] == z[0]);
-                    zc = __all_sync(0xffffffffu, eq);
+                    for (int i = lane; i < ND; i += TL) eq = eq && (z[i] == z[0]);
+                    zc = __all_sync(tm, eq);
                 }
                 if (inc <= d.newton_tol * scale) prev_full = false, kk = d.newton_max - 1;
             }
@@ -1478,7 +1484,7 @@ __global__ void __maxnreg__(96)
                 flag = 0;
                 if (lane == 0) d.flag[k] = 0;
             }
-            __syncwarp();
+            __syncwarp(tm);
         }
         // friction coefficient of the previous stage on the momentum GL points
         // (scalar path; the r path forms it inside momentum_block)
@@ -1488,120 +1494,120 @@ __global__ void __maxnreg__(96)
             const unsigned cmp = d.cmask[(size_t)sa.prev_buf * n + k];
             for (int f = 0; f < 3; ++f) {
                 const double* up = ufield(d, sa.prev_buf, f, ND) + k * ND;
-                for (int i = lane; i < ND; i += 32) o[i] = up[i];
-                __syncwarp();
-                tens_interp<ND1, NG>(tb.Bg, o, tmp, pg + f * NGP, lane);
+                for (int i = lane; i < ND; i += TL) o[i] = up[i];
+                __syncwarp(tm);
+                tens_interp<ND1, NG, double, TL>(tb.Bg, o, tmp, pg + f * NGP, lane, tm);
                 if (cmp & (1u << f))
-                    for (int p = lane; p < NGP; p += 32) pg[f * NGP + p] = o[0];
-                __syncwarp();
+                    for (int p = lane; p < NGP; p += TL) pg[f * NGP + p] = o[0];
+                __syncwarp(tm);
             }
-            for (int p = lane; p < NGP; p += 32) {
+            for (int p = lane; p < NGP; p += TL) {
                 double V, A;
                 ST::VA(d, tb, k, SET_MOM, p % NG, p / NG, pg[p], V, A);
                 gam[p] = gamma_manning<double>(man, V, pg[NGP + p], pg[2 * NGP + p], g, eps);
             }
         } else {
-            for (int p = lane; p < NGP; p += 32) gam[p] = 0.0;
+            for (int p = lane; p < NGP; p += TL) gam[p] = 0.0;
         }
-        __syncwarp();
+        __syncwarp(tm);
         if (scalar) {
             double e;
             if (cm0 & 1u) e = su[0];
             else {
-                tens_interp<ND1, NM>(tb.Bm, su, tmp, pe, lane);
+                tens_interp<ND1, NM, double, TL>(tb.Bm, su, tmp, pe, lane, tm);
                 double s = 0.0;
-                for (int p = lane; p < NMP; p += 32) s += tb.wm[p % NM] * tb.wm[p / NM] * pe[p];
-                e = warp_sum(s);
+                for (int p = lane; p < NMP; p += TL) s += tb.wm[p % NM] * tb.wm[p / NM] * pe[p];
+                e = team_sum<TL>(s, tm);
             }
-            its = scalar_newton<R, Pix, MODE>(d, tb, k, J, Tbar, e, lane);
+            its = scalar_newton<R, Pix, MODE, TL>(d, tb, k, J, Tbar, e, lane, tm);
             // momentum: sums of the rows of the friction-modified mass matrix
             double den = 0.0, num[2] = {0.0, 0.0};
             for (int f = 0; f < 2; ++f) {
-                tens_interp<ND1, NG>(tb.Bg, su + (1 + f) * ND, tmp, pg + (3 + f) * NGP, lane);
+                tens_interp<ND1, NG, double, TL>(tb.Bg, su + (1 + f) * ND, tmp, pg + (3 + f) * NGP, lane, tm);
                 if (cm0 & (2u << f))
-                    for (int p = lane; p < NGP; p += 32) pg[(3 + f) * NGP + p] = su[(1 + f) * ND];
-                __syncwarp();
+                    for (int p = lane; p < NGP; p += TL) pg[(3 + f) * NGP + p] = su[(1 + f) * ND];
+                __syncwarp(tm);
             }
-            for (int p = lane; p < NGP; p += 32) {
+            for (int p = lane; p < NGP; p += TL) {
                 const double w = J * tb.wg[p % NG] * tb.wg[p / NG];
                 den += w * (1.0 + sa.add * dt * gam[p]);
                 num[0] += w * pg[3 * NGP + p];
                 num[1] += w * pg[4 * NGP + p];
             }
             double rs0 = 0.0, rs1 = 0.0, rcs = 0.0;
-            for (int i = lane; i < ND; i += 32) {
+            for (int i = lane; i < ND; i += TL) {
                 rs0 += rq[i];
                 rs1 += rq[ND + i];
                 rcs += rc[i] - d.CN[k * ND + i];
             }
-            den = warp_sum(den);
-            const double qxn = (warp_sum(num[0]) + warp_sum(rs0)) / den;
-            const double qyn = (warp_sum(num[1]) + warp_sum(rs1)) / den;
-            rcs = warp_sum(rcs);
+            den = team_sum<TL>(den, tm);
+            const double qxn = (team_sum<TL>(num[0], tm) + team_sum<TL>(rs0, tm)) / den;
+            const double qyn = (team_sum<TL>(num[1], tm) + team_sum<TL>(rs1, tm)) / den;
+            rcs = team_sum<TL>(rcs, tm);
             double Hs, As;
-            mass_scalar<R, Pix, MODE>(d, tb, k, J, e, lane, Hs, As);
+            mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, Hs, As, tm);
             const bool tr_ok = Hs > 1e-14 * J * d.hlim;
             const double cn = tr_ok ? (d.CNbar[k] + rcs) / Hs : 0.0;
-            for (int i = lane; i < ND; i += 32) {
+            for (int i = lane; i < ND; i += TL) {
                 o[i] = e;
                 o[ND + i] = qxn;
                 o[2 * ND + i] = qyn;
                 o[3 * ND + i] = tr_ok ? cn : su[3 * ND + i];
             }
-            __syncwarp();
+            __syncwarp(tm);
             if (sa.make_llin) {
-                for (int p = lane; p < NGP; p += 32) {
+                for (int p = lane; p < NGP; p += TL) {
                     const double w = J * tb.wg[p % NG] * tb.wg[p / NG] * gam[p];
                     pg[3 * NGP + p] = -w * qxn;
                     pg[4 * NGP + p] = -w * qyn;
                 }
-                __syncwarp();
-                tens_test<ND1, NG>(tb.Bg, pg + 3 * NGP, tmp, M, lane);
-                tens_test<ND1, NG>(tb.Bg, pg + 4 * NGP, tmp, M + ND, lane);
-                for (int i = lane; i < ND; i += 32) {
+                __syncwarp(tm);
+                tens_test<ND1, NG, double, TL>(tb.Bg, pg + 3 * NGP, tmp, M, lane, tm);
+                tens_test<ND1, NG, double, TL>(tb.Bg, pg + 4 * NGP, tmp, M + ND, lane, tm);
+                for (int i = lane; i < ND; i += TL) {
                     d.llin[(size_t)k * ND + i] = M[i];
                     d.llin[(size_t)n * ND + (size_t)k * ND + i] = M[ND + i];
                 }
             }
         } else {
             // momentum (FP64, or FP32 in the FP32-bulk path)
-            momentum_block<R, Pix, MODE, B>(d, tb, k, J, man, dt, sa.add, need_gam, sa.make_llin != 0,
+            momentum_block<R, Pix, MODE, B, TL>(d, tb, k, J, man, dt, sa.add, need_gam, sa.make_llin != 0,
                                             sa.prev_buf, su, cm0, rq, (B*)mw, (B*)mt, pe, tmp, o + ND,
-                                            M, lane);
+                                            M, lane, tm);
             if (sa.make_llin) {
-                for (int i = lane; i < ND; i += 32) {
+                for (int i = lane; i < ND; i += TL) {
                     d.llin[(size_t)k * ND + i] = M[i];
                     d.llin[(size_t)n * ND + (size_t)k * ND + i] = M[ND + i];
                 }
-                __syncwarp();
+                __syncwarp(tm);
             }
             // tracer: H(zeta^(l)) C = C~ + dt sum a R with the depth-weighted mass matrix
-            for (int i = lane; i < ND; i += 32) {
+            for (int i = lane; i < ND; i += TL) {
                 o[i] = z[i];
                 o[3 * ND + i] = rc[i];
             }
-            __syncwarp();
-            solve_mass_mixed<ND1, NM>(tb, pV, o + 3 * ND, Mf, Yf, invf, rf, xs, rs, qs, tmp, M, Y,
-                                      pinv, lane);
+            __syncwarp(tm);
+            solve_mass_mixed<ND1, NM, TL>(tb, pV, o + 3 * ND, Mf, Yf, invf, rf, xs, rs, qs, tmp, M,
+                                          Y, pinv, lane, tm);
         }
-        __syncwarp();
+        __syncwarp(tm);
         // write v^(l) and its constant-field mask
         unsigned cmo = 0;
         for (int f = 0; f < 4; ++f) {
             bool eq = true;
-            for (int i = lane; i < ND; i += 32) eq = eq && (o[f * ND + i] == o[f * ND]);
-            if (__all_sync(0xffffffffu, eq)) cmo |= (1u << f);
+            for (int i = lane; i < ND; i += TL) eq = eq && (o[f * ND + i] == o[f * ND]);
+            if (__all_sync(tm, eq)) cmo |= (1u << f);
         }
         bool fin = true;
-        for (int i = lane; i < 4 * ND; i += 32) {
+        for (int i = lane; i < 4 * ND; i += TL) {
             const double v = o[i];
             fin = fin && isfinite(v);
             ufield(d, sa.out_buf, i / ND, ND)[k * ND + (i % ND)] = v;
         }
-        if (!__all_sync(0xffffffffu, fin)) bad = 1;
+        if (!__all_sync(tm, fin)) bad = 1;
         if (lane == 0) d.cmask[(size_t)sa.out_buf * n + k] = (uint8_t)cmo;
         its_max = max(its_max, its);
-        __syncwarp();
+        __syncwarp(tm);
     }
     if (lane == 0) {
         if (its_max) atomicMax(&d.sc->maxits, its_max);
