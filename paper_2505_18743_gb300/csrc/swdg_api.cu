@@ -626,9 +626,11 @@ static int grid_for(int64_t n, int wpb = WPB) {
 }
 
 // default shapes: WPB warps per block, one block per WPB cells (grid-stride
-// beyond 152 x 64 blocks)
+// beyond 152 x 64 blocks); the stage update (two cells per warp) 2 warps per
+// block, which its shared memory per cell favours
 static void default_shapes(swdg_ctx* c) {
     for (int i = 0; i < KK_N; ++i) c->shp[i] = Shape{grid_for(c->n), WPB};
+    c->shp[KK_STAGE] = Shape{grid_for(c->n, 4), 2};
     c->tuned = false;
 }
 
