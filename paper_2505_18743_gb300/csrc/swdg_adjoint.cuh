@@ -672,7 +672,12 @@ __global__ void __maxnreg__(128)
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
     extern __shared__ double smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    // two cells per warp, one per team of 16 lanes (at r <= 2 a cell's loops
+    // run over at most 16 nodes and points): "warp" is the team within the
+    // block, "lane" the lane within the team, wpb the teams per block
+    constexpr int TL = 16;
+    const int warp = threadIdx.x / TL, lane = threadIdx.x % TL, wpb = blockDim.x / TL;
+    const unsigned tm = 0xFFFFu << (threadIdx.x & 16); // the team's lanes
     double* vb = smem + warp * stage_vjp_smem<R>(); // [4][ND] cotangent of v^(l)
     double* pz = vb + 4 * ND;          // [NMP] zeta^(l) at the mass points
     double* pc = pz + NMP;             // [NMP] c^(l)
@@ -709,57 +714,57 @@ __global__ void __maxnreg__(128)
     };
 
     for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n; k += (int64_t)gridDim.x * wpb) {
-        for (int i = lane; i < 4 * ND; i += 32) vb[i] = a.vb[(i / ND) * fs + k * ND + (i % ND)];
+        for (int i = lane; i < 4 * ND; i += TL) vb[i] = a.vb[(i / ND) * fs + k * ND + (i % ND)];
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
         const double man = d.manning[k];
         const bool scalar = a.flag[k] == 0;
         const bool need_gam = (a.add != 0.0 || a.make_llin) && man != 0.0;
         double dsum = 0.0, nsum = 0.0;
-        __syncwarp();
+        __syncwarp(tm);
         // friction coefficient of v^(l-1) on the momentum points (forward values)
         if (need_gam) {
             const unsigned cmp = a.cmp[k];
             for (int f = 0; f < 3; ++f) {
-                tens_interp<ND1, NG>(tb.Bg, a.up + f * fs + k * ND, tmp, g3 + f * NGP, lane);
+                tens_interp<ND1, NG, double, TL>(tb.Bg, a.up + f * fs + k * ND, tmp, g3 + f * NGP, lane, tm);
                 if (cmp & (1u << f))
-                    for (int p = lane; p < NGP; p += 32) g3[f * NGP + p] = a.up[f * fs + k * ND];
-                __syncwarp();
+                    for (int p = lane; p < NGP; p += TL) g3[f * NGP + p] = a.up[f * fs + k * ND];
+                __syncwarp(tm);
             }
-            for (int p = lane; p < NGP; p += 32) {
+            for (int p = lane; p < NGP; p += TL) {
                 double V, A;
                 ST::VA(d, tb, k, SET_MOM, p % NG, p / NG, g3[p], V, A);
                 gam[p] = gamma_manning<double>(man, V, g3[NGP + p], g3[2 * NGP + p], g, eps);
             }
         } else {
-            for (int p = lane; p < NGP; p += 32) gam[p] = 0.0;
+            for (int p = lane; p < NGP; p += TL) gam[p] = 0.0;
         }
-        for (int p = lane; p < NGP; p += 32) gb[p] = 0.0;
-        __syncwarp();
+        for (int p = lane; p < NGP; p += TL) gb[p] = 0.0;
+        __syncwarp(tm);
         if (!scalar) {
             // linearised friction Llin_f = -S^T (D0 gamma S Q_f) formed by this stage
             if (a.make_llin && a.llb_in && need_gam) {
                 for (int f = 0; f < 2; ++f) {
-                    tens_interp<ND1, NG>(tb.Bg, a.uo + (1 + f) * fs + k * ND, tmp, SQ + f * NGP, lane);
-                    tens_interp<ND1, NG>(tb.Bg, a.llb_in + f * fs + k * ND, tmp, Xb + f * NGP, lane);
+                    tens_interp<ND1, NG, double, TL>(tb.Bg, a.uo + (1 + f) * fs + k * ND, tmp, SQ + f * NGP, lane, tm);
+                    tens_interp<ND1, NG, double, TL>(tb.Bg, a.llb_in + f * fs + k * ND, tmp, Xb + f * NGP, lane, tm);
                 }
-                for (int p = lane; p < NGP; p += 32) {
+                for (int p = lane; p < NGP; p += TL) {
                     const double D0 = J * tb.wg[p % NG] * tb.wg[p / NG];
                     gb[p] -= D0 * (SQ[p] * Xb[p] + SQ[NGP + p] * Xb[NGP + p]);
                     Xb[p] *= -D0 * gam[p];
                     Xb[NGP + p] *= -D0 * gam[p];
                 }
-                __syncwarp();
+                __syncwarp(tm);
                 for (int f = 0; f < 2; ++f) {
-                    tens_test<ND1, NG>(tb.Bg, Xb + f * NGP, tmp, x, lane);
-                    for (int i = lane; i < ND; i += 32) vb[(1 + f) * ND + i] += x[i];
-                    __syncwarp();
+                    tens_test<ND1, NG, double, TL>(tb.Bg, Xb + f * NGP, tmp, x, lane, tm);
+                    for (int i = lane; i < ND; i += TL) vb[(1 + f) * ND + i] += x[i];
+                    __syncwarp(tm);
                 }
             }
             // tracer: rcb = H_c^-1 c_bar, H_c = B^T diag(J w V(zeta^(l))) B
             const unsigned cmo = a.cmo[k];
-            tens_interp<ND1, NM>(tb.Bm, a.uo + k * ND, tmp, pz, lane);
-            tens_interp<ND1, NM>(tb.Bm, a.uo + 3 * fs + k * ND, tmp, pc, lane);
-            for (int p = lane; p < NMP; p += 32) {
+            tens_interp<ND1, NM, double, TL>(tb.Bm, a.uo + k * ND, tmp, pz, lane, tm);
+            tens_interp<ND1, NM, double, TL>(tb.Bm, a.uo + 3 * fs + k * ND, tmp, pc, lane, tm);
+            for (int p = lane; p < NMP; p += TL) {
                 if (cmo & 1u) pz[p] = a.uo[k * ND];
                 if (cmo & 8u) pc[p] = a.uo[3 * fs + k * ND];
                 double V, A;
@@ -768,32 +773,32 @@ __global__ void __maxnreg__(128)
                 pV[p] = w * V;
                 pA[p] = w * A;
             }
-            __syncwarp();
-            assemble_mass<ND1, NM>(tb, pV, Y, M, lane);
-            for (int i = lane; i < ND; i += 32) rcb[i] = vb[3 * ND + i];
-            __syncwarp();
-            chol_solve<ND>(M, rcb, inv, lane);
+            __syncwarp(tm);
+            assemble_mass<ND1, NM, TL>(tb, pV, Y, M, lane, tm);
+            for (int i = lane; i < ND; i += TL) rcb[i] = vb[3 * ND + i];
+            __syncwarp(tm);
+            chol_solve<ND, TL>(M, rcb, inv, lane, tm);
             // dH_c/dzeta: zeta_bar(p) -= J w A rcb(p) c(p); the same for delta
-            tens_interp<ND1, NM>(tb.Bm, rcb, tmp, pw, lane);
-            for (int p = lane; p < NMP; p += 32) {
+            tens_interp<ND1, NM, double, TL>(tb.Bm, rcb, tmp, pw, lane, tm);
+            for (int p = lane; p < NMP; p += TL) {
                 pw[p] = -pA[p] * pw[p] * pc[p];
                 dsum += pw[p];
             }
-            __syncwarp();
-            tens_test<ND1, NM>(tb.Bm, pw, tmp, x, lane);
-            for (int i = lane; i < ND; i += 32) {
+            __syncwarp(tm);
+            tens_test<ND1, NM, double, TL>(tb.Bm, pw, tmp, x, lane, tm);
+            for (int i = lane; i < ND; i += TL) {
                 vb[i] += x[i];
                 a.CNb[k * ND + i] += rcb[i];
                 to_res(3, i, k, rcb[i], false);
             }
-            __syncwarp();
+            __syncwarp(tm);
             // momentum: X_bar = S^-T Q_bar; rq_bar = S^-1 (X_bar / D); q^n part D0 X_bar / D;
             // D_bar = -X_bar (S Q) / D -> gamma_bar
             for (int f = 0; f < 2; ++f) {
-                kron_apply<ND1, true, MXP>(tb.Bginv, vb + (1 + f) * ND, tmp, Xb + f * NGP, 1.0, lane);
-                tens_interp<ND1, NG>(tb.Bg, a.uo + (1 + f) * fs + k * ND, tmp, SQ + f * NGP, lane);
+                kron_apply<ND1, true, MXP, double, TL>(tb.Bginv, vb + (1 + f) * ND, tmp, Xb + f * NGP, 1.0, lane, tm);
+                tens_interp<ND1, NG, double, TL>(tb.Bg, a.uo + (1 + f) * fs + k * ND, tmp, SQ + f * NGP, lane, tm);
             }
-            for (int p = lane; p < NGP; p += 32) {
+            for (int p = lane; p < NGP; p += TL) {
                 const double D0 = J * tb.wg[p % NG] * tb.wg[p / NG];
                 const double D = D0 * (1.0 + a.add * dt * gam[p]);
                 gb[p] -= (Xb[p] * SQ[p] + Xb[NGP + p] * SQ[NGP + p]) / D * D0 * a.add * dt;
@@ -802,111 +807,111 @@ __global__ void __maxnreg__(128)
                 SQ[p] = Xb[p] * D0;           // q^n cotangent at the points
                 SQ[NGP + p] = Xb[NGP + p] * D0;
             }
-            __syncwarp();
+            __syncwarp(tm);
             for (int f = 0; f < 2; ++f) {
-                kron_apply<ND1, false, MXP>(tb.Bginv, Xb + f * NGP, tmp, x, 1.0, lane);
-                for (int i = lane; i < ND; i += 32) {
+                kron_apply<ND1, false, MXP, double, TL>(tb.Bginv, Xb + f * NGP, tmp, x, 1.0, lane, tm);
+                for (int i = lane; i < ND; i += TL) {
                     to_res(1 + f, i, k, x[i], false);
                     to_res(1 + f, i, k, x[i], true);
                 }
-                __syncwarp();
-                tens_test<ND1, NG>(tb.Bg, SQ + f * NGP, tmp, x, lane);
-                for (int i = lane; i < ND; i += 32) a.ubn[(1 + f) * fs + k * ND + i] += x[i];
-                __syncwarp();
+                __syncwarp(tm);
+                tens_test<ND1, NG, double, TL>(tb.Bg, SQ + f * NGP, tmp, x, lane, tm);
+                for (int i = lane; i < ND; i += TL) a.ubn[(1 + f) * fs + k * ND + i] += x[i];
+                __syncwarp(tm);
             }
             // continuity: T_bar = M(zeta^(l))^-1 zeta_bar, M = B^T diag(J w A) B; the
             // offset moves H(zeta^(l)) by J w A: delta_bar -= sum J w A T_bar(p)
-            assemble_mass<ND1, NM>(tb, pA, Y, M, lane);
-            for (int i = lane; i < ND; i += 32) Tb[i] = vb[i];
-            __syncwarp();
-            chol_solve<ND>(M, Tb, inv, lane);
-            tens_interp<ND1, NM>(tb.Bm, Tb, tmp, pw, lane);
-            for (int p = lane; p < NMP; p += 32) dsum -= pA[p] * pw[p];
-            for (int i = lane; i < ND; i += 32) {
+            assemble_mass<ND1, NM, TL>(tb, pA, Y, M, lane, tm);
+            for (int i = lane; i < ND; i += TL) Tb[i] = vb[i];
+            __syncwarp(tm);
+            chol_solve<ND, TL>(M, Tb, inv, lane, tm);
+            tens_interp<ND1, NM, double, TL>(tb.Bm, Tb, tmp, pw, lane, tm);
+            for (int p = lane; p < NMP; p += TL) dsum -= pA[p] * pw[p];
+            for (int i = lane; i < ND; i += TL) {
                 a.HNb[k * ND + i] += Tb[i];
                 to_res(0, i, k, Tb[i], false);
             }
-            __syncwarp();
+            __syncwarp(tm);
         } else {
             // the r_K = 0 path: one value per field, test function 1
             const double e = a.uo[k * ND], cl = a.uo[3 * fs + k * ND];
             const double vq[2] = {a.uo[fs + k * ND], a.uo[2 * fs + k * ND]};
             double ez = 0.0, qs[2] = {0.0, 0.0}, cs = 0.0;
-            for (int i = lane; i < ND; i += 32) {
+            for (int i = lane; i < ND; i += TL) {
                 ez += vb[i];
                 qs[0] += vb[ND + i];
                 qs[1] += vb[2 * ND + i];
                 cs += vb[3 * ND + i];
             }
-            ez = warp_sum(ez);
-            qs[0] = warp_sum(qs[0]);
-            qs[1] = warp_sum(qs[1]);
-            cs = warp_sum(cs);
+            ez = team_sum<TL>(ez, tm);
+            qs[0] = team_sum<TL>(qs[0], tm);
+            qs[1] = team_sum<TL>(qs[1], tm);
+            cs = team_sum<TL>(cs, tm);
             if (a.make_llin && a.llb_in && need_gam) {
                 for (int f = 0; f < 2; ++f)
-                    tens_interp<ND1, NG>(tb.Bg, a.llb_in + f * fs + k * ND, tmp, Xb + f * NGP, lane);
+                    tens_interp<ND1, NG, double, TL>(tb.Bg, a.llb_in + f * fs + k * ND, tmp, Xb + f * NGP, lane, tm);
                 double s0 = 0.0, s1 = 0.0;
-                for (int p = lane; p < NGP; p += 32) {
+                for (int p = lane; p < NGP; p += TL) {
                     const double D0 = J * tb.wg[p % NG] * tb.wg[p / NG];
                     gb[p] -= D0 * (vq[0] * Xb[p] + vq[1] * Xb[NGP + p]);
                     s0 -= D0 * gam[p] * Xb[p];
                     s1 -= D0 * gam[p] * Xb[NGP + p];
                 }
-                qs[0] += warp_sum(s0);
-                qs[1] += warp_sum(s1);
+                qs[0] += team_sum<TL>(s0, tm);
+                qs[1] += team_sum<TL>(s1, tm);
             }
             double Hs, As;
-            mass_scalar<R, Pix, MODE>(d, tb, k, J, e, lane, Hs, As);
+            mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, Hs, As, tm);
             // tracer: c = (CNbar + dt sum a sum_i R_i) / Hbar(e), or c^n in a dry cell
             if (Hs > 1e-14 * J * d.hlim) {
                 const double rsb = cs / Hs, Hsb = -cs * cl / Hs;
                 ez += Hsb * As;
                 if (lane == 0) dsum += Hsb * As;
-                for (int i = lane; i < ND; i += 32) {
+                for (int i = lane; i < ND; i += TL) {
                     a.CNb[k * ND + i] += rsb;
                     to_res(3, i, k, rsb, false);
                 }
             } else {
-                for (int i = lane; i < ND; i += 32) a.ubn[3 * fs + k * ND + i] += vb[3 * ND + i];
+                for (int i = lane; i < ND; i += TL) a.ubn[3 * fs + k * ND + i] += vb[3 * ND + i];
             }
             // momentum: q = (sum_p D0 q^n(p) + sum_i rq_i) / sum_p D
             double den = 0.0;
-            for (int p = lane; p < NGP; p += 32) {
+            for (int p = lane; p < NGP; p += TL) {
                 const double D0 = J * tb.wg[p % NG] * tb.wg[p / NG];
                 den += D0 * (1.0 + a.add * dt * gam[p]);
             }
-            den = warp_sum(den);
+            den = team_sum<TL>(den, tm);
             const double denb = -(qs[0] * vq[0] + qs[1] * vq[1]) / den;
-            for (int p = lane; p < NGP; p += 32) {
+            for (int p = lane; p < NGP; p += TL) {
                 const double D0 = J * tb.wg[p % NG] * tb.wg[p / NG];
                 gb[p] += denb * D0 * a.add * dt;
                 Xb[p] = D0 * qs[0] / den;
                 Xb[NGP + p] = D0 * qs[1] / den;
             }
-            __syncwarp();
+            __syncwarp(tm);
             for (int f = 0; f < 2; ++f) {
-                tens_test<ND1, NG>(tb.Bg, Xb + f * NGP, tmp, x, lane);
-                for (int i = lane; i < ND; i += 32) {
+                tens_test<ND1, NG, double, TL>(tb.Bg, Xb + f * NGP, tmp, x, lane, tm);
+                for (int i = lane; i < ND; i += TL) {
                     a.ubn[(1 + f) * fs + k * ND + i] += x[i];
                     to_res(1 + f, i, k, qs[f] / den, false);
                     to_res(1 + f, i, k, qs[f] / den, true);
                 }
-                __syncwarp();
+                __syncwarp(tm);
             }
             // continuity: Hbar(e) = HNbar + dt sum a sum_i F_i (the offset moves Hbar by A)
             if (As > 0.0) {
                 const double tsb = ez / As;
                 if (lane == 0) dsum -= ez;
-                for (int i = lane; i < ND; i += 32) {
+                for (int i = lane; i < ND; i += TL) {
                     a.HNb[k * ND + i] += tsb;
                     to_res(0, i, k, tsb, false);
                 }
             }
-            __syncwarp();
+            __syncwarp(tm);
         }
         // friction coefficient of v^(l-1): gamma(n, V(zeta), qx, qy) at each point
         if (need_gam) {
-            for (int p = lane; p < NGP; p += 32) {
+            for (int p = lane; p < NGP; p += TL) {
                 double V, A;
                 ST::VA(d, tb, k, SET_MOM, p % NG, p / NG, g3[p], V, A);
                 const double qx = g3[NGP + p], qy = g3[2 * NGP + p], gbp = gb[p];
@@ -921,19 +926,19 @@ __global__ void __maxnreg__(128)
                 dsum += gbp * dg[0] * A;
                 nsum += gbp * dg[3];
             }
-            __syncwarp();
+            __syncwarp(tm);
             for (int f = 0; f < 3; ++f) {
-                tens_test<ND1, NG>(tb.Bg, g3 + f * NGP, tmp, x, lane);
-                for (int i = lane; i < ND; i += 32) a.ubp[f * fs + k * ND + i] += x[i];
-                __syncwarp();
+                tens_test<ND1, NG, double, TL>(tb.Bg, g3 + f * NGP, tmp, x, lane, tm);
+                for (int i = lane; i < ND; i += TL) a.ubp[f * fs + k * ND + i] += x[i];
+                __syncwarp(tm);
             }
         }
-        const double ds = warp_sum(dsum), ns = warp_sum(nsum);
+        const double ds = team_sum<TL>(dsum, tm), ns = team_sum<TL>(nsum, tm);
         if (lane == 0) {
             a.dbar[k] += ds;
             a.nbar[k] += ns;
         }
-        __syncwarp();
+        __syncwarp(tm);
     }
 }
 

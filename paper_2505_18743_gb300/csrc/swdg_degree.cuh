@@ -17,7 +17,7 @@ struct Launchers {
     static constexpr size_t stage_b = 2 * sizeof(double) * stage_smem<R>();
     static constexpr size_t diag_b = sizeof(double) * (2 * S::ND + 2 * S::NMP + 2 * S::NM * S::NM);
     static constexpr size_t vjp_b = sizeof(double) * vjp_smem<R>();
-    static constexpr size_t svjp_b = sizeof(double) * stage_vjp_smem<R>();
+    static constexpr size_t svjp_b = 2 * sizeof(double) * stage_vjp_smem<R>(); // two cells per warp
     static constexpr size_t bvjp_b = sizeof(double) * begin_vjp_smem<R>();
     static constexpr size_t ind_b = sizeof(double) * indicator_smem<R>();
     static constexpr size_t remap_b = sizeof(double) * remap_smem<R>();
@@ -64,7 +64,9 @@ struct Launchers {
     }
     static void stage_vjp(const Dev& d, const Tables& tb, const StageVjpArgs& a, Shape s,
                           cudaStream_t st) {
-        k_stage_vjp<R, Pix, MODE><<<s.grid, 32 * s.wpb, svjp_b * s.wpb, st>>>(d, tb, a);
+        const int64_t need = (d.n + 2 * s.wpb - 1) / (2 * s.wpb);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(s.grid, need));
+        k_stage_vjp<R, Pix, MODE><<<grid, 32 * s.wpb, svjp_b * s.wpb, st>>>(d, tb, a);
     }
     static void begin_vjp(const Dev& d, const Tables& tb, const BeginVjpArgs& a, Shape s,
                           cudaStream_t st) {
