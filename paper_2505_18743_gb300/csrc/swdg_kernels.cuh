@@ -1025,14 +1025,24 @@ struct StageArgs {
 };
 
 template <int R>
+constexpr int stage_union_live() {
+    // in doubles: friction points [6 NGP], the FP32 solve's float M, Y, inv, r
+    // (8-byte padded), the momentum block scratch (B-typed, sized in doubles:
+    // nodal pair, points, tmp pair)
+    using S = Sz<R>;
+    return 6 * S::NGP + (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 2 * S::ND + 1) / 2 + 1 +
+           2 * S::ND + 6 * S::NGP + 2 * S::ND1 * S::NG;
+}
+template <int R>
 constexpr int stage_smem() {
     using S = Sz<R>;
-    return 4 * S::ND + 5 * S::ND + 3 * S::NMP + 2 * S::NM * S::NM + S::ND1 * S::ND1 * S::NM +
-           S::ND * S::ND + 6 * S::NGP + 4 * S::ND + S::ND +
-           // mixed-precision solve: x, r (ND), q (NMP), float M, Y, inv, r
-           2 * S::ND + S::NMP + (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 2 * S::ND + 1) / 2 + 1 +
-           // momentum block scratch (B-typed, sized in doubles): nodal pair, points, tmp pair
-           2 * S::ND + 6 * S::NGP + 2 * S::ND1 * S::NG;
+    // the FP64 fallback's Y and M [ND1 ND1 NM + ND ND] share the last region
+    // with what is dead whenever the fallback runs (see k_stage)
+    constexpr int fb = S::ND1 * S::ND1 * S::NM + S::ND * S::ND;
+    constexpr int un = stage_union_live<R>() > fb ? stage_union_live<R>() : fb;
+    return 4 * S::ND + 5 * S::ND + 3 * S::NMP + 2 * S::NM * S::NM + 4 * S::ND + S::ND +
+           // mixed-precision solve: x, r (ND), q (NMP)
+           2 * S::ND + S::NMP + un;
 }
 
 // Cholesky of the SPD matrix M (ND x ND, row-major, lower part used) on a
@@ -1363,15 +1373,19 @@ __global__ void __maxnreg__(96)
     double* pV = pe + NMP;                      // [NMP]
     double* pA = pV + NMP;                      // [NMP]
     double* tmp = pA + NMP;                     // [2 NM NM]
-    double* Y = tmp + 2 * NM * NM;              // [ND1 ND1 NM]
-    double* M = Y + ND1 * ND1 * NM;             // [ND ND]
-    double* pg = M + ND * ND;                   // [6][NGP]
-    double* o = pg + 6 * NGP;                   // [4][ND]
+    double* o = tmp + 2 * NM * NM;              // [4][ND]
     double* pinv = o + 4 * ND;                  // [ND] reciprocal Cholesky pivots
-    double* xs = pinv + ND;                     // [ND] refinement iterate
-    double* rs = xs + ND;                       // [ND] refinement residual
+    double* xs = pinv + ND;                     // [ND] refinement iterate (also scratch [2 ND]
+    double* rs = xs + ND;                       // [ND] refinement residual   with rs outside a solve)
     double* qs = rs + ND;                       // [NMP]
-    float* Mf = (float*)(qs + NMP);             // [ND ND]
+    // the last region: friction points pg, the FP32 solve's arrays, the
+    // momentum scratch; the FP64 fallback's Y, M overlay it, since the
+    // fallback runs only inside a solve (the momentum scratch idle, pg unused
+    // off the scalar path, the FP32 arrays given up)
+    double* pg = qs + NMP;                      // [6][NGP]
+    double* Y = pg;                             // [ND1 ND1 NM] (fallback)
+    double* M = Y + ND1 * ND1 * NM;             // [ND ND] (fallback)
+    float* Mf = (float*)(pg + 6 * NGP);         // [ND ND]
     float* Yf = Mf + ND * ND;                   // [ND1 ND1 NM]
     float* invf = Yf + ND1 * ND1 * NM;          // [ND]
     float* rf = invf + ND;                      // [ND]
@@ -1562,22 +1576,22 @@ __global__ void __maxnreg__(96)
                     pg[4 * NGP + p] = -w * qyn;
                 }
                 __syncwarp(tm);
-                tens_test<ND1, NG, double, TL>(tb.Bg, pg + 3 * NGP, tmp, M, lane, tm);
-                tens_test<ND1, NG, double, TL>(tb.Bg, pg + 4 * NGP, tmp, M + ND, lane, tm);
+                tens_test<ND1, NG, double, TL>(tb.Bg, pg + 3 * NGP, tmp, xs, lane, tm);
+                tens_test<ND1, NG, double, TL>(tb.Bg, pg + 4 * NGP, tmp, rs, lane, tm);
                 for (int i = lane; i < ND; i += TL) {
-                    d.llin[(size_t)k * ND + i] = M[i];
-                    d.llin[(size_t)n * ND + (size_t)k * ND + i] = M[ND + i];
+                    d.llin[(size_t)k * ND + i] = xs[i];
+                    d.llin[(size_t)n * ND + (size_t)k * ND + i] = xs[ND + i];
                 }
             }
         } else {
             // momentum (FP64, or FP32 in the FP32-bulk path)
             momentum_block<R, Pix, MODE, B, TL>(d, tb, k, J, man, dt, sa.add, need_gam, sa.make_llin != 0,
                                             sa.prev_buf, su, cm0, rq, (B*)mw, (B*)mt, pe, tmp, o + ND,
-                                            M, lane, tm);
+                                            xs, lane, tm);
             if (sa.make_llin) {
                 for (int i = lane; i < ND; i += TL) {
-                    d.llin[(size_t)k * ND + i] = M[i];
-                    d.llin[(size_t)n * ND + (size_t)k * ND + i] = M[ND + i];
+                    d.llin[(size_t)k * ND + i] = xs[i];
+                    d.llin[(size_t)n * ND + (size_t)k * ND + i] = xs[ND + i];
                 }
                 __syncwarp(tm);
             }
