@@ -62,18 +62,18 @@ def units_per_step(wl):
 # faces_l: k_faces of stage l, residual_l: k_residual).  These kernels are
 # bound by the FP64 pipe: GB300's FP64 rate is the roofline.
 FLOPS_PER_CELL = {"step_begin": 2187, "faces_1": 1683, "faces_2": 1850, "faces_3": 1851,
-                  "residual_1": 9452, "residual_2": 10000, "residual_3": 9998,
-                  "stage_2": 9284, "stage_3": 10070, "final": 7770}
+                  "residual_1": 9449, "residual_2": 10000, "residual_3": 9997, "stage_2": 8257,
+                  "stage_3": 9049, "final": 6747}
 # the FP32-bulk kernels' FP64 flops (their FP32 work runs on the 60x faster FP32 pipe)
 FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "faces_1": 230, "faces_2": 400, "faces_3": 400,
                            "residual_1": 3299, "residual_2": 3843, "residual_3": 3843,
-                           "stage_2": 5992, "stage_3": 6244, "final": 6024}
+                           "stage_2": 4965, "stage_3": 5223, "final": 5001}
 # DRAM bytes per launch from an ncu capture of the current kernels (FP64
 # path); {} (traffic null) whenever the kernels changed after the capture
-DRAM_BYTES_PER_LAUNCH = {"step_begin": 59139072, "faces_1": 154420736, "faces_2": 154474752,
-                         "faces_3": 154984704, "residual_1": 171870208, "residual_2": 174084096,
-                         "residual_3": 173044224, "stage_2": 156064768, "stage_3": 248926208,
-                         "final": 254206976}
+DRAM_BYTES_PER_LAUNCH = {"step_begin": 59105792, "faces_1": 154295552, "faces_2": 154544896,
+                         "faces_3": 154638848, "residual_1": 171804416, "residual_2": 173751552,
+                         "residual_3": 172974336, "stage_2": 156237568, "stage_3": 251846912,
+                         "final": 256461568}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
 
 
