@@ -422,6 +422,9 @@ def amr_variant(args, stream, dev, world, cycles=4, every=5):
     return {"workload": "lagoon 256x128 coarse cells, 2 levels, r=2, |grad c| indicator, "
                         "adaptation every 5 steps",
             "cells": cells, "step_ms": [round(x, 3) for x in step_ms],
+            # DoF-stage updates/s of the steps of each cycle (on that cycle's mesh)
+            "updates_per_s": [cells[i] * 4 * (wl.degree + 1) ** 2 * STAGES / (step_ms[i] / 1e3)
+                              for i in range(len(step_ms))],
             "adapt_ms": [round(x, 2) for x in adapt_ms],
             "adapt_split_ms_indicator_forest_rebuild": split,
             "adaptation_share_of_wall_time": sum(adapt_ms) / (steps_total + sum(adapt_ms)),
