@@ -167,7 +167,8 @@ __device__ __forceinline__ double team_sum(double v, unsigned tm) {
     for (int o = TL / 2; o > 0; o >>= 1) v += __shfl_xor_sync(tm, v, o);
     return v;
 }
-// maxima of non-negative values (no NaN) over the team's lanes tm by their bit patterns
+// maxima of non-negative values (no NaN) over the team's lanes tm by their bit
+// patterns, which order like the values: integer reductions, off the FP64 pipe
 __device__ __forceinline__ float team_max_nonneg(float v, unsigned tm) {
     return __uint_as_float(__reduce_max_sync(tm, __float_as_uint(v)));
 }
@@ -178,19 +179,6 @@ __device__ __forceinline__ double team_max_nonneg(double v, unsigned tm) {
     const unsigned ml = __reduce_max_sync(tm, hi == mh ? lo : 0u);
     return __longlong_as_double((long long)(((unsigned long long)mh << 32) | ml));
 }
-// maxima of non-negative values (no NaN) over the warp by their bit patterns,
-// which order like the values: integer reductions, off the FP64 pipe
-__device__ __forceinline__ float warp_max_nonneg(float v) {
-    return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
-}
-__device__ __forceinline__ double warp_max_nonneg(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
-    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
-    return __longlong_as_double((long long)(((unsigned long long)mh << 32) | ml));
-}
-
 __device__ __forceinline__ double* ufield(const Dev& d, int buf, int f, int nd) {
     return d.U + ((size_t)buf * 4 + f) * (size_t)d.n * nd;
 }
