@@ -175,6 +175,17 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def omp_threads(k):
+    """set the OpenMP thread count of the oracle's runtime (libgomp); False if
+    the runtime cannot be reached"""
+    import ctypes
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(k))
+        return True
+    except (OSError, AttributeError):
+        return False
+
+
 def cpu_oracle_rate(seconds=15.0, window=(184, 120, 24, 24)):
     """the oracle (as it stands) on a crop of the workload, steps until about
     `seconds` of CPU work; returns (updates/s, cores, sample text)"""
@@ -571,6 +582,12 @@ def run_gpu(args, rank, world, local):
         rate, cores, sample = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": rate, "unit": "updates/s", "cores": cores,
                                 "kind": "oracle", "sample": sample}
+        # the same oracle on one thread (a shorter sample)
+        if omp_threads(1):
+            r1, _, s1 = cpu_oracle_rate(seconds=5.0)
+            omp_threads(cores)
+            line["cpu_baseline"]["single_thread"] = {"value": r1, "unit": "updates/s",
+                                                     "cores": 1, "sample": s1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
