@@ -70,10 +70,7 @@ FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "faces_1": 230, "faces_2": 400, "
                            "stage_2": 4965, "stage_3": 5223, "final": 5001}
 # DRAM bytes per launch from an ncu capture of the current kernels (FP64
 # path); {} (traffic null) whenever the kernels changed after the capture
-DRAM_BYTES_PER_LAUNCH = {"step_begin": 59105792, "faces_1": 154295552, "faces_2": 154544896,
-                         "faces_3": 154638848, "residual_1": 171804416, "residual_2": 173751552,
-                         "residual_3": 172974336, "stage_2": 156237568, "stage_3": 251846912,
-                         "final": 256461568}
+DRAM_BYTES_PER_LAUNCH = {}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
 
 

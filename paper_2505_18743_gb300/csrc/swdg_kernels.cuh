@@ -1026,12 +1026,12 @@ struct StageArgs {
 
 template <int R>
 constexpr int stage_union_live() {
-    // in doubles: friction points [6 NGP], the FP32 solve's float M, Y, inv, r
-    // (8-byte padded), the momentum block scratch (B-typed, sized in doubles:
-    // nodal pair, points, tmp pair)
+    // in doubles: friction points [6 NGP] (also the momentum block's point
+    // arrays), the FP32 solve's float M, Y, inv, r (8-byte padded), the
+    // momentum block's nodal pair and tmp pair (B-typed, sized in doubles)
     using S = Sz<R>;
     return 6 * S::NGP + (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 2 * S::ND + 1) / 2 + 1 +
-           2 * S::ND + 6 * S::NGP + 2 * S::ND1 * S::NG;
+           2 * S::ND + 2 * S::ND1 * S::NG;
 }
 template <int R>
 constexpr int stage_smem() {
@@ -1277,17 +1277,18 @@ template <int R, typename Pix, int MODE, typename T, int TL = 32>
 __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double J, double man,
                                double dt, double add, bool need_gam, bool make_llin, int prev_buf,
                                const double* su, unsigned cm0, const double* rq, T* w0, T* w1,
-                               double* zp, double* tmpd, double* Q, double* llin, int lane, unsigned tm = 0xffffffffu) {
+                               T* pts, double* zp, double* tmpd, double* Q, double* llin, int lane,
+                               unsigned tm = 0xffffffffu) {
     using S = Sz<R>;
     constexpr int ND1 = S::ND1, ND = S::ND, NG = S::NG, NGP = S::NGP;
     const auto Bg = tab_or<T>(tb.Bg, tb.BgF);
     const T(*Bginv)[MXP] = nullptr;
     if constexpr (sizeof(T) == sizeof(double)) Bginv = (const T(*)[MXP])tb.Bginv;
     else Bginv = (const T(*)[MXP])tb.BginvF;
-    // w0: [2][ND] nodal pair, [6][NGP] point arrays; w1: [2][ND1 NG] tmp pair.
-    // The two discharge components are contracted side by side.
+    // w0: [2][ND] nodal pair; w1: [2][ND1 NG] tmp pair; pts: [6][NGP] point
+    // arrays.  The two discharge components are contracted side by side.
     T* nod = w0;              // [2][ND]
-    T* pg = w0 + 2 * ND;      // [6][NGP]: 0,1 S^-T rq / point values; 2 gamma; 3,4 q^n; 5 spare
+    T* pg = pts;              // [6][NGP]: 0,1 S^-T rq / point values; 2 gamma; 3,4 q^n; 5 spare
     T* tmp = w1;
     T* tmp1 = w1 + ND1 * NG;
     T* gam = pg + 2 * NGP;
@@ -1378,10 +1379,11 @@ __global__ void __maxnreg__(96)
     double* xs = pinv + ND;                     // [ND] refinement iterate (also scratch [2 ND]
     double* rs = xs + ND;                       // [ND] refinement residual   with rs outside a solve)
     double* qs = rs + ND;                       // [NMP]
-    // the last region: friction points pg, the FP32 solve's arrays, the
+    // the last region: friction points pg (the scalar path's; the momentum
+    // block's point arrays on the other path), the FP32 solve's arrays, the
     // momentum scratch; the FP64 fallback's Y, M overlay it, since the
-    // fallback runs only inside a solve (the momentum scratch idle, pg unused
-    // off the scalar path, the FP32 arrays given up)
+    // fallback runs only inside a solve (the momentum block idle, the FP32
+    // arrays given up)
     double* pg = qs + NMP;                      // [6][NGP]
     double* Y = pg;                             // [ND1 ND1 NM] (fallback)
     double* M = Y + ND1 * ND1 * NM;             // [ND ND] (fallback)
@@ -1391,7 +1393,7 @@ __global__ void __maxnreg__(96)
     float* rf = invf + ND;                      // [ND]
     // momentum scratch, 8-byte aligned after the float arrays
     double* mw = (double*)((((uintptr_t)(rf + ND)) + 7) & ~(uintptr_t)7);
-    double* mt = mw + 2 * ND + 6 * NGP;
+    double* mt = mw + 2 * ND;
     const int64_t n = d.n;
     const double g = d.g, eps = d.eps;
     int its_max = 0;
@@ -1586,7 +1588,8 @@ __global__ void __maxnreg__(96)
         } else {
             // momentum (FP64, or FP32 in the FP32-bulk path)
             momentum_block<R, Pix, MODE, B, TL>(d, tb, k, J, man, dt, sa.add, need_gam, sa.make_llin != 0,
-                                            sa.prev_buf, su, cm0, rq, (B*)mw, (B*)mt, pe, tmp, o + ND,
+                                            sa.prev_buf, su, cm0, rq, (B*)mw, (B*)mt, (B*)pg, pe, tmp,
+                                            o + ND,
                                             xs, lane, tm);
             if (sa.make_llin) {
                 for (int i = lane; i < ND; i += TL) {
