@@ -612,40 +612,75 @@ __global__ void __maxnreg__(96)
         __syncwarp();
         // test integration, y-contraction.  FP64: F (x, y), R (x, y); B: Gx, Gy
         // (x; y + v), Lx, Ly (v)
-        for (int i = lane; i < 2 * NV * ND1; i += 32) {
-            const int cf = i / (NV * ND1), r_ = i % (NV * ND1), al = r_ / ND1, b = r_ % ND1;
-            double sx = 0.0, so = 0.0;
+        if constexpr (F64) {
+            // every single 5-term sum is one job, so the lanes stay busy: jobs
+            // 0,1 F/R x-part (Bv), 2,3 F/R y-part (Dv), 4,5 Gx/Gy x-part (Bv),
+            // 6,7 Lx/Ly (Bv), NV ND1 entries each; then the Gx/Gy y + v parts
+            constexpr int NE = NV * ND1;
+            for (int i = lane; i < 8 * NE; i += 32) {
+                const int job = i / NE, r_ = i % NE, al = r_ / ND1, b = r_ % ND1;
+                const int c2 = job & 1, kind = job >> 1;
+                const double(*Tb)[MXN] = kind == 1 ? tb.Dv : tb.Bv;
+                const double* X = kind == 0   ? Xd + (2 * c2) * NVP
+                                  : kind == 1 ? Xd + (2 * c2 + 1) * NVP
+                                  : kind == 2 ? (const double*)XB + 3 * c2 * NVP
+                                              : (const double*)XB + (6 + c2) * NVP;
+                double* out = kind == 0   ? sd + ((c2 * 2 + 0) * NV + al) * ND1 + b
+                              : kind == 1 ? sd + ((c2 * 2 + 1) * NV + al) * ND1 + b
+                              : kind == 2 ? (double*)sB + ((c2 * 2 + 0) * NV + al) * ND1 + b
+                                          : (double*)sB + (((2 + c2) * 2 + 1) * NV + al) * ND1 + b;
+                double acc = 0.0;
 #pragma unroll
-            for (int be = 0; be < NV; ++be) {
-                const int p = al + NV * be;
-                sx += tb.Bv[be][b] * Xd[(2 * cf) * NVP + p];
-                so += tb.Dv[be][b] * Xd[(2 * cf + 1) * NVP + p];
+                for (int be = 0; be < NV; ++be) acc += Tb[be][b] * X[al + NV * be];
+                *out = acc;
             }
-            sd[((cf * 2 + 0) * NV + al) * ND1 + b] = sx;
-            sd[((cf * 2 + 1) * NV + al) * ND1 + b] = so;
-        }
-        // Gx, Gy: grad-x part, and grad-y + value parts
-        for (int i = lane; i < 2 * NV * ND1; i += 32) {
-            const int cg = i / (NV * ND1), r_ = i % (NV * ND1), al = r_ / ND1, b = r_ % ND1;
-            const B* Xg = XB + 3 * cg * NVP;
-            B sx = B(0), so = B(0);
+            for (int i = lane; i < 2 * NE; i += 32) {
+                const int cg = i / NE, r_ = i % NE, al = r_ / ND1, b = r_ % ND1;
+                const B* Xg = XB + 3 * cg * NVP;
+                B so = B(0);
 #pragma unroll
-            for (int be = 0; be < NV; ++be) {
-                const int p = al + NV * be;
-                sx += BvB[be][b] * Xg[p];
-                so += DvB[be][b] * Xg[NVP + p] + BvB[be][b] * Xg[2 * NVP + p];
+                for (int be = 0; be < NV; ++be) {
+                    const int p = al + NV * be;
+                    so += DvB[be][b] * Xg[NVP + p] + BvB[be][b] * Xg[2 * NVP + p];
+                }
+                sB[((cg * 2 + 1) * NV + al) * ND1 + b] = so;
             }
-            sB[((cg * 2 + 0) * NV + al) * ND1 + b] = sx;
-            sB[((cg * 2 + 1) * NV + al) * ND1 + b] = so;
-        }
-        // Lx, Ly: value parts only
-        for (int i = lane; i < 2 * NV * ND1; i += 32) {
-            const int cl = i / (NV * ND1), r_ = i % (NV * ND1), al = r_ / ND1, b = r_ % ND1;
-            const B* Xl = XB + (6 + cl) * NVP;
-            B so = B(0);
+        } else {
+            for (int i = lane; i < 2 * NV * ND1; i += 32) {
+                const int cf = i / (NV * ND1), r_ = i % (NV * ND1), al = r_ / ND1, b = r_ % ND1;
+                double sx = 0.0, so = 0.0;
 #pragma unroll
-            for (int be = 0; be < NV; ++be) so += BvB[be][b] * Xl[al + NV * be];
-            sB[(((2 + cl) * 2 + 1) * NV + al) * ND1 + b] = so;
+                for (int be = 0; be < NV; ++be) {
+                    const int p = al + NV * be;
+                    sx += tb.Bv[be][b] * Xd[(2 * cf) * NVP + p];
+                    so += tb.Dv[be][b] * Xd[(2 * cf + 1) * NVP + p];
+                }
+                sd[((cf * 2 + 0) * NV + al) * ND1 + b] = sx;
+                sd[((cf * 2 + 1) * NV + al) * ND1 + b] = so;
+            }
+            // Gx, Gy: grad-x part, and grad-y + value parts
+            for (int i = lane; i < 2 * NV * ND1; i += 32) {
+                const int cg = i / (NV * ND1), r_ = i % (NV * ND1), al = r_ / ND1, b = r_ % ND1;
+                const B* Xg = XB + 3 * cg * NVP;
+                B sx = B(0), so = B(0);
+#pragma unroll
+                for (int be = 0; be < NV; ++be) {
+                    const int p = al + NV * be;
+                    sx += BvB[be][b] * Xg[p];
+                    so += DvB[be][b] * Xg[NVP + p] + BvB[be][b] * Xg[2 * NVP + p];
+                }
+                sB[((cg * 2 + 0) * NV + al) * ND1 + b] = sx;
+                sB[((cg * 2 + 1) * NV + al) * ND1 + b] = so;
+            }
+            // Lx, Ly: value parts only
+            for (int i = lane; i < 2 * NV * ND1; i += 32) {
+                const int cl = i / (NV * ND1), r_ = i % (NV * ND1), al = r_ / ND1, b = r_ % ND1;
+                const B* Xl = XB + (6 + cl) * NVP;
+                B so = B(0);
+#pragma unroll
+                for (int be = 0; be < NV; ++be) so += BvB[be][b] * Xl[al + NV * be];
+                sB[(((2 + cl) * 2 + 1) * NV + al) * ND1 + b] = so;
+            }
         }
         __syncwarp();
         // x-contraction into rs = [F, Gx, Gy, R, Lx, Ly]: F and R in FP64
