@@ -11,6 +11,8 @@
 #pragma once
 #include "swdg_common.cuh"
 
+#include <utility>
+
 namespace swdg {
 
 constexpr int WPB = 4;    // default warps per block
@@ -1062,11 +1064,11 @@ struct StageArgs {
 template <int R>
 constexpr int stage_union_live() {
     // in doubles: friction points [6 NGP] (also the momentum block's point
-    // arrays), the FP32 solve's float M, Y, inv, r (8-byte padded), the
-    // momentum block's nodal pair and tmp pair (B-typed, sized in doubles)
+    // arrays), the FP32 solve's float M, Y (8-byte padded), the momentum
+    // block's nodal pair and tmp pair (B-typed, sized in doubles)
     using S = Sz<R>;
-    return 6 * S::NGP + (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 2 * S::ND + 1) / 2 + 1 +
-           2 * S::ND + 2 * S::ND1 * S::NG;
+    return 6 * S::NGP + (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 1) / 2 + 1 + 2 * S::ND +
+           2 * S::ND1 * S::NG;
 }
 template <int R>
 constexpr int stage_smem() {
@@ -1123,83 +1125,6 @@ __device__ bool chol_solve(double* M, double* b, double* inv, int lane, unsigned
     return true;
 }
 
-// FP32 Cholesky factorisation (lower part of M, reciprocal pivots in inv);
-// returns false on a non-positive pivot
-template <int ND, int TL = 32>
-__device__ bool chol_factor_f(float* M, float* inv, int lane, unsigned tm = 0xffffffffu) {
-    for (int j = 0; j < ND; ++j) {
-        __syncwarp(tm);
-        const float djj = M[j * ND + j];
-        if (!(djj > 0.0f)) return false;
-        const float ljj = sqrtf(djj);
-        const float r = 1.0f / ljj;
-        __syncwarp(tm);
-        for (int i = j + 1 + lane; i < ND; i += TL) M[i * ND + j] *= r;
-        if (lane == 0) {
-            M[j * ND + j] = ljj;
-            inv[j] = r;
-        }
-        __syncwarp(tm);
-        const int m = ND - j - 1;
-        for (int idx = lane; idx < m * m; idx += TL) {
-            const int i = j + 1 + idx / m, l = j + 1 + idx % m;
-            if (l <= i) M[i * ND + l] -= M[i * ND + j] * M[l * ND + j];
-        }
-    }
-    __syncwarp(tm);
-    return true;
-}
-
-// (L L^T)^-1 b in FP32 with the factor of chol_factor_f, in place
-template <int ND, int TL = 32>
-__device__ void chol_subst_f(const float* M, const float* inv, float* b, int lane, unsigned tm = 0xffffffffu) {
-    for (int j = 0; j < ND; ++j) {
-        const float yj = b[j] * inv[j];
-        __syncwarp(tm);
-        for (int i = j + 1 + lane; i < ND; i += TL) b[i] -= M[i * ND + j] * yj;
-        if (lane == 0) b[j] = yj;
-        __syncwarp(tm);
-    }
-    for (int j = ND - 1; j >= 0; --j) {
-        const float xj = b[j] * inv[j];
-        __syncwarp(tm);
-        for (int i = lane; i < j; i += TL) b[i] -= M[j * ND + i] * xj;
-        if (lane == 0) b[j] = xj;
-        __syncwarp(tm);
-    }
-}
-
-// FP32 copy of M_(a,b),(c,d) = sum c_{al,be} Bm[al][a] Bm[al][c] Bm[be][b] Bm[be][d]
-// from the FP32 basis table and one FP32 copy of the weights cw (conversions
-// run on the FP64 pipe: converting inside the sums would cost one per term)
-template <int ND1, int NM, int TL = 32>
-__device__ __forceinline__ void assemble_mass_f(const Tables& tb, const double* cw, float* Y,
-                                                float* M, int lane, unsigned tm = 0xffffffffu) {
-    constexpr int ND = ND1 * ND1;
-    static_assert(NM * NM <= ND * ND, "the weights are staged in M");
-    float* cwf = M; // M is written only by the second pass
-    for (int p = lane; p < NM * NM; p += TL) cwf[p] = (float)cw[p];
-    __syncwarp(tm);
-    for (int i = lane; i < ND1 * ND1 * NM; i += TL) {
-        const int a = i / (ND1 * NM), r_ = i % (ND1 * NM), c = r_ / NM, be = r_ % NM;
-        float s = 0.0f;
-#pragma unroll
-        for (int al = 0; al < NM; ++al) s += cwf[al + NM * be] * tb.BmF[al][a] * tb.BmF[al][c];
-        Y[i] = s;
-    }
-    __syncwarp(tm);
-    for (int i = lane; i < ND * ND; i += TL) {
-        const int r_ = i / ND, s_ = i % ND;
-        const int a = r_ % ND1, b = r_ / ND1, c = s_ % ND1, dd = s_ / ND1;
-        float s = 0.0f;
-#pragma unroll
-        for (int be = 0; be < NM; ++be)
-            s += Y[(a * ND1 + c) * NM + be] * tb.BmF[be][b] * tb.BmF[be][dd];
-        M[i] = s;
-    }
-    __syncwarp(tm);
-}
-
 // M_(a,b),(c,d) = sum_{al,be} c_{al,be} Bm[al][a] Bm[al][c] Bm[be][b] Bm[be][d]
 template <int ND1, int NM, int TL = 32>
 __device__ __forceinline__ void assemble_mass(const Tables& tb, const double* cw, double* Y,
@@ -1225,6 +1150,129 @@ __device__ __forceinline__ void assemble_mass(const Tables& tb, const double* cw
     __syncwarp(tm);
 }
 
+// Index of element (i, t) of an FP32 factor stored by rows.  For a
+// power-of-two order the column is XOR-swizzled with i / 2, so that a team's
+// lanes reading one element of each row, or of each column, hit distinct
+// shared-memory banks; an odd order needs no swizzle.
+template <int ND>
+__device__ __forceinline__ int lrow_idx(int i, int t) {
+    if constexpr ((ND & (ND - 1)) == 0) return i * ND + (t ^ ((i >> 1) & (ND - 1)));
+    else return i * ND + t;
+}
+
+// The steps of a Cholesky factorisation with row i of the matrix in the
+// lane's registers a (lower part used).  Step J takes the pivot from lane J,
+// scales column J and updates the columns l > J with L_lJ from lane l.  The
+// steps are expanded from index sequences, so that every index into a is a
+// constant and the row stays in registers.  After a non-positive pivot the
+// steps go on (no branch) and ok is false.
+template <int ND, int TL, int J, int L>
+__device__ __forceinline__ void chol_row_update(float (&a)[ND], int i, unsigned tm) {
+    constexpr int l = J + 1 + L;
+    const float llj = __shfl_sync(tm, a[J], l, TL); // L_lJ
+    if (l <= i) a[l] -= a[J] * llj;
+}
+template <int ND, int TL, int J, int... L>
+__device__ __forceinline__ void chol_row_step(float (&a)[ND], int i, float& rinv, bool& ok,
+                                              unsigned tm, std::integer_sequence<int, L...>) {
+    const float djj = __shfl_sync(tm, a[J], J, TL); // the same on every lane of the team
+    ok = ok && djj > 0.0f;
+    const float ljj = sqrtf(djj);
+    const float r = 1.0f / ljj;
+    if (i == J) {
+        a[J] = ljj;
+        rinv = r;
+    } else if (i > J) {
+        a[J] *= r;
+    }
+    (chol_row_update<ND, TL, J, L>(a, i, tm), ...);
+}
+template <int ND, int TL, int... J>
+__device__ __forceinline__ void chol_rows(float (&a)[ND], int i, float& rinv, bool& ok, unsigned tm,
+                                          std::integer_sequence<int, J...>) {
+    (chol_row_step<ND, TL, J>(a, i, rinv, ok, tm, std::make_integer_sequence<int, ND - J - 1>{}),
+     ...);
+}
+
+// FP32 copy of M_(a,b),(c,d) = sum c_{al,be} Bm[al][a] Bm[al][c] Bm[be][b] Bm[be][d],
+// assembled and Cholesky-factored with one row per lane (ND <= TL).  The
+// weights cw are converted once (conversions run on the FP64 pipe: converting
+// inside the sums would cost one per term); lane i forms the lower part of
+// row i of M from the FP32 basis table, the factor's column updates take the
+// pivot column from the other lanes by shuffles, and L is stored by rows in
+// Mf (lrow_idx).  The lane's reciprocal pivot 1/L_ii comes back in rinv.
+// Returns false on a non-positive pivot.
+template <int ND1, int NM, int TL>
+__device__ bool mass_factor_rows_f(const Tables& tb, const double* cw, float* Y, float* Mf,
+                                   float& rinv, int lane, unsigned tm) {
+    constexpr int ND = ND1 * ND1;
+    static_assert(ND <= TL, "one row per lane");
+    static_assert(NM * NM <= ND * ND, "the weights are staged in Mf");
+    float* cwf = Mf; // Mf is written only once the factor is done
+    for (int p = lane; p < NM * NM; p += TL) cwf[p] = (float)cw[p];
+    __syncwarp(tm);
+    for (int i = lane; i < ND1 * ND1 * NM; i += TL) {
+        const int a = i / (ND1 * NM), r_ = i % (ND1 * NM), c = r_ / NM, be = r_ % NM;
+        float s = 0.0f;
+#pragma unroll
+        for (int al = 0; al < NM; ++al) s += cwf[al + NM * be] * tb.BmF[al][a] * tb.BmF[al][c];
+        Y[i] = s;
+    }
+    __syncwarp(tm);
+    // lanes past the last row repeat it and store nothing
+    const int i = lane < ND ? lane : ND - 1;
+    const int ar = i % ND1, br = i / ND1;
+    float bb[NM];
+#pragma unroll
+    for (int be = 0; be < NM; ++be) bb[be] = tb.BmF[be][br];
+    float a[ND];
+#pragma unroll
+    for (int t = 0; t < ND; ++t) {
+        float s = 0.0f;
+#pragma unroll
+        for (int be = 0; be < NM; ++be)
+            s += Y[(ar * ND1 + t % ND1) * NM + be] * bb[be] * tb.BmF[be][t / ND1];
+        a[t] = s;
+    }
+    bool ok = true;
+    rinv = 0.0f;
+    chol_rows<ND, TL>(a, i, rinv, ok, tm, std::make_integer_sequence<int, ND>{});
+    if (ok && lane < ND) {
+#pragma unroll
+        for (int t = 0; t < ND; ++t)
+            if (t <= i) Mf[lrow_idx<ND>(i, t)] = a[t];
+    }
+    __syncwarp(tm);
+    return ok;
+}
+
+// (L L^T)^-1 b in FP32 with the factor of mass_factor_rows_f: lane i brings
+// b_i and gets x_i; the solved component of each step is passed by a
+// shuffle (forward, then backward substitution, column by column).
+template <int ND, int TL>
+__device__ __forceinline__ float chol_subst_rows_f(const float* Mf, float rinv, float bv, int lane,
+                                                   unsigned tm) {
+    const int i = lane < ND ? lane : ND - 1;
+    float lr[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) lr[j] = j < i ? Mf[lrow_idx<ND>(i, j)] : 0.0f; // row i of L
+#pragma unroll
+    for (int j = 0; j < ND; ++j) { // L y = b
+        const float yj = __shfl_sync(tm, bv * rinv, j, TL);
+        if (i == j) bv = yj;
+        else if (i > j) bv -= lr[j] * yj;
+    }
+#pragma unroll
+    for (int j = 0; j < ND; ++j) lr[j] = j > i ? Mf[lrow_idx<ND>(j, i)] : 0.0f; // column i of L
+#pragma unroll
+    for (int j = ND - 1; j >= 0; --j) { // L^T x = y
+        const float xj = __shfl_sync(tm, bv * rinv, j, TL);
+        if (i == j) bv = xj;
+        else if (i < j) bv -= lr[j] * xj;
+    }
+    return bv;
+}
+
 // Solve H x = b for the depth-weighted mass matrix H = B^T diag(cw) B (the
 // tracer matrix of Eq. mass_matrix_concentration, or the masked Jacobian of
 // Eq. mass_matrix) by mixed-precision iterative refinement: H is assembled and
@@ -1233,16 +1281,17 @@ __device__ __forceinline__ void assemble_mass(const Tables& tb, const double* cw
 // when a correction, or the next one as predicted from the contraction of
 // the last two, is below 1e-15 of x; if that does not happen within 6 sweeps
 // (an ill-conditioned near-dry cell), the FP64 Cholesky decides.  x (FP64, in place of b on
-// return).  Scratch: Mf, Yf (float), r, t (ND doubles), q (NMP doubles),
-// tmp (2 NM NM doubles), M, Y (double, fallback).
+// return).  Scratch: Mf [ND ND], Yf [ND1 ND1 NM] (float), x, r (ND doubles),
+// q (NMP doubles), tmp (2 NM NM doubles), M, Y, inv (double, fallback).
 template <int ND1, int NM, int TL = 32>
 __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, float* Mf,
-                                 float* Yf, float* invf, float* rf, double* x, double* r,
-                                 double* q, double* tmp, double* M, double* Y, double* inv,
-                                 int lane, unsigned tm = 0xffffffffu) {
+                                 float* Yf, double* x, double* r, double* q, double* tmp,
+                                 double* M, double* Y, double* inv, int lane,
+                                 unsigned tm = 0xffffffffu) {
     constexpr int ND = ND1 * ND1, NMP = NM * NM;
-    assemble_mass_f<ND1, NM, TL>(tb, cw, Yf, Mf, lane, tm);
-    bool ok = chol_factor_f<ND, TL>(Mf, invf, lane, tm);
+    static_assert(ND <= TL, "one unknown per lane");
+    float rinv; // the lane's reciprocal FP32 pivot
+    bool ok = mass_factor_rows_f<ND1, NM, TL>(tb, cw, Yf, Mf, rinv, lane, tm);
     if (ok) {
         for (int i = lane; i < ND; i += TL) {
             x[i] = 0.0;
@@ -1252,16 +1301,14 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
         ok = false;
         double dprev = 0.0; // max |correction| of the previous sweep
         for (int sweep = 0; sweep < 6; ++sweep) {
-            for (int i = lane; i < ND; i += TL) rf[i] = (float)r[i];
-            __syncwarp(tm);
-            chol_subst_f<ND, TL>(Mf, invf, rf, lane, tm);
+            // the lane's component of the correction
+            const float v =
+                chol_subst_rows_f<ND, TL>(Mf, rinv, lane < ND ? (float)r[lane] : 0.0f, lane, tm);
             // max |correction| and max |x| (a NaN counts as 0, as under fmax),
             // reduced on their bit patterns
-            static_assert(ND <= TL, "one unknown per lane");
             float da = 0.0f;
             double xa = 0.0;
             if (lane < ND) {
-                const float v = rf[lane];
                 x[lane] += (double)v;
                 da = (v == v) ? fabsf(v) : 0.0f;
                 const unsigned long long xb =
@@ -1424,10 +1471,8 @@ __global__ void __maxnreg__(96)
     double* M = Y + ND1 * ND1 * NM;             // [ND ND] (fallback)
     float* Mf = (float*)(pg + 6 * NGP);         // [ND ND]
     float* Yf = Mf + ND * ND;                   // [ND1 ND1 NM]
-    float* invf = Yf + ND1 * ND1 * NM;          // [ND]
-    float* rf = invf + ND;                      // [ND]
     // momentum scratch, 8-byte aligned after the float arrays
-    double* mw = (double*)((((uintptr_t)(rf + ND)) + 7) & ~(uintptr_t)7);
+    double* mw = (double*)((((uintptr_t)(Yf + ND1 * ND1 * NM)) + 7) & ~(uintptr_t)7);
     double* mt = mw + 2 * ND;
     const int64_t n = d.n;
     const double g = d.g, eps = d.eps;
@@ -1506,7 +1551,7 @@ __global__ void __maxnreg__(96)
                 } else {
                     for (int i = lane; i < ND; i += TL) o[ND + i] = o[i];
                     __syncwarp(tm);
-                    if (!solve_mass_mixed<ND1, NM, TL>(tb, pA, o + ND, Mf, Yf, invf, rf, xs, rs, qs,
+                    if (!solve_mass_mixed<ND1, NM, TL>(tb, pA, o + ND, Mf, Yf, xs, rs, qs,
                                                        tmp, M, Y, pinv, lane, tm)) {
                         scalar = true;
                         break;
@@ -1639,7 +1684,7 @@ __global__ void __maxnreg__(96)
                 o[3 * ND + i] = rc[i];
             }
             __syncwarp(tm);
-            solve_mass_mixed<ND1, NM, TL>(tb, pV, o + 3 * ND, Mf, Yf, invf, rf, xs, rs, qs, tmp, M,
+            solve_mass_mixed<ND1, NM, TL>(tb, pV, o + 3 * ND, Mf, Yf, xs, rs, qs, tmp, M,
                                           Y, pinv, lane, tm);
         }
         __syncwarp(tm);
