@@ -70,10 +70,10 @@ FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "faces_1": 230, "faces_2": 400, "
                            "stage_2": 4965, "stage_3": 5223, "final": 5001}
 # DRAM bytes per launch from an ncu capture of the current kernels (FP64
 # path); {} (traffic null) whenever the kernels changed after the capture
-DRAM_BYTES_PER_LAUNCH = {"step_begin": 59064064, "faces_1": 154470144, "faces_2": 154417408,
-                         "faces_3": 154550784, "residual_1": 171589632, "residual_2": 173660672,
-                         "residual_3": 173016832, "stage_2": 156521728, "stage_3": 252119808,
-                         "final": 257224704}
+DRAM_BYTES_PER_LAUNCH = {"step_begin": 59051008, "faces_1": 154396672, "faces_2": 154386944,
+                         "faces_3": 154586880, "residual_1": 170340352, "residual_2": 172822528,
+                         "residual_3": 171862784, "stage_2": 152415232, "stage_3": 245341952,
+                         "final": 251504640}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
 
 

@@ -370,27 +370,28 @@ __global__ void __launch_bounds__(32 * MAXWPB)
         }
         __syncwarp();
         // faces: one (sub)face point per lane, as the forward
-        unsigned char fi[4];
-        int base[5];
-        base[0] = 0;
+        unsigned fi[4]; // indexed by constants only (registers)
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            fi[f] = d.finfo ? d.finfo[k * 4 + f] : 0;
-            base[f + 1] = base[f] + (((fi[f] & 3) == FI_COARSE) ? 2 : 1) * NM;
-        }
+        for (int f = 0; f < 4; ++f) fi[f] = d.finfo ? d.finfo[k * 4 + f] : 0;
+        // the face points of faces 0..3 start at 0, b1, b2, b3 (2 NM points on
+        // a coarse 2:1 face, else NM)
+        auto npts = [&](unsigned inf) { return (((inf & 3) == FI_COARSE) ? 2 : 1) * NM; };
+        const int b1 = npts(fi[0]), b2 = b1 + npts(fi[1]), b3 = b2 + npts(fi[2]),
+                  b4 = b3 + npts(fi[3]);
         // as for the volume points: with at most 16 face points per conforming
         // cell the two halves share a point, directions 0-2 and 3-4
         constexpr bool FSPLIT = 4 * NM <= 16;
         constexpr int FW = FSPLIT ? 3 : 5;
         const int fb0 = FSPLIT ? (lane >> 4) * FW : 0;
         constexpr int FSTEP = FSPLIT ? 16 : 32;
-        for (int it0 = 0; it0 < base[4]; it0 += FSTEP) {
+        for (int it0 = 0; it0 < b4; it0 += FSTEP) {
             const int il = it0 + (FSPLIT ? (lane & 15) : lane);
-            const bool iv = il < base[4]; // a lane past the last point computes point 0, unused
+            const bool iv = il < b4; // a lane past the last point computes point 0, unused
             const int it = iv ? il : 0;
-            const int f = (it >= base[1]) + (it >= base[2]) + (it >= base[3]);
-            const int r_ = it - base[f], h = r_ / NM, al = r_ % NM;
-            const unsigned info = fi[f];
+            const int f = (it >= b1) + (it >= b2) + (it >= b3);
+            const int r_ = it - (f == 0 ? 0 : f == 1 ? b1 : f == 2 ? b2 : b3), h = r_ / NM,
+                      al = r_ % NM;
+            const unsigned info = f == 0 ? fi[0] : f == 1 ? fi[1] : f == 2 ? fi[2] : fi[3];
             const bool coarse = (info & 3) == FI_COARSE, fine = (info & 3) == FI_FINE;
             const int half = (int)(info >> 2);
             const double nx = (f == 0) ? -1.0 : (f == 1) ? 1.0 : 0.0;
@@ -667,7 +668,7 @@ constexpr int stage_vjp_smem() {
 template <int R, typename Pix, int MODE>
 __global__ void __maxnreg__(128)
     k_stage_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
-                const StageVjpArgs a) {
+                const __grid_constant__ StageVjpArgs a) {
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
@@ -970,7 +971,7 @@ constexpr int begin_vjp_smem() {
 template <int R, typename Pix, int MODE>
 __global__ void __maxnreg__(96)
     k_begin_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
-                const BeginVjpArgs a) {
+                const __grid_constant__ BeginVjpArgs a) {
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;

@@ -115,7 +115,7 @@ constexpr int remap_smem() {
 
 template <int R>
 __global__ void __launch_bounds__(32 * MAXWPB)
-    k_remap(const __grid_constant__ Tables tb, const RemapArgs a) {
+    k_remap(const __grid_constant__ Tables tb, const __grid_constant__ RemapArgs a) {
     using S = Sz<R>;
     constexpr int ND1 = S::ND1, ND = S::ND, NG = S::NG, NGP = S::NGP;
     extern __shared__ double smem[];

@@ -714,23 +714,24 @@ __global__ void __maxnreg__(96)
         // faces: one (sub)face point per lane; a coarse cell integrates each
         // 2:1 face over the GLL points of both fine halves
         double dtl = 0.0;
-        unsigned char fi[4];
-        int base[5];
-        base[0] = 0;
+        unsigned fi[4]; // indexed by constants only (registers)
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            fi[f] = d.finfo ? d.finfo[k * 4 + f] : 0;
-            base[f + 1] = base[f] + (((fi[f] & 3) == FI_COARSE) ? 2 : 1) * NM;
-        }
+        for (int f = 0; f < 4; ++f) fi[f] = d.finfo ? d.finfo[k * 4 + f] : 0;
         if (d.fflux) {
             // the face fluxes of this cell, computed once per face point by k_faces
             const double* F = d.fflux + k * (32 * NM);
             for (int i = lane; i < 32 * NM; i += 32) fh[i] = F[i];
         } else {
-            for (int it = lane; it < base[4]; it += 32) {
-                const int f = (it >= base[1]) + (it >= base[2]) + (it >= base[3]);
-                const int r_ = it - base[f], h = r_ / NM, al = r_ % NM;
-                const unsigned info = fi[f];
+            // the face points of faces 0..3 start at 0, b1, b2, b3 (2 NM points
+            // on a coarse 2:1 face, else NM)
+            auto npts = [&](unsigned inf) { return (((inf & 3) == FI_COARSE) ? 2 : 1) * NM; };
+            const int b1 = npts(fi[0]), b2 = b1 + npts(fi[1]), b3 = b2 + npts(fi[2]),
+                      b4 = b3 + npts(fi[3]);
+            for (int it = lane; it < b4; it += 32) {
+                const int f = (it >= b1) + (it >= b2) + (it >= b3);
+                const int r_ = it - (f == 0 ? 0 : f == 1 ? b1 : f == 2 ? b2 : b3), h = r_ / NM,
+                          al = r_ % NM;
+                const unsigned info = f == 0 ? fi[0] : f == 1 ? fi[1] : f == 2 ? fi[2] : fi[3];
                 const bool coarse = (info & 3) == FI_COARSE;
                 B raw[4], pres, lam, out[4];
                 bool own_first, bnd;
@@ -1436,7 +1437,8 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
 
 template <int R, typename Pix, int MODE, typename B>
 __global__ void __maxnreg__(96)
-    k_stage(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, const StageArgs sa) {
+    k_stage(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
+            const __grid_constant__ StageArgs sa) {
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
