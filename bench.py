@@ -70,10 +70,10 @@ FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "faces_1": 230, "faces_2": 400, "
                            "stage_2": 4965, "stage_3": 5223, "final": 5001}
 # DRAM bytes per launch from an ncu capture of the current kernels (FP64
 # path); {} (traffic null) whenever the kernels changed after the capture
-DRAM_BYTES_PER_LAUNCH = {"step_begin": 59051008, "faces_1": 154396672, "faces_2": 154386944,
-                         "faces_3": 154586880, "residual_1": 170340352, "residual_2": 172822528,
-                         "residual_3": 171862784, "stage_2": 152415232, "stage_3": 245341952,
-                         "final": 251504640}
+DRAM_BYTES_PER_LAUNCH = {"step_begin": 59110144, "faces_1": 154510080, "faces_2": 154032384,
+                         "faces_3": 154688000, "residual_1": 170770176, "residual_2": 172908032,
+                         "residual_3": 171634688, "stage_2": 152008704, "stage_3": 245230080,
+                         "final": 251635968}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
 
 

@@ -179,6 +179,17 @@ __device__ __forceinline__ double team_max_nonneg(double v, unsigned tm) {
     const unsigned ml = __reduce_max_sync(tm, hi == mh ? lo : 0u);
     return __longlong_as_double((long long)(((unsigned long long)mh << 32) | ml));
 }
+// equality and finiteness of doubles tested on their bit patterns, on the
+// integer pipe (FP64 compares take the FP64 pipe).  same_bits differs from ==
+// only for +0 against -0 and for NaN: a constant-field mask may treat those
+// either way, since a field marked non-constant takes the general path.
+__device__ __forceinline__ bool same_bits(double a, double b) {
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool finite_bits(double v) {
+    constexpr long long EXP = 0x7ff0000000000000ll;
+    return (__double_as_longlong(v) & EXP) != EXP;
+}
 __device__ __forceinline__ double* ufield(const Dev& d, int buf, int f, int nd) {
     return d.U + ((size_t)buf * 4 + f) * (size_t)d.n * nd;
 }

@@ -1572,7 +1572,7 @@ __global__ void __maxnreg__(96)
                 __syncwarp(tm);
                 {
                     bool eq = true;
-                    for (int i = lane; i < ND; i += TL) eq = eq && (z[i] == z[0]);
+                    for (int i = lane; i < ND; i += TL) eq = eq && same_bits(z[i], z[0]);
                     zc = __all_sync(tm, eq);
                 }
                 if (inc <= d.newton_tol * scale) prev_full = false, kk = d.newton_max - 1;
@@ -1694,13 +1694,13 @@ __global__ void __maxnreg__(96)
         unsigned cmo = 0;
         for (int f = 0; f < 4; ++f) {
             bool eq = true;
-            for (int i = lane; i < ND; i += TL) eq = eq && (o[f * ND + i] == o[f * ND]);
+            for (int i = lane; i < ND; i += TL) eq = eq && same_bits(o[f * ND + i], o[f * ND]);
             if (__all_sync(tm, eq)) cmo |= (1u << f);
         }
         bool fin = true;
         for (int i = lane; i < 4 * ND; i += TL) {
             const double v = o[i];
-            fin = fin && isfinite(v);
+            fin = fin && finite_bits(v);
             ufield(d, sa.out_buf, i / ND, ND)[k * ND + (i % ND)] = v;
         }
         if (!__all_sync(tm, fin)) bad = 1;
@@ -1736,7 +1736,7 @@ __global__ void k_masks(const __grid_constant__ Dev d, int buf) {
         for (int f = 0; f < 4; ++f) {
             const double* u = ufield(d, buf, f, ND) + k * ND;
             bool eq = true;
-            for (int i = lane; i < ND; i += 32) eq = eq && (u[i] == u[0]);
+            for (int i = lane; i < ND; i += 32) eq = eq && same_bits(u[i], u[0]);
             if (__all_sync(0xffffffffu, eq)) cm |= (1u << f);
         }
         if (lane == 0) d.cmask[(size_t)buf * d.n + k] = (uint8_t)cm;
