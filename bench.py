@@ -62,7 +62,7 @@ def units_per_step(wl):
 # faces_l: k_faces of stage l, residual_l: k_residual).  These kernels are
 # bound by the FP64 pipe: GB300's FP64 rate is the roofline.
 FLOPS_PER_CELL = {"step_begin": 2187, "faces_1": 1683, "faces_2": 1850, "faces_3": 1851,
-                  "residual_1": 9449, "residual_2": 10000, "residual_3": 9997, "stage_2": 8257,
+                  "residual_1": 8685, "residual_2": 9230, "residual_3": 9230, "stage_2": 8257,
                   "stage_3": 9049, "final": 6747}
 # the FP32-bulk kernels' FP64 flops (their FP32 work runs on the 60x faster FP32 pipe)
 FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "faces_1": 230, "faces_2": 400, "faces_3": 400,
@@ -70,10 +70,10 @@ FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "faces_1": 230, "faces_2": 400, "
                            "stage_2": 4965, "stage_3": 5223, "final": 5001}
 # DRAM bytes per launch from an ncu capture of the current kernels (FP64
 # path); {} (traffic null) whenever the kernels changed after the capture
-DRAM_BYTES_PER_LAUNCH = {"step_begin": 59110144, "faces_1": 154510080, "faces_2": 154032384,
-                         "faces_3": 154688000, "residual_1": 170770176, "residual_2": 172908032,
-                         "residual_3": 171634688, "stage_2": 152008704, "stage_3": 245230080,
-                         "final": 251635968}
+DRAM_BYTES_PER_LAUNCH = {"step_begin": 59130624, "faces_1": 154138624, "faces_2": 154429184,
+                         "faces_3": 154680832, "residual_1": 170563328, "residual_2": 173243648,
+                         "residual_3": 171883776, "stage_2": 152387328, "stage_3": 244866560,
+                         "final": 251608576}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
 
 

@@ -227,6 +227,22 @@ __device__ __forceinline__ T gamma_manning(T n, T h, T qx, T qy, T g, T eps) {
     return g * n * n * sqrt(qx * qx + qy * qy) / (hdes * hdes * cbrt(hdes));
 }
 
+// the velocity factor and the Manning coefficient of one point together: on
+// the wet branch (h >= eps, where h_des = h) both come from the one
+// reciprocal 1/h, with h^(-7/3) = (1/h)^2 cbrt(1/h); otherwise as
+// vel_factor and gamma_manning
+template <typename T>
+__device__ __forceinline__ void vel_gamma(T n, T h, T qx, T qy, T g, T eps, T& fv, T& gam) {
+    if (h >= eps && h > T(0)) {
+        const T rh = T(1) / h;
+        fv = rh;
+        gam = (n == T(0)) ? T(0) : g * n * n * sqrt(qx * qx + qy * qy) * (rh * rh) * cbrt(rh);
+    } else {
+        fv = vel_factor<T>(h, eps);
+        gam = gamma_manning<T>(n, h, qx, qy, g, eps);
+    }
+}
+
 // sub-grid wet depth V and wet area A of sub-cell (ia, ib) of point set `set`
 // (mode S): V = sum_k w_k max(eta + z_k, 0), A = sum_k w_k [eta + z_k > 0]
 template <typename Pix>

@@ -582,9 +582,9 @@ __global__ void __maxnreg__(96)
             double h, A;
             ST::VA(d, tb, k, SET_VOL, al, be, z, h, A);
             const B hB = (B)h;
-            const B fv = vel_factor<B>(hB, epsB);
+            B fv, gam;
+            vel_gamma<B>(manB, hB, qx, qy, gB, epsB, fv, gam);
             const B ux = fv * qx, uy = fv * qy;
-            const B gam = gamma_manning<B>(manB, hB, qx, qy, gB, epsB);
             const double w = J * tb.wv[al] * tb.wv[be];
             const B wB = (B)w, wx = (B)(w * ihx), wy = (B)(w * ihy);
             Xd[0 * NVP + p] = (double)(wx * qx);
