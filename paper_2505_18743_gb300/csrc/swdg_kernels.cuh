@@ -1063,24 +1063,25 @@ struct StageArgs {
 };
 
 template <int R>
-constexpr int stage_union_live() {
-    // in doubles: friction points [6 NGP] (also the momentum block's point
-    // arrays), the FP32 solve's float M, Y (8-byte padded), the momentum
-    // block's nodal pair and tmp pair (B-typed, sized in doubles)
+constexpr int stage_union() {
+    // in doubles, one region for what is never live at the same time: the
+    // friction points / the momentum block's point arrays [6 NGP] with its
+    // nodal and tmp pairs (B-typed, sized in doubles); the FP32 solve's float
+    // M, Y (8-byte padded); the FP64 fallback's M [ND ND]
     using S = Sz<R>;
-    return 6 * S::NGP + (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 1) / 2 + 1 + 2 * S::ND +
-           2 * S::ND1 * S::NG;
+    constexpr int mom = 6 * S::NGP + 2 * S::ND + 2 * S::ND1 * S::NG;
+    constexpr int f32 = (S::ND * S::ND + S::ND1 * S::ND1 * S::NM + 1) / 2;
+    constexpr int fb = S::ND * S::ND;
+    constexpr int m = mom > f32 ? mom : f32;
+    return m > fb ? m : fb;
 }
 template <int R>
 constexpr int stage_smem() {
     using S = Sz<R>;
-    // the FP64 fallback's Y and M [ND1 ND1 NM + ND ND] share the last region
-    // with what is dead whenever the fallback runs (see k_stage)
-    constexpr int fb = S::ND1 * S::ND1 * S::NM + S::ND * S::ND;
-    constexpr int un = stage_union_live<R>() > fb ? stage_union_live<R>() : fb;
-    return 4 * S::ND + 5 * S::ND + 3 * S::NMP + 2 * S::NM * S::NM + 4 * S::ND + S::ND +
-           // mixed-precision solve: x, r (ND), q (NMP)
-           2 * S::ND + S::NMP + un;
+    // the FP64 fallback's Y [ND1 ND1 NM] overlays tmp, x, r (see k_stage)
+    static_assert(S::ND1 * S::ND1 * S::NM <= 2 * S::NM * S::NM + 2 * S::ND, "fallback Y");
+    return 4 * S::ND + 5 * S::ND + 3 * S::NMP + 2 * S::NM * S::NM + 2 * S::ND + 4 * S::ND +
+           stage_union<R>();
 }
 
 // Cholesky of the SPD matrix M (ND x ND, row-major, lower part used) on a
@@ -1458,24 +1459,27 @@ __global__ void __maxnreg__(96)
     double* pV = pe + NMP;                      // [NMP]
     double* pA = pV + NMP;                      // [NMP]
     double* tmp = pA + NMP;                     // [2 NM NM]
-    double* o = tmp + 2 * NM * NM;              // [4][ND]
-    double* pinv = o + 4 * ND;                  // [ND] reciprocal Cholesky pivots
-    double* xs = pinv + ND;                     // [ND] refinement iterate (also scratch [2 ND]
+    double* xs = tmp + 2 * NM * NM;             // [ND] refinement iterate (also scratch [2 ND]
     double* rs = xs + ND;                       // [ND] refinement residual   with rs outside a solve)
-    double* qs = rs + ND;                       // [NMP]
+    double* o = rs + ND;                        // [4][ND]
+    // the refinement's q [NMP] is pe, idle inside a solve (pe holds the
+    // interpolated iterate only while V and A are evaluated)
+    double* qs = pe;
     // the last region: friction points pg (the scalar path's; the momentum
-    // block's point arrays on the other path), the FP32 solve's arrays, the
-    // momentum scratch; the FP64 fallback's Y, M overlay it, since the
-    // fallback runs only inside a solve (the momentum block idle, the FP32
-    // arrays given up)
-    double* pg = qs + NMP;                      // [6][NGP]
-    double* Y = pg;                             // [ND1 ND1 NM] (fallback)
-    double* M = Y + ND1 * ND1 * NM;             // [ND ND] (fallback)
-    float* Mf = (float*)(pg + 6 * NGP);         // [ND ND]
+    // block's point arrays on the other path) with the momentum scratch, or
+    // the FP32 solve's arrays, or the FP64 fallback's M.  The momentum block
+    // runs between the two solves; the fallback runs only inside a solve, when
+    // the FP32 arrays are given up, and its Y and pivots take tmp, x, r and q,
+    // which are idle then.
+    double* un = o + 4 * ND;
+    double* pg = un;                            // [6][NGP]
+    double* mw = pg + 6 * NGP;                  // momentum nodal pair [2 ND] (B)
+    double* mt = mw + 2 * ND;                   // momentum tmp pair [2 ND1 NG] (B)
+    float* Mf = (float*)un;                     // [ND ND]
     float* Yf = Mf + ND * ND;                   // [ND1 ND1 NM]
-    // momentum scratch, 8-byte aligned after the float arrays
-    double* mw = (double*)((((uintptr_t)(Yf + ND1 * ND1 * NM)) + 7) & ~(uintptr_t)7);
-    double* mt = mw + 2 * ND;
+    double* M = un;                             // [ND ND] (fallback)
+    double* Y = tmp;                            // [ND1 ND1 NM] (fallback)
+    double* pinv = qs;                          // [ND] (fallback)
     const int64_t n = d.n;
     const double g = d.g, eps = d.eps;
     int its_max = 0;
