@@ -70,10 +70,10 @@ FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "faces_1": 230, "faces_2": 400, "
                            "stage_2": 4965, "stage_3": 5223, "final": 5001}
 # DRAM bytes per launch from an ncu capture of the current kernels (FP64
 # path); {} (traffic null) whenever the kernels changed after the capture
-DRAM_BYTES_PER_LAUNCH = {"step_begin": 59217920, "faces_1": 154471168, "faces_2": 154491904,
-                         "faces_3": 155040512, "residual_1": 170648576, "residual_2": 172891136,
-                         "residual_3": 172018688, "stage_2": 152381952, "stage_3": 244749568,
-                         "final": 251613696}
+DRAM_BYTES_PER_LAUNCH = {"step_begin": 58935808, "faces_1": 154463744, "faces_2": 154456832,
+                         "faces_3": 155003648, "residual_1": 170799616, "residual_2": 173084416,
+                         "residual_3": 172475392, "stage_2": 152635648, "stage_3": 244360192,
+                         "final": 251701504}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
 
 

@@ -758,27 +758,31 @@ __global__ void __maxnreg__(96)
             if (lane == 0) atomic_max_pos(&d.mb[mem].rmax, m);
         }
         __syncwarp();
-        // lift the face fluxes onto the nodes of each face
-        for (int i = lane; i < 4 * ND; i += 32) {
-            const int cf = i / ND, j = i % ND, a = j % ND1, b = j / ND1;
-            double s = 0.0;
+        // lift the face fluxes onto the nodes of each face: one item per field,
+        // face and node along it, the x faces (0, 1: node columns a = 0 and
+        // ND1 - 1) in one pass and the y faces (2, 3: rows b = 0 and ND1 - 1) in
+        // the next, so that the items of a pass touch distinct nodes and every
+        // lane does the same work
 #pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                const bool on = (f == 0 && a == 0) || (f == 1 && a == ND1 - 1) || (f == 2 && b == 0) ||
-                                (f == 3 && b == ND1 - 1);
-                if (!on) continue;
-                const int tn = f < 2 ? b : a; // tangential node index along the face
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int i = lane; i < 4 * 2 * ND1; i += 32) {
+                const int cf = i / (2 * ND1), r_ = i % (2 * ND1), f = 2 * pass + r_ / ND1;
+                const int tn = r_ % ND1; // node index along the face
+                const unsigned inf = f == 0 ? fi[0] : f == 1 ? fi[1] : f == 2 ? fi[2] : fi[3];
                 const double* fp = fh + (cf * 4 + f) * 2 * NM;
-                if ((fi[f] & 3) == FI_COARSE) {
+                double s = 0.0;
+                if ((inf & 3) == FI_COARSE) {
+#pragma unroll
                     for (int al = 0; al < NM; ++al)
                         s += tb.BmH[0][al][tn] * fp[al] + tb.BmH[1][al][tn] * fp[NM + al];
                 } else {
+#pragma unroll
                     for (int al = 0; al < NM; ++al) s += tb.Bm[al][tn] * fp[al];
                 }
+                rs[cf * ND + face_node<ND1>(f, tn)] -= s;
             }
-            rs[cf * ND + j] -= s;
+            __syncwarp();
         }
-        __syncwarp();
         for (int i = lane; i < 6 * ND; i += 32)
             rfield(d, stage, i / ND, ND)[k * ND + (i % ND)] = rs[i];
         __syncwarp();
