@@ -592,29 +592,42 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             }
             __syncwarp();
         }
-        // lift the face-point cotangents onto the face nodes, then write
+        // lift the face-point cotangents onto the face nodes, then write.  The
+        // node values go to shared memory (the point cotangents xv are consumed
+        // by now) and the faces are added in two uniform passes, the x faces
+        // (node columns a = 0, ND1 - 1) and then the y faces (rows b = 0,
+        // ND1 - 1), one item per field, face and node along it, as in the
+        // forward residual
+        double* uacc = xv; // [4][ND]
         for (int i = lane, c_ = 0; i < ND; i += 32, ++c_) {
-            const int a = i % ND1, b = i / ND1;
 #pragma unroll
-            for (int cf = 0; cf < 4; ++cf) {
-                double s = ub[cf * NC + c_];
+            for (int cf = 0; cf < 4; ++cf) uacc[cf * ND + i] = ub[cf * NC + c_];
+        }
+        __syncwarp();
 #pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    const bool on = (f == 0 && a == 0) || (f == 1 && a == ND1 - 1) ||
-                                    (f == 2 && b == 0) || (f == 3 && b == ND1 - 1);
-                    if (!on) continue;
-                    const int tn = f < 2 ? b : a;
-                    const double* fp = xf + (cf * 4 + f) * 2 * NM;
-                    if ((fi[f] & 3) == FI_COARSE) {
-                        for (int al = 0; al < NM; ++al)
-                            s += tb.BmH[0][al][tn] * fp[al] + tb.BmH[1][al][tn] * fp[NM + al];
-                    } else {
-                        for (int al = 0; al < NM; ++al) s += tb.Bm[al][tn] * fp[al];
-                    }
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int i = lane; i < 4 * 2 * ND1; i += 32) {
+                const int cf = i / (2 * ND1), r_ = i % (2 * ND1), f = 2 * pass + r_ / ND1;
+                const int tn = r_ % ND1; // node index along the face
+                const unsigned inf = f == 0 ? fi[0] : f == 1 ? fi[1] : f == 2 ? fi[2] : fi[3];
+                const double* fp = xf + (cf * 4 + f) * 2 * NM;
+                double s = 0.0;
+                if ((inf & 3) == FI_COARSE) {
+#pragma unroll
+                    for (int al = 0; al < NM; ++al)
+                        s += tb.BmH[0][al][tn] * fp[al] + tb.BmH[1][al][tn] * fp[NM + al];
+                } else {
+#pragma unroll
+                    for (int al = 0; al < NM; ++al) s += tb.Bm[al][tn] * fp[al];
                 }
-                if (accumulate) ubar[cf * fs + k * ND + i] += s;
-                else ubar[cf * fs + k * ND + i] = s;
+                uacc[cf * ND + face_node<ND1>(f, tn)] += s;
             }
+            __syncwarp();
+        }
+        for (int i = lane; i < 4 * ND; i += 32) {
+            const int cf = i / ND, j = i % ND;
+            if (accumulate) ubar[cf * fs + k * ND + j] += uacc[i];
+            else ubar[cf * fs + k * ND + j] = uacc[i];
         }
         const double ds = warp_sum(dsum), ns = warp_sum(nsum);
         if (lane == 0) {
