@@ -229,7 +229,7 @@ def run_reference(args, rank, world):
     rate = units_per_step(wl) * args.steps / el
     cores = int(os.environ["OMP_NUM_THREADS"])
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "updates/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": "16x16-cell crop (184,120), CPU oracle"},
