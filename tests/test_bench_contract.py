@@ -54,3 +54,44 @@ def test_reference_arm_under_two_gloo_ranks_prints_once():
     lines = _lines(p.stdout)
     assert len(lines) == 1
     _check_line(lines[0], 2, 1, 3)
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def test_clock_summary_reports_median_max_and_throttle_reasons(tmp_path):
+    bench = _bench()
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "bad line"]
+    p = tmp_path / "clocks.csv"
+    p.write_text("\n".join(rows) + "\n")
+    s = bench.ClockSampler()
+    s.path = str(p)
+    out = s.summary()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                   "samples": 3}
+    # every throttle reason the timing rules name is reported
+    p.write_text("0, 1500, 2070, 1000, 0x68, Active, Active, Active, Not Active\n")
+    s.path = str(p)
+    assert s.summary()["reasons"] == ["hw_slowdown", "hw_thermal_slowdown",
+                                      "sw_thermal_slowdown"]
+    # no samples at all: said so, not left empty
+    s.path = str(tmp_path / "missing.csv")
+    assert s.summary()["reasons"] == ["unavailable"]
+
+
+def test_algorithmic_bytes_match_the_per_cell_model():
+    """r = 3, 16 x 16 f32 pixels per cell: residual 4 + 6 fields of 16 f64
+    nodes, the 1 KB tile and 57 B of geometry; stage update v^n, H and C~,
+    nres residual sets of 6 fields and the output state."""
+    b = _bench().algorithmic_bytes_per_cell
+    assert b("residual_2") == 4 * 16 * 8 + 6 * 16 * 8 + 16 * 16 * 4 + 57 == 2361
+    assert b("stage_2", nres=1) == 2121 and b("final", nres=3) == 3657
+    assert b("step_begin") == 1865 and b("faces_1") == 4 * 16 * 8 + 57
+    assert _bench().units_per_step(type("W", (), {"degree": 3, "mesh": type(
+        "M", (), {"n": 65536})})()) == 65536 * 4 * 16 * 3
