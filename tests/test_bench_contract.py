@@ -95,3 +95,35 @@ def test_algorithmic_bytes_match_the_per_cell_model():
     assert b("step_begin") == 1865 and b("faces_1") == 4 * 16 * 8 + 57
     assert _bench().units_per_step(type("W", (), {"degree": 3, "mesh": type(
         "M", (), {"n": 65536})})()) == 65536 * 4 * 16 * 3
+
+
+def _max_worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), CUDA_VISIBLE_DEVICES="")
+    sys.path.insert(0, ROOT)
+    import bench
+    r, w, _ = bench.dist_init(world)
+    assert (r, w) == (rank, world)
+    bench.barrier(w)
+    # each rank's timed region; the job's time is the slowest rank's
+    out[rank] = bench.max_over_ranks(10.0 + 5.0 * rank, w)
+    bench.barrier(w)
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_takes_the_slowest_of_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_max_worker, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=300)
+            assert p.exitcode == 0
+        assert dict(out) == {0: 15.0, 1: 15.0}
