@@ -526,25 +526,42 @@ __global__ void __maxnreg__(96)
         const double t = (c_stage == 0.0) ? d.mb[mem].t : d.mb[mem].t + c_stage * get_dt(d, mem);
         __syncwarp();
         // x-contractions: zeta (value, d/dxi) in FP64, qx, qy, c in B
-        for (int i = lane; i < 2 * ND1 * NV; i += 32) {
-            const int f = i / (ND1 * NV), r_ = i % (ND1 * NV), b = r_ / NV, al = r_ % NV;
-            double s = 0.0;
-            if (f == 0) {
+        if constexpr (F64) {
+            // one job list over the five contractions, the table selected
+            // per job (no branch inside a warp): jobs 0..1 zeta value and
+            // d/dxi into tz, jobs 2..4 qx, qy, c into tB (B = double here)
+            constexpr int NE = ND1 * NV;
+            for (int i = lane; i < 5 * NE; i += 32) {
+                const int f = i / NE, r_ = i % NE, b = r_ / NV, al = r_ % NV;
+                const double(*Tb)[MXN] = f == 1 ? tb.Dv : tb.Bv;
+                const double* u = su + (f < 2 ? 0 : f - 1) * ND + ND1 * b;
+                double s = 0.0;
 #pragma unroll
-                for (int a = 0; a < ND1; ++a) s += tb.Bv[al][a] * su[ND1 * b + a];
-            } else {
-#pragma unroll
-                for (int a = 0; a < ND1; ++a) s += tb.Dv[al][a] * su[ND1 * b + a];
+                for (int a = 0; a < ND1; ++a) s += Tb[al][a] * u[a];
+                if (f < 2) tz[i] = s;
+                else tB[i - 2 * NE] = s;
             }
-            tz[i] = s;
-        }
-        for (int i = lane; i < 3 * ND1 * NV; i += 32) {
-            const int f = i / (ND1 * NV), r_ = i % (ND1 * NV), b = r_ / NV, al = r_ % NV;
-            const B* u = suB + (1 + f) * ND + ND1 * b;
-            B s = B(0);
+        } else {
+            for (int i = lane; i < 2 * ND1 * NV; i += 32) {
+                const int f = i / (ND1 * NV), r_ = i % (ND1 * NV), b = r_ / NV, al = r_ % NV;
+                double s = 0.0;
+                if (f == 0) {
 #pragma unroll
-            for (int a = 0; a < ND1; ++a) s += BvB[al][a] * u[a];
-            tB[i] = s;
+                    for (int a = 0; a < ND1; ++a) s += tb.Bv[al][a] * su[ND1 * b + a];
+                } else {
+#pragma unroll
+                    for (int a = 0; a < ND1; ++a) s += tb.Dv[al][a] * su[ND1 * b + a];
+                }
+                tz[i] = s;
+            }
+            for (int i = lane; i < 3 * ND1 * NV; i += 32) {
+                const int f = i / (ND1 * NV), r_ = i % (ND1 * NV), b = r_ / NV, al = r_ % NV;
+                const B* u = suB + (1 + f) * ND + ND1 * b;
+                B s = B(0);
+#pragma unroll
+                for (int a = 0; a < ND1; ++a) s += BvB[al][a] * u[a];
+                tB[i] = s;
+            }
         }
         // tracer numerical diffusion (Eq. numdiff): grad c in FP64
         const double nu = d.nu_c ? d.nu_c[k] : 0.0;
