@@ -77,3 +77,55 @@ def rel_inf(a, b, floor=0.0):
     if den == 0.0:
         return float(np.abs(a - b).max()) if a.size else 0.0
     return float(np.abs(a - b).max()) / den
+
+
+FIELDS = ("F", "Gx", "Gy", "R", "Lx", "Ly")
+
+
+def residual_errors(got, ref, floor_frac=1e-3):
+    """Per-field relative errors of a residual against the oracle's: for each
+    field f, max|got_f - ref_f| / max(max|ref_f|, floor_frac * max|ref_f|), the
+    floor taken from the same field only, so a small field (F or L next to
+    the g h grad zeta term of G) is held to its own scale.  ``got`` and ``ref``
+    map field names to arrays; a field that is zero in the oracle is compared
+    absolutely."""
+    out = {}
+    for k in ref:
+        r = np.asarray(ref[k], dtype=np.float64)
+        g = np.asarray(got[k], dtype=np.float64)
+        own = float(np.abs(r).max()) if r.size else 0.0
+        out[k] = rel_inf(g, r, floor=floor_frac * own)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Thacker's oscillating paraboloid (Sec. 4.3).  The free surface is taken with
+# a plus sign, zeta = h0 (s - 1 - R^2/a^2 (s^2 - 1)), s = sqrt(1 - A^2) /
+# (1 - A cos(omega t)): with the depth z_b = h0 (1 - R^2/a^2) this gives
+# h = zeta + z_b = h0 s (1 - s R^2/a^2), which solves the equations with the
+# printed velocity (checked in the tests); the leading minus sign of the
+# printed formula does not.
+# ---------------------------------------------------------------------------
+class Thacker:
+    def __init__(self, g=9.81, sign=1.0):
+        p = golden_dict("thacker_parameters.txt")
+        self.g, self.sign = g, sign
+        self.h0, self.L, self.a, self.r0 = p["h0"], p["L"], p["a"], p["r0"]
+        self.h_lim, self.eps400, self.periods = p["h_lim"], p["eps_at_400"], int(p["periods"])
+        self.omega = np.sqrt(8 * g * self.h0) / self.a
+        self.A = (self.a ** 2 - self.r0 ** 2) / (self.a ** 2 + self.r0 ** 2)
+        self.T = 2 * np.pi / self.omega
+
+    def zb(self, X, Y):
+        R2 = (X - self.L / 2) ** 2 + (Y - self.L / 2) ** 2
+        return self.h0 * (1 - R2 / self.a ** 2)
+
+    def __call__(self, X, Y, t):
+        """free surface (of the paraboloid, also where it lies below the
+        ground) and velocity"""
+        R2 = (X - self.L / 2) ** 2 + (Y - self.L / 2) ** 2
+        den = 1 - self.A * np.cos(self.omega * t)
+        s = np.sqrt(1 - self.A ** 2) / den
+        zeta = self.sign * self.h0 * (s - 1 - R2 / self.a ** 2 * (s * s - 1))
+        f = self.A * self.omega * np.sin(self.omega * t) / (2 * den)
+        return zeta, f * (X - self.L / 2), f * (Y - self.L / 2)
