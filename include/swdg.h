@@ -393,10 +393,17 @@ int swdg_autotune(swdg_ctx* ctx, int repeats, double* report);
  * context: the caller passes every input and output as device buffers, and
  * the only scratch (the step scalars, the pixel-overlap table and one
  * constant-field byte per cell, about 1.01 MiB in all) lives in a fixed array
- * inside the library, reserved on each GPU that loads it until the process
- * exits.  It calls no cudaMalloc/cudaFree.
- *   cfg: degree 1..3, subgrid_mode 0 (pixel sub-cells), g, eps_vel, cfl and
- *        stream are used (stream NULL: the legacy stream);
+ * inside the library, held on each GPU where the library's device code is
+ * loaded until the process exits.  It calls no cudaMalloc/cudaFree.  CUDA
+ * loads device code lazily by default: the array and this degree's kernels
+ * are placed on a device at the first call there (for that degree), which
+ * itself needs about 1 MiB plus the kernels' code of free device memory.  So
+ * make one warm-up call per degree while memory is still free, or run the
+ * process with CUDA_MODULE_LOADING=EAGER, which places everything when the
+ * library is loaded.
+ *   cfg: degree 1..3, subgrid_mode 0 (pixel sub-cells), precision 0 (FP64;
+ *        anything else is SWDG_EINVAL), g, eps_vel, cfl and stream are used
+ *        (stream NULL: the legacy stream);
  *   n_cells <= SWDG_NOALLOC_MAX_CELLS, else SWDG_EINVAL;
  *   hxhy [n][2], nbr [n][4][2] (conforming faces only),
  *   tiles [n][P][P] depth pixels of each cell (P <= 32, dtype SWDG_PIX_*),
@@ -406,10 +413,13 @@ int swdg_autotune(swdg_ctx* ctx, int repeats, double* report);
  *   residual [6][n][(r+1)^2] (F, Gx, Gy, R, Lx, Ly) and dt_out [1] (may be
  *   NULL): device outputs;  err (may be NULL): message on failure.
  * The first call on a device looks up the scratch array's address for that
- * device, so make it before any stream capture.  Every call shares the one
- * scratch array (it is re-initialised at each call); calls that overlap on
- * the GPU (other streams, other threads) race on it.  Synchronises the
- * stream before returning. */
+ * device and keeps it for the life of the process; after cudaDeviceReset()
+ * on that device the kept address is stale, so do not call this entry point
+ * on a device again after resetting it.  Every call shares the one scratch
+ * array (it is re-initialised at each call); calls that overlap on the GPU
+ * (other streams, other threads) race on it.  Each call reads a status word
+ * back and synchronises the stream before returning, so no call may be made
+ * inside stream capture. */
 #define SWDG_NOALLOC_MAX_CELLS 1048576
 int swdg_residual_noalloc(const swdg_config* cfg, int64_t n_cells, const double* hxhy,
                           const int32_t* nbr, const void* tiles, int pixels_per_side, int pix_dtype,

@@ -2555,8 +2555,9 @@ int swdg_autotune(swdg_ctx* ctx, int repeats, double* report) {
 // ---------------------------------------------------------------------------
 // allocation-free residual: its only scratch is this file-scope array (step
 // scalars in the first 256 bytes, then the pixel-overlap table, then one
-// constant-field mask byte per cell), reserved on every GPU that loads the
-// library
+// constant-field mask byte per cell), held on every GPU where the library's
+// device code is loaded (lazily, at the first call, unless the process loads
+// modules eagerly)
 // ---------------------------------------------------------------------------
 constexpr size_t NOALLOC_OV_BYTES = ((sizeof(OvTab) + 255) / 256) * 256;
 static __device__ __align__(256) unsigned char
@@ -2611,10 +2612,11 @@ extern "C" int swdg_residual_noalloc(const swdg_config* cfg, int64_t n, const do
                                      const double* bc_amp, const double* bc_period,
                                      const double* bc_phase, const double* state, double t,
                                      double* residual, double* dt_out, char* err, int err_len) {
-    if (!cfg || cfg->degree < 1 || cfg->degree > 3 || cfg->subgrid_mode != 0 || !(cfg->g > 0) ||
-        !(cfg->eps_vel > 0) || !(cfg->cfl > 0))
+    if (!cfg || cfg->degree < 1 || cfg->degree > 3 || cfg->subgrid_mode != 0 ||
+        cfg->precision != 0 || !(cfg->g > 0) || !(cfg->eps_vel > 0) || !(cfg->cfl > 0))
         return noalloc_fail(err, err_len, SWDG_EINVAL,
-                            "residual_noalloc: degree 1..3, subgrid_mode 0, g, eps_vel, cfl > 0");
+                            "residual_noalloc: degree 1..3, subgrid_mode 0, precision 0 (FP64), "
+                            "g, eps_vel, cfl > 0");
     if (n < 1 || n > SWDG_NOALLOC_MAX_CELLS)
         return noalloc_fail(err, err_len, SWDG_EINVAL,
                             "residual_noalloc: n_cells must be in 1..SWDG_NOALLOC_MAX_CELLS "

@@ -1,12 +1,16 @@
-"""The allocation-free residual (swdg_residual_noalloc) against the context
-residual (swdg_residual + swdg_cfl_dt), through the C-ABI, on two calls in a
-row.  It is for callers that cannot allocate device memory, so it takes every
-buffer from the caller and keeps its scratch in a fixed array of the library.
+"""The allocation-free residual (swdg_residual_noalloc) against the FP64
+oracle and against the context residual (swdg_residual + swdg_cfl_dt),
+through the C-ABI, on two calls in a row.  It is for callers that cannot
+allocate device memory (a memory pool that forbids new allocations, a device
+whose memory is already reserved), so it takes every buffer from the caller
+and keeps its scratch in a fixed array of the library; the free device
+memory is checked to stay unchanged across a call.
 """
 import numpy as np
 import pytest
 
-from helpers import rel_inf
+from helpers import residual_errors
+from oracle.oracle import Oracle
 from paper_2505_18743_gb300 import swdg
 from paper_2505_18743_gb300 import workloads as W
 
@@ -41,19 +45,33 @@ def run_case(wl, states, t):
     d_dt = torch.empty(1, dtype=torch.float64, device=dev)
     cfg = swdg.swdg_config(wl.degree, 0, 0, wl.tableau, wl.g, wl.eps_vel, wl.h_lim, wl.eps0,
                            wl.cfl, 20, 1e-12, torch.cuda.current_stream(dev).cuda_stream)
-    for st in states:  # two calls in a row share the library's scratch
+    ora = Oracle.from_workload(wl)
+    d_states = [torch.tensor(np.stack(st), dtype=torch.float64, device=dev).contiguous()
+                for st in states]
+    torch.cuda.synchronize(dev)
+    for call, (st, d_state) in enumerate(zip(states, d_states)):
+        # two calls in a row share the library's scratch
         ctx.set_state(*st)
         ref = ctx.residual(t)
         dt_ref = ctx.cfl_dt(t)
-        d_state = torch.tensor(np.stack(st), dtype=torch.float64, device=dev).contiguous()
+        ora.set_state(*st)
+        ro = ora.residual(t)
+        dt_ora = ora.cfl_dt(t)
+        torch.cuda.synchronize(dev)
+        free0, _ = torch.cuda.mem_get_info(dev)
         swdg.residual_noalloc(cfg, n, d_hxhy, d_nbr, d_tiles, P, pix, d_man, d_state, t, d_res,
                               d_dt, bc=wl.boundaries)
         torch.cuda.synchronize(dev)
-        got = d_res.cpu().numpy()
-        scale = max(float(np.abs(v).max()) for v in ref.values())
-        for i, k in enumerate(("F", "Gx", "Gy", "R", "Lx", "Ly")):
-            assert rel_inf(got[i], ref[k], floor=1e-3 * scale) <= TOL, k
-        assert abs(float(d_dt.item()) - dt_ref) <= 1e-13 * dt_ref
+        free1, _ = torch.cuda.mem_get_info(dev)
+        if call > 0:  # the first call may still load the library's device code
+            assert free1 == free0, (free0, free1)
+        got = dict(zip(("F", "Gx", "Gy", "R", "Lx", "Ly"), d_res.cpu().numpy()))
+        err_ora = residual_errors(got, ro)
+        assert max(err_ora.values()) <= TOL, err_ora
+        err_ctx = residual_errors(got, ref)
+        assert max(err_ctx.values()) <= TOL, err_ctx
+        dt = float(d_dt.item())
+        assert abs(dt - dt_ora) <= 1e-13 * dt_ora and abs(dt - dt_ref) <= 1e-13 * dt_ref
     ctx.close()
 
 
@@ -85,3 +103,9 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                               one, one)
     assert e.value.code == swdg.SWDG_EINVAL
     assert "1048576" in str(e.value)
+    # only the FP64 residual exists without a context: FP32-bulk is refused
+    cfg32 = swdg.swdg_config(1, 1, 0, 0, 9.81, 0.01, 0.01, 1e-6, 0.1, 20, 1e-12, None)
+    with pytest.raises(swdg.SwdgError) as e:
+        swdg.residual_noalloc(cfg32, 1, one, one, one, 8, swdg.SWDG_PIX_F64, one, one, 0.0,
+                              one, one)
+    assert e.value.code == swdg.SWDG_EINVAL and "precision" in str(e.value)
