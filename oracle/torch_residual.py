@@ -30,9 +30,9 @@ Definitions (each evaluated directly, no sum factorisation):
 Derivative conventions at the kinks (the reading the adjoint takes):
   * max(x, 0) inside V has derivative [x > 0] (Eq. mask's strict inequality);
   * the min of the reconstruction follows its first argument at ties (the
-    side's own operator); the max of the wave speeds follows the side with
-    the lower cell index (the forward evaluates each face once, in that
-    order);
+    side's own operator); the max of the wave speeds takes the mean of both
+    sides' derivatives at an exact tie (the symmetric subgradient, which does
+    not depend on the numbering of the cells);
   * |x| and sqrt(x) have derivative 0 at x = 0;
   * the constant-field rule (a field with equal nodal values is evaluated as
     that constant) is a rounding device: the polynomial is differentiated.
@@ -97,8 +97,11 @@ def _min_first(a, b):
     return torch.where(a <= b, a, b)
 
 
-def _max_first(a, b):
-    return torch.where(a >= b, a, b)
+
+def _max_sym(a, b):
+    """max(a, b) whose derivative at an exact tie is the mean of both sides'
+    (the symmetric element of the subdifferential); the value is unchanged"""
+    return torch.where(a > b, a, torch.where(a < b, b, 0.5 * (a + b)))
 
 
 class TorchResidual:
@@ -371,11 +374,9 @@ class TorchResidual:
         fm, fp = self.vel(hm), self.vel(hp)
         umx, umy, upx, upy = fm * qxm, fm * qym, fp * qxp, fp * qyp
         unm, unp = umx * nx + umy * ny, upx * nx + upy * ny
-        # wave speed bound: at a tie the side with the lower cell index decides
-        # (the face is evaluated once, lower index first)
-        lm_, lp_ = torch.abs(unm) + _sqrt0(g * hm), torch.abs(unp) + _sqrt0(g * hp)
-        own_low = (~self.has_nb | (iK < iN))[:, None]
-        lam = torch.where(own_low, _max_first(lm_, lp_), _max_first(lp_, lm_))
+        # wave speed bound: at an exact tie the derivative is the mean of both
+        # sides' (independent of which cell of the face is which)
+        lam = _max_sym(torch.abs(unm) + _sqrt0(g * hm), torch.abs(unp) + _sqrt0(g * hp))
         qsmx, qsmy, qspx, qspy = hsm * umx, hsm * umy, hsp * upx, hsp * upy
         fF = 0.5 * ((qsmx + qspx) * nx + (qsmy + qspy) * ny) + 0.5 * lam * (hsm - hsp)
         pres = g * 0.5 * (hsm + hsp) * 0.5 * (hsm - hsp)

@@ -15,8 +15,10 @@
 // derivative A = dV/d(eta) = dV/d(delta).
 //
 // Derivative conventions at the kinks: max(x, 0) -> [x > 0] (Eq. mask); the
-// reconstruction's min and the wave-speed max follow their first argument at
-// ties, the first argument being the side whose residual is differentiated;
+// reconstruction's min follows its first argument at ties, the first argument
+// being the side whose residual is differentiated; the wave-speed max takes
+// the symmetric subgradient (half of each side's derivative) at exact ties,
+// so the derivative does not depend on the order of the face's two cells;
 // |x| and sqrt(x) have derivative 0 at 0; a constant field is differentiated
 // as its polynomial.
 #pragma once
@@ -59,6 +61,10 @@ __device__ __forceinline__ D1 fabs(D1 a) {
     return D1(::fabs(a.v), a.v > 0.0 ? a.d : (a.v < 0.0 ? -a.d : 0.0));
 }
 __device__ __forceinline__ D1 fmax(D1 a, D1 b) { return a.v >= b.v ? a : b; }
+// the wave-speed bound: the symmetric subgradient at an exact tie
+__device__ __forceinline__ D1 wave_speed_max(D1 a, D1 b) {
+    return a.v > b.v ? a : (a.v < b.v ? b : D1(a.v, 0.5 * (a.d + b.d)));
+}
 __device__ __forceinline__ D1 fmin(D1 a, D1 b) { return a.v <= b.v ? a : b; }
 
 // value and W directional derivatives (all directions in one evaluation)
@@ -163,6 +169,15 @@ __device__ __forceinline__ DN<W> fabs(const DN<W>& a) {
 }
 template <int W>
 __device__ __forceinline__ DN<W> fmax(const DN<W>& a, const DN<W>& b) { return a.v >= b.v ? a : b; }
+template <int W>
+__device__ __forceinline__ DN<W> wave_speed_max(const DN<W>& a, const DN<W>& b) {
+    if (a.v != b.v) return a.v > b.v ? a : b;
+    DN<W> m;
+    m.v = a.v;
+#pragma unroll
+    for (int i = 0; i < W; ++i) m.d[i] = 0.5 * (a.d[i] + b.d[i]);
+    return m;
+}
 template <int W>
 __device__ __forceinline__ DN<W> fmin(const DN<W>& a, const DN<W>& b) { return a.v <= b.v ? a : b; }
 

@@ -287,6 +287,14 @@ __device__ __forceinline__ void face_trace(const double* u, size_t fstride, unsi
     }
 }
 
+// The wave-speed bound's maximum (Eq. lxf_parameter).  For plain arithmetic
+// types it is fmax; the adjoint's dual types overload it (found by
+// argument-dependent lookup) with the symmetric subgradient at exact ties.
+template <typename T>
+__device__ __forceinline__ T wave_speed_max(T a, T b) {
+    return fmax(a, b);
+}
+
 // Rusanov flux with hydrostatic reconstruction at one face point, seen from
 // side A with outward normal (nx, ny) (Eqs. lxf_parameter, velocity,
 // hydro_rec_vars, mass_rhs, discharge_rhs, r_concentration).  hA = V_A(zeta_A),
@@ -302,7 +310,7 @@ __device__ __forceinline__ void rusanov(T qxA, T qyA, T cA, T hA, T hsA, T qxB, 
     T fA = vel_factor<T>(hA, eps), fB = vel_factor<T>(hB, eps);
     T uAx = fA * qxA, uAy = fA * qyA, uBx = fB * qxB, uBy = fB * qyB;
     T unA = uAx * nx + uAy * ny, unB = uBx * nx + uBy * ny;
-    T l = fmax(fabs(unA) + sqrt(g * hA), fabs(unB) + sqrt(g * hB));
+    T l = wave_speed_max(fabs(unA) + sqrt(g * hA), fabs(unB) + sqrt(g * hB));
     T qsAx = hsA * uAx, qsAy = hsA * uAy, qsBx = hsB * uBx, qsBy = hsB * uBy;
     out[0] = half * ((qsAx + qsBx) * nx + (qsAy + qsBy) * ny) + half * l * dhAB;
     out[1] = half * (qsAx * unA + qsBx * unB) + half * l * (qsAx - qsBx);

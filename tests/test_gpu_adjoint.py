@@ -76,3 +76,13 @@ def test_residual_vjp_with_dry_cells_and_friction():
     wl.qx = 0.01 * np.cos(4 * Yn) + 0.0 * Xn
     wl.manning = np.full(wl.mesh.n, 0.03)
     compare(wl, t=0.0, check_delta=False)  # flat floor away from the bump
+
+
+def test_residual_vjp_at_exact_wave_speed_ties():
+    """the checkerboard case (exact wave-speed ties with discharge jumps at
+    every interior face): the symmetric subgradient of the oracle, under two
+    numberings of the cells"""
+    wl = A.checkerboard_ties()
+    compare(wl, t=0.0, check_delta=False)  # flat bottom: one-sided offset derivative
+    perm = np.random.default_rng(13).permutation(wl.mesh.n)
+    compare(A.renumbered_workload(wl, perm), t=0.0, check_delta=False)

@@ -165,3 +165,55 @@ def test_vjp_is_finite_with_dry_cells_and_a_lake_at_rest():
     # a fully dry cell (every pixel above the surface): no momentum sensitivity
     rv = residual_value(tr, [z, zero, zero, np.ones_like(z)], np.full(n, 0.03), np.zeros(n))
     assert np.abs(rv["F"]).max() < 1e-12
+
+
+def renumbered(mesh, perm):
+    """the mesh with old cell perm[i] as new cell i"""
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    nbr = mesh.nbr[perm].copy()
+    nbr = np.where(nbr >= 0, inv[np.maximum(nbr, 0)], nbr).astype(np.int32)
+    return W.Mesh(mesh.x0y0[perm].copy(), mesh.hxhy[perm].copy(), nbr)
+
+
+def checkerboard_ties():
+    """On a flat bottom, a continuous elevation with discharges whose sign
+    flips from cell to cell (a checkerboard: the flows meet or part at every
+    face) gives both sides of every interior face point the same wave-speed
+    bound |u.n| + sqrt(g h) while the discharge jumps, so the maximum ties
+    exactly where its derivative matters."""
+    mesh, ras = W.flat_periodic(6, 5, 600.0, 500.0, 4.0, 1, pix=2, periodic=(False, False))
+    X, Y = W.nodal_coordinates(mesh, 1)
+    ij = np.rint((mesh.x0y0[:, 0] / 100.0) + (mesh.x0y0[:, 1] / 100.0)).astype(int)
+    sgn = np.where(ij % 2 == 0, 1.0, -1.0)[:, None]
+    zeta = 0.2 * np.sin(X / 170.0) * np.cos(Y / 130.0)
+    qx = sgn * (0.3 + 0.2 * np.cos(Y / 90.0))
+    qy = sgn * 0.1 * np.sin(X / 110.0)
+    c = 0.5 + 0.3 * np.sin((X + Y) / 200.0)
+    man = np.random.default_rng(11).uniform(0.01, 0.04, mesh.n)
+    return W.Workload("checkerboard-ties", 1, mesh, ras, zeta, qx, qy, c, manning=man)
+
+
+def renumbered_workload(wl, perm):
+    m2 = renumbered(wl.mesh, perm)
+    return W.Workload(wl.name + "-renumbered", wl.degree, m2, wl.raster,
+                      *[a[perm] for a in wl.state()], manning=wl.manning[perm])
+
+
+def test_vjp_at_wave_speed_ties_does_not_depend_on_cell_numbering():
+    """At the exact ties of the checkerboard case the wave-speed maximum's
+    derivative is the symmetric subgradient, which a renumbering of the
+    cells (the same discrete operator) leaves unchanged; a rule that let the
+    lower cell index decide would move derivative from one cell of the face
+    to the other."""
+    wl = checkerboard_ties()
+    rng = np.random.default_rng(12)
+    n, nd = wl.mesh.n, wl.zeta.shape[1]
+    cot = [rng.standard_normal((n, nd)) for _ in range(6)]
+    base = residual_vjp(torch_res(wl), wl.state(), wl.manning, np.zeros(n), cot)
+    perm = rng.permutation(n)
+    w2 = renumbered_workload(wl, perm)
+    got = residual_vjp(torch_res(w2), w2.state(), w2.manning, np.zeros(n), [a[perm] for a in cot])
+    for b, g in zip(base, got):
+        scale = max(float(np.abs(b).max()), 1e-30)
+        assert np.abs(g - b[perm]).max() <= 1e-13 * scale
