@@ -89,7 +89,9 @@ def test_noalloc_residual_matches_context_closed_basin():
 def test_noalloc_residual_matches_context_tidal_beach_crop():
     wl = W.tidal_beach(window=(0, 120, 12, 10))
     Xn, Yn = W.nodal_coordinates(wl.mesh, 3)
-    s0 = (0.3 * np.sin(Xn / 400.0), 0.2 * np.cos(Yn / 200.0), np.zeros_like(Xn), wl.c)
+    # every field varies in x and y, so each residual field carries signal
+    s0 = (0.3 * np.sin(Xn / 400.0) * np.cos(Yn / 300.0), 0.2 * np.cos(Yn / 200.0),
+          0.1 * np.sin(Xn / 250.0), wl.c)
     run_case(wl, [s0, perturbed(s0, 2)], 1500.0)
 
 
