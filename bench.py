@@ -13,8 +13,9 @@ working set is about 0.5 GB), so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl swdg|reference]
 
-N > 1 runs one independent replica per GPU (the path has no exchange on one
-box; see the design notes) and reports the whole-job rate ("weak" scaling).
+N > 1 runs one independent replica per GPU and reports the whole-job rate
+("weak" scaling): the path would shard by spatial domain with a face-trace
+halo per stage, but each call here holds one GPU, so no exchange is built.
 The reference arm (--impl reference) is the CPU oracle timed on the host's
 cores on a bounded crop of the same workload.
 """
@@ -74,11 +75,26 @@ DRAM_BYTES_PER_LAUNCH = {"step_begin": 58935808, "faces_1": 154463744, "faces_2"
                          "faces_3": 155003648, "residual_1": 170799616, "residual_2": 173084416,
                          "residual_3": 172475392, "stage_2": 152635648, "stage_3": 244360192,
                          "final": 251701504}
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (recipe); the FMA probe measured 1.19-1.26
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2.07 GHz x 2 DFMA/clk x 2), if no probe
+
+
+def measured_pipe_peaks():
+    """the FP64 and FP32 FMA-chain peaks of this GPU, measured now by the
+    library's probe (swdg_probe_fma): {dtype: (TFLOP/s, ms)}"""
+    from paper_2505_18743_gb300 import swdg
+    out = {}
+    for name, code in (("fp64", swdg.SWDG_PIX_F64), ("fp32", swdg.SWDG_PIX_F32)):
+        try:
+            out[name] = swdg.probe_fma(code)
+        except swdg.SwdgError:
+            pass
+    return out
 
 
 def algorithmic_bytes_per_cell(kernel, r=3, P=16, pix_bytes=4, nres=3):
-    """Bytes one launch must move per cell (model of the design notes):
+    """Algorithmic bytes one launch must move per cell (each input read once,
+each output written once; intermediates that a fused path would keep on
+chip -- the face slots -- are left out):
     residual: own state 4 nd f64 in, 6 nd f64 out, the pixel tile, geometry;
     stage update: v^n in, H/C~ in, nres residual sets of 6 nd in, state out."""
     nd = (r + 1) ** 2
@@ -395,6 +411,34 @@ def adjoint_variant(args, stream, dev, world, nsteps=200, every=20, ngauges=50):
     return out
 
 
+def long_run_variant(args, stream, dev, world, chunks=10, chunk=100):
+    """The tidal beach's whole 1000-step run (from its initial state at
+    t = 0), timed in chunks of 100 steps with CUDA events: the per-step cost
+    over the run, and the water-mass balance and wet-dry state at its end."""
+    import torch
+    from paper_2505_18743_gb300 import swdg
+    wl = W.tidal_beach()
+    ctx = swdg.Context.from_workload(wl, stream=stream.cuda_stream)
+    d0 = ctx.diagnostics()
+    t = 0.0
+    per = []
+    for _ in range(chunks):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        s0.record(stream)
+        t = ctx.step(chunk, -1.0, t)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        per.append(max_over_ranks(s0.elapsed_time(s1), world) / chunk)
+    d1 = ctx.diagnostics()
+    ctx.close()
+    return {"workload": WORKLOAD + f", steps 1..{chunks * chunk} from t = 0",
+            "ms_per_step_by_chunk_of_100": [round(x, 4) for x in per],
+            "spread": (max(per) - min(per)) / min(per), "t_end_s": t,
+            "r_cells_start_end": [d0["r_cells"], d1["r_cells"]],
+            "positivity_violations": d1["positivity_violations"]}
+
+
 def amr_variant(args, stream, dev, world, cycles=4, every=5):
     """Dynamic h-adaptation on the lagoon (256 x 128 coarse cells of
     195 x 234 m, two refinement levels, r = 2, 8192 x 4096 f32 raster, tide
@@ -494,10 +538,19 @@ def run_gpu(args, rank, world, local):
     bpc = sum(algorithmic_bytes_per_cell(k, nres=nres.get(k, STAGES)) for k in slots) / len(slots)
     hbm_ach = bpc * wl.mesh.n / (avg_ms / 1e3) / 1e9
     traffic = [(DRAM_BYTES_PER_LAUNCH if prec == 0 else {}).get(k) for k in slots]
-    roof = {"bound": "alu", "kernel": dom_fn, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+    pipe = measured_pipe_peaks()
+    if "fp64" in pipe:
+        fp64_peak = pipe["fp64"][0]
+        peak_src = ("FP64 pipe, measured in this run by the FMA-chain probe (swdg_probe_fma), "
+                    "of measured")
+    else:
+        fp64_peak = FP64_PEAK_TFLOPS
+        peak_src = "FP64 pipe, nominal 152 SMs x 2.07 GHz x 4 flop/clk (probe unavailable)"
+    roof = {"bound": "alu", "kernel": dom_fn, "achieved": ach, "peak": fp64_peak,
+            "unit": "TFLOP/s", "frac": ach / fp64_peak,
             "traffic": (sum(traffic) / len(traffic)) if all(x is not None for x in traffic) else None,
-            "peak_source": "FP64 pipe, recipe nominal 1.25 TFLOP/s (probe 1.19-1.26)",
+            "peak_source": peak_src,
+            "pipe_peaks_measured_tflops": {k: round(v[0], 3) for k, v in pipe.items()},
             "flops_per_launch": flops, "avg_launch_ms": avg_ms, "share": share[dom_fn] / total,
             "hbm_view": {"achieved_gbs": hbm_ach, "peak_gbs": pk["hbm_gbs"],
                          "frac": hbm_ach / pk["hbm_gbs"], "peak_source": src},
@@ -538,9 +591,13 @@ def run_gpu(args, rank, world, local):
         e32.record(stream)
         torch.cuda.synchronize(dev)
         ms32 = max_over_ranks(s32.elapsed_time(e32), world)
-        # replay the FP64 context's extra profile/e2e steps so both reach the same step count
+        # replay the FP64 context's extra profile/e2e steps so both reach the same
+        # step count: the profiled steps (kernels launched one by one, timed each)
+        # and the rest as plain steps
+        kms32, t32 = ctx32.step_profile(nprof, -1.0, t32)
+        per32 = {SLOTS[i]: round(kms32[i] / nprof, 4) for i in range(len(SLOTS)) if kms32[i] > 0}
         extra = nprof + e2e_steps
-        t32 = ctx32.step(extra, -1.0, t32)
+        t32 = ctx32.step(e2e_steps, -1.0, t32)
         st32 = ctx32.get_state()
         errs = {}
         qscale = max(float(np.abs(ref_state[1]).max()), float(np.abs(ref_state[2]).max()), 1e-3)
@@ -552,6 +609,7 @@ def run_gpu(args, rank, world, local):
         variants["fp32_bulk"] = {
             "value": units * args.steps * world / (ms32 / 1e3), "unit": "updates/s",
             "ms_per_step": ms32 / args.steps, "dtype": "f64 elevation/sub-grid/solves, f32 bulk",
+            "per_launch_ms": per32,
             "max_rel_state_err_vs_fp64": errs,
             "steps_compared": args.warmup + args.steps + extra,
             "mass_rel_diff_vs_fp64": abs(d32["mass"] - d64["mass"]) / d64["mass"],
@@ -559,8 +617,8 @@ def run_gpu(args, rank, world, local):
         ctx32.close()
 
     if prec == 0:
-        for name, fn in (("ensemble", ensemble_variant), ("adjoint", adjoint_variant),
-                         ("amr", amr_variant)):
+        for name, fn in (("long_run", long_run_variant), ("ensemble", ensemble_variant),
+                         ("adjoint", adjoint_variant), ("amr", amr_variant)):
             if name in want:
                 variants[name] = fn(args, stream, dev, world)
 
@@ -601,7 +659,7 @@ def main():
     ap.add_argument("--impl", default="swdg", choices=["swdg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--variants", default="fp32_bulk,ensemble,adjoint,amr",
+    ap.add_argument("--variants", default="fp32_bulk,long_run,ensemble,adjoint,amr",
                     help="comma-separated variants to run after the headline line")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32bulk"],
                     help="arithmetic of the timed context (fp64 is the headline workload)")

@@ -385,6 +385,16 @@ int swdg_get_shapes(const swdg_ctx* ctx, int* out);
  * kind.  Requires a state; call it outside stream capture. */
 int swdg_autotune(swdg_ctx* ctx, int repeats, double* report);
 
+/* Measurement helper (the paper has no counterpart): the arithmetic peak of
+ * the current device for one precision, measured by independent FMA chains
+ * in registers (8 chains per thread, 256 threads per block, SMs x resident
+ * blocks; no memory traffic), best of three timed launches after one warm-up
+ * on the legacy stream.  dtype SWDG_PIX_F64 or SWDG_PIX_F32; tflops [1] and
+ * ms [1] (host, either may be NULL) receive 2 x FMAs / time and the launch
+ * time.  Allocates 8 bytes of device memory for the duration of the call.
+ * Returns SWDG_EINVAL for another dtype, SWDG_ECUDA on a CUDA error. */
+int swdg_probe_fma(int dtype, double* tflops, double* ms);
+
 /* Allocation-free residual (the paper has no counterpart; this exists for
  * callers that cannot allocate device memory -- for example code running
  * inside a memory pool that forbids new allocations, or a host that has

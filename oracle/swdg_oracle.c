@@ -7,7 +7,7 @@
  * physical coordinates, and every linear system is assembled densely and
  * solved by Gaussian elimination with partial pivoting.
  *
- * Readings of the paper taken here (each listed in the design notes):
+ * Readings of the paper taken where it is silent or ambiguous:
  *  - mode S: the point p of a tensor rule owns the sub-cell given by its
  *    cumulative weights; V_p(eta) = sum_k w_k max(eta + z_k, 0) and
  *    A_p(eta) = sum_k w_k [eta + z_k > 0] over the pixel area fractions w_k;

@@ -19,7 +19,10 @@ time step:
     tracer system (Eq. algebraic_concentration), then the residual of the
     stage at t + c_l dt;
   * the final combination with b, b~, the last stage entering with the
-    linearised friction it solved (the R8 reading of the design notes).
+    linearised friction it solved (the paper does not say which friction
+    term the last implicit stage contributes; this one reproduces the
+    stiffly accurate TR-BDF2 stage, whereas re-evaluating L at the last stage
+    state diverges for stiff friction).
 
 Differentiation: every discrete decision (degree flags, r_K = 0 fallbacks,
 Newton iterations) is taken without gradients, and each converged nonlinear

@@ -102,7 +102,7 @@ struct swdg_ctx {
            *llin = nullptr, *HN = nullptr, *CN = nullptr, *HNbar = nullptr, *CNbar = nullptr,
            *zpts = nullptr, *zmax = nullptr, *zmin = nullptr, *zabs = nullptr, *diag = nullptr;
     int32_t* nbr = nullptr;
-    uint8_t *cmask = nullptr, *flag = nullptr, *finfo = nullptr, *pcls = nullptr;
+    uint8_t *cmask = nullptr, *flag = nullptr, *wet0 = nullptr, *finfo = nullptr, *pcls = nullptr;
     int64_t* tile_off = nullptr;
     OvTab* ov = nullptr;
     double* zhang = nullptr;
@@ -722,7 +722,8 @@ int swdg_create(const swdg_config* cfg, swdg_ctx** out) {
 static void free_mesh(swdg_ctx* c) {
     cudaFree(c->x0y0); cudaFree(c->hxhy); cudaFree(c->ihxhy); cudaFree(c->manning); cudaFree(c->U); cudaFree(c->res);
     cudaFree(c->llin); cudaFree(c->HN); cudaFree(c->CN); cudaFree(c->HNbar); cudaFree(c->CNbar);
-    cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->diag); cudaFree(c->finfo);
+    cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->wet0); cudaFree(c->diag);
+    cudaFree(c->finfo);
     cudaFree(c->adj);
     c->adj = nullptr;
     cudaFree(c->gdev);
@@ -751,7 +752,7 @@ static void free_mesh(swdg_ctx* c) {
     c->x0y0 = c->hxhy = c->ihxhy = c->manning = c->U = c->res = c->llin = c->HN = c->CN = c->HNbar =
         c->CNbar = c->diag = nullptr;
     c->nbr = nullptr;
-    c->cmask = c->flag = c->finfo = nullptr;
+    c->cmask = c->flag = c->wet0 = c->finfo = nullptr;
 }
 static void free_bathy(swdg_ctx* c) {
     cudaFree(c->tiles); cudaFree(c->zpts); cudaFree(c->zmax); cudaFree(c->zmin); cudaFree(c->zabs);
@@ -878,6 +879,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     CK(cudaMalloc(&ctx->CNbar, n * sizeof(double)));
     CK(cudaMalloc(&ctx->cmask, (size_t)NBUF * n));
     CK(cudaMalloc(&ctx->flag, n));
+    CK(cudaMalloc(&ctx->wet0, n));
     CK(cudaMalloc(&ctx->diag, 4 * n * sizeof(double) + 8 * sizeof(double)));
     CK(cudaMemcpyAsync(ctx->x0y0, x0y0, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->hxhy, hxhy, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
@@ -890,6 +892,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     CK(cudaMemsetAsync(ctx->manning, 0, n * sizeof(double), ctx->st));
     CK(cudaMemsetAsync(ctx->llin, 0, 2 * n * nd * sizeof(double), ctx->st));
     CK(cudaMemsetAsync(ctx->flag, ctx->R, n, ctx->st));
+    CK(cudaMemsetAsync(ctx->wet0, 0, n, ctx->st));
     CK(cudaMemsetAsync(ctx->cmask, 0, (size_t)NBUF * n, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     ctx->x0y0_h.assign(x0y0, x0y0 + 2 * n);
@@ -942,6 +945,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     d.HNbar = ctx->HNbar;
     d.CNbar = ctx->CNbar;
     d.flag = ctx->flag;
+    d.wet0 = ctx->wet0;
     d.any_friction = 0;
     default_shapes(ctx);
     ctx->has_mesh = true;
@@ -2551,6 +2555,69 @@ int swdg_autotune(swdg_ctx* ctx, int repeats, double* report) {
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------------------
+// arithmetic peak probe: independent FMA chains in registers, no memory
+// traffic; the measured FP64 (or FP32) rate is the roofline of the kernels
+// that are bound by that pipe
+// ---------------------------------------------------------------------------
+template <typename T, int CH>
+__global__ void __launch_bounds__(256) k_fma_chains(T b, T c, int iters, T* sink) {
+    T a[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) a[j] = (T)(threadIdx.x + j);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < CH; ++j) a[j] = fma(a[j], b, c);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < CH; ++j) s += a[j];
+    if (s == T(-1.2345e-7)) *sink = s; // never true: keeps the chains alive
+}
+
+template <typename T>
+static int probe_fma_run(int iters, double* tflops, double* ms_out) {
+    constexpr int CH = 8, TPB = 256;
+    int dev = 0, nsm = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fma_chains<T, CH>, TPB, 0) !=
+            cudaSuccess ||
+        occ < 1)
+        return SWDG_ECUDA;
+    const int grid = nsm * occ;
+    T* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(T));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 0.0f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) { // the first launch warms up
+        cudaEventRecord(e0, 0);
+        k_fma_chains<T, CH><<<grid, TPB>>>((T)0.999999, (T)1e-3, iters, sink);
+        cudaEventRecord(e1, 0);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    if (e != cudaSuccess || !(best > 0.0f)) return SWDG_ECUDA;
+    const double flops = 2.0 * CH * (double)iters * grid * TPB;
+    if (tflops) *tflops = flops / (best * 1e-3) / 1e12;
+    if (ms_out) *ms_out = best;
+    return SWDG_OK;
+}
+
+extern "C" int swdg_probe_fma(int dtype, double* tflops, double* ms) {
+    if (dtype == SWDG_PIX_F64) return probe_fma_run<double>(4096, tflops, ms);
+    if (dtype == SWDG_PIX_F32) return probe_fma_run<float>(65536, tflops, ms);
+    return SWDG_EINVAL;
+}
 
 // ---------------------------------------------------------------------------
 // allocation-free residual: its only scratch is this file-scope array (step

@@ -121,6 +121,9 @@ struct Dev {
     double* HNbar;
     double* CNbar;
     uint8_t* flag;
+    // 1 where every mass point of the cell was fully wet at zeta^n (written by
+    // the step start with H(zeta^n); null: unknown)
+    uint8_t* wet0;
     Scalars* sc;
     Member* mb;            // member clocks [nmemb] (a single member: &sc->m0)
     const int32_t* memb;   // member of each cell (null: every cell in member 0)

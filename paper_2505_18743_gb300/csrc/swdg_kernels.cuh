@@ -979,13 +979,17 @@ __global__ void __launch_bounds__(32 * MAXWPB)
         // zeta and c at the mass points
         tens_interp<ND1, NM>(tb.Bm, su, tmp, pe, lane);
         tens_interp<ND1, NM>(tb.Bm, su + 3 * ND, tmp, pc, lane);
+        bool allfull = true;
         for (int p = lane; p < NMP; p += 32) {
             if (cm & 1u) pe[p] = su[0];
             if (cm & 8u) pc[p] = su[3 * ND];
             double V, A;
-            ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pe[p], V, A);
+            bool full;
+            ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pe[p], V, A, full);
             pV[p] = V;
+            allfull = allfull && full && A != 0.0;
         }
+        allfull = __all_sync(0xffffffffu, allfull);
         __syncwarp();
         double mu = INFINITY;
         for (int p = lane; p < NMP; p += 32) mu = fmin(mu, pV[p]);
@@ -1069,6 +1073,7 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             d.CNbar[k] = cb;
             d.flag[k] = (uint8_t)flag;
             d.cmask[k] = (uint8_t)cm;
+            if (d.wet0) d.wet0[k] = (uint8_t)(flag != 0 && allfull);
         }
         __syncwarp();
     }
@@ -1378,6 +1383,42 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
     return chol_solve<ND, TL>(M, b, inv, lane, tm);
 }
 
+// Tracer stage solve of the FP32-bulk path (Eq. algebraic_concentration,
+// H(zeta^(l)) C = b with the depth-weighted mass matrix H = B^T diag(cw) B):
+// C = c0 + delta, where c0 = sum_i b_i / sum_i s_i is the cell's mean
+// concentration (s = H 1, the row sums of H, i.e. H_i(zeta^(l)) of the
+// continuity equation, in FP64), delta = H^-1 (b - c0 s) is solved once in
+// FP32 (FP32 factor of mass_factor_rows_f), and a constant correction makes
+// sum_i (H C)_i = sum_i s_i C_i equal sum_i b_i in FP64, so the tracer mass
+// is kept to FP64 round-off and a constant tracer (b = c s) stays constant up
+// to the rounding of b - c0 s.  A failed FP32 factor falls back to the FP64
+// Cholesky.  b: right-hand side in, C out (FP64).  Scratch: Mf, Yf (float),
+// s (ND doubles), tmp (2 NM NM doubles), M, Y, inv (fallback).
+template <int ND1, int NM, int TL>
+__device__ void solve_tracer_bulk(const Tables& tb, const double* cw, double* b, float* Mf,
+                                  float* Yf, double* s, double* tmp, double* M, double* Y,
+                                  double* inv, int lane, unsigned tm) {
+    constexpr int ND = ND1 * ND1;
+    static_assert(ND <= TL, "one unknown per lane");
+    float rinv;
+    if (!mass_factor_rows_f<ND1, NM, TL>(tb, cw, Yf, Mf, rinv, lane, tm)) {
+        assemble_mass<ND1, NM, TL>(tb, cw, Y, M, lane, tm);
+        chol_solve<ND1 * ND1, TL>(M, b, inv, lane, tm);
+        return;
+    }
+    tens_test<ND1, NM, double, TL>(tb.Bm, cw, tmp, s, lane, tm); // s_i = (H 1)_i
+    const double bi = lane < ND ? b[lane] : 0.0, si = lane < ND ? s[lane] : 0.0;
+    const double sb = team_sum<TL>(bi, tm), ss = team_sum<TL>(si, tm);
+    const double c0 = ss > 0.0 ? sb / ss : 0.0;
+    const float v = chol_subst_rows_f<ND, TL>(Mf, rinv, (float)(bi - c0 * si), lane, tm);
+    const double xi = lane < ND ? c0 + (double)v : 0.0;
+    const double m = team_sum<TL>(si * xi, tm);
+    const double alpha = ss > 0.0 ? (sb - m) / ss : 0.0;
+    __syncwarp(tm);
+    if (lane < ND) b[lane] = xi + alpha;
+    __syncwarp(tm);
+}
+
 // Momentum stage solve of an r_K = r cell in arithmetic T (Eq. algebraic_discharge
 // with the friction-modified mass matrix of Eq. mass_matrix_discharge on the
 // (r+1)^2 Gauss-Legendre points, inverted as S^-1 D^-1 S^-T):
@@ -1550,13 +1591,21 @@ __global__ void __maxnreg__(96)
             for (int i = lane; i < ND; i += TL) z[i] = su[i];
             bool zc = (cm0 & 1u) != 0;
             bool prev_full = false;
+            // every mass point fully wet at zeta^n (known from the step start,
+            // which evaluated H(zeta^n) = HN from the same state by the same
+            // arithmetic): the first Newton step needs no evaluation, since
+            // H(zeta^n) - T = HN - T and M(zeta^n) is the constant mass matrix
+            const bool full0 = d.wet0 != nullptr && d.wet0[k] != 0 && d.newton_max > 0;
             __syncwarp(tm);
             // each pass evaluates V, A at the current iterate; the last pass is
             // the evaluation at the result (for the tracer matrix and the
             // completely-dry test)
             for (int kk = 0;; ++kk) {
-                tens_interp<ND1, NM, double, TL>(tb.Bm, z, tmp, pe, lane, tm);
                 int ndry = 0, npart = 0;
+                if (kk == 0 && full0) {
+                    for (int i = lane; i < ND; i += TL) o[i] = d.HN[k * ND + i] - T[i];
+                } else {
+                tens_interp<ND1, NM, double, TL>(tb.Bm, z, tmp, pe, lane, tm);
                 for (int p = lane; p < NMP; p += TL) {
                     if (zc) pe[p] = z[0];
                     double V, A;
@@ -1579,6 +1628,7 @@ __global__ void __maxnreg__(96)
                 __syncwarp(tm);
                 tens_test<ND1, NM, double, TL>(tb.Bm, pV, tmp, o, lane, tm); // H_i(zeta_k)
                 for (int i = lane; i < ND; i += TL) o[i] -= T[i];
+                }
                 __syncwarp(tm);
                 if (npart == 0) {
                     // M is the constant mass matrix, inverted by its tensor factors
@@ -1719,8 +1769,12 @@ __global__ void __maxnreg__(96)
                 o[3 * ND + i] = rc[i];
             }
             __syncwarp(tm);
-            solve_mass_mixed<ND1, NM, TL>(tb, pV, o + 3 * ND, Mf, Yf, xs, rs, qs, tmp, M,
-                                          Y, pinv, lane, tm);
+            if constexpr (sizeof(B) == sizeof(float))
+                solve_tracer_bulk<ND1, NM, TL>(tb, pV, o + 3 * ND, Mf, Yf, xs, tmp, M, Y, pinv,
+                                               lane, tm);
+            else
+                solve_mass_mixed<ND1, NM, TL>(tb, pV, o + 3 * ND, Mf, Yf, xs, rs, qs, tmp, M,
+                                              Y, pinv, lane, tm);
         }
         __syncwarp(tm);
         // write v^(l) and its constant-field mask

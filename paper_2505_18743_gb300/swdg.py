@@ -108,6 +108,7 @@ SIGNATURES = {
     "swdg_set_shape": (_I, [_P, _I, _I, _I]),
     "swdg_get_shapes": (_I, [_P, _P]),
     "swdg_autotune": (_I, [_P, _I, _P]),
+    "swdg_probe_fma": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "swdg_last_error": (ctypes.c_char_p, [_P]),
     "swdg_destroy": (None, [_P]),
 }
@@ -182,6 +183,16 @@ def forest_adapt(forest, lij, flags):
         if nout.value <= cap:
             raise SwdgError(rc, "swdg_forest_adapt failed")
         cap = nout.value
+
+
+def probe_fma(dtype):
+    """Measured FMA-chain peak of the current device for SWDG_PIX_F64 or
+    SWDG_PIX_F32: (TFLOP/s, ms of the best launch)."""
+    tf, ms = _D(0.0), _D(0.0)
+    rc = load().swdg_probe_fma(dtype, ctypes.byref(tf), ctypes.byref(ms))
+    if rc:
+        raise SwdgError(rc, "swdg_probe_fma failed")
+    return tf.value, ms.value
 
 
 def forest_mesh(forest, lij):

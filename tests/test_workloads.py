@@ -1,4 +1,5 @@
-"""The synthetic inputs follow the recipe the design notes state: the tidal
+"""The synthetic inputs follow their stated recipe (the generators'
+docstrings in workloads.py): the tidal
 beach's depth profile, its |k|^-1 fractal noise of rms 1.5 m, eight channels
 3-5 pixels wide and 3 m deeper across the beach, the boundary, friction and
 tracer data, seeded and reproducible.  CPU only."""
