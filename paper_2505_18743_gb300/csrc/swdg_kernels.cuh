@@ -927,10 +927,17 @@ __device__ int scalar_newton(const Dev& d, const Tables& tb, int64_t k, double J
     constexpr int ND = Sz<R>::ND;
     double H, A;
     mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, H, A, tm);
-    if (A == 0.0) e = -d.zmax[k] + d.eps0;
+    // the first iteration reuses this evaluation unless the start moves to the
+    // dry start of Eq. initial_guess
+    bool have = true;
+    if (A == 0.0) {
+        e = -d.zmax[k] + d.eps0;
+        have = false;
+    }
     int it = 0;
     for (int kk = 0; kk < d.newton_max; ++kk) {
-        mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, H, A, tm);
+        if (!have) mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, H, A, tm);
+        have = false;
         if (A == 0.0) break;
         const double dd = (H - target) / A;
         e -= dd;
