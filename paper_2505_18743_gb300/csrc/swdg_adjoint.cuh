@@ -38,9 +38,12 @@ __device__ __forceinline__ D1 operator+(D1 a, D1 b) { return D1(a.v + b.v, a.d +
 __device__ __forceinline__ D1 operator-(D1 a, D1 b) { return D1(a.v - b.v, a.d - b.d); }
 __device__ __forceinline__ D1 operator-(D1 a) { return D1(-a.v, -a.d); }
 __device__ __forceinline__ D1 operator*(D1 a, D1 b) { return D1(a.v * b.v, a.d * b.v + a.v * b.d); }
+// a / b through one reciprocal of b (the value is a.v (1/b.v), within an ulp
+// of the forward's quotient; only derivatives are taken from dual values)
 __device__ __forceinline__ D1 operator/(D1 a, D1 b) {
-    const double q = a.v / b.v;
-    return D1(q, (a.d - q * b.d) / b.v);
+    const double ib = 1.0 / b.v;
+    const double q = a.v * ib;
+    return D1(q, (a.d - q * b.d) * ib);
 }
 __device__ __forceinline__ D1& operator+=(D1& a, D1 b) { return a = a + b; }
 __device__ __forceinline__ D1& operator*=(D1& a, D1 b) { return a = a * b; }
@@ -125,11 +128,12 @@ __device__ __forceinline__ DN<W> operator*(const DN<W>& a, const DN<W>& b) {
     for (int i = 0; i < W; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
     return r;
 }
+// a / b through one reciprocal of b, as for D1
 template <int W>
 __device__ __forceinline__ DN<W> operator/(const DN<W>& a, const DN<W>& b) {
     DN<W> r;
-    r.v = a.v / b.v;
     const double ib = 1.0 / b.v;
+    r.v = a.v * ib;
 #pragma unroll
     for (int i = 0; i < W; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
     return r;
@@ -171,11 +175,12 @@ template <int W>
 __device__ __forceinline__ DN<W> fmax(const DN<W>& a, const DN<W>& b) { return a.v >= b.v ? a : b; }
 template <int W>
 __device__ __forceinline__ DN<W> wave_speed_max(const DN<W>& a, const DN<W>& b) {
-    if (a.v != b.v) return a.v > b.v ? a : b;
+    // selects only (no branch over the whole value): a, b, or at a tie the mean
+    const bool gt = a.v > b.v, lt = a.v < b.v;
     DN<W> m;
-    m.v = a.v;
+    m.v = gt ? a.v : b.v;
 #pragma unroll
-    for (int i = 0; i < W; ++i) m.d[i] = 0.5 * (a.d[i] + b.d[i]);
+    for (int i = 0; i < W; ++i) m.d[i] = gt ? a.d[i] : (lt ? b.d[i] : 0.5 * (a.d[i] + b.d[i]));
     return m;
 }
 template <int W>
@@ -207,8 +212,10 @@ __device__ __forceinline__ void side_flux(T qxA, T qyA, T cA, T hA, T hsA, T qxB
     out[2] = out[2] - pres * T(ny);
 }
 
+// register cap: 176 keeps 11 warps resident per SM at r <= 2 (no spills at
+// r = 2); r = 3 carries all six directions per lane and keeps more
 template <int R, typename Pix, int MODE>
-__global__ void __launch_bounds__(32 * MAXWPB)
+__global__ void __maxnreg__(R == 3 ? 232 : 176)
     k_residual_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
                    const double* __restrict__ u, const uint8_t* __restrict__ cmask,
                    const double* __restrict__ rbar, double* __restrict__ ubar,
@@ -274,12 +281,16 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             tc[i] = s;
         }
         __syncwarp();
-        // volume points: one per lane.  When the points fit in half a warp the
-        // two halves take the same point, each with half of the 8 input
-        // directions (lane + 16 hands its four to lane), so the dual
-        // arithmetic runs on all 32 lanes
+        // volume points: one per lane.  Of the 8 input directions of a point
+        // (z, z_xi, z_eta, qx, qy, c, delta, n) the dual numbers carry the first
+        // six: z and delta enter only through h = V(z + delta), so their
+        // derivatives are equal, and n only through gamma, which is
+        // proportional to n^2 (d gamma / dn = 2 gamma / n).  When the points
+        // fit in half a warp the two halves take the same point, each with
+        // three of the six directions (lane + 16 hands its three to lane), so
+        // the dual arithmetic runs on all 32 lanes
         constexpr bool VSPLIT = NVP <= 16;
-        constexpr int VW = VSPLIT ? 4 : 8;         // directions per lane
+        constexpr int VW = VSPLIT ? 3 : 6;         // directions per lane
         const int vb0 = VSPLIT ? (lane >> 4) * VW : 0; // first direction of this lane
         constexpr int VSTEP = VSPLIT ? 16 : 32;
         double dsum = 0.0, nsum = 0.0;
@@ -326,8 +337,8 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                                    cb[4][0], cb[5][0]};                        // Lx, Ly
             double xb[8];
             {
-                // input directions: 0 z, 1 z_xi, 2 z_eta, 3 qx, 4 qy, 5 c, 6 delta, 7 n
-                // (this lane: vb0 .. vb0 + VW - 1)
+                // dual directions: 0 z, 1 z_xi, 2 z_eta, 3 qx, 4 qy, 5 c
+                // (this lane: vb0 .. vb0 + VW - 1); 6 delta = 0 and 7 n follow
                 using DV = ad::DN<VW>;
                 const DV zx = DV::seed(zxd, 1 - vb0) * DV(ihx);
                 const DV zy = DV::seed(zyd, 2 - vb0) * DV(ihy);
@@ -335,8 +346,7 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                 const DV vc = DV::seed(c, 5 - vb0);
                 DV h(V);
                 h.set(0 - vb0, A);
-                h.set(6 - vb0, A);
-                const DV nn = DV::seed(man, 7 - vb0);
+                const DV nn(man);
                 const DV fv = vel_factor<DV>(h, DV(eps));
                 const DV ux = fv * vqx, uy = fv * vqy;
                 const DV gam = gamma_manning<DV>(nn, h, vqx, vqy, DV(g), DV(eps));
@@ -357,6 +367,10 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                     for (int dir = 0; dir < VW; ++dir)
                         xb[VW + dir] = __shfl_down_sync(0xffffffffu, xb[dir], 16);
                 }
+                xb[6] = xb[0]; // delta: as z, through h = V(z + delta)
+                // n: X_10 = -w gamma qx, X_11 = -w gamma qy with gamma ~ n^2
+                const double dgdn = man != 0.0 ? 2.0 * gam.v / man : 0.0;
+                xb[7] = -(Xb[10] * w * dgdn * qx + Xb[11] * w * dgdn * qy);
             }
             // tracer numerical diffusion (Eq. numdiff): X_2 -= w nu h c_xi / hx^2,
             // X_3 -= w nu h c_eta / hy^2 (linear in grad c; h = V(z + delta))
@@ -550,74 +564,50 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             }
         }
         __syncwarp();
-        // transposed interpolation of the volume-point cotangents: y, then x
-        // zeta: q = 0 holds the (Bv, Bv) z and (Bv, Dv) z_eta parts, q = 1 the
-        // (Dv, Bv) z_xi part, both after the y-contraction
-        for (int i = lane; i < 2 * NV * ND1; i += 32) {
-            const int q = i / (NV * ND1), r_ = i % (NV * ND1), al = r_ / ND1, b = r_ % ND1;
-            double s = 0.0;
-            if (q == 0) {
+        // transposed interpolation of the volume-point cotangents, every field
+        // in one uniform pass per direction.  y: segments of NV ND1 jobs --
+        // 0 zeta (Bv z + Dv z_eta), 1 zeta (Bv z_xi), 2 qx, 3 qy (Bv), 4 c
+        // (Bv c + Dv c_eta), 5 c (Bv c_xi); the diffusion rows c_xi, c_eta are
+        // zero without diffusion.  x: per field, Bv on the first segment plus
+        // Dv on the second (zeta: 0, 1; c: 4, 5; qx, qy: none).  The
+        // cotangent x-contractions tc are consumed by now and hold ty.
+        {
+            constexpr int NY = NV * ND1;
+            double* ty = tc; // [6][NV][ND1]
+            const int nseg = nu != 0.0 ? 6 : 5;
+            for (int i = lane; i < nseg * NY; i += 32) {
+                const int seg = i / NY, r_ = i % NY, al = r_ / ND1, b = r_ % ND1;
+                const int src1 = seg == 0 ? 0 : seg == 1 ? 1 : seg == 5 ? 6 : seg + 1;
+                const double* x1 = xv + src1 * NVP + al;
+                const double* x2 = xv + (seg == 0 ? 2 : 7) * NVP + al;
+                const double m2 = (seg == 0 || seg == 4) ? 1.0 : 0.0;
+                double s_ = 0.0;
 #pragma unroll
                 for (int be = 0; be < NV; ++be)
-                    s += tb.Bv[be][b] * xv[0 * NVP + al + NV * be] +
-                         tb.Dv[be][b] * xv[2 * NVP + al + NV * be];
-            } else {
-#pragma unroll
-                for (int be = 0; be < NV; ++be) s += tb.Bv[be][b] * xv[1 * NVP + al + NV * be];
-            }
-            tt[i] = s;
-        }
-        __syncwarp();
-        constexpr int NC = (ND + 31) / 32; // nodes per lane
-        double ub[4 * NC];
-        for (int i = lane, c_ = 0; i < ND; i += 32, ++c_) {
-            const int a = i % ND1, b = i / ND1;
-            double s = 0.0;
-#pragma unroll
-            for (int al = 0; al < NV; ++al)
-                s += tb.Bv[al][a] * tt[(0 * NV + al) * ND1 + b] +
-                     tb.Dv[al][a] * tt[(1 * NV + al) * ND1 + b];
-            ub[c_] = s;
-        }
-        __syncwarp();
-        // qx, qy, c: (Bv, Bv) transposes; c also (Dv, Bv) c_xi and (Bv, Dv) c_eta
-        for (int fl = 0; fl < 3; ++fl) {
-            const bool grad = fl == 2 && nu != 0.0;
-            for (int i = lane; i < NV * ND1; i += 32) {
-                const int al = i / ND1, b = i % ND1;
-                double s = 0.0, s1 = 0.0;
-#pragma unroll
-                for (int be = 0; be < NV; ++be) {
-                    s += tb.Bv[be][b] * xv[(3 + fl) * NVP + al + NV * be];
-                    if (grad)
-                        s += tb.Dv[be][b] * xv[7 * NVP + al + NV * be],
-                            s1 += tb.Bv[be][b] * xv[6 * NVP + al + NV * be];
-                }
-                tt[i] = s;
-                tt[NV * ND1 + i] = s1;
+                    s_ += tb.Bv[be][b] * x1[NV * be] + m2 * (tb.Dv[be][b] * x2[NV * be]);
+                ty[i] = s_;
             }
             __syncwarp();
-            for (int i = lane, c_ = 0; i < ND; i += 32, ++c_) {
-                const int a = i % ND1, b = i / ND1;
-                double s = 0.0;
+            double* uacc = xv; // [4][ND]: the point cotangents are consumed by now
+            for (int i = lane; i < 4 * ND; i += 32) {
+                const int fl = i / ND, j = i % ND, a = j % ND1, b = j / ND1;
+                // (without diffusion the c_xi segment is not formed: t2 = t1, times 0)
+                const int sa = fl == 0 ? 0 : fl + 1, sb = fl == 0 ? 1 : (nu != 0.0 ? 5 : sa);
+                const double m2 = (fl == 0 || (fl == 3 && nu != 0.0)) ? 1.0 : 0.0;
+                const double* t1 = ty + sa * NY + b;
+                const double* t2 = ty + sb * NY + b;
+                double s_ = 0.0;
 #pragma unroll
                 for (int al = 0; al < NV; ++al)
-                    s += tb.Bv[al][a] * tt[al * ND1 + b] + tb.Dv[al][a] * tt[NV * ND1 + al * ND1 + b];
-                ub[(1 + fl) * NC + c_] = s;
+                    s_ += tb.Bv[al][a] * t1[al * ND1] + m2 * (tb.Dv[al][a] * t2[al * ND1]);
+                uacc[i] = s_;
             }
-            __syncwarp();
         }
         // lift the face-point cotangents onto the face nodes, then write.  The
-        // node values go to shared memory (the point cotangents xv are consumed
-        // by now) and the faces are added in two uniform passes, the x faces
-        // (node columns a = 0, ND1 - 1) and then the y faces (rows b = 0,
-        // ND1 - 1), one item per field, face and node along it, as in the
-        // forward residual
-        double* uacc = xv; // [4][ND]
-        for (int i = lane, c_ = 0; i < ND; i += 32, ++c_) {
-#pragma unroll
-            for (int cf = 0; cf < 4; ++cf) uacc[cf * ND + i] = ub[cf * NC + c_];
-        }
+        // faces are added in two uniform passes, the x faces (node columns
+        // a = 0, ND1 - 1) and then the y faces (rows b = 0, ND1 - 1), one item
+        // per field, face and node along it, as in the forward residual
+        double* uacc = xv;
         __syncwarp();
 #pragma unroll
         for (int pass = 0; pass < 2; ++pass) {
