@@ -201,13 +201,13 @@ constexpr int vjp_smem() {
 
 // the face fluxes of one face point seen from side A (outward normal n_A):
 // {F, Gx, Gy, R} of side A's residual including its pressure term
-template <typename T>
+template <typename T, bool DC = false>
 __device__ __forceinline__ void side_flux(T qxA, T qyA, T cA, T hA, T hsA, T qxB, T qyB, T cB,
                                           T hB, T hsB, double nx, double ny, double g, double eps,
-                                          T out[4]) {
+                                          T out[4], T* dc = nullptr) {
     T pres, lam;
-    rusanov<T>(qxA, qyA, cA, hA, hsA, qxB, qyB, cB, hB, hsB, hsA - hsB, T(nx), T(ny), T(g), T(eps),
-               out, pres, lam);
+    rusanov<T, DC>(qxA, qyA, cA, hA, hsA, qxB, qyB, cB, hB, hsB, hsA - hsB, T(nx), T(ny), T(g),
+                   T(eps), out, pres, lam, dc);
     out[1] = out[1] - pres * T(nx);
     out[2] = out[2] - pres * T(ny);
 }
@@ -407,10 +407,14 @@ __global__ void __maxnreg__(R == 3 ? 232 : 176)
         auto npts = [&](unsigned inf) { return (((inf & 3) == FI_COARSE) ? 2 : 1) * NM; };
         const int b1 = npts(fi[0]), b2 = b1 + npts(fi[1]), b3 = b2 + npts(fi[2]),
                   b4 = b3 + npts(fi[3]);
-        // as for the volume points: with at most 16 face points per conforming
-        // cell the two halves share a point, directions 0-2 and 3-4
+        // the own side's directions at a face point: zeta, qx, qy and delta
+        // are carried by dual numbers; the tracer flux is linear in the
+        // concentrations, so the c direction is its partial derivative dc
+        // (from the same flux evaluation).  As for the volume points: with at
+        // most 16 face points per conforming cell the two halves share a
+        // point, directions 0-1 and 2-3
         constexpr bool FSPLIT = 4 * NM <= 16;
-        constexpr int FW = FSPLIT ? 3 : 5;
+        constexpr int FW = FSPLIT ? 2 : 4;
         const int fb0 = FSPLIT ? (lane >> 4) * FW : 0;
         constexpr int FSTEP = FSPLIT ? 16 : 32;
         for (int it0 = 0; it0 < b4; it0 += FSTEP) {
@@ -442,7 +446,7 @@ __global__ void __maxnreg__(R == 3 ? 232 : 176)
             const int32_t s0 = d.nbr[k * 8 + f * 2];
             double hm, Am;
             own_VA(tm[0], hm, Am);
-            double xb[5], xl[FW];
+            double xb[5], xl[FW], xc = 0.0; // xc: the c direction
             if (s0 >= 0) {
                 const int64_t nb = coarse ? (int64_t)(h ? d.nbr[k * 8 + f * 2 + 1] : s0) : (int64_t)s0;
                 const int fo = f ^ 1;
@@ -463,16 +467,16 @@ __global__ void __maxnreg__(R == 3 ? 232 : 176)
                 nb_VA(tm[0], Vnm, Anm);
                 own_VA(tp[0], Vop, Aop);
                 {
-                    // directions of the own side: 0 zeta, 1 qx, 2 qy, 3 c, 4 delta
+                    // dual directions of the own side: 0 zeta, 1 qx, 2 qy, 3 delta
                     // (this lane: fb0 .. fb0 + FW - 1)
                     using DF = ad::DN<FW>;
                     const DF qxm = DF::seed(tm[1], 1 - fb0), qym = DF::seed(tm[2], 2 - fb0);
-                    const DF cmv = DF::seed(tm[3], 3 - fb0);
+                    const DF cmv(tm[3]);
                     DF hmD(hm), vnmD(Vnm), vopD(Vop);
                     hmD.set(0 - fb0, Am);   // own operator at own zeta
-                    hmD.set(4 - fb0, Am);
+                    hmD.set(3 - fb0, Am);
                     vnmD.set(0 - fb0, Anm); // neighbour's operator at own zeta
-                    vopD.set(4 - fb0, Aop); // own operator at neighbour's zeta
+                    vopD.set(3 - fb0, Aop); // own operator at neighbour's zeta
                     const DF hpD(hp);
                     const DF hsm = ad::fmin(hmD, vnmD), hsp = ad::fmin(hpD, vopD);
                     const DF qxp(tp[1]), qyp(tp[2]), cpv(tp[3]);
@@ -488,9 +492,9 @@ __global__ void __maxnreg__(R == 3 ? 232 : 176)
                     const DF bc = own_low ? cpv : cmv, bh = own_low ? hpD : hmD;
                     const DF bhs = own_low ? hsp : hsm;
                     const double nAx = own_low ? nx : -nx, nAy = own_low ? ny : -ny;
-                    DF raw[4], pres, lam;
-                    rusanov<DF>(aqx, aqy, ac, ah, ahs, bqx, bqy, bc, bh, bhs, ahs - bhs, DF(nAx), DF(nAy),
-                                DF(g), DF(eps), raw, pres, lam);
+                    DF raw[4], pres, lam, dcs[2];
+                    rusanov<DF, true>(aqx, aqy, ac, ah, ahs, bqx, bqy, bc, bh, bhs, ahs - bhs,
+                                      DF(nAx), DF(nAy), DF(g), DF(eps), raw, pres, lam, dcs);
                     const DF pnx = pres * DF(nAx), pny = pres * DF(nAy);
                     const DF so(own_low ? 1.0 : -1.0), sn(own_low ? -1.0 : 1.0);
                     DF oo[4], on[4]; // own side's flux, the neighbour's (its own normal)
@@ -509,6 +513,9 @@ __global__ void __maxnreg__(R == 3 ? 232 : 176)
                         for (int cf = 0; cf < 4; ++cf) s_ += ym[cf] * oo[cf].d[dir] + yp[cf] * on[cf].d[dir];
                         xl[dir] = s_;
                     }
+                    // c of the own side: only the tracer flux, R_own = so raw3,
+                    // R_nb = sn raw3
+                    xc = (ym[3] * so.v + yp[3] * sn.v) * (own_low ? dcs[0].v : dcs[1].v);
                 }
             } else {
                 const int tag = -1 - s0;
@@ -526,21 +533,22 @@ __global__ void __maxnreg__(R == 3 ? 232 : 176)
                 {
                     using DF = ad::DN<FW>;
                     const DF qxm = DF::seed(tm[1], 1 - fb0), qym = DF::seed(tm[2], 2 - fb0);
-                    const DF cmv = DF::seed(tm[3], 3 - fb0);
+                    const DF cmv(tm[3]);
                     DF hmD(hm);
                     hmD.set(0 - fb0, Am);
-                    hmD.set(4 - fb0, Am);
+                    hmD.set(3 - fb0, Am);
                     DF qxp = qxm, qyp = qym, hpD = hmD;
                     if (tide) {
                         hpD = DF(Vt); // ghost elevation fixed, same operator
-                        hpD.set(4 - fb0, At);
+                        hpD.set(3 - fb0, At);
                     } else {
                         const DF qn = qxm * DF(nx) + qym * DF(ny);
                         qxp = qxm - DF(2.0) * qn * DF(nx);
                         qyp = qym - DF(2.0) * qn * DF(ny);
                     }
-                    DF oo[4];
-                    side_flux<DF>(qxm, qym, cmv, hmD, hmD, qxp, qyp, cmv, hpD, hpD, nx, ny, g, eps, oo);
+                    DF oo[4], dcs[2];
+                    side_flux<DF, true>(qxm, qym, cmv, hmD, hmD, qxp, qyp, cmv, hpD, hpD, nx, ny, g,
+                                        eps, oo, dcs);
 #pragma unroll
                     for (int dir = 0; dir < FW; ++dir) {
                         double s_ = 0.0;
@@ -548,15 +556,24 @@ __global__ void __maxnreg__(R == 3 ? 232 : 176)
                         for (int cf = 0; cf < 4; ++cf) s_ += ym[cf] * oo[cf].d[dir];
                         xl[dir] = s_;
                     }
+                    // the ghost carries the own concentration: both partials
+                    xc = ym[3] * (dcs[0].v + dcs[1].v);
                 }
             }
             // all lanes (the branches have joined): gather the five directions
-#pragma unroll
-            for (int dir = 0; dir < FW; ++dir) xb[dir] = xl[dir];
+            // xb = {zeta, qx, qy, c, delta}
             if constexpr (FSPLIT) {
-                xb[3] = __shfl_down_sync(0xffffffffu, xl[0], 16);
+                xb[0] = xl[0];
+                xb[1] = xl[1];
+                xb[2] = __shfl_down_sync(0xffffffffu, xl[0], 16);
                 xb[4] = __shfl_down_sync(0xffffffffu, xl[1], 16);
+            } else {
+                xb[0] = xl[0];
+                xb[1] = xl[1];
+                xb[2] = xl[2];
+                xb[4] = xl[3];
             }
+            xb[3] = xc;
             if (iv && (!FSPLIT || lane < 16)) {
 #pragma unroll
                 for (int cf = 0; cf < 4; ++cf) xf[((cf * 4 + f) * 2 + h) * NM + al] = xb[cf];

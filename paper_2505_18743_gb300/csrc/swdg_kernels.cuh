@@ -300,10 +300,12 @@ __device__ __forceinline__ T wave_speed_max(T a, T b) {
 // hydro_rec_vars, mass_rhs, discharge_rhs, r_concentration).  hA = V_A(zeta_A),
 // hsA = min(V_A(zeta_A), V_B(zeta_A)).  out = {F, Gx_cons, Gy_cons, R}; the
 // non-conservative pressure scalar g {{h*}} (h*A - h*B)/2 is returned apart.
-template <typename T>
+// DC (the adjoint): dc = {dR/dcA, dR/dcB}, the tracer flux's partial
+// derivatives in the two concentrations (it is linear in each).
+template <typename T, bool DC = false>
 __device__ __forceinline__ void rusanov(T qxA, T qyA, T cA, T hA, T hsA, T qxB, T qyB, T cB, T hB,
                                         T hsB, T dhAB, T nx, T ny, T g, T eps, T out[4], T& pres,
-                                        T& lam) {
+                                        T& lam, T* dc = nullptr) {
     // dhAB = h*A - h*B, formed in FP64 by the caller (the well-balanced part of
     // the reconstruction); the tracer jump h*A cA - h*B cB = dhAB cA + h*B (cA - cB)
     const T half = T(0.5);
@@ -319,6 +321,11 @@ __device__ __forceinline__ void rusanov(T qxA, T qyA, T cA, T hA, T hsA, T qxB, 
              half * l * (dhAB * cA + hsB * (cA - cB));
     pres = g * half * (hsA + hsB) * half * dhAB;
     lam = l;
+    if constexpr (DC) {
+        // R = 1/2 (qs_A cA + qs_B cB).n + l/2 (h*A cA - h*B cB)
+        dc[0] = half * (qsAx * nx + qsAy * ny) + half * l * hsA;
+        dc[1] = half * (qsBx * nx + qsBy * ny) - half * l * hsB;
+    }
 }
 
 __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double v) {
