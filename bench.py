@@ -257,6 +257,138 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def member_oracle_leg(wls, runs, nsteps, max_cells):
+    """CPU-baseline leg of an ensemble variant: the oracle (as it stands, on
+    the host cores) runs each member with at most ``max_cells`` cells from its
+    initial state for ``nsteps`` CFL steps, once; ``runs`` maps a name to
+    (member states, member times) of ensembles that took the same steps.
+    Returns the oracle's rate and, per run, each member's error against it
+    (elevation and tracer against max(|oracle|, 1), discharge against the
+    oracle's max |q|, the relative difference of the member's time; None for
+    members not run) and the worst of them."""
+    from oracle.oracle import Oracle
+    errs = {k: [] for k in runs}
+    cells, t0 = 0, time.perf_counter()
+    for m, wl in enumerate(wls):
+        if wl.mesh.n > max_cells:
+            for k in runs:
+                errs[k].append(None)
+            continue
+        o = Oracle.from_workload(wl)
+        to = o.step(nsteps, -1.0, 0.0)
+        so = o.get_state()
+        cells += wl.mesh.n
+        qs = max(float(np.abs(so[1]).max()), float(np.abs(so[2]).max()), 1e-3)
+        for k, (states, times) in runs.items():
+            st = states[m]
+            errs[k].append({
+                "zeta": float(np.abs(st[0] - so[0]).max()) / max(float(np.abs(so[0]).max()), 1.0),
+                "q": max(float(np.abs(st[i] - so[i]).max()) for i in (1, 2)) / qs,
+                "c": float(np.abs(st[3] - so[3]).max()),
+                "t_rel": abs(times[m] - to) / to})
+    el = time.perf_counter() - t0
+    nd = (wls[0].degree + 1) ** 2
+    done = sum(1 for e in next(iter(errs.values())) if e is not None)
+    leg = {"value": cells * 4 * nd * STAGES * nsteps / el, "unit": "updates/s",
+           "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+           "sample": f"{done} members with <= {max_cells} cells, {nsteps} CFL steps each, "
+                     f"{el:.1f} s"}
+    out = {}
+    for k, e in errs.items():
+        ok = [x for x in e if x is not None]
+        out[f"per_member_oracle_err_{k}"] = [
+            None if x is None else {a: float(f"{b:.3g}") for a, b in x.items()} for x in e]
+        out[f"max_member_oracle_err_{k}"] = (
+            {a: max(x[a] for x in ok) for a in ("zeta", "q", "c", "t_rel")} if ok else {})
+    return leg, out
+
+
+def fresh_ensemble_states(wls, stream, nsteps, precision):
+    """member states and times of a fresh ensemble after nsteps CFL steps"""
+    from paper_2505_18743_gb300 import swdg
+    e = swdg.Ensemble.from_workloads(wls, stream=stream.cuda_stream, precision=precision)
+    e.step(nsteps)
+    tm, _ = e.times()
+    st = [e.member_state(m) for m in range(len(wls))]
+    e.close()
+    return st, list(tm)
+
+
+def timed_ms(fn, stream, dev, world):
+    import torch
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    s0.record(stream)
+    fn()
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    return max_over_ranks(s0.elapsed_time(s1), world)
+
+
+def ensemble_small_variant(args, stream, dev, world, members=64, n=32):
+    """Many small members, where one launch over all of them should matter:
+    64 tidal beaches of 32 x 32 cells each (the ensemble recipe with every
+    mesh 32^2: 65 536 cells in all), r = 2, 8 x 8 px per cell, per-member tide
+    and Manning n.  FP32-bulk and FP64 ensembles (one CUDA graph per step)
+    against the same members as 64 sequential FP64 contexts; the graph's step
+    time against the sum of its kernels' times (what a single persistent
+    kernel could at most save); and, as the CPU-baseline leg, every member's
+    error against the oracle after the same steps."""
+    from paper_2505_18743_gb300 import swdg
+    wls = W.beach_ensemble(members=members, sizes=(n,))
+    nd = (wls[0].degree + 1) ** 2
+    cells = sum(w.mesh.n for w in wls)
+    units = cells * 4 * nd * STAGES
+    steps = max(5, min(args.steps, 20))
+    out = {"workload": f"{members} tidal beaches of {n}x{n} cells ({cells} cells), r=2, 8x8 "
+                       "px/cell, RK32-IMEX, per-member tide and Manning n", "steps": steps}
+    ens = swdg.Ensemble.from_workloads(wls, stream=stream.cuda_stream, precision=1)
+    ens.autotune(repeats=1)
+    for _ in range(args.warmup):
+        ens.step(1)
+    ms = timed_ms(lambda: ens.step(steps), stream, dev, world)
+    kms, _ = ens.step_profile(steps)
+    ksum = sum(kms) / steps
+    out["fp32_bulk_ensemble"] = {"value": units * steps * world / (ms / 1e3), "unit": "updates/s",
+                                 "ms_per_step": ms / steps,
+                                 "kernel_ms_per_step_sum": ksum,
+                                 "launches_per_step": 3 * STAGES + 1}
+    ens64 = swdg.Ensemble.from_workloads(wls, stream=stream.cuda_stream)
+    ens64.autotune(repeats=1)
+    for _ in range(args.warmup):
+        ens64.step(1)
+    ms64 = timed_ms(lambda: ens64.step(steps), stream, dev, world)
+    out["fp64_ensemble"] = {"value": units * steps * world / (ms64 / 1e3), "unit": "updates/s",
+                            "ms_per_step": ms64 / steps}
+    seq = [swdg.Context.from_workload(w, stream=stream.cuda_stream) for w in wls]
+    ts = [0.0] * len(seq)
+    for i, c in enumerate(seq):
+        for _ in range(args.warmup):
+            ts[i] = c.step(1, -1.0, ts[i])
+
+    def run_seq():
+        for i, c in enumerate(seq):
+            ts[i] = c.step(steps, -1.0, ts[i])
+
+    mss = timed_ms(run_seq, stream, dev, world)
+    out["fp64_sequential_baseline"] = {"value": units * steps * world / (mss / 1e3),
+                                       "unit": "updates/s", "ms_per_step": mss / steps}
+    out["speedup_fp64_ensemble_vs_sequential"] = mss / ms64
+    out["speedup_fp32_bulk_ensemble_vs_sequential_fp64"] = mss / ms
+    for c in seq:
+        c.close()
+    if not args.no_cpu_baseline:
+        k = 8
+        runs = {"fp64": fresh_ensemble_states(wls, stream, k, 0),
+                "fp32_bulk": fresh_ensemble_states(wls, stream, k, 1)}
+        leg, errs = member_oracle_leg(wls, runs, k, n * n)
+        out["cpu_baseline"] = leg
+        out.update(errs)
+    ens.close()
+    ens64.close()
+    return out
+
+
 def ensemble_variant(args, stream, dev, world, members=64):
     """A 64-member parameter sweep of tidal beaches (mesh N x N with N drawn
     from 32, 64, 128, 256; r = 2; 8 x 8 px per cell; tide amplitude and
@@ -328,6 +460,13 @@ def ensemble_variant(args, stream, dev, world, members=64):
         worst["c"] = max(worst["c"], float(np.abs(a[3] - b[3]).max()))
     out["max_rel_member_err_fp32_bulk_vs_fp64"] = worst
     out["steps_compared"] = args.warmup + steps
+    if not args.no_cpu_baseline:
+        # CPU-baseline leg: the oracle on the members of 32^2 and 64^2 cells
+        k = 8
+        leg, errs = member_oracle_leg(wls, {"fp32_bulk": fresh_ensemble_states(wls, stream, k, 1)},
+                                      k, 64 * 64)
+        out["cpu_baseline"] = leg
+        out.update(errs)
     for c in seq:
         c.close()
     ens.close()
@@ -618,6 +757,7 @@ def run_gpu(args, rank, world, local):
 
     if prec == 0:
         for name, fn in (("long_run", long_run_variant), ("ensemble", ensemble_variant),
+                         ("ensemble_small", ensemble_small_variant),
                          ("adjoint", adjoint_variant), ("amr", amr_variant)):
             if name in want:
                 variants[name] = fn(args, stream, dev, world)
@@ -659,7 +799,7 @@ def main():
     ap.add_argument("--impl", default="swdg", choices=["swdg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--variants", default="fp32_bulk,long_run,ensemble,adjoint,amr",
+    ap.add_argument("--variants", default="fp32_bulk,long_run,ensemble,ensemble_small,adjoint,amr",
                     help="comma-separated variants to run after the headline line")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32bulk"],
                     help="arithmetic of the timed context (fp64 is the headline workload)")
