@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace swdg {
 
 constexpr int MXP = 6;    // max quadrature points per direction (GL 5 for r = 3)
@@ -210,6 +212,23 @@ __device__ __forceinline__ double get_dt(const Dev& d, int m) {
     return d.sc->fixed_dt >= 0.0 ? d.sc->fixed_dt : d.cfl / __longlong_as_double(d.mb[m].rmax);
 }
 
+// x^(-1/3) of a positive double: an FP32 reciprocal-cube-root seed refined by
+// two Newton-Raphson steps for z^-3 = x in FP64, z <- z + z (1 - x z^3) / 3
+// (quadratic convergence, no division: ~1e-7 -> ~1e-14 -> rounding).  Values
+// outside the FP32 seed's comfortable range take 1 / cbrt(x).
+__device__ __forceinline__ double inv_cbrt(double x) {
+    const float xf = (float)x;
+    if (!(xf > 1e-30f && xf < 1e30f)) return 1.0 / cbrt(x);
+    double z = (double)rcbrtf(xf);
+    constexpr double third = 1.0 / 3.0;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double e = fma(-x, z * z * z, 1.0);
+        z = fma(z * third, e, z);
+    }
+    return z;
+}
+
 // desingularised velocity factor u = f q, Eq. velocity (T = double or float)
 template <typename T>
 __device__ __forceinline__ T vel_factor(T h, T eps) {
@@ -227,7 +246,13 @@ __device__ __forceinline__ T gamma_manning(T n, T h, T qx, T qy, T g, T eps) {
         T h4 = (h * h) * (h * h), e4 = (eps * eps) * (eps * eps);
         hdes = sqrt(e4 + h4) / (sqrt(T(2)) * h);
     }
-    return g * n * n * sqrt(qx * qx + qy * qy) / (hdes * hdes * cbrt(hdes));
+    if constexpr (std::is_same<T, double>::value) {
+        // h_des^(-7/3) = z^7 with z = h_des^(-1/3): no division, no cbrt
+        const double z = inv_cbrt(hdes), z3 = z * z * z;
+        return g * n * n * sqrt(qx * qx + qy * qy) * (z3 * z3 * z);
+    } else {
+        return g * n * n * sqrt(qx * qx + qy * qy) / (hdes * hdes * cbrt(hdes));
+    }
 }
 
 // the velocity factor and the Manning coefficient of one point together: on
@@ -239,7 +264,10 @@ __device__ __forceinline__ void vel_gamma(T n, T h, T qx, T qy, T g, T eps, T& f
     if (h >= eps && h > T(0)) {
         const T rh = T(1) / h;
         fv = rh;
-        gam = (n == T(0)) ? T(0) : g * n * n * sqrt(qx * qx + qy * qy) * (rh * rh) * cbrt(rh);
+        T c3; // h^(-1/3)
+        if constexpr (std::is_same<T, double>::value) c3 = inv_cbrt(h);
+        else c3 = cbrt(rh);
+        gam = (n == T(0)) ? T(0) : g * n * n * sqrt(qx * qx + qy * qy) * (rh * rh) * c3;
     } else {
         fv = vel_factor<T>(h, eps);
         gam = gamma_manning<T>(n, h, qx, qy, g, eps);
