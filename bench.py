@@ -58,23 +58,43 @@ def units_per_step(wl):
     return wl.mesh.n * 4 * nd * STAGES
 
 
-# FP64 flops one launch performs per cell on this workload: active-lane
-# 2 DFMA + DMUL + DADD counted by ncu (profiles/fp64_ops_tidal_beach_256x256_r3.md;
-# faces_l: k_faces of stage l, residual_l: k_residual).  These kernels are
-# bound by the FP64 pipe: GB300's FP64 rate is the roofline.
-FLOPS_PER_CELL = {"step_begin": 2187, "faces_1": 1683, "faces_2": 1850, "faces_3": 1851,
-                  "residual_1": 8685, "residual_2": 9230, "residual_3": 9230, "stage_2": 8257,
-                  "stage_3": 9049, "final": 6747}
-# the FP32-bulk kernels' FP64 flops (their FP32 work runs on the 60x faster FP32 pipe)
-FLOPS_PER_CELL_FP32BULK = {"step_begin": 2187, "faces_1": 230, "faces_2": 400, "faces_3": 400,
-                           "residual_1": 3299, "residual_2": 3843, "residual_3": 3843,
-                           "stage_2": 4965, "stage_3": 5223, "final": 5001}
-# DRAM bytes per launch from an ncu capture of the current kernels (FP64
-# path); {} (traffic null) whenever the kernels changed after the capture
-DRAM_BYTES_PER_LAUNCH = {"step_begin": 58935808, "faces_1": 154463744, "faces_2": 154456832,
-                         "faces_3": 155003648, "residual_1": 170799616, "residual_2": 173084416,
-                         "residual_3": 172475392, "stage_2": 152635648, "stage_3": 244360192,
-                         "final": 251701504}
+COUNTERS = os.path.join(ROOT, "profiles", "counters_tidal_beach_256x256_r3.txt")
+
+
+def kernel_sources_hash():
+    """sha256 (first 16 hex digits) over the CUDA sources, name and bytes of
+    each file of the package's csrc/ in name order"""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2505_18743_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        h.update(b"\0")
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_counters(path=COUNTERS):
+    """the ncu counters of one step's launches (profiles/counters_...txt):
+    ({precision: {slot: (fp64 flops per cell, fp32 flops per cell, DRAM bytes
+    per launch)}}, whether they were taken on the current kernel sources).
+    The kernels here are bound by the FP64 pipe, so the FP64 flops per cell
+    give the roofline's achieved rate."""
+    table, sha = {}, None
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if not parts or parts[0].startswith("#"):
+                continue
+            if parts[0] == "sources_sha256_16":
+                sha = parts[1]
+                continue
+            prec, slot, f64, f32, dram = parts[:5]
+            table.setdefault(prec, {})[slot] = (float(f64), float(f32), float(dram))
+    return table, sha == kernel_sources_hash()
+
+
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2.07 GHz x 2 DFMA/clk x 2), if no probe
 
 
@@ -669,14 +689,16 @@ def run_gpu(args, rank, world, local):
     dom_fn = max(share, key=share.get)
     slots = [k for k in per_launch if fn_of(k) == dom_fn]
     avg_ms = sum(per_launch[k] for k in slots) / len(slots)
-    table = FLOPS_PER_CELL if prec == 0 else FLOPS_PER_CELL_FP32BULK
-    flops = sum(table[k] for k in slots) / len(slots) * wl.mesh.n
+    counters, fresh = load_counters()
+    table = counters["fp64" if prec == 0 else "fp32bulk"]
+    flops = sum(table[k][0] for k in slots) / len(slots) * wl.mesh.n
     ach = flops / (avg_ms / 1e3) / 1e12
     pk, src = peaks()
     nres = {"stage_2": 1, "stage_3": 2, "stage_4": 3, "final": STAGES}
     bpc = sum(algorithmic_bytes_per_cell(k, nres=nres.get(k, STAGES)) for k in slots) / len(slots)
     hbm_ach = bpc * wl.mesh.n / (avg_ms / 1e3) / 1e9
-    traffic = [(DRAM_BYTES_PER_LAUNCH if prec == 0 else {}).get(k) for k in slots]
+    # DRAM bytes per launch from the ncu capture, only while it matches the kernels
+    traffic = [table[k][2] if fresh else None for k in slots]
     pipe = measured_pipe_peaks()
     if "fp64" in pipe:
         fp64_peak = pipe["fp64"][0]
@@ -690,6 +712,8 @@ def run_gpu(args, rank, world, local):
             "traffic": (sum(traffic) / len(traffic)) if all(x is not None for x in traffic) else None,
             "peak_source": peak_src,
             "pipe_peaks_measured_tflops": {k: round(v[0], 3) for k, v in pipe.items()},
+            "counters": "profiles/counters_tidal_beach_256x256_r3.txt" + ("" if fresh else
+                                                                         " (stale: kernels changed)"),
             "flops_per_launch": flops, "avg_launch_ms": avg_ms, "share": share[dom_fn] / total,
             "hbm_view": {"achieved_gbs": hbm_ach, "peak_gbs": pk["hbm_gbs"],
                          "frac": hbm_ach / pk["hbm_gbs"], "peak_source": src},

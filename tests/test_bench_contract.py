@@ -127,3 +127,19 @@ def test_max_over_ranks_takes_the_slowest_of_two_gloo_ranks():
             p.join(timeout=300)
             assert p.exitcode == 0
         assert dict(out) == {0: 15.0, 1: 15.0}
+
+
+def test_counters_profile_covers_every_launch_slot():
+    """bench.py takes its roofline flops and DRAM traffic from the committed
+    ncu summary: every launch slot of a step, both precisions, with the
+    hash of the kernel sources it was taken on"""
+    import bench
+    table, _ = bench.load_counters()
+    slots = {"step_begin", "faces_1", "faces_2", "faces_3", "residual_1", "residual_2",
+             "residual_3", "stage_2", "stage_3", "final"}
+    for prec in ("fp64", "fp32bulk"):
+        assert set(table[prec]) == slots
+        for f64, f32, dram in table[prec].values():
+            assert f64 > 0 and dram > 0
+    h = bench.kernel_sources_hash()
+    assert len(h) == 16 and h == bench.kernel_sources_hash()
