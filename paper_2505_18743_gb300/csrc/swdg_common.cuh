@@ -195,6 +195,28 @@ __device__ __forceinline__ bool finite_bits(double v) {
     constexpr long long EXP = 0x7ff0000000000000ll;
     return (__double_as_longlong(v) & EXP) != EXP;
 }
+// v == 0.0 (either sign) on the bit pattern
+__device__ __forceinline__ bool zero_bits(double v) {
+    return (__double_as_longlong(v) << 1) == 0;
+}
+// Order-preserving integer key of a double that is not NaN: a > b exactly when
+// okey(a) > okey(b), except that -0 keys below +0 (negative doubles have their
+// non-sign bits flipped, so they order as negative integers).
+__device__ __forceinline__ long long okey(double v) {
+    const long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+// the key of -z for a threshold -z, with -0 taken as +0, so that
+// okey(eta) > nkey_neg(z) is exactly eta > -z for every eta that is not NaN
+// (for eta = +-0 and -z = -0 both are false)
+__device__ __forceinline__ long long nkey_neg(double z) {
+    long long b = __double_as_longlong(z) ^ (long long)0x8000000000000000ull;
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ bool nan_bits(double v) {
+    return (__double_as_longlong(v) & 0x7fffffffffffffffll) > 0x7ff0000000000000ll;
+}
 __device__ __forceinline__ double* ufield(const Dev& d, int buf, int f, int nd) {
     return d.U + ((size_t)buf * 4 + f) * (size_t)d.n * nd;
 }

@@ -189,16 +189,21 @@ struct Site {
     // mean depth and A = 1; entirely dry (eta <= -max z_b) gives V = A = 0;
     // otherwise the pixels are summed.  The per-cell bounds are optional (the
     // allocation-free residual has none): without them every sub-cell sums.
+    // The two tests run on order-preserving integer keys (integer pipe); they
+    // decide exactly as eta > -zmin and !(eta > -zmax), a NaN eta reading as
+    // dry as under IEEE comparisons.
     static __device__ __forceinline__ bool shortcut(const Dev& d, int64_t k, double eta,
                                                     double zbar, double& V, double& A, bool& full) {
         if (d.zmin == nullptr) return false;
-        if (eta > -d.zmin[k]) {
+        const bool nan = nan_bits(eta);
+        const long long ek = okey(eta);
+        if (!nan && ek > nkey_neg(d.zmin[k])) {
             V = eta + zbar;
             A = 1.0;
             full = true;
             return true;
         }
-        if (!(eta > -d.zmax[k])) {
+        if (nan || !(ek > nkey_neg(d.zmax[k]))) {
             V = 0.0;
             A = 0.0;
             full = false;
@@ -1001,7 +1006,7 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             bool full;
             ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pe[p], V, A, full);
             pV[p] = V;
-            allfull = allfull && full && A != 0.0;
+            allfull = allfull && full && !zero_bits(A);
         }
         allfull = __all_sync(0xffffffffu, allfull);
         __syncwarp();
@@ -1627,7 +1632,7 @@ __global__ void __maxnreg__(96)
                     ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pe[p], V, A, full);
                     pV[p] = J * tb.wm[p % NM] * tb.wm[p / NM] * V;
                     pA[p] = J * tb.wm[p % NM] * tb.wm[p / NM] * A;
-                    if (A == 0.0) ndry++;
+                    if (zero_bits(A)) ndry++;
                     else if (!full) npart++;
                 }
                 ndry = __reduce_add_sync(tm, ndry);
