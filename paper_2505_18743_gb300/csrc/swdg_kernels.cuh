@@ -933,12 +933,47 @@ __device__ __forceinline__ void mass_scalar(const Dev& d, const Tables& tb, int6
     A = team_sum<TL>(a, tm);
 }
 
+// The same mean depth and wet area for a constant elevation e, in mode S as
+// one sum over the cell's pixels: the mass sub-cells tile the cell, so the
+// pixel k of a P x P tile carries 1/P^2 of the area whatever sub-cells it
+// is split among, and Hbar(e) = J / P^2 sum_k max(e + z_k, 0), Abar = J / P^2
+// #{e + z_k > 0} (equal to mass_scalar up to rounding, with P^2 terms
+// instead of the sub-cells' split pixels).  Cells wholly wet or dry, and mode
+// P, take mass_scalar (its shortcut makes it cheap there).
+template <int R, typename Pix, int MODE, int TL = 32>
+__device__ __forceinline__ void mass_scalar_pixels(const Dev& d, const Tables& tb, int64_t k,
+                                                   double J, double e, int lane, double& H,
+                                                   double& A, unsigned tm = 0xffffffffu) {
+    using ST = Site<R, Pix, MODE>;
+    const bool mixed = MODE == 0 && d.zmin != nullptr && !nan_bits(e) &&
+                       !(okey(e) > nkey_neg(d.zmin[k])) && okey(e) > nkey_neg(d.zmax[k]);
+    if (!mixed) {
+        mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, H, A, tm);
+        return;
+    }
+    const OvTab& o = ST::tab(d, k);
+    const Pix* t = ST::tile(d, o, k);
+    const int np = o.P * o.P;
+    double h = 0.0;
+    int a = 0;
+    for (int i = lane; i < np; i += TL) {
+        const double dd = e + (double)t[i];
+        if (dd > 0.0) {
+            h += dd;
+            ++a;
+        }
+    }
+    const double w = J / (double)np;
+    H = w * team_sum<TL>(h, tm);
+    A = w * (double)__reduce_add_sync(tm, a);
+}
+
 template <int R, typename Pix, int MODE, int TL = 32>
 __device__ int scalar_newton(const Dev& d, const Tables& tb, int64_t k, double J, double target,
                              double& e, int lane, unsigned tm = 0xffffffffu) {
     constexpr int ND = Sz<R>::ND;
     double H, A;
-    mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, H, A, tm);
+    mass_scalar_pixels<R, Pix, MODE, TL>(d, tb, k, J, e, lane, H, A, tm);
     // the first iteration reuses this evaluation unless the start moves to the
     // dry start of Eq. initial_guess
     bool have = true;
@@ -948,7 +983,7 @@ __device__ int scalar_newton(const Dev& d, const Tables& tb, int64_t k, double J
     }
     int it = 0;
     for (int kk = 0; kk < d.newton_max; ++kk) {
-        if (!have) mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, H, A, tm);
+        if (!have) mass_scalar_pixels<R, Pix, MODE, TL>(d, tb, k, J, e, lane, H, A, tm);
         have = false;
         if (A == 0.0) break;
         const double dd = (H - target) / A;
@@ -1694,11 +1729,14 @@ __global__ void __maxnreg__(96)
             const unsigned cmp = d.cmask[(size_t)sa.prev_buf * n + k];
             for (int f = 0; f < 3; ++f) {
                 const double* up = ufield(d, sa.prev_buf, f, ND) + k * ND;
-                for (int i = lane; i < ND; i += TL) o[i] = up[i];
-                __syncwarp(tm);
-                tens_interp<ND1, NG, double, TL>(tb.Bg, o, tmp, pg + f * NGP, lane, tm);
-                if (cmp & (1u << f))
-                    for (int p = lane; p < NGP; p += TL) pg[f * NGP + p] = o[0];
+                if (cmp & (1u << f)) { // a constant field: its value at every point
+                    const double v0 = up[0];
+                    for (int p = lane; p < NGP; p += TL) pg[f * NGP + p] = v0;
+                } else {
+                    for (int i = lane; i < ND; i += TL) o[i] = up[i];
+                    __syncwarp(tm);
+                    tens_interp<ND1, NG, double, TL>(tb.Bg, o, tmp, pg + f * NGP, lane, tm);
+                }
                 __syncwarp(tm);
             }
             for (int p = lane; p < NGP; p += TL) {
@@ -1723,9 +1761,11 @@ __global__ void __maxnreg__(96)
             // momentum: sums of the rows of the friction-modified mass matrix
             double den = 0.0, num[2] = {0.0, 0.0};
             for (int f = 0; f < 2; ++f) {
-                tens_interp<ND1, NG, double, TL>(tb.Bg, su + (1 + f) * ND, tmp, pg + (3 + f) * NGP, lane, tm);
                 if (cm0 & (2u << f))
                     for (int p = lane; p < NGP; p += TL) pg[(3 + f) * NGP + p] = su[(1 + f) * ND];
+                else
+                    tens_interp<ND1, NG, double, TL>(tb.Bg, su + (1 + f) * ND, tmp, pg + (3 + f) * NGP,
+                                                     lane, tm);
                 __syncwarp(tm);
             }
             for (int p = lane; p < NGP; p += TL) {
