@@ -1785,7 +1785,7 @@ __global__ void __maxnreg__(96)
             const double qyn = (team_sum<TL>(num[1], tm) + team_sum<TL>(rs1, tm)) / den;
             rcs = team_sum<TL>(rcs, tm);
             double Hs, As;
-            mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, Hs, As, tm);
+            mass_scalar_pixels<R, Pix, MODE, TL>(d, tb, k, J, e, lane, Hs, As, tm);
             const bool tr_ok = Hs > 1e-14 * J * d.hlim;
             const double cn = tr_ok ? (d.CNbar[k] + rcs) / Hs : 0.0;
             for (int i = lane; i < ND; i += TL) {
