@@ -216,10 +216,19 @@ __device__ __forceinline__ void side_flux(T qxA, T qyA, T cA, T hA, T hsA, T qxB
 // r = 2); r = 3 carries all six directions per lane and keeps more
 template <int R, typename Pix, int MODE>
 __global__ void __maxnreg__(R == 3 ? 232 : 176)
-    k_residual_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
+    k_residual_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb_g,
                    const double* __restrict__ u, const uint8_t* __restrict__ cmask,
                    const double* __restrict__ rbar, double* __restrict__ ubar,
                    double* __restrict__ nbar, double* __restrict__ dbar, int accumulate) {
+    // the basis tables in shared memory, as in the forward residual (lane-indexed reads)
+    __shared__ Tables s_tb;
+    {
+        const unsigned* src = (const unsigned*)&tb_g;
+        unsigned* dst = (unsigned*)&s_tb;
+        for (int i = threadIdx.x; i < (int)(sizeof(Tables) / 4); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+    const Tables& tb = s_tb;
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NV = S::NV, NVP = S::NVP, NM = S::NM;

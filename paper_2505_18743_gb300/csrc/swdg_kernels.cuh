@@ -504,8 +504,19 @@ __device__ __forceinline__ void side_flux(const B raw[4], B pres, bool own_first
 
 template <int R, typename Pix, int MODE, typename B>
 __global__ void __maxnreg__(96)
-    k_residual(const __grid_constant__ Dev d, const __grid_constant__ Tables tb, int buf,
+    k_residual(const __grid_constant__ Dev d, const __grid_constant__ Tables tb_g, int buf,
                int stage, double c_stage, int want_dt) {
+    // the basis tables in shared memory: the contractions index them by lane
+    // (a different row or column per lane), which the constant cache would
+    // serialise (measured: -3 % per launch)
+    __shared__ Tables s_tb;
+    {
+        const unsigned* src = (const unsigned*)&tb_g;
+        unsigned* dst = (unsigned*)&s_tb;
+        for (int i = threadIdx.x; i < (int)(sizeof(Tables) / 4); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+    const Tables& tb = s_tb;
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NV = S::NV, NVP = S::NVP, NM = S::NM;
