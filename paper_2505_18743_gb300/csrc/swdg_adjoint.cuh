@@ -711,8 +711,16 @@ constexpr int stage_vjp_smem() {
 
 template <int R, typename Pix, int MODE>
 __global__ void __maxnreg__(128)
-    k_stage_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
+    k_stage_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb_g,
                 const __grid_constant__ StageVjpArgs a) {
+    __shared__ Tables s_tb; // basis tables in shared memory (lane-indexed reads)
+    {
+        const unsigned* src = (const unsigned*)&tb_g;
+        unsigned* dst = (unsigned*)&s_tb;
+        for (int i = threadIdx.x; i < (int)(sizeof(Tables) / 4); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+    const Tables& tb = s_tb;
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
@@ -906,7 +914,7 @@ __global__ void __maxnreg__(128)
                 qs[1] += team_sum<TL>(s1, tm);
             }
             double Hs, As;
-            mass_scalar<R, Pix, MODE, TL>(d, tb, k, J, e, lane, Hs, As, tm);
+            mass_scalar_pixels<R, Pix, MODE, TL>(d, tb, k, J, e, lane, Hs, As, tm);
             // tracer: c = (CNbar + dt sum a sum_i R_i) / Hbar(e), or c^n in a dry cell
             if (Hs > 1e-14 * J * d.hlim) {
                 const double rsb = cs / Hs, Hsb = -cs * cl / Hs;
@@ -1014,8 +1022,16 @@ constexpr int begin_vjp_smem() {
 
 template <int R, typename Pix, int MODE>
 __global__ void __maxnreg__(96)
-    k_begin_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb,
+    k_begin_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb_g,
                 const __grid_constant__ BeginVjpArgs a) {
+    __shared__ Tables s_tb; // basis tables in shared memory (lane-indexed reads)
+    {
+        const unsigned* src = (const unsigned*)&tb_g;
+        unsigned* dst = (unsigned*)&s_tb;
+        for (int i = threadIdx.x; i < (int)(sizeof(Tables) / 4); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+    const Tables& tb = s_tb;
     using S = Sz<R>;
     using ST = Site<R, Pix, MODE>;
     constexpr int ND1 = S::ND1, ND = S::ND, NM = S::NM, NMP = S::NMP, NG = S::NG, NGP = S::NGP;
@@ -1123,7 +1139,7 @@ __global__ void __maxnreg__(96)
             // zeta~ = e with Hbar(e, delta) = m(zeta^n, delta); dry: e = -max(z_b + delta)
             if (m > 0.0) {
                 double Hs, As;
-                mass_scalar<R, Pix, MODE>(d, tb, k, J, a.un[k * ND], lane, Hs, As);
+                mass_scalar_pixels<R, Pix, MODE>(d, tb, k, J, a.un[k * ND], lane, Hs, As);
                 if (As > 0.0) mb += ez / As;
             }
             if (lane == 0) dsum -= ez;
