@@ -212,10 +212,10 @@ __device__ __forceinline__ void side_flux(T qxA, T qyA, T cA, T hA, T hsA, T qxB
     out[2] = out[2] - pres * T(ny);
 }
 
-// register cap: 176 keeps 11 warps resident per SM at r <= 2 (no spills at
+// register cap: 160 keeps 12 warps resident per SM at r <= 2 (no spills at
 // r = 2); r = 3 carries all six directions per lane and keeps more
 template <int R, typename Pix, int MODE>
-__global__ void __maxnreg__(R == 3 ? 232 : 176)
+__global__ void __maxnreg__(R == 3 ? 232 : 160)
     k_residual_vjp(const __grid_constant__ Dev d, const __grid_constant__ Tables tb_g,
                    const double* __restrict__ u, const uint8_t* __restrict__ cmask,
                    const double* __restrict__ rbar, double* __restrict__ ubar,
@@ -817,15 +817,19 @@ __global__ void __maxnreg__(128)
             const unsigned cmo = a.cmo[k];
             tens_interp<ND1, NM, double, TL>(tb.Bm, a.uo + k * ND, tmp, pz, lane, tm);
             tens_interp<ND1, NM, double, TL>(tb.Bm, a.uo + 3 * fs + k * ND, tmp, pc, lane, tm);
+            bool allfull = true; // every pixel of every mass sub-cell wet at zeta^(l)
             for (int p = lane; p < NMP; p += TL) {
                 if (cmo & 1u) pz[p] = a.uo[k * ND];
                 if (cmo & 8u) pc[p] = a.uo[3 * fs + k * ND];
                 double V, A;
-                ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pz[p], V, A);
+                bool full;
+                ST::VA(d, tb, k, SET_MASS, p % NM, p / NM, pz[p], V, A, full);
                 const double w = J * tb.wm[p % NM] * tb.wm[p / NM];
                 pV[p] = w * V;
                 pA[p] = w * A;
+                allfull = allfull && full && !zero_bits(A);
             }
+            allfull = __all_sync(tm, allfull);
             __syncwarp(tm);
             assemble_mass<ND1, NM, TL>(tb, pV, Y, M, lane, tm);
             for (int i = lane; i < ND; i += TL) rcb[i] = vb[3 * ND + i];
@@ -874,10 +878,16 @@ __global__ void __maxnreg__(128)
             }
             // continuity: T_bar = M(zeta^(l))^-1 zeta_bar, M = B^T diag(J w A) B; the
             // offset moves H(zeta^(l)) by J w A: delta_bar -= sum J w A T_bar(p)
-            assemble_mass<ND1, NM, TL>(tb, pA, Y, M, lane, tm);
-            for (int i = lane; i < ND; i += TL) Tb[i] = vb[i];
-            __syncwarp(tm);
-            chol_solve<ND, TL>(M, Tb, inv, lane, tm);
+            if (allfull) {
+                // wholly wet: M = J (M1 x M1), inverted by its tensor factors (as the
+                // forward's Newton step there)
+                kron_apply<ND1, false, MXN, double, TL>(tb.M1inv, vb, tmp, Tb, 1.0 / J, lane, tm);
+            } else {
+                assemble_mass<ND1, NM, TL>(tb, pA, Y, M, lane, tm);
+                for (int i = lane; i < ND; i += TL) Tb[i] = vb[i];
+                __syncwarp(tm);
+                chol_solve<ND, TL>(M, Tb, inv, lane, tm);
+            }
             tens_interp<ND1, NM, double, TL>(tb.Bm, Tb, tmp, pw, lane, tm);
             for (int p = lane; p < NMP; p += TL) dsum -= pA[p] * pw[p];
             for (int i = lane; i < ND; i += TL) {
