@@ -545,13 +545,15 @@ __global__ void __maxnreg__(96)
         for (int i = lane; i < 4 * ND; i += 32) {
             const double v = ufield(d, buf, i / ND, ND)[k * ND + (i % ND)];
             su[i] = v;
-            if constexpr (!F64) suB[i] = (B)v;
+            if constexpr (!F64)
+                if (i >= ND) suB[i] = (B)v; // qx, qy, c (the elevation stays FP64)
         }
         const unsigned cm = d.cmask[(size_t)buf * n + k];
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
         const double ihx = d.ihxhy ? d.ihxhy[2 * k] : 1.0 / hx;
         const double ihy = d.ihxhy ? d.ihxhy[2 * k + 1] : 1.0 / hy;
         const B manB = (B)d.manning[k];
+        const B JB = (B)J, ihxB = (B)ihx, ihyB = (B)ihy;
         // the member's stage time t^n + c_l dt (boundary data)
         const int mem = member_of(d, k);
         const double t = (c_stage == 0.0) ? d.mb[mem].t : d.mb[mem].t + c_stage * get_dt(d, mem);
@@ -634,7 +636,16 @@ __global__ void __maxnreg__(96)
             vel_gamma<B>(manB, hB, qx, qy, gB, epsB, fv, gam);
             const B ux = fv * qx, uy = fv * qy;
             const double w = J * tb.wv[al] * tb.wv[be];
-            const B wB = (B)w, wx = (B)(w * ihx), wy = (B)(w * ihy);
+            B wB, wx, wy;
+            if constexpr (F64) {
+                wB = w;
+                wx = w * ihx;
+                wy = w * ihy;
+            } else { // the weights of the FP32 terms in FP32 (no conversions per point)
+                wB = JB * tb.wvF[al] * tb.wvF[be];
+                wx = wB * ihxB;
+                wy = wB * ihyB;
+            }
             Xd[0 * NVP + p] = (double)(wx * qx);
             Xd[1 * NVP + p] = (double)(wy * qy);
             Xd[2 * NVP + p] = (double)(wx * c * qx);
@@ -1458,11 +1469,15 @@ __device__ bool solve_mass_mixed(const Tables& tb, const double* cw, double* b, 
 // is kept to FP64 round-off and a constant tracer (b = c s) stays constant up
 // to the rounding of b - c0 s.  A failed FP32 factor falls back to the FP64
 // Cholesky.  b: right-hand side in, C out (FP64).  Scratch: Mf, Yf (float),
-// s (ND doubles), tmp (2 NM NM doubles), M, Y, inv (fallback).
+// s (ND doubles), tmp (2 NM NM doubles), M, Y, inv (fallback).  s_known: the
+// continuity target T when the Newton solve ended on its certificate (H is
+// affine between the last two iterates, so H(zeta^(l)) = T up to the
+// rounding of the last update): it stands for s = H 1 = H(zeta^(l)); null:
+// s is integrated from cw.
 template <int ND1, int NM, int TL>
 __device__ void solve_tracer_bulk(const Tables& tb, const double* cw, double* b, float* Mf,
                                   float* Yf, double* s, double* tmp, double* M, double* Y,
-                                  double* inv, int lane, unsigned tm) {
+                                  double* inv, const double* s_known, int lane, unsigned tm) {
     constexpr int ND = ND1 * ND1;
     static_assert(ND <= TL, "one unknown per lane");
     float rinv;
@@ -1471,8 +1486,9 @@ __device__ void solve_tracer_bulk(const Tables& tb, const double* cw, double* b,
         chol_solve<ND1 * ND1, TL>(M, b, inv, lane, tm);
         return;
     }
-    tens_test<ND1, NM, double, TL>(tb.Bm, cw, tmp, s, lane, tm); // s_i = (H 1)_i
-    const double bi = lane < ND ? b[lane] : 0.0, si = lane < ND ? s[lane] : 0.0;
+    if (s_known == nullptr) tens_test<ND1, NM, double, TL>(tb.Bm, cw, tmp, s, lane, tm); // s_i = (H 1)_i
+    const double* sv = s_known ? s_known : s;
+    const double bi = lane < ND ? b[lane] : 0.0, si = lane < ND ? sv[lane] : 0.0;
     const double sb = team_sum<TL>(bi, tm), ss = team_sum<TL>(si, tm);
     const double c0 = ss > 0.0 ? sb / ss : 0.0;
     const float v = chol_subst_rows_f<ND, TL>(Mf, rinv, (float)(bi - c0 * si), lane, tm);
@@ -1652,6 +1668,7 @@ __global__ void __maxnreg__(96)
         bool scalar = (flag == 0);
         int its = 0;
         __syncwarp(tm);
+        bool cert = false; // the Newton solve ended on its one-step certificate
         if (!scalar) {
             for (int i = lane; i < ND; i += TL) z[i] = su[i];
             bool zc = (cm0 & 1u) != 0;
@@ -1688,7 +1705,10 @@ __global__ void __maxnreg__(96)
                 // on the segment between them and M(previous) is its exact
                 // Jacobian, so this iterate solves H = T (the fully wet case of
                 // Sec. 3.4); no verification step is needed
-                if (kk > 0 && prev_full && npart == 0) break;
+                if (kk > 0 && prev_full && npart == 0) {
+                    cert = true;
+                    break;
+                }
                 if (kk == d.newton_max) break;
                 __syncwarp(tm);
                 tens_test<ND1, NM, double, TL>(tb.Bm, pV, tmp, o, lane, tm); // H_i(zeta_k)
@@ -1841,7 +1861,7 @@ __global__ void __maxnreg__(96)
             __syncwarp(tm);
             if constexpr (sizeof(B) == sizeof(float))
                 solve_tracer_bulk<ND1, NM, TL>(tb, pV, o + 3 * ND, Mf, Yf, xs, tmp, M, Y, pinv,
-                                               lane, tm);
+                                               cert ? T : nullptr, lane, tm);
             else
                 solve_mass_mixed<ND1, NM, TL>(tb, pV, o + 3 * ND, Mf, Yf, xs, rs, qs, tmp, M,
                                               Y, pinv, lane, tm);
