@@ -831,10 +831,13 @@ __global__ void __maxnreg__(128)
             }
             allfull = __all_sync(tm, allfull);
             __syncwarp(tm);
-            assemble_mass<ND1, NM, TL>(tb, pV, Y, M, lane, tm);
+            // the forward's mixed-precision solve (FP32 factor, FP64 refinement to
+            // 1e-15, FP64 Cholesky fallback); its FP32 arrays overlay M and Y, its
+            // iterate and residual take x and Tb, its points pw (all idle here)
             for (int i = lane; i < ND; i += TL) rcb[i] = vb[3 * ND + i];
             __syncwarp(tm);
-            chol_solve<ND, TL>(M, rcb, inv, lane, tm);
+            solve_mass_mixed<ND1, NM, TL>(tb, pV, rcb, (float*)M, (float*)Y, x, Tb, pw, tmp, M, Y,
+                                          inv, lane, tm);
             // dH_c/dzeta: zeta_bar(p) -= J w A rcb(p) c(p); the same for delta
             tens_interp<ND1, NM, double, TL>(tb.Bm, rcb, tmp, pw, lane, tm);
             for (int p = lane; p < NMP; p += TL) {
