@@ -101,6 +101,7 @@ struct swdg_ctx {
     double *x0y0 = nullptr, *hxhy = nullptr, *ihxhy = nullptr, *manning = nullptr, *U = nullptr, *res = nullptr,
            *llin = nullptr, *HN = nullptr, *CN = nullptr, *HNbar = nullptr, *CNbar = nullptr,
            *zpts = nullptr, *zmax = nullptr, *zmin = nullptr, *zabs = nullptr, *diag = nullptr;
+    float2* zsb = nullptr; // sub-cell depth bounds (mode S)
     int32_t* nbr = nullptr;
     uint8_t *cmask = nullptr, *flag = nullptr, *wet0 = nullptr, *finfo = nullptr, *pcls = nullptr;
     int64_t* tile_off = nullptr;
@@ -420,12 +421,28 @@ __device__ double subcell_mean(const Pix* tile, const OvTab& o, int setx, int ia
     return s;
 }
 
-// one warp per cell: mean depth of every sub-cell of the three point sets and
-// of the coarse-side strips of its 2:1 faces (mode S)
+// the smallest and largest depth of the pixels a sub-cell overlaps
+template <typename Pix>
+__device__ float2 subcell_bounds(const Pix* tile, const OvTab& o, int setx, int ia, int sety,
+                                 int ib) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int j = 0; j < o.cnt[sety][ib]; ++j)
+        for (int a = 0; a < o.cnt[setx][ia]; ++a) {
+            const double z = (double)tile[(size_t)(o.lo[sety][ib] + j) * o.P + o.lo[setx][ia] + a];
+            lo = fmin(lo, z);
+            hi = fmax(hi, z);
+        }
+    // rounded outwards: looser bounds only make the sub-grid shortcut rarer
+    return make_float2(__double2float_rd(lo), __double2float_ru(hi));
+}
+
+// one warp per cell: mean depth (and depth bounds, zsb non-null) of every
+// sub-cell of the three point sets and of the coarse-side strips of its 2:1
+// faces (mode S)
 template <typename Pix>
 __global__ void k_subcell_means(const Pix* __restrict__ tiles, const int64_t* off,
                                 const uint8_t* pcls, const OvTab* ov, const uint8_t* finfo, int nv,
-                                int nm, int ng, double* zpts, double* zhang, int64_t n) {
+                                int nm, int ng, double* zpts, double* zhang, float2* zsb, int64_t n) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int nzp = nv * nv + nm * nm + ng * ng;
@@ -446,6 +463,7 @@ __global__ void k_subcell_means(const Pix* __restrict__ tiles, const int64_t* of
                     }
                 }
                 zpts[k * nzp + i] = subcell_mean(tile, o, set, p % q, set, p / q);
+                if (zsb) zsb[k * nzp + i] = subcell_bounds(tile, o, set, p % q, set, p / q);
             } else {
                 const int r = i - nzp, f = r / (2 * nm), h = (r / nm) % 2, al = r % nm;
                 double v = 0.0;
@@ -757,6 +775,8 @@ static void free_mesh(swdg_ctx* c) {
 }
 static void free_bathy(swdg_ctx* c) {
     cudaFree(c->tiles); cudaFree(c->zpts); cudaFree(c->zmax); cudaFree(c->zmin); cudaFree(c->zabs);
+    cudaFree(c->zsb);
+    c->zsb = nullptr;
     cudaFree(c->zhang); cudaFree(c->tile_off); cudaFree(c->pcls); cudaFree(c->ov);
     cudaFree(c->tiles0); cudaFree(c->zpts0);
     c->tiles0 = nullptr;
@@ -1028,6 +1048,7 @@ static int upload_bathy(swdg_ctx* ctx, int nseg, const void* const* rasters, int
     CK(cudaMalloc(&ctx->zmin, n * sizeof(double)));
     CK(cudaMalloc(&ctx->zabs, n * sizeof(double)));
     CK(cudaMalloc(&ctx->zpts, (size_t)n * nzp_ * sizeof(double)));
+    if (ctx->mode == 0) CK(cudaMalloc(&ctx->zsb, (size_t)n * nzp_ * sizeof(float2)));
     CK(cudaMalloc(&ctx->zhang, (size_t)n * 8 * nm_ * sizeof(double)));
     // one raster on the device at a time; a single raster of an adaptive
     // context stays there (and a rebuild re-tiles from it)
@@ -1098,14 +1119,14 @@ static int upload_bathy(swdg_ctx* ctx, int nseg, const void* const* rasters, int
                                                          ctx->zabs);
             k_subcell_means<float><<<gw, 256, 0, ctx->st>>>(
                 (const float*)ctx->tiles, ctx->tile_off, ctx->pcls, ctx->ov, ctx->finfo, nv_, nm_, ng_,
-                ctx->zpts, ctx->zhang, n);
+                ctx->zpts, ctx->zhang, ctx->zsb, n);
         } else {
             k_tile_bounds<double><<<gw, 256, 0, ctx->st>>>((const double*)ctx->tiles, ctx->tile_off,
                                                           ctx->pcls, ctx->ov, n, ctx->zmax,
                                                           ctx->zmin, ctx->zabs);
             k_subcell_means<double><<<gw, 256, 0, ctx->st>>>(
                 (const double*)ctx->tiles, ctx->tile_off, ctx->pcls, ctx->ov, ctx->finfo, nv_, nm_,
-                ng_, ctx->zpts, ctx->zhang, n);
+                ng_, ctx->zpts, ctx->zhang, ctx->zsb, n);
         }
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->st));
@@ -1151,6 +1172,7 @@ static int upload_bathy(swdg_ctx* ctx, int nseg, const void* const* rasters, int
     d.ov = ctx->ov;
     d.zhang = ctx->zhang;
     d.zpts = ctx->zpts;
+    d.zsb = ctx->mode == 0 ? ctx->zsb : nullptr;
     d.zmax = ctx->zmax;
     d.zmin = ctx->zmin;
     d.zabs = ctx->zabs;
@@ -2021,14 +2043,14 @@ int swdg_set_bathymetry_offset(swdg_ctx* ctx, const double* delta, int where) {
                                                          ctx->zabs);
             k_subcell_means<float><<<gw, 256, 0, ctx->st>>>(
                 (const float*)ctx->tiles, ctx->tile_off, ctx->pcls, ctx->ov, ctx->finfo, nv_, nm_, ng_,
-                ctx->zpts, ctx->zhang, n);
+                ctx->zpts, ctx->zhang, ctx->zsb, n);
         } else {
             k_tile_bounds<double><<<gw, 256, 0, ctx->st>>>((const double*)ctx->tiles, ctx->tile_off,
                                                           ctx->pcls, ctx->ov, n, ctx->zmax,
                                                           ctx->zmin, ctx->zabs);
             k_subcell_means<double><<<gw, 256, 0, ctx->st>>>(
                 (const double*)ctx->tiles, ctx->tile_off, ctx->pcls, ctx->ov, ctx->finfo, nv_, nm_,
-                ng_, ctx->zpts, ctx->zhang, n);
+                ng_, ctx->zpts, ctx->zhang, ctx->zsb, n);
         }
     } else {
         if (!ctx->zpts0) { // keep the uploaded samples: [n][nzp] then [n][8 nm]

@@ -113,6 +113,9 @@ struct Dev {
     const double* zmax; // dry-start level of Eq. initial_guess (max z_b of the cell)
     const double* zmin; // min z_b of the cell: every pixel is wet when eta > -zmin
     const double* zabs; // max |z_b| of the cell (Newton tolerance scale)
+    // [cell][NZP] (min, max) of the pixel depths of each sub-cell of the three
+    // point sets (mode S; min rounded down, max up); null: the cell's bounds
+    const float2* zsb;
     const double* manning;
     const double* nu_c; // tracer numerical diffusivity per cell (Eq. numdiff); null: none
     double* U;

@@ -195,15 +195,21 @@ struct Site {
     static __device__ __forceinline__ bool shortcut(const Dev& d, int64_t k, double eta,
                                                     double zbar, double& V, double& A, bool& full) {
         if (d.zmin == nullptr) return false;
+        return shortcut_b(eta, d.zmin[k], d.zmax[k], zbar, V, A, full);
+    }
+    // the same tests against the bounds zlo <= z_k <= zhi of a set of pixels
+    static __device__ __forceinline__ bool shortcut_b(double eta, double zlo, double zhi,
+                                                      double zbar, double& V, double& A,
+                                                      bool& full) {
         const bool nan = nan_bits(eta);
         const long long ek = okey(eta);
-        if (!nan && ek > nkey_neg(d.zmin[k])) {
+        if (!nan && ek > nkey_neg(zlo)) {
             V = eta + zbar;
             A = 1.0;
             full = true;
             return true;
         }
-        if (nan || !(ek > nkey_neg(d.zmax[k]))) {
+        if (nan || !(ek > nkey_neg(zhi))) {
             V = 0.0;
             A = 0.0;
             full = false;
@@ -217,10 +223,18 @@ struct Site {
                                               int ia, int ib, double eta, double& V, double& A,
                                               bool& full) {
         if (MODE == 0) {
-            if (d.zmin != nullptr &&
-                shortcut(d, k, eta, d.zpts[(size_t)k * S::NZP + offset(set) + ia + count(set) * ib],
-                         V, A, full))
-                return;
+            if (d.zmin != nullptr) {
+                const size_t ip = (size_t)k * S::NZP + offset(set) + ia + count(set) * ib;
+                const double zbar = d.zpts[ip];
+                // the cell's depth bounds first (one value per cell, cached); where
+                // the waterline crosses the cell, the sub-cell's own bounds, so that
+                // only the sub-cells it crosses sum their pixels
+                if (shortcut_b(eta, d.zmin[k], d.zmax[k], zbar, V, A, full)) return;
+                if (d.zsb != nullptr) {
+                    const float2 b = d.zsb[ip];
+                    if (shortcut_b(eta, (double)b.x, (double)b.y, zbar, V, A, full)) return;
+                }
+            }
             const OvTab& o = tab(d, k);
             subgrid_S<Pix>(tile(d, o, k), o, set, ia, set, ib, eta, V, A, full);
         } else {
