@@ -1,8 +1,10 @@
 """The C-ABI library builds for sm_103a, loads without a GPU and exports every
-function declared in include/swdg.h (no compute call is made here)."""
+function declared in include/swdg.h (no compute call is made here, except
+by the gpu-marked probe test at the end)."""
 import ctypes
 import os
 import re
+import pytest
 
 from paper_2505_18743_gb300 import build as B
 from paper_2505_18743_gb300 import swdg
@@ -33,3 +35,17 @@ def test_invalid_config_is_rejected_without_touching_the_gpu():
     h = ctypes.c_void_p()
     assert lib.swdg_create(ctypes.byref(cfg), ctypes.byref(h)) == swdg.SWDG_EINVAL
     assert not h.value
+
+
+@pytest.mark.gpu
+def test_fma_probe_measures_the_pipes():
+    """swdg_probe_fma: FP64 and FP32 FMA-chain rates of the device, positive
+    and in the order the hardware fixes (FP32 well above FP64)"""
+    import torch
+    assert torch.cuda.is_available()
+    B.build()
+    f64, ms64 = swdg.probe_fma(swdg.SWDG_PIX_F64)
+    f32, ms32 = swdg.probe_fma(swdg.SWDG_PIX_F32)
+    assert f64 > 0.1 and ms64 > 0.0 and f32 > 10 * f64
+    with pytest.raises(swdg.SwdgError):
+        swdg.probe_fma(7)
