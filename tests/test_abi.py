@@ -49,3 +49,14 @@ def test_fma_probe_measures_the_pipes():
     assert f64 > 0.1 and ms64 > 0.0 and f32 > 10 * f64
     with pytest.raises(swdg.SwdgError):
         swdg.probe_fma(7)
+
+
+def test_noalloc_refuses_an_empty_mesh_before_any_device_call():
+    """swdg_residual_noalloc checks its sizes before it touches a pointer or
+    the device: n = 0 (and n above its scratch) come back SWDG_EINVAL"""
+    cfg = swdg.swdg_config(1, 0, 0, 0, 9.81, 0.01, 0.01, 1e-6, 0.1, 20, 1e-12, None)
+    for n in (0, -1, 1048577):
+        with pytest.raises(swdg.SwdgError) as e:
+            swdg.residual_noalloc(cfg, n, None, None, None, 8, swdg.SWDG_PIX_F64, None, None, 0.0,
+                                  None, None)
+        assert e.value.code == swdg.SWDG_EINVAL and "n_cells" in str(e.value)

@@ -493,3 +493,72 @@ def test_thacker_paraboloid_steps_mode_p():
     assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
     assert abs(d1["tracer_mass"] - d0["tracer_mass"]) <= 1e-13 * d0["tracer_mass"]
     assert 0 < d1["r_cells"] < wl.mesh.n
+
+
+# ----------------------------------------------------------------------------
+# degenerate cases
+# ----------------------------------------------------------------------------
+def one_cell(degree, mode):
+    """a single 100 m cell with walls on all four faces, a 3 m bump under 5 m
+    of water (16 x 16 pixels), a tilted surface, discharges and a tracer
+    gradient"""
+    L, P = 100.0, 16
+    mesh = W.uniform_mesh(1, 1, L, L)
+    dx = L / P
+    xc = (np.arange(P) + 0.5) * dx
+    Xp, Yp = np.meshgrid(xc, xc)
+    ras = W.Raster(5.0 - 3.0 * np.exp(-((Xp - 60) ** 2 + (Yp - 40) ** 2) / 30.0 ** 2), 0.0, 0.0, dx, dx)
+    X, Y = W.nodal_coordinates(mesh, degree)
+    zeta = 0.3 * (X - 50) / 50
+    qx = 0.2 * np.sin(np.pi * X / L)
+    qy = -0.1 * np.sin(np.pi * Y / L)
+    c = 0.5 + 0.3 * X / L
+    b = {1: 1 / 6, 2: 1 / 12, 3: 1 / 20}[degree]
+    return W.Workload("one-cell", degree, mesh, ras, zeta, qx, qy, c, tableau=0,
+                      cfl=0.9 * b / (2 - np.sqrt(2)), subgrid_mode=mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_single_cell_domain(mode):
+    """one cell (an odd count: the stage update's second team has no cell),
+    walls only: residual and 30 RK32-IMEX steps against the oracle"""
+    wl = one_cell(3, mode)
+    ctx, ora = pair(wl)
+    check_residual(ctx, ora)
+    d0, d1, _ = _steps_with_diagnostics(ctx, ora, 30, 0.0)
+    assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+    assert d1["r_cells"] == 1
+
+
+def test_all_dry_domain():
+    """every cell dry (the surface 20 m below the deepest point): zero
+    residual, degree 0 everywhere, each cell moved to its dry-start level
+    (Eq. initial_guess), no water or tracer created; the CFL step is bounded
+    by the wave-speed floor, so the steps are huge but finite"""
+    wl = W.closed_basin()
+    wl.zeta = -20.0 * np.ones_like(wl.zeta)
+    wl.qx[:] = 0.0
+    wl.qy[:] = 0.0
+    ctx, ora = pair(wl)
+    rg = ctx.residual(0.0)
+    for k, v in rg.items():
+        assert not np.any(v), k
+    tg = ctx.step(3, -1.0, 0.0)
+    to = ora.step(3, -1.0, 0.0)
+    assert np.isfinite(tg) and abs(tg - to) <= 1e-10 * to
+    check_state(ctx, ora)
+    dg = ctx.diagnostics()
+    assert dg["mass"] == 0.0 and dg["tracer_mass"] == 0.0
+    assert dg["r_cells"] == 0 and dg["positivity_violations"] == 0
+    z = ctx.get_state()[0]
+    assert np.all(z < 0.0)
+
+
+def test_empty_mesh_is_rejected():
+    """n = 0 cells: the context refuses the mesh with SWDG_EINVAL (nothing is
+    launched); the allocation-free residual's refusal is checked on the CPU"""
+    wl = W.closed_basin()
+    ctx = swdg.Context(**wl.config())
+    with pytest.raises(swdg.SwdgError) as e:
+        ctx.upload_mesh(wl.mesh.x0y0[:0], wl.mesh.hxhy[:0], wl.mesh.nbr[:0])
+    assert e.value.code == swdg.SWDG_EINVAL
