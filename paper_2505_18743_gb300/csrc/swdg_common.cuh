@@ -176,6 +176,22 @@ __device__ __forceinline__ double team_sum(double v, unsigned tm) {
     for (int o = TL / 2; o > 0; o >>= 1) v += __shfl_xor_sync(tm, v, o);
     return v;
 }
+// two team sums at once, each bit for bit the team_sum of its value: the first
+// level of the butterfly sums a on the team's lower half and b on its upper
+// half (one addition per lane for both), the other levels run on both halves
+// together, and a last exchange gives every lane both results.  Each level
+// adds the same pairs as team_sum (addition commutes), so the tree is the
+// same; the FP64 additions halve.  Teams are aligned groups of TL lanes.
+template <int TL>
+__device__ __forceinline__ void team_sum2(double& a, double& b, unsigned tm) {
+    const bool hi = (threadIdx.x & (TL / 2)) != 0;
+    double v = (hi ? b : a) + __shfl_xor_sync(tm, hi ? a : b, TL / 2);
+#pragma unroll
+    for (int o = TL / 4; o > 0; o >>= 1) v += __shfl_xor_sync(tm, v, o);
+    const double w = __shfl_xor_sync(tm, v, TL / 2);
+    a = hi ? w : v;
+    b = hi ? v : w;
+}
 // maxima of non-negative values (no NaN) over the team's lanes tm by their bit
 // patterns, which order like the values: integer reductions, off the FP64 pipe
 __device__ __forceinline__ float team_max_nonneg(float v, unsigned tm) {

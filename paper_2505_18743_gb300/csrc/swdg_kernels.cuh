@@ -938,7 +938,7 @@ __global__ void __maxnreg__(80)
             // one atomic per warp when its jobs share a member, else per job
             const int m0 = __shfl_sync(0xffffffffu, mem, 0);
             if (__all_sync(0xffffffffu, mem == m0 || mem < 0)) {
-                const double m = warp_max(v);
+                const double m = team_max_nonneg(v, 0xffffffffu); // v >= 0, never NaN
                 if (lane == 0 && m0 >= 0) atomic_max_pos(&d.mb[m0].rmax, m);
             } else if (mem >= 0) {
                 atomic_max_pos(&d.mb[mem].rmax, v);
@@ -965,8 +965,9 @@ __device__ __forceinline__ void mass_scalar(const Dev& d, const Tables& tb, int6
         h += w * V;
         a += w * Ap;
     }
-    H = team_sum<TL>(h, tm);
-    A = team_sum<TL>(a, tm);
+    team_sum2<TL>(h, a, tm);
+    H = h;
+    A = a;
 }
 
 // The same mean depth and wet area for a constant elevation e, in mode S as
@@ -1081,10 +1082,11 @@ __global__ void __launch_bounds__(32 * MAXWPB)
         }
         allfull = __all_sync(0xffffffffu, allfull);
         __syncwarp();
-        double mu = INFINITY;
-        for (int p = lane; p < NMP; p += 32) mu = fmin(mu, pV[p]);
-        mu = warp_min(mu);
-        const int flag = (do_switch && !(mu > d.hlim)) ? 0 : R;
+        // r_K = 0 where the smallest wet depth of the mass points is at most
+        // h_lim (a NaN depth never counts, as under fmin)
+        bool low = false;
+        for (int p = lane; p < NMP; p += 32) low = low || pV[p] <= d.hlim;
+        const int flag = (do_switch && __any_sync(0xffffffffu, low)) ? 0 : R;
         if (flag == 0) {
             // remap to r_K = 0: mass-exact zeta, GL means of q, tracer-mass-exact c
             double m = 0.0, tr = 0.0;
@@ -1093,8 +1095,7 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                 m += w * pV[p];
                 tr += w * pV[p] * pc[p];
             }
-            m = warp_sum(m);
-            tr = warp_sum(tr);
+            team_sum2<32>(m, tr, 0xffffffffu);
             for (int f = 0; f < 3; ++f) {
                 tens_interp<ND1, NG>(tb.Bg, su + (1 + f) * ND, tmp, pg + f * NGP, lane);
             }
@@ -1106,7 +1107,8 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                     mq[f] += w * v;
                 }
             }
-            for (int f = 0; f < 3; ++f) mq[f] = warp_sum(mq[f]);
+            team_sum2<32>(mq[0], mq[1], 0xffffffffu);
+            mq[2] = warp_sum(mq[2]);
             const double cnew = (m > 1e-14 * J * d.hlim) ? tr / m : mq[2];
             double emax = -INFINITY;
             for (int p = lane; p < NMP; p += 32) emax = fmax(emax, pe[p]);
@@ -1146,14 +1148,11 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             hb += w * pV[p];
             cb += w * pV[p] * pc[p];
             px[p] = w * pV[p];
+            pc[p] = px[p] * pc[p]; // c is not needed beyond C~
         }
-        hb = warp_sum(hb);
-        cb = warp_sum(cb);
+        team_sum2<32>(hb, cb, 0xffffffffu);
         __syncwarp();
-        tens_test<ND1, NM>(tb.Bm, px, tmp, out, lane);
-        for (int p = lane; p < NMP; p += 32) px[p] *= pc[p];
-        __syncwarp();
-        tens_test<ND1, NM>(tb.Bm, px, tmp, out + ND, lane);
+        tens_test2<ND1, NM>(tb.Bm, px, pc, tmp, tmp + NM * NM, out, out + ND, lane);
         for (int i = lane; i < ND; i += 32) {
             d.HN[k * ND + i] = out[i];
             d.CN[k * ND + i] = out[ND + i];
@@ -1503,7 +1502,8 @@ __device__ void solve_tracer_bulk(const Tables& tb, const double* cw, double* b,
     if (s_known == nullptr) tens_test<ND1, NM, double, TL>(tb.Bm, cw, tmp, s, lane, tm); // s_i = (H 1)_i
     const double* sv = s_known ? s_known : s;
     const double bi = lane < ND ? b[lane] : 0.0, si = lane < ND ? sv[lane] : 0.0;
-    const double sb = team_sum<TL>(bi, tm), ss = team_sum<TL>(si, tm);
+    double sb = bi, ss = si;
+    team_sum2<TL>(sb, ss, tm);
     const double c0 = ss > 0.0 ? sb / ss : 0.0;
     const float v = chol_subst_rows_f<ND, TL>(Mf, rinv, (float)(bi - c0 * si), lane, tm);
     const double xi = lane < ND ? c0 + (double)v : 0.0;
@@ -1747,8 +1747,7 @@ __global__ void __maxnreg__(96)
                     inc += fabs(o[ND + i]);
                     scale += 1.0 + fabs(z[i]) + d.zabs[k];
                 }
-                inc = team_sum<TL>(inc, tm);
-                scale = team_sum<TL>(scale, tm);
+                team_sum2<TL>(inc, scale, tm);
                 its++;
                 prev_full = (npart == 0);
                 __syncwarp(tm);
@@ -1825,10 +1824,11 @@ __global__ void __maxnreg__(96)
                 rs1 += rq[ND + i];
                 rcs += rc[i] - d.CN[k * ND + i];
             }
-            den = team_sum<TL>(den, tm);
-            const double qxn = (team_sum<TL>(num[0], tm) + team_sum<TL>(rs0, tm)) / den;
-            const double qyn = (team_sum<TL>(num[1], tm) + team_sum<TL>(rs1, tm)) / den;
-            rcs = team_sum<TL>(rcs, tm);
+            team_sum2<TL>(den, rcs, tm);
+            team_sum2<TL>(num[0], rs0, tm);
+            team_sum2<TL>(num[1], rs1, tm);
+            const double qxn = (num[0] + rs0) / den;
+            const double qyn = (num[1] + rs1) / den;
             double Hs, As;
             mass_scalar_pixels<R, Pix, MODE, TL>(d, tb, k, J, e, lane, Hs, As, tm);
             const bool tr_ok = Hs > 1e-14 * J * d.hlim;
