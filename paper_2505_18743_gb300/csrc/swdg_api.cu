@@ -327,7 +327,10 @@ static bool build_tables(int R, Tables& tb) {
             tb.BmHF[1][q][a] = (float)tb.BmH[1][q][a];
             tb.BginvF[a][q] = (float)tb.Bginv[a][q];
         }
-    for (int q = 0; q < MXP; ++q) tb.wvF[q] = (float)tb.wv[q];
+    for (int q = 0; q < MXP; ++q) {
+        tb.wvF[q] = (float)tb.wv[q];
+        tb.wgF[q] = (float)tb.wg[q];
+    }
     return true;
 }
 

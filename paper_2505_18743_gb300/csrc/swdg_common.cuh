@@ -73,6 +73,7 @@ struct Tables {
     float BvF[MXP][MXN], DvF[MXP][MXN], BmF[MXP][MXN], BmHF[2][MXP][MXN], BgF[MXP][MXN];
     float BginvF[MXN][MXP];
     float wvF[MXP];                             // volume GL weights (FP32-bulk residual)
+    float wgF[MXP];                             // momentum GL weights (FP32-bulk stage update)
     double xs[MXN];                             // support nodes on [0, 1]
     double xq[3][MXP];                          // nodes of the three point sets on [0, 1]
 };

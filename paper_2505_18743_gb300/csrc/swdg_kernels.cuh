@@ -360,12 +360,14 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
 template <int R, typename B>
 constexpr int res_smem() {
     // in doubles: su [4 ND], tz [2 ND1 NV], Xd [4 NVP], sd [4 NV ND1], fh [32 NM], rs [6 ND],
-    // tc [2 ND1 NV] (tracer diffusion), then B-typed: suB [4 ND], tB [3 ND1 NV], XB [8 NVP],
+    // tc [2 ND1 NV] (tracer diffusion), then B-typed: suB [4 ND], tB [3 ND1 NV] (B = double;
+    // [5 ND1 NV] for B = float, with the elevation's two x-contractions), XB [8 NVP],
     // sB [8 NV ND1]
     using S = Sz<R>;
     constexpr int nd = 4 * S::ND + 2 * S::ND1 * S::NV + 4 * S::NVP + 4 * S::NV * S::ND1 +
                        32 * S::NM + 6 * S::ND + 2 * S::ND1 * S::NV;
-    constexpr int nb = 4 * S::ND + 3 * S::ND1 * S::NV + 8 * S::NVP + 8 * S::NV * S::ND1;
+    constexpr int ntb = sizeof(B) == sizeof(double) ? 3 : 5;
+    constexpr int nb = 4 * S::ND + ntb * S::ND1 * S::NV + 8 * S::NVP + 8 * S::NV * S::ND1;
     return nd + (nb * (int)sizeof(B) + 7) / 8;
 }
 
@@ -545,8 +547,9 @@ __global__ void __maxnreg__(96)
     double* tc = rs + 6 * ND;           // [2][ND1][NV] x-contractions of c (value, d/dxi), FP64
     constexpr bool F64 = sizeof(B) == sizeof(double);
     B* suB = F64 ? (B*)su : (B*)(tc + 2 * ND1 * NV); // [4][ND] (the FP64 state itself when B = double)
-    B* tB = (B*)(tc + 2 * ND1 * NV) + 4 * ND;        // [3][ND1][NV]: qx, qy, c
-    B* XB = tB + 3 * ND1 * NV;          // [8][NVP]: Gx (x, y, v), Gy (x, y, v), Lx, Ly
+    // [3][ND1][NV]: qx, qy, c; B = float: [5][ND1][NV], then zeta (value, d/dxi)
+    B* tB = (B*)(tc + 2 * ND1 * NV) + 4 * ND;
+    B* XB = tB + (F64 ? 3 : 5) * ND1 * NV; // [8][NVP]: Gx (x, y, v), Gy (x, y, v), Lx, Ly
     B* sB = XB + 8 * NVP;               // [8][NV][ND1]
     const auto BvB = tab_or<B>(tb.Bv, tb.BvF);
     const auto DvB = tab_or<B>(tb.Dv, tb.DvF);
@@ -559,15 +562,30 @@ __global__ void __maxnreg__(96)
         for (int i = lane; i < 4 * ND; i += 32) {
             const double v = ufield(d, buf, i / ND, ND)[k * ND + (i % ND)];
             su[i] = v;
-            if constexpr (!F64)
-                if (i >= ND) suB[i] = (B)v; // qx, qy, c (the elevation stays FP64)
+            // B = float: an FP32 copy of all four fields (the elevation enters
+            // FP32 arithmetic only through its gradient; its value stays FP64)
+            if constexpr (!F64) suB[i] = (B)v;
         }
         const unsigned cm = d.cmask[(size_t)buf * n + k];
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
         const double ihx = d.ihxhy ? d.ihxhy[2 * k] : 1.0 / hx;
         const double ihy = d.ihxhy ? d.ihxhy[2 * k + 1] : 1.0 / hy;
-        const B manB = (B)d.manning[k];
-        const B JB = (B)J, ihxB = (B)ihx, ihyB = (B)ihy;
+        B manB, JB, ihxB, ihyB;
+        if constexpr (F64) {
+            manB = d.manning[k];
+            JB = J;
+            ihxB = ihx;
+            ihyB = ihy;
+        } else {
+            // the four per-cell values converted once per warp (lanes 0..3),
+            // since conversions occupy the FP64 pipe
+            const int q = lane & 3;
+            const float f = (float)(q == 0 ? d.manning[k] : q == 1 ? J : q == 2 ? ihx : ihy);
+            manB = __shfl_sync(0xffffffffu, f, 0);
+            JB = __shfl_sync(0xffffffffu, f, 1);
+            ihxB = __shfl_sync(0xffffffffu, f, 2);
+            ihyB = __shfl_sync(0xffffffffu, f, 3);
+        }
         // the member's stage time t^n + c_l dt (boundary data)
         const int mem = member_of(d, k);
         const double t = (c_stage == 0.0) ? d.mb[mem].t : d.mb[mem].t + c_stage * get_dt(d, mem);
@@ -589,24 +607,22 @@ __global__ void __maxnreg__(96)
                 else tB[i - 2 * NE] = s;
             }
         } else {
-            for (int i = lane; i < 2 * ND1 * NV; i += 32) {
-                const int f = i / (ND1 * NV), r_ = i % (ND1 * NV), b = r_ / NV, al = r_ % NV;
+            // the elevation's value in FP64 (the sub-grid depth); in B: qx, qy,
+            // c, and the elevation's value and d/dxi for its gradient
+            for (int i = lane; i < ND1 * NV; i += 32) {
+                const int b = i / NV, al = i % NV;
                 double s = 0.0;
-                if (f == 0) {
 #pragma unroll
-                    for (int a = 0; a < ND1; ++a) s += tb.Bv[al][a] * su[ND1 * b + a];
-                } else {
-#pragma unroll
-                    for (int a = 0; a < ND1; ++a) s += tb.Dv[al][a] * su[ND1 * b + a];
-                }
+                for (int a = 0; a < ND1; ++a) s += tb.Bv[al][a] * su[ND1 * b + a];
                 tz[i] = s;
             }
-            for (int i = lane; i < 3 * ND1 * NV; i += 32) {
+            for (int i = lane; i < 5 * ND1 * NV; i += 32) {
                 const int f = i / (ND1 * NV), r_ = i % (ND1 * NV), b = r_ / NV, al = r_ % NV;
-                const B* u = suB + (1 + f) * ND + ND1 * b;
+                const B* u = suB + (f < 3 ? 1 + f : 0) * ND + ND1 * b;
+                const B(*Tb)[MXN] = f == 4 ? DvB : BvB;
                 B s = B(0);
 #pragma unroll
-                for (int a = 0; a < ND1; ++a) s += BvB[al][a] * u[a];
+                for (int a = 0; a < ND1; ++a) s += Tb[al][a] * u[a];
                 tB[i] = s;
             }
         }
@@ -626,23 +642,43 @@ __global__ void __maxnreg__(96)
         // y-contraction and pointwise physics, one volume point per lane
         for (int p = lane; p < NVP; p += 32) {
             const int al = p % NV, be = p / NV;
-            double z = 0.0, zxd = 0.0, zyd = 0.0;
-            B qx = B(0), qy = B(0), c = B(0);
+            double z = 0.0;
+            B qx = B(0), qy = B(0), c = B(0), zx, zy;
+            if constexpr (F64) {
+                double zxd = 0.0, zyd = 0.0;
+#pragma unroll
+                for (int b = 0; b < ND1; ++b) {
+                    z += tb.Bv[be][b] * tz[b * NV + al];
+                    zxd += tb.Bv[be][b] * tz[(ND1 + b) * NV + al];
+                    zyd += tb.Dv[be][b] * tz[b * NV + al];
+                }
+                if (cm & 1u) { z = su[0]; zxd = 0.0; zyd = 0.0; }
+                zx = zxd * ihx;
+                zy = zyd * ihy;
+            } else {
+                // the gradient of the elevation in FP32 (it enters only the
+                // FP32 pressure term g h grad zeta)
+                B zxd = B(0), zyd = B(0);
+#pragma unroll
+                for (int b = 0; b < ND1; ++b) {
+                    z += tb.Bv[be][b] * tz[b * NV + al];
+                    zxd += BvB[be][b] * tB[(4 * ND1 + b) * NV + al];
+                    zyd += DvB[be][b] * tB[(3 * ND1 + b) * NV + al];
+                }
+                if (cm & 1u) { z = su[0]; zxd = B(0); zyd = B(0); }
+                zx = zxd * ihxB;
+                zy = zyd * ihyB;
+            }
 #pragma unroll
             for (int b = 0; b < ND1; ++b) {
-                z += tb.Bv[be][b] * tz[b * NV + al];
-                zxd += tb.Bv[be][b] * tz[(ND1 + b) * NV + al];
-                zyd += tb.Dv[be][b] * tz[b * NV + al];
                 const B Bb = BvB[be][b];
                 qx += Bb * tB[(0 * ND1 + b) * NV + al];
                 qy += Bb * tB[(1 * ND1 + b) * NV + al];
                 c += Bb * tB[(2 * ND1 + b) * NV + al];
             }
-            if (cm & 1u) { z = su[0]; zxd = 0.0; zyd = 0.0; }
             if (cm & 2u) qx = suB[ND];
             if (cm & 4u) qy = suB[2 * ND];
             if (cm & 8u) c = suB[3 * ND];
-            const B zx = (B)(zxd * ihx), zy = (B)(zyd * ihy);
             double h, A;
             ST::VA(d, tb, k, SET_VOL, al, be, z, h, A);
             const B hB = (B)h;
@@ -1542,6 +1578,30 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
     T* tmp1 = w1 + ND1 * NG;
     T* gam = pg + 2 * NGP;
     const int64_t n = d.n;
+    constexpr bool F64 = sizeof(T) == sizeof(double);
+    // per-cell values in T: for T = float converted once per team (lanes
+    // 0..4), since conversions occupy the FP64 pipe
+    T JT, manT, gT, epsT, adtT;
+    if constexpr (F64) {
+        JT = J;
+        manT = man;
+        gT = d.g;
+        epsT = d.eps;
+        adtT = add * dt;
+    } else {
+        const int q = lane < 5 ? lane : 0;
+        const float f = (float)(q == 0 ? J : q == 1 ? man : q == 2 ? d.g : q == 3 ? d.eps : add * dt);
+        JT = __shfl_sync(tm, f, 0, TL);
+        manT = __shfl_sync(tm, f, 1, TL);
+        gT = __shfl_sync(tm, f, 2, TL);
+        epsT = __shfl_sync(tm, f, 3, TL);
+        adtT = __shfl_sync(tm, f, 4, TL);
+    }
+    // the quadrature weight of momentum point p (T = float: FP32 weights)
+    auto wpt = [&](int p) -> T {
+        if constexpr (F64) return J * tb.wg[p % NG] * tb.wg[p / NG];
+        else return JT * tb.wgF[p % NG] * tb.wgF[p / NG];
+    };
     if (need_gam) {
         const unsigned cmp = d.cmask[(size_t)prev_buf * n + k];
         const double* uz = ufield(d, prev_buf, 0, ND) + k * ND;
@@ -1561,8 +1621,7 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
         for (int p = lane; p < NGP; p += TL) {
             double V, A;
             Site<R, Pix, MODE>::VA(d, tb, k, SET_MOM, p % NG, p / NG, zp[p], V, A);
-            gam[p] = gamma_manning<T>((T)man, (T)V, pg[3 * NGP + p], pg[4 * NGP + p], (T)d.g,
-                                      (T)d.eps);
+            gam[p] = gamma_manning<T>(manT, (T)V, pg[3 * NGP + p], pg[4 * NGP + p], gT, epsT);
         }
     } else {
         for (int p = lane; p < NGP; p += TL) gam[p] = T(0);
@@ -1579,8 +1638,8 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
     __syncwarp(tm);
     kron_apply2<ND1, true, MXP, T, TL>(Bginv, nod, nod + ND, tmp, tmp1, pg, pg + NGP, T(1), lane, tm);
     for (int p = lane; p < NGP; p += TL) {
-        const T w = (T)(J * tb.wg[p % NG] * tb.wg[p / NG]);
-        const T rD = T(1) / (w * (T(1) + (T)(add * dt) * gam[p]));
+        const T w = wpt(p);
+        const T rD = T(1) / (w * (T(1) + adtT * gam[p]));
         pg[0 * NGP + p] = (w * pg[3 * NGP + p] + pg[0 * NGP + p]) * rD;
         pg[1 * NGP + p] = (w * pg[4 * NGP + p] + pg[1 * NGP + p]) * rD;
     }
@@ -1590,7 +1649,7 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
     __syncwarp(tm);
     if (make_llin) {
         for (int p = lane; p < NGP; p += TL) {
-            const T w = (T)(J * tb.wg[p % NG] * tb.wg[p / NG]) * gam[p];
+            const T w = wpt(p) * gam[p];
             pg[3 * NGP + p] = -w * pg[p];
             pg[4 * NGP + p] = -w * pg[NGP + p];
         }
