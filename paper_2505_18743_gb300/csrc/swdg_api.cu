@@ -102,6 +102,7 @@ struct swdg_ctx {
            *llin = nullptr, *HN = nullptr, *CN = nullptr, *HNbar = nullptr, *CNbar = nullptr,
            *zpts = nullptr, *zmax = nullptr, *zmin = nullptr, *zabs = nullptr, *diag = nullptr;
     float2* zsb = nullptr; // sub-cell depth bounds (mode S)
+    float* uF = nullptr;   // FP32 copy of U (FP32-bulk)
     int32_t* nbr = nullptr;
     uint8_t *cmask = nullptr, *flag = nullptr, *wet0 = nullptr, *finfo = nullptr, *pcls = nullptr;
     int64_t* tile_off = nullptr;
@@ -746,6 +747,8 @@ static void free_mesh(swdg_ctx* c) {
     cudaFree(c->llin); cudaFree(c->HN); cudaFree(c->CN); cudaFree(c->HNbar); cudaFree(c->CNbar);
     cudaFree(c->nbr); cudaFree(c->cmask); cudaFree(c->flag); cudaFree(c->wet0); cudaFree(c->diag);
     cudaFree(c->finfo);
+    cudaFree(c->uF);
+    c->uF = nullptr;
     cudaFree(c->adj);
     c->adj = nullptr;
     cudaFree(c->gdev);
@@ -895,6 +898,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     CK(cudaMalloc(&ctx->finfo, 4 * n));
     CK(cudaMalloc(&ctx->manning, n * sizeof(double)));
     CK(cudaMalloc(&ctx->U, (size_t)NBUF * 4 * n * nd * sizeof(double)));
+    if (ctx->cfg.precision == 1) CK(cudaMalloc(&ctx->uF, (size_t)NBUF * 4 * n * nd * sizeof(float)));
     CK(cudaMalloc(&ctx->res, (size_t)MXS * 6 * n * nd * sizeof(double)));
     CK(cudaMalloc(&ctx->llin, 2 * n * nd * sizeof(double)));
     CK(cudaMalloc(&ctx->HN, n * nd * sizeof(double)));
@@ -961,6 +965,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     d.njobs = ctx->njobs;
     d.manning = ctx->manning;
     d.U = ctx->U;
+    d.uF = ctx->uF;
     d.cmask = ctx->cmask;
     d.res = ctx->res;
     d.llin = ctx->llin;
@@ -2556,6 +2561,9 @@ int swdg_autotune(swdg_ctx* ctx, int repeats, double* report) {
     // restore the state, masks, counters and clocks the tuning steps advanced
     cudaMemcpyAsync(ctx->U, usave, ubytes, cudaMemcpyDeviceToDevice, ctx->st);
     cudaMemcpyAsync(ctx->cmask, msave, n, cudaMemcpyDeviceToDevice, ctx->st);
+    // the FP32 copy of buffer 0 follows the restored state (the masks it
+    // recomputes are the restored ones: a function of the state)
+    if (ctx->uF) ctx->L.masks(ctx->d, 0, ctx->shp[KK_AUX], ctx->st);
     cudaMemcpyAsync(ctx->sc, &sc0, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->st);
     cudaMemcpyAsync(ctx->d.mb, clocks.data(), clocks.size() * sizeof(Member),
                     cudaMemcpyHostToDevice, ctx->st);

@@ -120,6 +120,10 @@ struct Dev {
     const double* manning;
     const double* nu_c; // tracer numerical diffusivity per cell (Eq. numdiff); null: none
     double* U;
+    // FP32 copy of U in the same layout (FP32-bulk contexts; null otherwise),
+    // written wherever U and its masks are written (k_masks, the step start,
+    // the stage update), read by the FP32 face and residual arithmetic
+    float* uF;
     uint8_t* cmask;
     double* res;
     double* llin;
@@ -240,6 +244,9 @@ __device__ __forceinline__ bool nan_bits(double v) {
 }
 __device__ __forceinline__ double* ufield(const Dev& d, int buf, int f, int nd) {
     return d.U + ((size_t)buf * 4 + f) * (size_t)d.n * nd;
+}
+__device__ __forceinline__ float* ufieldF(const Dev& d, int buf, int f, int nd) {
+    return d.uF + ((size_t)buf * 4 + f) * (size_t)d.n * nd;
 }
 __device__ __forceinline__ double* rfield(const Dev& d, int stage, int f, int nd) {
     return d.res + ((size_t)stage * 6 + f) * (size_t)d.n * nd;

@@ -371,11 +371,12 @@ constexpr int res_smem() {
     return nd + (nb * (int)sizeof(B) + 7) / 8;
 }
 
-// traces of zeta (FP64) and of qx, qy, c (type B) at face point al of face f
+// traces of zeta (FP64) and of qx, qy, c (type B) at face point al of face f;
+// u32 (B = float, nullable): the FP32 copy of u, same layout and stride
 template <int ND1, typename B>
-__device__ __forceinline__ void face_trace_mixed(const double* u, size_t fstride, unsigned cm, int f,
-                                                 const double (*Bd)[MXN], const B (*Bb)[MXN],
-                                                 int al, double& z, B t[3]) {
+__device__ __forceinline__ void face_trace_mixed(const double* u, const float* u32, size_t fstride,
+                                                 unsigned cm, int f, const double (*Bd)[MXN],
+                                                 const B (*Bb)[MXN], int al, double& z, B t[3]) {
     if (cm & 1u) z = u[0];
     else {
         double s = 0.0;
@@ -386,6 +387,20 @@ __device__ __forceinline__ void face_trace_mixed(const double* u, size_t fstride
 #pragma unroll
     for (int fl = 1; fl < 4; ++fl) {
         const double* uf = u + fl * fstride;
+        if constexpr (sizeof(B) == sizeof(float)) {
+            if (u32 != nullptr) { // the same values as (float)uf[.], without conversions
+                const float* vf = u32 + fl * fstride;
+                if (cm & (1u << fl)) {
+                    t[fl - 1] = vf[0];
+                    continue;
+                }
+                B s = B(0);
+#pragma unroll
+                for (int j = 0; j < ND1; ++j) s += Bb[al][j] * vf[face_node<ND1>(f, j)];
+                t[fl - 1] = s;
+                continue;
+            }
+        }
         if (cm & (1u << fl)) {
             t[fl - 1] = (B)uf[0];
             continue;
@@ -418,7 +433,8 @@ __device__ __forceinline__ const B (*tab_or(const double (*d)[MXN], const float 
 // the wave speed bound of the point.
 template <int R, typename Pix, int MODE, typename B>
 __device__ __forceinline__ void face_point(const Dev& d, const Tables& tb, int64_t k, const double* uk,
-                                           size_t ustride, unsigned cm, int buf, int f, int h, int al,
+                                           const float* ukF, size_t ustride, unsigned cm, int buf,
+                                           int f, int h, int al,
                                            unsigned info, double hx, double hy, int mem, double t,
                                            B raw[4], B& pres, B& lam, bool& own_first, bool& bnd,
                                            int64_t& nb_out) {
@@ -434,7 +450,7 @@ __device__ __forceinline__ void face_point(const Dev& d, const Tables& tb, int64
     const double ny = (f == 2) ? -1.0 : (f == 3) ? 1.0 : 0.0;
     double zm;
     B tm[3];
-    face_trace_mixed<ND1, B>(uk, ustride, cm, f, coarse ? tb.BmH[h] : tb.Bm,
+    face_trace_mixed<ND1, B>(uk, ukF, ustride, cm, f, coarse ? tb.BmH[h] : tb.Bm,
                              coarse ? tab_or<B>(tb.BmH[h], tb.BmHF[h]) : BmB, al, zm, tm);
     int ia, ib;
     face_site_index<NM>(f, al, ia, ib);
@@ -451,7 +467,8 @@ __device__ __forceinline__ void face_point(const Dev& d, const Tables& tb, int64
     if (s0 >= 0) {
         const int64_t nb = coarse ? (int64_t)(h ? d.nbr[k * 8 + f * 2 + 1] : s0) : (int64_t)s0;
         const int fo = f ^ 1;
-        face_trace_mixed<ND1, B>(ufield(d, buf, 0, ND) + nb * ND, (size_t)n * ND,
+        face_trace_mixed<ND1, B>(ufield(d, buf, 0, ND) + nb * ND,
+                                 d.uF ? ufieldF(d, buf, 0, ND) + nb * ND : nullptr, (size_t)n * ND,
                                  d.cmask[(size_t)buf * n + nb], fo, fine ? tb.BmH[half] : tb.Bm,
                                  fine ? tab_or<B>(tb.BmH[half], tb.BmHF[half]) : BmB, al, zp, tp);
         int ja, jb;
@@ -559,12 +576,21 @@ __global__ void __maxnreg__(96)
     const int64_t n = d.n;
 
     for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n; k += (int64_t)gridDim.x * wpb) {
-        for (int i = lane; i < 4 * ND; i += 32) {
-            const double v = ufield(d, buf, i / ND, ND)[k * ND + (i % ND)];
-            su[i] = v;
-            // B = float: an FP32 copy of all four fields (the elevation enters
-            // FP32 arithmetic only through its gradient; its value stays FP64)
-            if constexpr (!F64) suB[i] = (B)v;
+        if constexpr (F64) {
+            for (int i = lane; i < 4 * ND; i += 32) su[i] = ufield(d, buf, i / ND, ND)[k * ND + (i % ND)];
+        } else {
+            // B = float: all four fields in FP32 (the elevation enters FP32
+            // arithmetic only through its gradient), from the FP32 copy of the
+            // state where the context keeps one; in FP64 the elevation, and the
+            // other fields only where something still reads them in FP64 (the
+            // tracer diffusion, the inline face integration)
+            const bool all64 = !d.uF || !d.fflux || (d.nu_c && d.nu_c[k] != 0.0);
+            for (int i = lane; i < 4 * ND; i += 32) {
+                const bool z64 = i < ND || all64;
+                const double v = z64 ? ufield(d, buf, i / ND, ND)[k * ND + (i % ND)] : 0.0;
+                su[i] = v;
+                suB[i] = d.uF ? ufieldF(d, buf, i / ND, ND)[k * ND + (i % ND)] : (B)v;
+            }
         }
         const unsigned cm = d.cmask[(size_t)buf * n + k];
         const double hx = d.hxhy[2 * k], hy = d.hxhy[2 * k + 1], J = hx * hy;
@@ -845,8 +871,8 @@ __global__ void __maxnreg__(96)
                 B raw[4], pres, lam, out[4];
                 bool own_first, bnd;
                 int64_t nb;
-                face_point<R, Pix, MODE, B>(d, tb, k, su, ND, cm, buf, f, h, al, info, hx, hy, mem, t,
-                                            raw, pres, lam, own_first, bnd, nb);
+                face_point<R, Pix, MODE, B>(d, tb, k, su, nullptr, ND, cm, buf, f, h, al, info, hx, hy,
+                                            mem, t, raw, pres, lam, own_first, bnd, nb);
                 if (bnd) {
 #pragma unroll
                     for (int cf = 0; cf < 4; ++cf) out[cf] = raw[cf];
@@ -935,7 +961,8 @@ __global__ void __maxnreg__(80)
             B raw[4], pres, lam, out[4];
             bool own_first, bnd;
             int64_t nb;
-            face_point<R, Pix, MODE, B>(d, tb, k, ufield(d, buf, 0, ND) + k * ND, (size_t)n * ND,
+            face_point<R, Pix, MODE, B>(d, tb, k, ufield(d, buf, 0, ND) + k * ND,
+                                        d.uF ? ufieldF(d, buf, 0, ND) + k * ND : nullptr, (size_t)n * ND,
                                         d.cmask[(size_t)buf * n + k], buf, f, h, al, info, hx, hy,
                                         mem, t, raw, pres, lam, own_first, bnd, nb);
             if (bnd) {
@@ -1166,7 +1193,10 @@ __global__ void __launch_bounds__(32 * MAXWPB)
                 for (int i = lane; i < ND; i += 32) su[i] = e;
             }
             __syncwarp();
-            for (int i = lane; i < 4 * ND; i += 32) ufield(d, 0, i / ND, ND)[k * ND + (i % ND)] = su[i];
+            for (int i = lane; i < 4 * ND; i += 32) {
+                ufield(d, 0, i / ND, ND)[k * ND + (i % ND)] = su[i];
+                if (d.uF) ufieldF(d, 0, i / ND, ND)[k * ND + (i % ND)] = (float)su[i];
+            }
             cm = 15u;
             for (int p = lane; p < NMP; p += 32) {
                 pe[p] = su[0];
@@ -1952,6 +1982,7 @@ __global__ void __maxnreg__(96)
             const double v = o[i];
             fin = fin && finite_bits(v);
             ufield(d, sa.out_buf, i / ND, ND)[k * ND + (i % ND)] = v;
+            if (d.uF) ufieldF(d, sa.out_buf, i / ND, ND)[k * ND + (i % ND)] = (float)v;
         }
         if (!__all_sync(tm, fin)) bad = 1;
         if (lane == 0) d.cmask[(size_t)sa.out_buf * n + k] = (uint8_t)cmo;
@@ -1988,6 +2019,8 @@ __global__ void k_masks(const __grid_constant__ Dev d, int buf) {
             bool eq = true;
             for (int i = lane; i < ND; i += 32) eq = eq && same_bits(u[i], u[0]);
             if (__all_sync(0xffffffffu, eq)) cm |= (1u << f);
+            if (d.uF)
+                for (int i = lane; i < ND; i += 32) ufieldF(d, buf, f, ND)[k * ND + i] = (float)u[i];
         }
         if (lane == 0) d.cmask[(size_t)buf * d.n + k] = (uint8_t)cm;
     }
