@@ -535,8 +535,11 @@ __device__ __forceinline__ void side_flux(const B raw[4], B pres, bool own_first
     out[3] = raw[3] * sg;
 }
 
+// 96 registers for the FP64 form; 80 for B = float (six blocks of four
+// warps per SM instead of five; measured 2 % faster despite a few spilled
+// registers, while the FP32-bulk stage update is slower at 80 or 72)
 template <int R, typename Pix, int MODE, typename B>
-__global__ void __maxnreg__(96)
+__global__ void __maxnreg__(sizeof(B) == 4 ? 80 : 96)
     k_residual(const __grid_constant__ Dev d, const __grid_constant__ Tables tb_g, int buf,
                int stage, double c_stage, int want_dt) {
     // the basis tables in shared memory: the contractions index them by lane
