@@ -1,8 +1,9 @@
 """FP32-bulk precision (swdg_config.precision = 1) against the FP64 oracle.
 
-The momentum, friction and flux arithmetic of the residual runs in FP32, so
-those results carry FP32 error (bounded here, and stated per result); the
-elevation and its gradient, the sub-grid integrals, the hydrostatic
+The momentum, friction and flux arithmetic of the residual runs in FP32
+(with the elevation's gradient, which only the FP32 pressure product
+uses), so those results carry FP32 error (bounded here, and stated per
+result); the elevation's values, the sub-grid integrals, the hydrostatic
 reconstruction (including the depth jump h*- - h*+), the continuity and
 tracer test integrals and every stage solve stay FP64, so the lake at rest,
 water mass and tracer mass hold to FP64 round-off as in the plain path.  A
@@ -100,3 +101,29 @@ def test_fp32bulk_steps_within_fp32_error_of_oracle():
     for name, a, b in zip(("zeta", "qx", "qy", "c"), sg, so):
         floor = 1.0 if name in ("zeta", "c") else qscale
         assert rel_inf(a, b, floor=floor) <= STATE_TOL_FP32, name
+
+
+def test_fp32bulk_state_copy_follows_every_state_write():
+    """FP32-bulk contexts keep an FP32 copy of the state for the FP32 face and
+    residual arithmetic; it must follow every write of the state.  The
+    autotuner steps on the context's own state and restores it: the residual
+    after it equals the one before bit for bit.  A stepped context and a
+    fresh one given the stepped state agree bit for bit, and so does the
+    first context after a new state upload."""
+    wl = island(3)
+    ctx = swdg.Context.from_workload(wl, precision=1)
+    r0 = ctx.residual(0.0)
+    ctx.autotune(repeats=1)
+    r1 = ctx.residual(0.0)
+    for k in r0:
+        assert np.array_equal(r0[k], r1[k]), k
+    ctx.step(3, -1.0, 0.0)
+    fresh = swdg.Context.from_workload(wl, precision=1)
+    fresh.set_state(*ctx.get_state())
+    rg, rf = ctx.residual(5.0), fresh.residual(5.0)
+    for k in rg:
+        assert np.array_equal(rg[k], rf[k]), k
+    ctx.set_state(*wl.state())
+    r2 = ctx.residual(0.0)
+    for k in r0:
+        assert np.array_equal(r0[k], r2[k]), k
