@@ -306,17 +306,29 @@ __device__ __forceinline__ T gamma_manning(T n, T h, T qx, T qy, T g, T eps) {
 }
 
 // the velocity factor and the Manning coefficient of one point together: on
-// the wet branch (h >= eps, where h_des = h) both come from the one
-// reciprocal 1/h, with h^(-7/3) = (1/h)^2 cbrt(1/h); otherwise as
-// vel_factor and gamma_manning
+// the wet branch (h >= eps, where h_des = h) both come from one root, in FP64
+// z = h^(-1/3) with 1/h = z^3 and h^(-7/3) = z^7 (1/h by division where
+// there is no friction), otherwise from 1/h with h^(-7/3) = (1/h)^2
+// cbrt(1/h); below eps as vel_factor and gamma_manning
 template <typename T>
 __device__ __forceinline__ void vel_gamma(T n, T h, T qx, T qy, T g, T eps, T& fv, T& gam) {
     if (h >= eps && h > T(0)) {
+        if constexpr (std::is_same<T, double>::value) {
+            if (n == 0.0) {
+                fv = 1.0 / h;
+                gam = 0.0;
+            } else {
+                // with friction, 1/h = z^3 from z = h^(-1/3) (a few ulp from the
+                // rounded quotient, no FP64 division); gamma ~ z^7
+                const double z = inv_cbrt(h), rh = z * z * z;
+                fv = rh;
+                gam = g * n * n * sqrt(qx * qx + qy * qy) * (rh * rh) * z;
+            }
+            return;
+        }
         const T rh = T(1) / h;
         fv = rh;
-        T c3; // h^(-1/3)
-        if constexpr (std::is_same<T, double>::value) c3 = inv_cbrt(h);
-        else c3 = cbrt(rh);
+        const T c3 = cbrt(rh); // h^(-1/3)
         gam = (n == T(0)) ? T(0) : g * n * n * sqrt(qx * qx + qy * qy) * (rh * rh) * c3;
     } else {
         fv = vel_factor<T>(h, eps);
