@@ -395,6 +395,16 @@ int swdg_autotune(swdg_ctx* ctx, int repeats, double* report);
  * Returns SWDG_EINVAL for another dtype, SWDG_ECUDA on a CUDA error. */
 int swdg_probe_fma(int dtype, double* tflops, double* ms);
 
+/* Test helper (the paper has no counterpart): the kernels' own root of the
+ * Manning term, z = h^(-1/3) (an FP32 reciprocal cube root refined by two
+ * Newton-Raphson steps for z^-3 = h in FP64; 1 / cbrt(h) outside the FP32
+ * range), and z^3, the 1/h the residual takes at wet points with friction,
+ * evaluated on the device for n host values h [n] > 0 into z [n] and
+ * rcp [n] (host).  1 <= n <= 2^24.  Allocates 24 n bytes of device memory for
+ * the duration of the call.  Returns SWDG_EINVAL for bad sizes or pointers,
+ * SWDG_ECUDA on a CUDA error. */
+int swdg_probe_roots(const double* h, int64_t n, double* z, double* rcp);
+
 /* Allocation-free residual (the paper has no counterpart; this exists for
  * callers that cannot allocate device memory -- for example code running
  * inside a memory pool that forbids new allocations, or a host that has

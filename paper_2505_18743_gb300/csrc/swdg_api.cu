@@ -2653,6 +2653,33 @@ extern "C" int swdg_probe_fma(int dtype, double* tflops, double* ms) {
     return SWDG_EINVAL;
 }
 
+// z = h^(-1/3) and z^3 as the kernels form them (inv_cbrt), one value per thread
+__global__ void k_probe_roots(const double* h, int64_t n, double* z, double* rcp) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double zi = inv_cbrt(h[i]);
+        z[i] = zi;
+        rcp[i] = zi * zi * zi;
+    }
+}
+
+extern "C" int swdg_probe_roots(const double* h, int64_t n, double* z, double* rcp) {
+    if (!h || !z || !rcp || n < 1 || n > (int64_t(1) << 24)) return SWDG_EINVAL;
+    double* dv = nullptr;
+    const size_t b = (size_t)n * sizeof(double);
+    if (cudaMalloc(&dv, 3 * b) != cudaSuccess) return SWDG_ECUDA;
+    bool ok = cudaMemcpy(dv, h, b, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+        const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+        k_probe_roots<<<grid, 256>>>(dv, n, dv + n, dv + 2 * n);
+        ok = cudaGetLastError() == cudaSuccess && cudaMemcpy(z, dv + n, b, cudaMemcpyDeviceToHost) ==
+                                                     cudaSuccess &&
+             cudaMemcpy(rcp, dv + 2 * n, b, cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+    cudaFree(dv);
+    return ok ? SWDG_OK : SWDG_ECUDA;
+}
+
 // ---------------------------------------------------------------------------
 // allocation-free residual: its only scratch is this file-scope array (step
 // scalars in the first 256 bytes, then the pixel-overlap table, then one

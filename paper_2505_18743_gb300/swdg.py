@@ -109,6 +109,7 @@ SIGNATURES = {
     "swdg_get_shapes": (_I, [_P, _P]),
     "swdg_autotune": (_I, [_P, _I, _P]),
     "swdg_probe_fma": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "swdg_probe_roots": (_I, [_P, _I64, _P, _P]),
     "swdg_last_error": (ctypes.c_char_p, [_P]),
     "swdg_destroy": (None, [_P]),
 }
@@ -193,6 +194,17 @@ def probe_fma(dtype):
     if rc:
         raise SwdgError(rc, "swdg_probe_fma failed")
     return tf.value, ms.value
+
+
+def probe_roots(h):
+    """the kernels' z = h^(-1/3) and z^3 for host values h > 0: (z, z^3)"""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    z, r = np.empty_like(h), np.empty_like(h)
+    rc = load().swdg_probe_roots(h.ctypes.data_as(_P), h.size, z.ctypes.data_as(_P),
+                                 r.ctypes.data_as(_P))
+    if rc:
+        raise SwdgError(rc, "swdg_probe_roots failed")
+    return z, r
 
 
 def forest_mesh(forest, lij):

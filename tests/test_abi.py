@@ -60,3 +60,23 @@ def test_noalloc_refuses_an_empty_mesh_before_any_device_call():
             swdg.residual_noalloc(cfg, n, None, None, None, 8, swdg.SWDG_PIX_F64, None, None, 0.0,
                                   None, None)
         assert e.value.code == swdg.SWDG_EINVAL and "n_cells" in str(e.value)
+
+
+@pytest.mark.gpu
+def test_manning_root_within_a_few_ulp():
+    """the kernels' own z = h^(-1/3) (FP32 seed, two Newton-Raphson steps for
+    z^-3 = h) against float64 libm roots, and z^3 against 1/h, over depths
+    from 1e-9 m to 1e5 m and beyond the FP32 range (the 1/cbrt branch)"""
+    import numpy as np
+    import torch
+    assert torch.cuda.is_available()
+    B.build()
+    rng = np.random.default_rng(11)
+    h = np.concatenate([np.logspace(-9, 5, 40001), rng.uniform(1e-3, 50.0, 20000),
+                        [1e-35, 3e-31, 7e30, 1e35, 1.0, 8.0, 27.0]])
+    z, r = swdg.probe_roots(h)
+    zr = 1.0 / np.cbrt(h)  # within about 1.5 ulp of h^(-1/3)
+    assert np.all(np.abs(z - zr) <= 4 * np.spacing(zr))
+    assert np.all(np.abs(r - 1.0 / h) <= 8 * np.spacing(1.0 / h))
+    with pytest.raises(swdg.SwdgError):
+        swdg.probe_roots(np.zeros(0))
