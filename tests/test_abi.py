@@ -65,8 +65,8 @@ def test_noalloc_refuses_an_empty_mesh_before_any_device_call():
 @pytest.mark.gpu
 def test_manning_root_within_a_few_ulp():
     """the kernels' own z = h^(-1/3) (FP32 seed, two Newton-Raphson steps for
-    z^-3 = h) against float64 libm roots, and z^3 against 1/h, over depths
-    from 1e-9 m to 1e5 m and beyond the FP32 range (the 1/cbrt branch)"""
+    z^-3 = h) against the exact root, and z^3 against 1/h, over depths from
+    1e-9 m to 1e5 m and beyond the FP32 range (the 1/cbrt branch)"""
     import numpy as np
     import torch
     assert torch.cuda.is_available()
@@ -75,8 +75,13 @@ def test_manning_root_within_a_few_ulp():
     h = np.concatenate([np.logspace(-9, 5, 40001), rng.uniform(1e-3, 50.0, 20000),
                         [1e-35, 3e-31, 7e30, 1e35, 1.0, 8.0, 27.0]])
     z, r = swdg.probe_roots(h)
-    zr = 1.0 / np.cbrt(h)  # within about 1.5 ulp of h^(-1/3)
-    assert np.all(np.abs(z - zr) <= 4 * np.spacing(zr))
-    assert np.all(np.abs(r - 1.0 / h) <= 8 * np.spacing(1.0 / h))
+    # exact checks in rational arithmetic (a libm cbrt can itself be a few ulp
+    # off): z within 2 ulp brackets the root, (z -+ 2 ulp)^3 h <= 1 <= ...,
+    # and z^3 is within 6 ulp of 1/h
+    from fractions import Fraction as Fr
+    for hi, zi, ri in zip(h.tolist(), z.tolist(), r.tolist()):
+        hf, du = Fr(hi), 2 * np.spacing(zi)
+        assert Fr(zi - du) ** 3 * hf <= 1 <= Fr(zi + du) ** 3 * hf, (hi, zi)
+        assert abs(Fr(ri) - 1 / hf) <= 6 * Fr(float(np.spacing(1.0 / hi))), (hi, ri)
     with pytest.raises(swdg.SwdgError):
         swdg.probe_roots(np.zeros(0))
