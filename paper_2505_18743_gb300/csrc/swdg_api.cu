@@ -105,6 +105,7 @@ struct swdg_ctx {
     float* uF = nullptr;   // FP32 copy of U (FP32-bulk)
     int32_t* nbr = nullptr;
     uint8_t *cmask = nullptr, *flag = nullptr, *wet0 = nullptr, *finfo = nullptr, *pcls = nullptr;
+    double* qpts = nullptr; // q^n at the momentum points (step start -> stage updates)
     int64_t* tile_off = nullptr;
     OvTab* ov = nullptr;
     double* zhang = nullptr;
@@ -749,6 +750,8 @@ static void free_mesh(swdg_ctx* c) {
     cudaFree(c->finfo);
     cudaFree(c->uF);
     c->uF = nullptr;
+    cudaFree(c->qpts);
+    c->qpts = nullptr;
     cudaFree(c->adj);
     c->adj = nullptr;
     cudaFree(c->gdev);
@@ -908,6 +911,9 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     CK(cudaMalloc(&ctx->cmask, (size_t)NBUF * n));
     CK(cudaMalloc(&ctx->flag, n));
     CK(cudaMalloc(&ctx->wet0, n));
+    // FP64 contexts only: the FP32-bulk momentum block interpolates FP32
+    // nodal values itself, so the step start's extra write would not pay
+    if (ctx->cfg.precision == 0) CK(cudaMalloc(&ctx->qpts, 2 * (size_t)n * nd * sizeof(double)));
     CK(cudaMalloc(&ctx->diag, 4 * n * sizeof(double) + 8 * sizeof(double)));
     CK(cudaMemcpyAsync(ctx->x0y0, x0y0, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->hxhy, hxhy, 2 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
@@ -975,6 +981,7 @@ int swdg_upload_mesh(swdg_ctx* ctx, int64_t n, const double* x0y0, const double*
     d.CNbar = ctx->CNbar;
     d.flag = ctx->flag;
     d.wet0 = ctx->wet0;
+    d.qpts = ctx->qpts;
     d.any_friction = 0;
     default_shapes(ctx);
     ctx->has_mesh = true;

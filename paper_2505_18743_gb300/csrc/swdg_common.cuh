@@ -135,6 +135,10 @@ struct Dev {
     // 1 where every mass point of the cell was fully wet at zeta^n (written by
     // the step start with H(zeta^n); null: unknown)
     uint8_t* wet0;
+    // [cell][2][(r+1)^2]: qx, qy of v^n at the momentum points, written by the
+    // step start (the same for every stage of the step; FP64 contexts); null:
+    // interpolated by the stage update itself
+    double* qpts;
     Scalars* sc;
     Member* mb;            // member clocks [nmemb] (a single member: &sc->m0)
     const int32_t* memb;   // member of each cell (null: every cell in member 0)

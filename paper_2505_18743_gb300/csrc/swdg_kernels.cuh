@@ -1226,6 +1226,14 @@ __global__ void __launch_bounds__(32 * MAXWPB)
             d.HN[k * ND + i] = out[i];
             d.CN[k * ND + i] = out[ND + i];
         }
+        // the discharges of v^n at the momentum points, the same for every
+        // stage of the step (the stage update reads them rather than
+        // interpolating v^n again; same sums, same constant fields)
+        if (d.qpts) {
+            tens_interp2<ND1, NG>(tb.Bg, su + ND, su + 2 * ND, tmp, tmp + NM * NM, pg, pg + NGP, lane);
+            for (int p = lane; p < 2 * NGP; p += 32)
+                d.qpts[k * 2 * NGP + p] = (cm & (2u << (p / NGP))) ? su[(1 + p / NGP) * ND] : pg[p];
+        }
         if (lane == 0) {
             d.HNbar[k] = hb;
             d.CNbar[k] = cb;
@@ -1660,13 +1668,18 @@ __device__ void momentum_block(const Dev& d, const Tables& tb, int64_t k, double
         for (int p = lane; p < NGP; p += TL) gam[p] = T(0);
     }
     __syncwarp(tm);
-    for (int i = lane; i < 2 * ND; i += TL) nod[i] = (T)su[ND + i];
-    __syncwarp(tm);
-    tens_interp2<ND1, NG, T, TL>(Bg, nod, nod + ND, tmp, tmp1, pg + 3 * NGP, pg + 4 * NGP, lane, tm);
-    if (cm0 & 2u)
-        for (int p = lane; p < NGP; p += TL) pg[3 * NGP + p] = (T)su[ND];
-    if (cm0 & 4u)
-        for (int p = lane; p < NGP; p += TL) pg[4 * NGP + p] = (T)su[2 * ND];
+    if (F64 && d.qpts != nullptr) { // q^n at the points, from the step start
+        for (int p = lane; p < 2 * NGP; p += TL) pg[3 * NGP + p] = (T)d.qpts[k * 2 * NGP + p];
+    } else {
+        for (int i = lane; i < 2 * ND; i += TL) nod[i] = (T)su[ND + i];
+        __syncwarp(tm);
+        tens_interp2<ND1, NG, T, TL>(Bg, nod, nod + ND, tmp, tmp1, pg + 3 * NGP, pg + 4 * NGP, lane,
+                                     tm);
+        if (cm0 & 2u)
+            for (int p = lane; p < NGP; p += TL) pg[3 * NGP + p] = (T)su[ND];
+        if (cm0 & 4u)
+            for (int p = lane; p < NGP; p += TL) pg[4 * NGP + p] = (T)su[2 * ND];
+    }
     for (int i = lane; i < 2 * ND; i += TL) nod[i] = (T)rq[i];
     __syncwarp(tm);
     kron_apply2<ND1, true, MXP, T, TL>(Bginv, nod, nod + ND, tmp, tmp1, pg, pg + NGP, T(1), lane, tm);
@@ -1896,13 +1909,18 @@ __global__ void __maxnreg__(96)
             its = scalar_newton<R, Pix, MODE, TL>(d, tb, k, J, Tbar, e, lane, tm);
             // momentum: sums of the rows of the friction-modified mass matrix
             double den = 0.0, num[2] = {0.0, 0.0};
-            for (int f = 0; f < 2; ++f) {
-                if (cm0 & (2u << f))
-                    for (int p = lane; p < NGP; p += TL) pg[(3 + f) * NGP + p] = su[(1 + f) * ND];
-                else
-                    tens_interp<ND1, NG, double, TL>(tb.Bg, su + (1 + f) * ND, tmp, pg + (3 + f) * NGP,
-                                                     lane, tm);
+            if (d.qpts) {
+                for (int p = lane; p < 2 * NGP; p += TL) pg[3 * NGP + p] = d.qpts[k * 2 * NGP + p];
                 __syncwarp(tm);
+            } else {
+                for (int f = 0; f < 2; ++f) {
+                    if (cm0 & (2u << f))
+                        for (int p = lane; p < NGP; p += TL) pg[(3 + f) * NGP + p] = su[(1 + f) * ND];
+                    else
+                        tens_interp<ND1, NG, double, TL>(tb.Bg, su + (1 + f) * ND, tmp,
+                                                         pg + (3 + f) * NGP, lane, tm);
+                    __syncwarp(tm);
+                }
             }
             for (int p = lane; p < NGP; p += TL) {
                 const double w = J * tb.wg[p % NG] * tb.wg[p / NG];
